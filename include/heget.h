@@ -1,0 +1,200 @@
+/*
+ * heget.h -- C ABI of the GB300-native HEGET hot path.
+ *
+ * The library evaluates tree-level helicity amplitudes of
+ *     u(p1, s1) ubar(p2, s2) -> gamma(k1, l1) ... gamma(kn, ln),   n = 2..8,
+ * at many phase-space points at once (Hagiwara et al., arXiv:0908.4403,
+ * Sec. 2.1 eqs. (6)-(8)), sums |M|^2 over helicities (Sec. 2.1 eq. (2)),
+ * generates flat massless n-body phase space (Sec. 2.1 eq. (4), RAMBO) with
+ * the photon cuts of Sec. 2.2 eqs. (9)-(10), and integrates the partonic
+ * cross section of Sec. 2.1 eq. (2) by Monte Carlo.
+ *
+ * Conventions shared by every call:
+ *  - Array arguments are DEVICE pointers owned by the caller (for example the
+ *    data_ptr() of a torch CUDA tensor) unless a parameter says "host".
+ *    The library never frees them and keeps no reference after a call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it and return without waiting, unless
+ *    their description says they synchronize.
+ *  - Momenta are FP64 GeV, layout [N][n+2][4]: particle order
+ *    (p1, p2, k1, ..., kn), components (E, px, py, pz).  p1 is the incoming
+ *    u along +z, p2 the incoming ubar along -z.
+ *  - Helicity index h in [0, 2^(n+2)): bit0 = s1 (1 -> +1/2, 0 -> -1/2),
+ *    bit1 = s2, bit(2+i) = lambda_{i+1} (1 -> +1, 0 -> -1).  A helicity
+ *    mask is an array of 2^(n+2)/32 uint32 words (1 word for n <= 3), bit h
+ *    of word h/32; NULL selects all 2^(n+2) combinations.
+ *  - Every call returns an int status (HEGET_OK = 0).  On failure,
+ *    heget_last_error() returns a message for the calling thread.  No call
+ *    aborts, prints, or allocates device memory except heget_create and the
+ *    calls documented to grow the context workspace.
+ */
+#ifndef HEGET_H
+#define HEGET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HEGET_OK 0
+#define HEGET_EINVAL 1    /* bad argument, or device-side input check failed */
+#define HEGET_ENOMEM 2    /* device allocation failed / admission impossible */
+#define HEGET_ECUDA 3     /* a CUDA runtime call failed */
+#define HEGET_ETIMEOUT 4  /* a bounded wait ran out */
+#define HEGET_EBUSY 5     /* no free slot (serving) */
+#define HEGET_ENOTFOUND 6 /* unknown ticket (serving) */
+
+/* arithmetic of the spinor / vertex / propagator chain */
+#define HEGET_FP32 32
+#define HEGET_FP64 64
+
+/* sqrt(s-hat) samplers */
+#define HEGET_SAMPLER_FIXED 0   /* sqrt(s-hat) = sqrt_s, boost rapidity y = 0 */
+#define HEGET_SAMPLER_UNIFORM 1 /* sqrt(s-hat) uniform in [lo, hi], y = 0 */
+#define HEGET_SAMPLER_TOY_PDF 2 /* x1, x2 ~ x^(-1/2)(1-x)^3, sqrt(s-hat) =
+                                   2 e_beam sqrt(x1 x2) > floor, y = ln(x1/x2)/2 */
+
+typedef struct heget_ctx heget_ctx;
+
+/* Physics parameters.  alpha: fine-structure constant; q_charge: quark
+ * charge in units of e (the couplings gal[0] = gal[1] = -e Q_q of Sec. 4 and
+ * Appendix B.3); cuts of Sec. 2.2: photon pT > pt_min, |eta| < eta_max,
+ * Delta R > dr_min (dr_min <= 0 disables the Delta R cut).  All cuts strict. */
+typedef struct {
+    double alpha;
+    double q_charge;
+    double pt_min;
+    double eta_max;
+    double dr_min;
+} heget_params;
+
+/* sqrt(s-hat) sampler (see HEGET_SAMPLER_*).  max_tries in [1, 64] bounds
+ * each rejection loop of the toy PDF; a point whose loops all fail is kept
+ * with weight 0 and mask 0. */
+typedef struct {
+    int kind;
+    double sqrt_s;   /* FIXED */
+    double lo, hi;   /* UNIFORM */
+    double e_beam;   /* TOY_PDF: hadronic sqrt(s) = 2 e_beam */
+    double floor;    /* TOY_PDF: accept sqrt(s-hat) > floor */
+    int max_tries;   /* TOY_PDF */
+} heget_sampler;
+
+/* Monte Carlo result of heget_xsec.  sigma_fb = scale * sum_w / n_total and
+ * err_fb = scale * sqrt((<w^2> - <w>^2)/(n_total - 1) ), with scale = 1,
+ * or 2 * accept for the toy PDF (q <-> qbar assignment of Sec. 2.1 eq. (1)
+ * and the sqrt(s-hat) floor acceptance accept = n_total / n_tries). */
+typedef struct {
+    double sigma_fb;
+    double err_fb;
+    double sum_w;     /* compensated sum of per-event weights (fb) */
+    double sum_w2;    /* compensated sum of squared weights (fb^2) */
+    double accept;
+    double reserved;
+    int64_t n_pass;   /* events passing the cuts */
+    int64_t n_total;  /* events generated (= N) */
+    int64_t n_tries;  /* outer sampler attempts (= N unless TOY_PDF) */
+    int64_t n_escalated; /* FP32 points recomputed in FP64 */
+} heget_xsec_result;
+
+/* Context: binds a CUDA device, holds the physics parameters (defaults:
+ * alpha = 1/137.035999, q_charge = 2/3, pt_min = 20, eta_max = 2.5,
+ * dr_min = 0.4) and a small workspace.  heget_create allocates the
+ * workspace on `device`; returns HEGET_ECUDA if the device is unusable. */
+int heget_create(int device, heget_ctx** out);
+void heget_destroy(heget_ctx* ctx);
+int heget_set_params(heget_ctx* ctx, const heget_params* p);   /* p: host */
+int heget_get_params(const heget_ctx* ctx, heget_params* p);   /* p: host */
+const char* heget_last_error(void);
+const char* heget_version(void);
+
+/* Phase space (Sec. 2.1 eq. (4); Sec. 3: random numbers -> phase-space point
+ * and Jacobian): for point i in [0, N), draw sqrt(s-hat) with a fixed value,
+ * generate n massless photons with RAMBO (Kleiss, Stirling, Ellis 1986) in
+ * the partonic CM frame with p1 = (rs/2)(1,0,0,1), p2 = (rs/2)(1,0,0,-1).
+ * Random numbers: Philox4x32-10 keyed by `seed`, counter (i, draw, stream),
+ * so point i depends only on (seed, i).
+ *   momenta: [N][n+2][4] FP64 (may be NULL); weights: [N] FP64 flat
+ *   phase-space weight Phi_n(s-hat) in GeV^(2n-4) (may be NULL).
+ * EINVAL: n not in [2, 8], N < 0, sqrt_s <= 0. */
+int heget_phase_space(heget_ctx* ctx, uint64_t seed, int64_t N, int n,
+                      double sqrt_s, double* momenta, double* weights,
+                      void* stream);
+
+/* General form: points i0 .. i0+N-1, sampler `smp` (host struct), the cut
+ * mask of Sec. 2.2 evaluated with eta_lab = eta_cm + y.  Any output may be
+ * NULL.  sqrt_s_out, y_out: [N] FP64; mask_out: [N] uint8 (1 = passes);
+ * tries_out: [N] int32 outer sampler attempts. */
+int heget_phase_space_ex(heget_ctx* ctx, uint64_t seed, int64_t i0, int64_t N,
+                         int n, const heget_sampler* smp, double* momenta,
+                         double* weights, double* sqrt_s_out, double* y_out,
+                         uint8_t* mask_out, int32_t* tries_out, void* stream);
+
+/* |M|^2 (Sec. 2.1 eqs. (2), (6)-(8)): for each point,
+ *   amp2[i] = sum_{h in hel_mask} |M_h|^2,
+ * M_h = sum over the n! photon orderings of the fermion-line chain, including
+ * the couplings (-e Q)^n; without colour, spin-average or 1/n! factors.
+ * precision: HEGET_FP32 (spinor algebra in FP32, propagator denominators
+ * from FP64 invariants) or HEGET_FP64.  momenta: [N][n+2][4]; amp2: [N].
+ * Host-side EINVAL: n not in [2, 8], N < 0, NULL arrays, bad precision.
+ * Device-side check: a point with a non-finite entry, or p1 / p2 not
+ * massless along +z / -z, gets amp2 = NaN and raises the context's input
+ * flag, reported as EINVAL by heget_check (which synchronizes). */
+int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta,
+               const uint32_t* hel_mask, int precision, double* amp2,
+               void* stream);
+
+/* Synchronizes `stream` and reports (then clears) the device-side input
+ * flag raised by heget_amp2 / heget_ward: HEGET_EINVAL if set. */
+int heget_check(heget_ctx* ctx, void* stream);
+
+/* Monte Carlo partonic cross section (Sec. 2.1 eq. (2); summation of
+ * Sec. 3.1 step 5) over points i0 .. i0+N-1: per event
+ *   w = (1/2s)(1/2^2)(1/3^2) 3 sum_h |M_h|^2 (1/n!) Phi_n(s) mask  [fb],
+ * accumulated in compensated FP64 (double-double per thread, then a
+ * fixed-order tree), so the result is deterministic for fixed arguments.
+ * result_dev: device array of sizeof(heget_xsec_result) bytes receiving the
+ * result; w_out (optional, may be NULL): [N] per-event weights.  Uses the
+ * context workspace (grown on demand; not thread-safe per context).
+ * Enqueues only. */
+int heget_xsec_async(heget_ctx* ctx, int n, uint64_t seed, int64_t i0,
+                     int64_t N, const heget_sampler* smp, int precision,
+                     heget_xsec_result* result_dev, double* w_out,
+                     void* stream);
+
+/* heget_xsec_async over points 0 .. N-1, then copies the result to the host
+ * struct `out` and synchronizes `stream`. */
+int heget_xsec(heget_ctx* ctx, int n, int64_t N, uint64_t seed,
+               const heget_sampler* smp, int precision,
+               heget_xsec_result* out, void* stream);
+
+/* heget_xsec_async in two halves: heget_xsec_launch enqueues only the fused
+ * event kernel, leaving its block partials in the context workspace;
+ * heget_xsec_finalize enqueues the fixed-order combination of the partials of
+ * the most recent heget_xsec_launch on this context into result_dev.  The
+ * pair is equivalent to heget_xsec_async and exists so that callers can time
+ * or graph-capture the halves separately. */
+int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0,
+                      int64_t N, const heget_sampler* smp, int precision,
+                      double* w_out, void* stream);
+int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
+                        void* stream);
+
+/* Device FMA throughput: runs independent FMA chains (8 per thread) in
+ * every thread of a grid that fills the GPU and reports the achieved rate in
+ * TFLOP/s (2 flops per FMA) in *tflops.  precision: HEGET_FP32 or HEGET_FP64.
+ * The measured denominator of the FMA-pipe roofline.  Synchronizes. */
+int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
+
+/* Compensated sums of x[0..N-1] (the accumulator of heget_xsec, exposed):
+ * out_dev[0] = sum x, out_dev[1] = sum x^2, each rounded once from a
+ * double-double accumulation in a fixed order.  out_dev: 2 doubles. */
+int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev,
+              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEGET_H */

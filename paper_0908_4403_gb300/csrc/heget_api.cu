@@ -1,0 +1,469 @@
+// heget_api.cu -- the C ABI of include/heget.h: context, argument checks,
+// launch shapes, the phase-space kernel and the fixed-order reductions.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "heget_kernels.cuh"
+#include "heget_internal.h"
+
+namespace heget {
+
+int occupancy_f32(int n, int tile, int* bpsm, size_t* smem);
+int occupancy_f64(int n, int tile, int* bpsm, size_t* smem);
+
+static thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(HEGET_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// phase-space kernel: one thread per point
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256)
+phase_space_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, double* __restrict__ mom,
+                   double* __restrict__ w, double* __restrict__ rs_out, double* __restrict__ y_out,
+                   uint8_t* __restrict__ mask_out, int32_t* __restrict__ tries_out) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < npts;
+         j += (long long)gridDim.x * blockDim.x) {
+        Event<N> ev;
+        generate_event<N>(seed, (uint64_t)(i0 + j), S, ph, ev);
+        if (mom) store_event_momenta<N>(ev, mom + (size_t)j * (N + 2) * 4);
+        if (w) w[j] = ev.ok ? phase_space_weight<N>(ev.rs * ev.rs) : 0.0;
+        if (rs_out) rs_out[j] = ev.rs;
+        if (y_out) y_out[j] = ev.y;
+        if (mask_out) mask_out[j] = (uint8_t)ev.mask;
+        if (tries_out) tries_out[j] = ev.tries;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order reductions
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) sum_kernel(const double* __restrict__ x, long long n,
+                                                  Partial* __restrict__ partials) {
+    __shared__ Partial scratch[8];
+    Partial a = zero_partial();
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const double v = x[i];
+        a.sw = dd_add_d(a.sw, v);
+        a.sw2 = dd_add_d(a.sw2, v * v);
+        a.ntotal += 1;
+    }
+    const Partial r = block_reduce_partial<256>(a, scratch);
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// Combines nparts block partials in index order.  mode 0: write the
+// heget_xsec_result (toy-PDF scale when kind == TOY_PDF); mode 1: write
+// (sum, sum of squares) to sums.
+__global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict__ partials, int nparts, int kind,
+                                                       int mode, heget_xsec_result* __restrict__ res,
+                                                       double* __restrict__ sums) {
+    __shared__ Partial scratch[8];
+    Partial a = zero_partial();
+    for (int b = threadIdx.x; b < nparts; b += 256) a = partial_add(a, partials[b]);
+    const Partial r = block_reduce_partial<256>(a, scratch);
+    if (threadIdx.x != 0) return;
+    const double sw = r.sw.hi + r.sw.lo, sw2 = r.sw2.hi + r.sw2.lo;
+    if (mode == 1) {
+        sums[0] = sw;
+        sums[1] = sw2;
+        return;
+    }
+    const double N = (double)r.ntotal;
+    const double mean = N > 0 ? sw / N : 0.0;
+    const double var = N > 1 ? fmax(0.0, (sw2 - sw * mean) / (N - 1.0)) : 0.0;
+    const double accept = r.ntries > 0 ? N / (double)r.ntries : 1.0;
+    const double scale = (kind == HEGET_SAMPLER_TOY_PDF) ? 2.0 * accept : 1.0;
+    heget_xsec_result o;
+    o.sigma_fb = scale * mean;
+    o.err_fb = N > 0 ? scale * sqrt(var / N) : 0.0;
+    o.sum_w = sw;
+    o.sum_w2 = sw2;
+    o.accept = accept;
+    o.reserved = 0;
+    o.n_pass = r.npass;
+    o.n_total = r.ntotal;
+    o.n_tries = r.ntries;
+    o.n_escalated = r.nesc;
+    *res = o;
+}
+
+// FMA-throughput probe: kPeakChains independent chains per thread, so the
+// FMA pipe, not the FMA latency, limits the rate.
+constexpr int kPeakChains = 8;
+
+template <class T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(int iters, double* __restrict__ sink) {
+    T x[kPeakChains];
+    const T a = T(0.999999), b = T(1e-7);
+#pragma unroll
+    for (int c = 0; c < kPeakChains; ++c) x[c] = T(threadIdx.x + c);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kPeakChains; ++c) x[c] = fma(x[c], a, b);
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < kPeakChains; ++c) s += x[c];
+    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)s;
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes
+// ---------------------------------------------------------------------------
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L) {
+    L->block = kBlockThreads;
+    const int per_round = kBlockThreads >> n;
+    // enough rounds per tile to amortise the generation phase, and tiles small
+    // enough at large n that the grid still covers every SM several times
+    static const int rounds_per_tile[9] = {0, 0, 4, 8, 16, 8, 8, 8, 8};
+    L->tile = per_round * rounds_per_tile[n];
+    if (n == 8) L->tile = 4;
+    if (n == 7) L->tile = 8;
+    int bpsm = 1;
+    size_t smem = 0;
+    const int e = precision == HEGET_FP32 ? occupancy_f32(n, L->tile, &bpsm, &smem)
+                                          : occupancy_f64(n, L->tile, &bpsm, &smem);
+    if (e) return e;
+    if (bpsm < 1) bpsm = 1;
+    L->smem = smem;
+    const long long tiles = (npts + L->tile - 1) / L->tile;
+    long long grid = tiles;
+    const long long cap = (long long)kMaxGrid;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    L->grid = (int)grid;
+    (void)num_sms;
+    return 0;
+}
+
+}  // namespace heget
+
+using namespace heget;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct heget_ctx {
+    int device = 0;
+    int num_sms = 0;
+    heget_params params{};
+    Partial* partials = nullptr;      // kMaxGrid block partials
+    int* flag = nullptr;              // device input-check flag
+    heget_xsec_result* res_dev = nullptr;
+    heget_xsec_result* res_host = nullptr;  // pinned
+    int last_parts = 0;               // block partials of the last heget_xsec_launch
+    int last_kind = 0;                // its sampler kind
+};
+
+static Physics physics_of(const heget_ctx* c) {
+    return Physics{c->params.alpha, c->params.q_charge, c->params.pt_min, c->params.eta_max, c->params.dr_min};
+}
+
+namespace {
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int check_sampler(const heget_sampler* s) {
+    if (!s) return fail(HEGET_EINVAL, "sampler is NULL");
+    switch (s->kind) {
+        case HEGET_SAMPLER_FIXED:
+            if (!(s->sqrt_s > 0) || !std::isfinite(s->sqrt_s)) return fail(HEGET_EINVAL, "sqrt_s must be > 0");
+            return HEGET_OK;
+        case HEGET_SAMPLER_UNIFORM:
+            if (!(s->lo > 0) || !(s->hi >= s->lo) || !std::isfinite(s->hi))
+                return fail(HEGET_EINVAL, "uniform sampler needs 0 < lo <= hi");
+            return HEGET_OK;
+        case HEGET_SAMPLER_TOY_PDF:
+            if (!(s->e_beam > 0) || !(s->floor >= 0) || !(s->floor < 2 * s->e_beam))
+                return fail(HEGET_EINVAL, "toy-PDF sampler needs e_beam > 0 and 0 <= floor < 2 e_beam");
+            if (s->max_tries < 1 || s->max_tries > 64) return fail(HEGET_EINVAL, "max_tries must be in [1, 64]");
+            return HEGET_OK;
+        default:
+            return fail(HEGET_EINVAL, "unknown sampler kind %d", s->kind);
+    }
+}
+
+SamplerArgs sampler_args(const heget_sampler* s) {
+    SamplerArgs a;
+    a.kind = s->kind;
+    a.max_tries = s->max_tries;
+    a.sqrt_s = s->sqrt_s;
+    a.lo = s->lo;
+    a.hi = s->hi;
+    a.e_beam = s->e_beam;
+    a.floor = s->floor;
+    return a;
+}
+
+int check_common(const heget_ctx* ctx, int n, long long N) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (n < kMinN || n > kMaxN) return fail(HEGET_EINVAL, "n = %d outside [2, 8]", n);
+    if (N < 0) return fail(HEGET_EINVAL, "N = %lld < 0", N);
+    return HEGET_OK;
+}
+
+int check_precision(int p) {
+    if (p != HEGET_FP32 && p != HEGET_FP64) return fail(HEGET_EINVAL, "precision must be 32 or 64, got %d", p);
+    return HEGET_OK;
+}
+}  // namespace
+
+extern "C" {
+
+const char* heget_last_error(void) { return g_err.c_str(); }
+const char* heget_version(void) { return "heget-gb300 0.1 (sm_103a)"; }
+
+int heget_create(int device, heget_ctx** out) {
+    if (!out) return fail(HEGET_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(HEGET_EINVAL, "device %d not present (%d devices)", device, count);
+    DeviceGuard g(device);
+    heget_ctx* c = new heget_ctx();
+    c->device = device;
+    c->params = heget_params{1.0 / 137.035999, 2.0 / 3.0, 20.0, 2.5, 0.4};
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(Partial) * (size_t)kMaxGrid);
+    if (e == cudaSuccess) e = cudaMalloc(&c->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->res_dev, sizeof(heget_xsec_result));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->res_host, sizeof(heget_xsec_result));
+    if (e != cudaSuccess) {
+        heget_destroy(c);
+        return cuda_fail(e, "heget_create");
+    }
+    *out = c;
+    return HEGET_OK;
+}
+
+void heget_destroy(heget_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->partials) cudaFree(c->partials);
+    if (c->flag) cudaFree(c->flag);
+    if (c->res_dev) cudaFree(c->res_dev);
+    if (c->res_host) cudaFreeHost(c->res_host);
+    delete c;
+}
+
+int heget_set_params(heget_ctx* ctx, const heget_params* p) {
+    if (!ctx || !p) return fail(HEGET_EINVAL, "NULL argument");
+    if (!(p->alpha > 0) || !std::isfinite(p->alpha) || !std::isfinite(p->q_charge) || p->q_charge == 0)
+        return fail(HEGET_EINVAL, "alpha must be > 0 and q_charge nonzero");
+    if (!(p->pt_min >= 0) || !(p->eta_max > 0)) return fail(HEGET_EINVAL, "cuts need pt_min >= 0, eta_max > 0");
+    ctx->params = *p;
+    return HEGET_OK;
+}
+
+int heget_get_params(const heget_ctx* ctx, heget_params* p) {
+    if (!ctx || !p) return fail(HEGET_EINVAL, "NULL argument");
+    *p = ctx->params;
+    return HEGET_OK;
+}
+
+int heget_phase_space_ex(heget_ctx* ctx, uint64_t seed, int64_t i0, int64_t N, int n, const heget_sampler* smp,
+                         double* momenta, double* weights, double* sqrt_s_out, double* y_out, uint8_t* mask_out,
+                         int32_t* tries_out, void* stream) {
+    int r = check_common(ctx, n, N);
+    if (r) return r;
+    if ((r = check_sampler(smp))) return r;
+    if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
+    if (N == 0) return HEGET_OK;
+    DeviceGuard g(ctx->device);
+    const SamplerArgs S = sampler_args(smp);
+    const Physics ph = physics_of(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long blocks_needed = (N + 255) / 256;
+    const int grid = (int)(blocks_needed < kMaxGrid ? blocks_needed : kMaxGrid);
+#define PS(NN) \
+    phase_space_kernel<NN><<<grid, 256, 0, st>>>(seed, i0, N, S, ph, momenta, weights, sqrt_s_out, y_out, mask_out, tries_out)
+    switch (n) {
+        case 2: PS(2); break;
+        case 3: PS(3); break;
+        case 4: PS(4); break;
+        case 5: PS(5); break;
+        case 6: PS(6); break;
+        case 7: PS(7); break;
+        case 8: PS(8); break;
+    }
+#undef PS
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "phase_space_kernel");
+    return HEGET_OK;
+}
+
+int heget_phase_space(heget_ctx* ctx, uint64_t seed, int64_t N, int n, double sqrt_s, double* momenta,
+                      double* weights, void* stream) {
+    heget_sampler s{HEGET_SAMPLER_FIXED, sqrt_s, 0, 0, 7000.0, 100.0, 64};
+    return heget_phase_space_ex(ctx, seed, 0, N, n, &s, momenta, weights, nullptr, nullptr, nullptr, nullptr, stream);
+}
+
+int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta, const uint32_t* hel_mask, int precision,
+               double* amp2, void* stream) {
+    int r = check_common(ctx, n, N);
+    if (r) return r;
+    if ((r = check_precision(precision))) return r;
+    if (N == 0) return HEGET_OK;
+    if (!momenta || !amp2) return fail(HEGET_EINVAL, "momenta and amp2 must be non-NULL");
+    if (((uintptr_t)momenta & 15) != 0) return fail(HEGET_EINVAL, "momenta must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    AmpLaunch L;
+    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L))) return cuda_fail((cudaError_t)r, "occupancy");
+    const Physics ph = physics_of(ctx);
+    cudaStream_t st = (cudaStream_t)stream;
+    r = precision == HEGET_FP32 ? launch_amp2_f32(n, momenta, N, hel_mask, amp2, ph, ctx->flag, L, st)
+                                : launch_amp2_f64(n, momenta, N, hel_mask, amp2, ph, ctx->flag, L, st);
+    if (r) return cuda_fail((cudaError_t)r, "amp2_kernel");
+    return HEGET_OK;
+}
+
+int heget_check(heget_ctx* ctx, void* stream) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "heget_check");
+    if (h) {
+        e = cudaMemsetAsync(ctx->flag, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "heget_check reset");
+        return fail(HEGET_EINVAL, "input check failed: non-finite momenta, or p1/p2 not massless along +z/-z");
+    }
+    return HEGET_OK;
+}
+
+int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N, const heget_sampler* smp,
+                      int precision, double* w_out, void* stream) {
+    int r = check_common(ctx, n, N);
+    if (r) return r;
+    if ((r = check_precision(precision))) return r;
+    if ((r = check_sampler(smp))) return r;
+    if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    AmpLaunch L;
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L)))
+        return cuda_fail((cudaError_t)r, "occupancy");
+    const Physics ph = physics_of(ctx);
+    const SamplerArgs S = sampler_args(smp);
+    if (N > 0) {
+        r = precision == HEGET_FP32 ? launch_xsec_f32(n, seed, i0, N, S, ph, ctx->partials, w_out, L, st)
+                                    : launch_xsec_f64(n, seed, i0, N, S, ph, ctx->partials, w_out, L, st);
+        if (r) return cuda_fail((cudaError_t)r, "xsec_kernel");
+    }
+    ctx->last_parts = N > 0 ? L.grid : 0;
+    ctx->last_kind = S.kind;
+    return HEGET_OK;
+}
+
+int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev, void* stream) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (!result_dev) return fail(HEGET_EINVAL, "result_dev is NULL");
+    DeviceGuard g(ctx->device);
+    finalize_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(ctx->partials, ctx->last_parts, ctx->last_kind, 0,
+                                                         result_dev, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "finalize_kernel");
+    return HEGET_OK;
+}
+
+int heget_xsec_async(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N, const heget_sampler* smp,
+                     int precision, heget_xsec_result* result_dev, double* w_out, void* stream) {
+    if (!result_dev) return fail(HEGET_EINVAL, "result_dev is NULL");
+    int r = heget_xsec_launch(ctx, n, seed, i0, N, smp, precision, w_out, stream);
+    if (r) return r;
+    return heget_xsec_finalize(ctx, result_dev, stream);
+}
+
+int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops) {
+    if (!ctx || !tflops) return fail(HEGET_EINVAL, "NULL argument");
+    int r = check_precision(precision);
+    if (r) return r;
+    DeviceGuard g(ctx->device);
+    const int blocks = ctx->num_sms * 8, threads = 256;
+    const int iters = precision == HEGET_FP32 ? 1024 : 256;
+    double* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&sink, sizeof(double) * blocks * threads);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0);
+        if (precision == HEGET_FP32)
+            fma_peak_kernel<float><<<blocks, threads>>>(iters, sink);
+        else
+            fma_peak_kernel<double><<<blocks, threads>>>(iters, sink);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best_ms) best_ms = ms;   // rep 0 is warm-up
+    }
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "heget_measure_fma_peak");
+    const double fmas = (double)blocks * threads * iters * kPeakChains;
+    *tflops = 2.0 * fmas / (best_ms * 1e-3) / 1e12;
+    return HEGET_OK;
+}
+
+int heget_xsec(heget_ctx* ctx, int n, int64_t N, uint64_t seed, const heget_sampler* smp, int precision,
+               heget_xsec_result* out, void* stream) {
+    if (!out) return fail(HEGET_EINVAL, "out is NULL");
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    int r = heget_xsec_async(ctx, n, seed, 0, N, smp, precision, ctx->res_dev, nullptr, stream);
+    if (r) return r;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->res_host, ctx->res_dev, sizeof(heget_xsec_result), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "heget_xsec");
+    *out = *ctx->res_host;
+    return HEGET_OK;
+}
+
+int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev, void* stream) {
+    if (!ctx || !out_dev) return fail(HEGET_EINVAL, "NULL argument");
+    if (N < 0) return fail(HEGET_EINVAL, "N < 0");
+    if (N > 0 && !x) return fail(HEGET_EINVAL, "x is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    long long blocks = (N + 255) / 256;
+    const int grid = (int)(blocks < 1 ? 1 : (blocks < 4 * ctx->num_sms ? blocks : 4 * ctx->num_sms));
+    if (N > 0) sum_kernel<<<grid, 256, 0, st>>>(x, N, ctx->partials);
+    finalize_kernel<<<1, 256, 0, st>>>(ctx->partials, N > 0 ? grid : 0, 0, 1, nullptr, out_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "heget_sum");
+    return HEGET_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// heget_kernels.cuh -- the hot-path kernels:
+//   amp2_kernel   : momenta [N][n+2][4] -> sum_h |M_h|^2          (heget_amp2)
+//   xsec_kernel   : RNG -> sqrt(s-hat) -> RAMBO -> cuts -> |M|^2 -> weight ->
+//                   double-double block partials, all in one pass  (heget_xsec)
+// plus the launch-shape bookkeeping shared with the host code.
+#pragma once
+
+#include "heget_amp.cuh"
+
+namespace heget {
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr size_t table_bytes() {
+    return align16(RoundTables<R, N, BLOCK>::bytes);
+}
+
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr size_t amp_smem_bytes(int tile) {
+    return table_bytes<R, N, BLOCK>() + align16((size_t)tile * sizeof(PointRec<N>));
+}
+
+// Load and check one input point; p1 must be massless along +z, p2 along -z.
+template <int N>
+__device__ __forceinline__ void load_point(const double* __restrict__ src, double cpl, PointRec<N>& rec,
+                                           int* __restrict__ flag) {
+    double v[(N + 2) * 4];
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int a = 0; a < (N + 2) * 2; ++a) {
+        const double2 x = __ldg(s2 + a);
+        v[2 * a] = x.x;
+        v[2 * a + 1] = x.y;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < (N + 2) * 4; ++a) ok = ok && isfinite(v[a]);
+    const double E1 = v[0], E2 = v[4];
+    const double tol = 1e-12;
+    ok = ok && E1 > 0 && E2 > 0;
+    ok = ok && fabs(v[1]) <= tol * E1 && fabs(v[2]) <= tol * E1 && fabs(v[3] - E1) <= tol * E1;
+    ok = ok && fabs(v[5]) <= tol * E2 && fabs(v[6]) <= tol * E2 && fabs(v[7] + E2) <= tol * E2;
+    const double s = 2.0 * (E1 * E2 - v[3] * v[7]);
+    const double irs = ok ? rsqrt(s) : 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rec.k[a][m] = v[8 + 4 * a + m] * irs;
+    rec.e1 = E1 * irs;
+    rec.e2 = E2 * irs;
+    double sp = 1;
+    for (int a = 2; a < N; ++a) sp /= s;
+    rec.fac = cpl * sp;
+    rec.wfac = 0;
+    rec.valid = ok;
+    rec.mask = 1;
+    rec.tries = 1;
+    rec.pad = 0;
+    if (!ok) atomicOr(flag, 1);
+}
+
+template <class R, int N, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __restrict__ mask,
+            double* __restrict__ out, int tile, Physics ph, int* __restrict__ flag) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PointRec<N>* recs = reinterpret_cast<PointRec<N>*>(smem + table_bytes<R, N, BLOCK>());
+    const float wh = lane_weight<N>(mask, threadIdx.x & ((1u << N) - 1));
+    const double cpl = coupling_pow(ph, N);
+    for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
+        const int cnt = (int)min((long long)tile, npts - t0);
+        for (int t = threadIdx.x; t < cnt; t += BLOCK)
+            load_point<N>(mom + (size_t)(t0 + t) * (N + 2) * 4, cpl, recs[t], flag);
+        __syncthreads();
+        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh, [&](int p, double S) {
+            out[t0 + p] = recs[p].valid ? S * recs[p].fac : __longlong_as_double(0x7ff8000000000000ll);
+        });
+    }
+}
+
+// Deterministic block reduction of per-thread partials (shuffle tree, then
+// warp leaders in order).  Uses `scratch` (BLOCK/32 Partials of shared
+// memory); result valid in thread 0.
+template <int BLOCK>
+__device__ __forceinline__ Partial block_reduce_partial(Partial a, Partial* scratch) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        Partial b;
+        b.sw.hi = __shfl_down_sync(0xffffffffu, a.sw.hi, off);
+        b.sw.lo = __shfl_down_sync(0xffffffffu, a.sw.lo, off);
+        b.sw2.hi = __shfl_down_sync(0xffffffffu, a.sw2.hi, off);
+        b.sw2.lo = __shfl_down_sync(0xffffffffu, a.sw2.lo, off);
+        b.npass = __shfl_down_sync(0xffffffffu, a.npass, off);
+        b.ntotal = __shfl_down_sync(0xffffffffu, a.ntotal, off);
+        b.ntries = __shfl_down_sync(0xffffffffu, a.ntries, off);
+        b.nesc = __shfl_down_sync(0xffffffffu, a.nesc, off);
+        a = partial_add(a, b);
+    }
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < BLOCK / 32; ++w) a = partial_add(a, scratch[w]);
+    return a;
+}
+
+__device__ __forceinline__ Partial zero_partial() {
+    Partial p;
+    p.sw = DD{0, 0};
+    p.sw2 = DD{0, 0};
+    p.npass = p.ntotal = p.ntries = p.nesc = 0;
+    return p;
+}
+
+template <class R, int N, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, int tile,
+            Partial* __restrict__ partials, double* __restrict__ w_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PointRec<N>* recs = reinterpret_cast<PointRec<N>*>(smem + table_bytes<R, N, BLOCK>());
+    const float wh = lane_weight<N>(nullptr, 0);
+    Partial acc = zero_partial();
+    for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
+        const int cnt = (int)min((long long)tile, npts - t0);
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) {
+            Event<N> ev;
+            generate_event<N>(seed, (uint64_t)(i0 + t0 + t), S, ph, ev);
+            event_to_rec<N>(ev, ph, recs[t]);
+            acc.npass += recs[t].mask;
+            acc.ntotal += 1;
+            acc.ntries += recs[t].tries;
+        }
+        __syncthreads();
+        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh, [&](int p, double Ssum) {
+            const double w = recs[p].valid ? Ssum * recs[p].fac * recs[p].wfac : 0.0;
+            acc.sw = dd_add_d(acc.sw, w);
+            acc.sw2 = dd_add_d(acc.sw2, w * w);
+            if (w_out) w_out[t0 + p] = w;
+        });
+    }
+    // the round tables are free now: reuse them as reduction scratch
+    const Partial r = block_reduce_partial<BLOCK>(acc, reinterpret_cast<Partial*>(smem));
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch descriptors (defined per precision in heget_f32.cu /
+// heget_f64.cu).
+// ---------------------------------------------------------------------------
+struct AmpLaunch {
+    int block, tile, grid;
+    size_t smem;
+};
+
+// Returns cudaError_t as int.
+int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
+                    const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st);
+int launch_amp2_f64(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
+                    const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st);
+int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
+                    const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
+                    cudaStream_t st);
+int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
+                    const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
+                    cudaStream_t st);
+// Default launch shape and the maximum resident blocks per SM.
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L);
+
+}  // namespace heget

@@ -1,0 +1,56 @@
+// heget_launch.cuh -- per-precision launch wrappers of the amplitude kernels.
+// Included by exactly one .cu per precision, which defines HEGET_REAL and
+// HEGET_SUFFIX before including it.
+#pragma once
+
+#include "heget_kernels.cuh"
+
+namespace heget {
+
+constexpr int kBlock = 256;
+
+template <class R, int N>
+static int launch_amp2_n(const double* mom, long long npts, const uint32_t* mask, double* out, const Physics& ph,
+                         int* flag, const AmpLaunch& L, cudaStream_t st) {
+    auto k = amp2_kernel<R, N, kBlock>;
+    const size_t smem = amp_smem_bytes<R, N, kBlock>(L.tile);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k<<<L.grid, kBlock, smem, st>>>(mom, npts, mask, out, L.tile, ph, flag);
+    return (int)cudaGetLastError();
+}
+
+template <class R, int N>
+static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                         Partial* partials, double* w_out, const AmpLaunch& L, cudaStream_t st) {
+    auto k = xsec_kernel<R, N, kBlock>;
+    const size_t smem = amp_smem_bytes<R, N, kBlock>(L.tile);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k<<<L.grid, kBlock, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out);
+    return (int)cudaGetLastError();
+}
+
+template <class R, int N>
+static int occupancy_n(int tile, int* blocks_per_sm, size_t* smem_out) {
+    const size_t smem = amp_smem_bytes<R, N, kBlock>(tile);
+    *smem_out = smem;
+    auto k = xsec_kernel<R, N, kBlock>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
+}
+
+#define HEGET_DISPATCH_N(n, CALL)       \
+    switch (n) {                        \
+        case 2: return CALL(2);         \
+        case 3: return CALL(3);         \
+        case 4: return CALL(4);         \
+        case 5: return CALL(5);         \
+        case 6: return CALL(6);         \
+        case 7: return CALL(7);         \
+        case 8: return CALL(8);         \
+        default: return (int)cudaErrorInvalidValue; \
+    }
+
+}  // namespace heget

@@ -1,0 +1,206 @@
+"""Thin ctypes binding of the C ABI in include/heget.h.
+
+Argument marshalling only: every step of the hot path runs in libheget.so.
+Device arrays are passed as raw pointers (``tensor.data_ptr()``); streams as
+``torch.cuda.Stream.cuda_stream`` integers (0 = legacy default stream).
+Loading fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libheget.so")
+
+HEGET_OK, HEGET_EINVAL, HEGET_ENOMEM, HEGET_ECUDA, HEGET_ETIMEOUT, HEGET_EBUSY, HEGET_ENOTFOUND = range(7)
+HEGET_FP32, HEGET_FP64 = 32, 64
+HEGET_SAMPLER_FIXED, HEGET_SAMPLER_UNIFORM, HEGET_SAMPLER_TOY_PDF = 0, 1, 2
+
+STATUS_NAMES = {0: "HEGET_OK", 1: "HEGET_EINVAL", 2: "HEGET_ENOMEM", 3: "HEGET_ECUDA",
+                4: "HEGET_ETIMEOUT", 5: "HEGET_EBUSY", 6: "HEGET_ENOTFOUND"}
+
+
+class HegetError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class heget_params(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("q_charge", C.c_double), ("pt_min", C.c_double),
+                ("eta_max", C.c_double), ("dr_min", C.c_double)]
+
+
+class heget_sampler(C.Structure):
+    _fields_ = [("kind", C.c_int), ("sqrt_s", C.c_double), ("lo", C.c_double), ("hi", C.c_double),
+                ("e_beam", C.c_double), ("floor", C.c_double), ("max_tries", C.c_int)]
+
+
+class heget_xsec_result(C.Structure):
+    _fields_ = [("sigma_fb", C.c_double), ("err_fb", C.c_double), ("sum_w", C.c_double),
+                ("sum_w2", C.c_double), ("accept", C.c_double), ("reserved", C.c_double),
+                ("n_pass", C.c_int64), ("n_total", C.c_int64), ("n_tries", C.c_int64),
+                ("n_escalated", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+def sampler_fixed(sqrt_s: float) -> heget_sampler:
+    return heget_sampler(HEGET_SAMPLER_FIXED, sqrt_s, 0.0, 0.0, 7000.0, 100.0, 64)
+
+
+def sampler_uniform(lo: float, hi: float) -> heget_sampler:
+    return heget_sampler(HEGET_SAMPLER_UNIFORM, 0.0, lo, hi, 7000.0, 100.0, 64)
+
+
+def sampler_toy_pdf(e_beam: float = 7000.0, floor: float = 100.0, max_tries: int = 64) -> heget_sampler:
+    return heget_sampler(HEGET_SAMPLER_TOY_PDF, 0.0, 0.0, 0.0, e_beam, floor, max_tries)
+
+
+_lib = None
+P, I32, I64, U64, D = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
+
+# name -> (restype, argtypes); the exported symbols of include/heget.h
+SIGNATURES = {
+    "heget_create": (I32, [I32, C.POINTER(P)]),
+    "heget_destroy": (None, [P]),
+    "heget_set_params": (I32, [P, C.POINTER(heget_params)]),
+    "heget_get_params": (I32, [P, C.POINTER(heget_params)]),
+    "heget_last_error": (C.c_char_p, []),
+    "heget_version": (C.c_char_p, []),
+    "heget_phase_space": (I32, [P, U64, I64, I32, D, P, P, P]),
+    "heget_phase_space_ex": (I32, [P, U64, I64, I64, I32, C.POINTER(heget_sampler), P, P, P, P, P, P, P]),
+    "heget_amp2": (I32, [P, I32, I64, P, P, I32, P, P]),
+    "heget_check": (I32, [P, P]),
+    "heget_xsec_async": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), I32, P, P, P]),
+    "heget_xsec": (I32, [P, I32, I64, U64, C.POINTER(heget_sampler), I32, C.POINTER(heget_xsec_result), P]),
+    "heget_xsec_launch": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), I32, P, P]),
+    "heget_xsec_finalize": (I32, [P, P, P]),
+    "heget_measure_fma_peak": (I32, [P, I32, C.POINTER(C.c_double)]),
+    "heget_sum": (I32, [P, P, I64, P, P]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libheget.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} not found: build it with paper_0908_4403_gb300.build.build() "
+                              "(there is no CPU fallback)")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != HEGET_OK:
+        raise HegetError(status, load().heget_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# one wrapper per C entry point, same names
+# ---------------------------------------------------------------------------
+
+def heget_create(device: int = 0):
+    h = P()
+    _check(load().heget_create(device, C.byref(h)))
+    return h
+
+
+def heget_destroy(ctx):
+    load().heget_destroy(ctx)
+
+
+def heget_set_params(ctx, alpha=1 / 137.035999, q_charge=2 / 3, pt_min=20.0, eta_max=2.5, dr_min=0.4):
+    p = heget_params(alpha, q_charge, pt_min, eta_max, dr_min)
+    _check(load().heget_set_params(ctx, C.byref(p)))
+
+
+def heget_get_params(ctx) -> heget_params:
+    p = heget_params()
+    _check(load().heget_get_params(ctx, C.byref(p)))
+    return p
+
+
+def heget_version() -> str:
+    return load().heget_version().decode()
+
+
+def heget_phase_space(ctx, seed, N, n, sqrt_s, momenta, weights=None, stream=None):
+    _check(load().heget_phase_space(ctx, seed, N, n, sqrt_s, _ptr(momenta), _ptr(weights), _stream(stream)))
+
+
+def heget_phase_space_ex(ctx, seed, i0, N, n, sampler, momenta=None, weights=None, sqrt_s=None, y=None,
+                         mask=None, tries=None, stream=None):
+    _check(load().heget_phase_space_ex(ctx, seed, i0, N, n, C.byref(sampler), _ptr(momenta), _ptr(weights),
+                                       _ptr(sqrt_s), _ptr(y), _ptr(mask), _ptr(tries), _stream(stream)))
+
+
+def heget_amp2(ctx, n, N, momenta, amp2, hel_mask=None, precision=HEGET_FP64, stream=None):
+    _check(load().heget_amp2(ctx, n, N, _ptr(momenta), _ptr(hel_mask), precision, _ptr(amp2), _stream(stream)))
+
+
+def heget_check(ctx, stream=None):
+    _check(load().heget_check(ctx, _stream(stream)))
+
+
+def heget_xsec_async(ctx, n, seed, i0, N, sampler, precision, result_dev, w_out=None, stream=None):
+    _check(load().heget_xsec_async(ctx, n, seed, i0, N, C.byref(sampler), precision, _ptr(result_dev),
+                                   _ptr(w_out), _stream(stream)))
+
+
+def heget_xsec(ctx, n, N, seed, sampler, precision=HEGET_FP32, stream=None) -> heget_xsec_result:
+    out = heget_xsec_result()
+    _check(load().heget_xsec(ctx, n, N, seed, C.byref(sampler), precision, C.byref(out), _stream(stream)))
+    return out
+
+
+def heget_xsec_launch(ctx, n, seed, i0, N, sampler, precision, w_out=None, stream=None):
+    _check(load().heget_xsec_launch(ctx, n, seed, i0, N, C.byref(sampler), precision, _ptr(w_out),
+                                    _stream(stream)))
+
+
+def heget_xsec_finalize(ctx, result_dev, stream=None):
+    _check(load().heget_xsec_finalize(ctx, _ptr(result_dev), _stream(stream)))
+
+
+def heget_measure_fma_peak(ctx, precision=HEGET_FP32) -> float:
+    v = C.c_double()
+    _check(load().heget_measure_fma_peak(ctx, precision, C.byref(v)))
+    return v.value
+
+
+def heget_sum(ctx, x, N, out_dev, stream=None):
+    _check(load().heget_sum(ctx, _ptr(x), N, _ptr(out_dev), _stream(stream)))
+
+
+def result_from_tensor(t) -> heget_xsec_result:
+    """Decode a heget_xsec_result stored in a (CPU) uint8/float64 tensor of 80 bytes."""
+    import numpy as np
+    raw = np.ascontiguousarray(t.cpu().numpy()).view(np.uint8).tobytes()
+    return heget_xsec_result.from_buffer_copy(raw[:C.sizeof(heget_xsec_result)])
