@@ -66,12 +66,12 @@ __device__ __forceinline__ Row<R> row_times(const Row<R>& r, const Row<R>& m0, c
     return o;
 }
 
-template <class R> __device__ __forceinline__ R to_r(double x);
-template <> __device__ __forceinline__ float to_r<float>(double x) { return __double2float_rn(x); }
-template <> __device__ __forceinline__ double to_r<double>(double x) { return x; }
 template <class R> __device__ __forceinline__ R recip(R x);
 template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
+template <class R> __device__ __forceinline__ R rsq(R x);
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 
 // Shared-memory tables of one round: P = BLOCK / 2^N points.
 // Entry layout [index][point][lambda] so that the lanes of a warp, which read
@@ -106,30 +106,34 @@ struct RoundTables {
 };
 
 // Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Two phases
-// separated by barriers; all threads of the block must call it.
+// separated by barriers; all threads of the block must call it.  Everything
+// here runs in R: the FP64 content (invariants) is already in the records.
 template <class R, int N, int BLOCK>
-__device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, const PointRec<N>* recs,
+__device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, const PointRec<R, N>* recs,
                                             int cnt) {
     using RT = RoundTables<R, N, BLOCK>;
     constexpr int P = RT::P, K = RT::K, NS = RT::NS;
     const int tid = threadIdx.x;
-    // (a) photon angles and propagator data per set T (q_T^2 in FP64)
+    // (a) photon angles, and propagator data per photon set T:
+    //     Qbar_T / t_T with t_T summed from the invariants
     constexpr int n_ph = P * N, n_sd = P * NS;
     for (int it = tid; it < n_ph + n_sd; it += BLOCK) {
         if (it < n_ph) {
             const int p = it / N, j = it - p * N;
             if (p >= cnt) continue;
-            const double* k = recs[p].k[j];
-            const double pt2 = k[1] * k[1] + k[2] * k[2];
-            const double kabs = sqrt(pt2 + k[3] * k[3]);
-            const double pt = sqrt(pt2);
+            const R* k = recs[p].k[j];
+            const R pt2 = k[1] * k[1] + k[2] * k[2];
+            const R ka2 = pt2 + k[3] * k[3];
+            const R rk = rsq<R>(ka2);
             Row<R> d;
-            d.ar = to_r<R>(pt / kabs);
-            d.ai = to_r<R>(k[3] / kabs);
-            if (pt > 1e-12 * kabs) {
-                d.br = to_r<R>(k[1] / pt);
-                d.bi = to_r<R>(k[2] / pt);
+            d.ai = k[3] * rk;                        // cos theta
+            if (pt2 > R(1e-24) * ka2) {
+                const R rpt = rsq<R>(pt2);
+                d.ar = pt2 * rpt * rk;               // sin theta
+                d.br = k[1] * rpt;                   // cos phi
+                d.bi = k[2] * rpt;                   // sin phi
             } else {  // photon along z: the phi -> 0 limit of the polarisation
+                d.ar = R(0);
                 d.br = R(1);
                 d.bi = R(0);
             }
@@ -138,8 +142,9 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
             const int r = it - n_ph;
             const int p = r / NS, T = r - p * NS;
             if (p >= cnt || T == 0 || T == NS - 1) continue;
-            const PointRec<N>& rc = recs[p];
-            double q0 = -rc.e2, q1 = 0, q2 = 0, q3 = rc.e2;
+            const PointRec<R, N>& rc = recs[p];
+            R q0 = -rc.e2, q1 = R(0), q2 = R(0), q3 = rc.e2;
+            double t = 0.0;   // FP64 sum of FP64 invariants, rounded once
 #pragma unroll
             for (int i = 0; i < N; ++i)
                 if (T >> i & 1) {
@@ -147,14 +152,17 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
                     q1 += rc.k[i][1];
                     q2 += rc.k[i][2];
                     q3 += rc.k[i][3];
+                    t += rc.m2[i] - rc.s2[i];
+#pragma unroll
+                    for (int j = i + 1; j < N; ++j)
+                        if (T >> j & 1) t += rc.sij[pair_index<N>(i, j)];
                 }
-            const double t = q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3;
-            const R it_ = recip<R>(to_r<R>(t));
+            const R it_ = recip<R>(R(t));
             Row<R> d;
-            d.ar = to_r<R>(q0 + q3) * it_;
-            d.ai = to_r<R>(q0 - q3) * it_;
-            d.br = to_r<R>(q1) * it_;
-            d.bi = to_r<R>(q2) * it_;
+            d.ar = (q0 + q3) * it_;
+            d.ai = (q0 - q3) * it_;
+            d.br = q1 * it_;
+            d.bi = q2 * it_;
             tb.SD[p * NS + T] = d;
         }
     }
@@ -195,8 +203,8 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
         st_row(tb.M1 + o, m1);
         if (T == (1 << j)) {
             const size_t oc = ((size_t)j * P + p) * 2 + lam_bit;
-            const R n1 = to_r<R>(sqrt(2.0 * recs[p].e1));
-            const R n2 = to_r<R>(sqrt(2.0 * recs[p].e2));
+            const R n1 = recs[p].n1;
+            const R n2 = recs[p].n2;
             st_row(tb.CL + oc, Row<R>{n1 * e00, R(0), n1 * e10r, n1 * e10i});
             st_row(tb.R1 + oc, Row<R>{n2 * m1.ar, n2 * m1.ai, n2 * m1.br, n2 * m1.bi});
         }
@@ -273,7 +281,7 @@ __device__ __forceinline__ float lane_weight(const uint32_t* mask, unsigned h) {
 // reduction yields S = sum_h w_h |A_h|^2 (scaled units); emit(p, S) is called
 // by exactly one thread per point (the group's first thread).
 template <class R, int N, int BLOCK, class Emit>
-__device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, const PointRec<N>* recs, int cnt,
+__device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, const PointRec<R, N>* recs, int cnt,
                                                  float wh, Emit emit) {
     using RT = RoundTables<R, N, BLOCK>;
     constexpr int P = RT::P;

@@ -32,21 +32,49 @@ int cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // phase-space kernel: one thread per point
 // ---------------------------------------------------------------------------
+// Momenta are generated into shared memory (point-minor) and written out
+// cooperatively, so the [N][n+2][4] stores are coalesced.
+constexpr int kPsBlock = 128;
+
 template <int N>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPsBlock)
 phase_space_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, double* __restrict__ mom,
                    double* __restrict__ w, double* __restrict__ rs_out, double* __restrict__ y_out,
                    uint8_t* __restrict__ mask_out, int32_t* __restrict__ tries_out) {
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < npts;
-         j += (long long)gridDim.x * blockDim.x) {
-        Event<N> ev;
-        generate_event<N>(seed, (uint64_t)(i0 + j), S, ph, ev);
-        if (mom) store_event_momenta<N>(ev, mom + (size_t)j * (N + 2) * 4);
-        if (w) w[j] = ev.ok ? phase_space_weight<N>(ev.rs * ev.rs) : 0.0;
-        if (rs_out) rs_out[j] = ev.rs;
-        if (y_out) y_out[j] = ev.y;
-        if (mask_out) mask_out[j] = (uint8_t)ev.mask;
-        if (tries_out) tries_out[j] = ev.tries;
+    __shared__ double stage[N * 4 * kPsBlock];
+    __shared__ double rs_s[kPsBlock];
+    constexpr int ROW = (N + 2) * 4;
+    for (long long j0 = (long long)blockIdx.x * kPsBlock; j0 < npts; j0 += (long long)gridDim.x * kPsBlock) {
+        const int cnt = (int)min((long long)kPsBlock, npts - j0);
+        const int t = threadIdx.x;
+        if (t < cnt) {
+            const long long j = j0 + t;
+            const MomView v{stage + t, kPsBlock};
+            EventInfo ev;
+            generate_event<N>(seed, (uint64_t)(i0 + j), S, ph, v, ev);
+            rs_s[t] = ev.rs;
+            if (w) w[j] = ev.ok ? phase_space_weight<N>(ev.rs * ev.rs) : 0.0;
+            if (rs_out) rs_out[j] = ev.rs;
+            if (y_out) y_out[j] = (S.kind == HEGET_SAMPLER_TOY_PDF && ev.ok) ? 0.5 * log(ev.x1 / ev.x2) : 0.0;
+            if (mask_out) mask_out[j] = (uint8_t)ev.mask;
+            if (tries_out) tries_out[j] = ev.tries;
+        }
+        __syncthreads();
+        if (mom) {
+            double* dst = mom + (size_t)j0 * ROW;
+            for (int e = threadIdx.x; e < cnt * ROW; e += kPsBlock) {
+                const int p = e / ROW, c = e - p * ROW, a = c >> 2, m = c & 3;
+                double val;
+                if (a >= 2) {
+                    val = stage[(4 * (a - 2) + m) * kPsBlock + p];
+                } else {   // p1 = (rs/2)(1,0,0,1), p2 = (rs/2)(1,0,0,-1)
+                    const double h = 0.5 * rs_s[p];
+                    val = m == 0 ? h : (m == 3 ? (a == 0 ? h : -h) : 0.0);
+                }
+                dst[e] = val;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -125,15 +153,15 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int iters, double* __rest
 // ---------------------------------------------------------------------------
 // launch shapes
 // ---------------------------------------------------------------------------
-int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L) {
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec) {
     L->block = kBlockThreads;
-    const int per_round = kBlockThreads >> n;
-    // enough rounds per tile to amortise the generation phase, and tiles small
-    // enough at large n that the grid still covers every SM several times
-    static const int rounds_per_tile[9] = {0, 0, 4, 8, 16, 8, 8, 8, 8};
-    L->tile = per_round * rounds_per_tile[n];
-    if (n == 8) L->tile = 4;
-    if (n == 7) L->tile = 8;
+    // Points per block tile.  amp2: four rounds of block/2^n points (keeps the
+    // staged rows and records small); xsec: one point per thread in the
+    // generation phase while that stays cheap against the tree (n <= 4), then
+    // small tiles so that large-n grids still cover every SM many times.
+    static const int amp2_tile[9] = {0, 0, 256, 128, 64, 32, 16, 8, 4};
+    static const int xsec_tile[9] = {0, 0, 256, 256, 256, 64, 32, 8, 4};
+    L->tile = xsec ? xsec_tile[n] : amp2_tile[n];
     int bpsm = 1;
     size_t smem = 0;
     const int e = precision == HEGET_FP32 ? occupancy_f32(n, L->tile, &bpsm, &smem)
@@ -170,8 +198,28 @@ struct heget_ctx {
     int last_kind = 0;                // its sampler kind
 };
 
-static Physics physics_of(const heget_ctx* c) {
-    return Physics{c->params.alpha, c->params.q_charge, c->params.pt_min, c->params.eta_max, c->params.dr_min};
+// Launch constants for n photons: couplings (4 pi alpha Q^2)^n, the event
+// weight constant (1/2)(1/2^2)(1/3^2) 3 (1/n!) c_n (4 pi alpha Q^2)^n in fb
+// (Sec. 2.1 eq. (2); Phi_n = c_n s^(n-2)), and the cut constants.
+static Physics physics_of(const heget_ctx* c, int n) {
+    const heget_params& p = c->params;
+    Physics ph{};
+    ph.alpha = p.alpha;
+    ph.q = p.q_charge;
+    ph.pt_min = p.pt_min;
+    ph.eta_max = p.eta_max;
+    ph.dr_min = p.dr_min;
+    const double g2 = 4.0 * M_PI * p.alpha * p.q_charge * p.q_charge;
+    double cpl = 1, nfact = 1;
+    for (int i = 0; i < n; ++i) cpl *= g2;
+    for (int i = 2; i <= n; ++i) nfact *= i;
+    ph.cpl = cpl;
+    ph.wconst = cpl * phase_space_const(n) / (24.0 * nfact) * 0.3893793721e12;
+    ph.sinh_eta = std::sinh(p.eta_max);
+    ph.cosh_eta = std::cosh(p.eta_max);
+    ph.sinh_dr = p.dr_min > 0 ? std::sinh(p.dr_min) : 0.0;
+    ph.cos_dr = p.dr_min > 0 ? std::cos(p.dr_min) : 1.0;
+    return ph;
 }
 
 namespace {
@@ -296,12 +344,12 @@ int heget_phase_space_ex(heget_ctx* ctx, uint64_t seed, int64_t i0, int64_t N, i
     if (N == 0) return HEGET_OK;
     DeviceGuard g(ctx->device);
     const SamplerArgs S = sampler_args(smp);
-    const Physics ph = physics_of(ctx);
+    const Physics ph = physics_of(ctx, n);
     cudaStream_t st = (cudaStream_t)stream;
-    const long long blocks_needed = (N + 255) / 256;
+    const long long blocks_needed = (N + kPsBlock - 1) / kPsBlock;
     const int grid = (int)(blocks_needed < kMaxGrid ? blocks_needed : kMaxGrid);
 #define PS(NN) \
-    phase_space_kernel<NN><<<grid, 256, 0, st>>>(seed, i0, N, S, ph, momenta, weights, sqrt_s_out, y_out, mask_out, tries_out)
+    phase_space_kernel<NN><<<grid, kPsBlock, 0, st>>>(seed, i0, N, S, ph, momenta, weights, sqrt_s_out, y_out, mask_out, tries_out)
     switch (n) {
         case 2: PS(2); break;
         case 3: PS(3); break;
@@ -333,8 +381,8 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta, const ui
     if (((uintptr_t)momenta & 15) != 0) return fail(HEGET_EINVAL, "momenta must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L))) return cuda_fail((cudaError_t)r, "occupancy");
-    const Physics ph = physics_of(ctx);
+    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, false))) return cuda_fail((cudaError_t)r, "occupancy");
+    const Physics ph = physics_of(ctx, n);
     cudaStream_t st = (cudaStream_t)stream;
     r = precision == HEGET_FP32 ? launch_amp2_f32(n, momenta, N, hel_mask, amp2, ph, ctx->flag, L, st)
                                 : launch_amp2_f64(n, momenta, N, hel_mask, amp2, ph, ctx->flag, L, st);
@@ -369,9 +417,9 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L)))
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L, true)))
         return cuda_fail((cudaError_t)r, "occupancy");
-    const Physics ph = physics_of(ctx);
+    const Physics ph = physics_of(ctx, n);
     const SamplerArgs S = sampler_args(smp);
     if (N > 0) {
         r = precision == HEGET_FP32 ? launch_xsec_f32(n, seed, i0, N, S, ph, ctx->partials, w_out, L, st)

@@ -165,8 +165,13 @@ __host__ __device__ __forceinline__ Partial partial_add(const Partial& a, const 
 // ---------------------------------------------------------------------------
 // Kernel arguments
 // ---------------------------------------------------------------------------
+// Physics constants of one launch (derived on the host from heget_params and n).
 struct Physics {
     double alpha, q, pt_min, eta_max, dr_min;
+    double cpl;                 // (4 pi alpha q^2)^n
+    double wconst;              // cpl c_n / (24 n!) GeV^-2 -> fb (weight = wconst S / s)
+    double sinh_eta, cosh_eta;  // sinh, cosh of eta_max
+    double sinh_dr, cos_dr;     // sinh, cos of dr_min
 };
 
 struct SamplerArgs {

@@ -16,47 +16,62 @@ __host__ __device__ constexpr size_t table_bytes() {
     return align16(RoundTables<R, N, BLOCK>::bytes);
 }
 
+// Shared memory: [region][records].  The region holds the round tables during
+// the amplitude rounds and, before them, the tile's FP64 momenta (input rows
+// for amp2, generated photons for xsec); the two uses never overlap in time.
+__host__ __device__ constexpr int amp2_row(int N) { return (N + 2) * 4 + 1; }   // odd stride: conflict-free rows
+
 template <class R, int N, int BLOCK>
-__host__ __device__ constexpr size_t amp_smem_bytes(int tile) {
-    return table_bytes<R, N, BLOCK>() + align16((size_t)tile * sizeof(PointRec<N>));
+__host__ __device__ constexpr size_t amp2_region_bytes(int tile) {
+    const size_t st = align16((size_t)tile * amp2_row(N) * sizeof(double));
+    return table_bytes<R, N, BLOCK>() > st ? table_bytes<R, N, BLOCK>() : st;
+}
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr size_t xsec_region_bytes(int tile) {
+    const size_t st = align16((size_t)tile * N * 4 * sizeof(double));
+    return table_bytes<R, N, BLOCK>() > st ? table_bytes<R, N, BLOCK>() : st;
+}
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr size_t amp2_smem_bytes(int tile) {
+    return amp2_region_bytes<R, N, BLOCK>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
+}
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr size_t xsec_smem_bytes(int tile) {
+    return xsec_region_bytes<R, N, BLOCK>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
 }
 
-// Load and check one input point; p1 must be massless along +z, p2 along -z.
-template <int N>
-__device__ __forceinline__ void load_point(const double* __restrict__ src, double cpl, PointRec<N>& rec,
-                                           int* __restrict__ flag) {
-    double v[(N + 2) * 4];
-    const double2* s2 = reinterpret_cast<const double2*>(src);
-#pragma unroll
-    for (int a = 0; a < (N + 2) * 2; ++a) {
-        const double2 x = __ldg(s2 + a);
-        v[2 * a] = x.x;
-        v[2 * a + 1] = x.y;
-    }
+// Record of one input row (smem, API layout [n+2][4]); p1 must be massless
+// along +z and p2 along -z, every entry finite.
+template <class R, int N>
+__device__ __forceinline__ void input_to_rec(const double* __restrict__ row, const Physics& ph, PointRec<R, N>& rec,
+                                             int* __restrict__ flag) {
     bool ok = true;
-#pragma unroll
-    for (int a = 0; a < (N + 2) * 4; ++a) ok = ok && isfinite(v[a]);
-    const double E1 = v[0], E2 = v[4];
+#pragma unroll 1
+    for (int a = 0; a < (N + 2) * 4; ++a) ok = ok && isfinite(row[a]);
+    const double E1 = row[0], E2 = row[4];
     const double tol = 1e-12;
     ok = ok && E1 > 0 && E2 > 0;
-    ok = ok && fabs(v[1]) <= tol * E1 && fabs(v[2]) <= tol * E1 && fabs(v[3] - E1) <= tol * E1;
-    ok = ok && fabs(v[5]) <= tol * E2 && fabs(v[6]) <= tol * E2 && fabs(v[7] + E2) <= tol * E2;
-    const double s = 2.0 * (E1 * E2 - v[3] * v[7]);
-    const double irs = ok ? rsqrt(s) : 0.0;
-#pragma unroll
+    ok = ok && fabs(row[1]) <= tol * E1 && fabs(row[2]) <= tol * E1 && fabs(row[3] - E1) <= tol * E1;
+    ok = ok && fabs(row[5]) <= tol * E2 && fabs(row[6]) <= tol * E2 && fabs(row[7] + E2) <= tol * E2;
+    const double s = ok ? 2.0 * (E1 * E2 - row[3] * row[7]) : 1.0;
+    const double is = 1.0 / s;
+    const double irs = sqrt(is);
+    const MomView v{const_cast<double*>(row) + 8, 1};
+#pragma unroll 1
     for (int a = 0; a < N; ++a)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) rec.k[a][m] = v[8 + 4 * a + m] * irs;
-    rec.e1 = E1 * irs;
-    rec.e2 = E2 * irs;
+        for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
+    fill_invariants<R, N>(v, E2, is, false, rec);
+    rec.e2 = R(E2 * irs);
+    rec.n1 = R(sqrt(2.0 * E1 * irs));
+    rec.n2 = R(sqrt(2.0 * E2 * irs));
     double sp = 1;
-    for (int a = 2; a < N; ++a) sp /= s;
-    rec.fac = cpl * sp;
+    for (int a = 2; a < N; ++a) sp *= is;
+    rec.fac = ph.cpl * sp;
     rec.wfac = 0;
     rec.valid = ok;
     rec.mask = 1;
     rec.tries = 1;
-    rec.pad = 0;
     if (!ok) atomicOr(flag, 1);
 }
 
@@ -65,13 +80,20 @@ __global__ void __launch_bounds__(BLOCK)
 amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __restrict__ mask,
             double* __restrict__ out, int tile, Physics ph, int* __restrict__ flag) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PointRec<N>* recs = reinterpret_cast<PointRec<N>*>(smem + table_bytes<R, N, BLOCK>());
+    double* stage = reinterpret_cast<double*>(smem);
+    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK>(tile));
     const float wh = lane_weight<N>(mask, threadIdx.x & ((1u << N) - 1));
-    const double cpl = coupling_pow(ph, N);
+    constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
-        for (int t = threadIdx.x; t < cnt; t += BLOCK)
-            load_point<N>(mom + (size_t)(t0 + t) * (N + 2) * 4, cpl, recs[t], flag);
+        // coalesced copy of the tile's rows into shared memory
+        const double* src = mom + (size_t)t0 * ROW;
+        for (int e = threadIdx.x; e < cnt * ROW; e += BLOCK) {
+            const int t = e / ROW;
+            stage[t * SROW + (e - t * ROW)] = __ldg(src + e);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         __syncthreads();
         amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh, [&](int p, double S) {
             out[t0 + p] = recs[p].valid ? S * recs[p].fac : __longlong_as_double(0x7ff8000000000000ll);
@@ -117,22 +139,24 @@ __global__ void __launch_bounds__(BLOCK)
 xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, int tile,
             Partial* __restrict__ partials, double* __restrict__ w_out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    PointRec<N>* recs = reinterpret_cast<PointRec<N>*>(smem + table_bytes<R, N, BLOCK>());
+    double* stage = reinterpret_cast<double*>(smem);
+    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK>(tile));
     const float wh = lane_weight<N>(nullptr, 0);
     Partial acc = zero_partial();
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
         for (int t = threadIdx.x; t < cnt; t += BLOCK) {
-            Event<N> ev;
-            generate_event<N>(seed, (uint64_t)(i0 + t0 + t), S, ph, ev);
-            event_to_rec<N>(ev, ph, recs[t]);
+            const MomView v{stage + t, tile};
+            EventInfo ev;
+            generate_event<N>(seed, (uint64_t)(i0 + t0 + t), S, ph, v, ev);
+            event_to_rec<R, N>(v, ev, ph, recs[t]);
             acc.npass += recs[t].mask;
             acc.ntotal += 1;
             acc.ntries += recs[t].tries;
         }
         __syncthreads();
         amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh, [&](int p, double Ssum) {
-            const double w = recs[p].valid ? Ssum * recs[p].fac * recs[p].wfac : 0.0;
+            const double w = recs[p].valid ? Ssum * recs[p].wfac : 0.0;
             acc.sw = dd_add_d(acc.sw, w);
             acc.sw2 = dd_add_d(acc.sw2, w * w);
             if (w_out) w_out[t0 + p] = w;
@@ -164,6 +188,6 @@ int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const Sa
                     const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
                     cudaStream_t st);
 // Default launch shape and the maximum resident blocks per SM.
-int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L);
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec);
 
 }  // namespace heget

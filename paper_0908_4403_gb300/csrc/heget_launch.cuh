@@ -13,7 +13,7 @@ template <class R, int N>
 static int launch_amp2_n(const double* mom, long long npts, const uint32_t* mask, double* out, const Physics& ph,
                          int* flag, const AmpLaunch& L, cudaStream_t st) {
     auto k = amp2_kernel<R, N, kBlock>;
-    const size_t smem = amp_smem_bytes<R, N, kBlock>(L.tile);
+    const size_t smem = amp2_smem_bytes<R, N, kBlock>(L.tile);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     k<<<L.grid, kBlock, smem, st>>>(mom, npts, mask, out, L.tile, ph, flag);
@@ -24,7 +24,7 @@ template <class R, int N>
 static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
                          Partial* partials, double* w_out, const AmpLaunch& L, cudaStream_t st) {
     auto k = xsec_kernel<R, N, kBlock>;
-    const size_t smem = amp_smem_bytes<R, N, kBlock>(L.tile);
+    const size_t smem = xsec_smem_bytes<R, N, kBlock>(L.tile);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     k<<<L.grid, kBlock, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out);
@@ -33,7 +33,7 @@ static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const Samp
 
 template <class R, int N>
 static int occupancy_n(int tile, int* blocks_per_sm, size_t* smem_out) {
-    const size_t smem = amp_smem_bytes<R, N, kBlock>(tile);
+    const size_t smem = xsec_smem_bytes<R, N, kBlock>(tile);
     *smem_out = smem;
     auto k = xsec_kernel<R, N, kBlock>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -2,6 +2,11 @@
 // samplers, RAMBO flat massless n-body phase space (Sec. 2.1 eq. (4);
 // Kleiss, Stirling, Ellis, CPC 40 (1986) 359), the photon cuts of Sec. 2.2
 // eqs. (9)-(10), and the per-point record the amplitude kernels consume.
+//
+// GB300 executes FP64 at about 1/64 of the FP32 rate, so this file keeps
+// FP64 for what needs it (RAMBO energies, angles and boosts; the Lorentz
+// invariants behind the propagator denominators; cut decisions) and avoids
+// FP64 transcendentals where an algebraic identity gives the same decision.
 #pragma once
 
 #include "heget_common.cuh"
@@ -11,18 +16,32 @@ namespace heget {
 // Point record staged in shared memory between event generation (or input
 // loading) and the amplitude rounds.  Momenta are divided by sqrt(s-hat) so
 // that the FP32 chain works on O(1) numbers; the mass dimension 4 - 2n of
-// |M|^2 is restored by `fac`.
-template <int N>
+// |M|^2 is restored by `fac`.  The Lorentz invariants stay in FP64; the
+// propagator denominators
+//   t_T = (sum_{i in T} k_i - p2)^2
+//       = sum_{i in T} k_i^2 + sum_{i<j in T} 2 k_i.k_j - sum_{i in T} 2 k_i.p2
+// are summed from them in FP64 and rounded once to R, so an FP32 chain sees
+// denominators with FP64 accuracy.
+template <class R, int N>
 struct alignas(16) PointRec {
-    double k[N][4];   // photon momenta / sqrt(s-hat)
-    double e1, e2;    // energies of p1 (+z) and p2 (-z) / sqrt(s-hat)
-    double fac;       // (4 pi alpha Q^2)^n s-hat^(2-n)
-    double wfac;      // event weight per unit |M|^2 sum (fb), 0 if masked
+    static constexpr int NP = N * (N - 1) / 2;
+    double fac;       // (4 pi alpha Q^2)^n s-hat^(2-n): scaled sum -> |M|^2
+    double wfac;      // scaled sum -> event weight (fb); 0 if masked
+    double sij[NP];   // 2 k_i.k_j / s-hat, i < j, index pair_index<N>(i, j)
+    double m2[N];     // k_i^2 / s-hat
+    double s2[N];     // 2 k_i.p2 / s-hat
+    R k[N][4];        // photon momenta / sqrt(s-hat)
+    R e2;             // energy of p2 / sqrt(s-hat)  (p2 = e2 (1, 0, 0, -1))
+    R n1, n2;         // sqrt(2 e1), sqrt(2 e2): spinor normalisations
     int valid;        // 0: amplitude not evaluated (bad input / sampler failure)
     int mask;         // passes the cuts
     int tries;        // outer sampler attempts
-    int pad;
 };
+
+template <int N>
+__host__ __device__ constexpr int pair_index(int i, int j) {  // i < j
+    return i * N - i * (i + 1) / 2 + (j - i - 1);
+}
 
 // Flat massless n-body volume constant: Phi_n(s) = c_n s^(n-2) with
 // c_n = (2 pi)^(4-3n) (pi/2)^(n-1) / ((n-1)! (n-2)!).
@@ -51,11 +70,14 @@ __device__ __forceinline__ double toy_pdf_x(const PointRng& rng, uint32_t& blk, 
     return -1.0;
 }
 
-// sqrt(s-hat), boost rapidity y and outer attempts for point i.
-__device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointRng& rng,
-                                              double& rs, double& y, int& tries, int& ok) {
+// sqrt(s-hat), the boost factor e^y = sqrt(x1/x2) of the partonic frame and
+// the outer attempts for point i.  y itself (a logarithm) is left to callers
+// that output it.
+__device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointRng& rng, double& rs, double& ey,
+                                              double& x1, double& x2, int& tries, int& ok) {
     ok = 1;
-    y = 0.0;
+    ey = 1.0;
+    x1 = x2 = 1.0;
     tries = 1;
     if (S.kind == HEGET_SAMPLER_FIXED) {
         rs = S.sqrt_s;
@@ -69,13 +91,15 @@ __device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointR
     }
     uint32_t blk = 0;
     for (int t = 1; t <= S.max_tries; ++t) {
-        const double x1 = toy_pdf_x(rng, blk, S.max_tries);
-        const double x2 = x1 < 0 ? -1.0 : toy_pdf_x(rng, blk, S.max_tries);
-        if (x1 < 0 || x2 < 0) break;
-        const double r = 2.0 * S.e_beam * sqrt(x1 * x2);
+        const double a = toy_pdf_x(rng, blk, S.max_tries);
+        const double b = a < 0 ? -1.0 : toy_pdf_x(rng, blk, S.max_tries);
+        if (a < 0 || b < 0) break;
+        const double r = 2.0 * S.e_beam * sqrt(a * b);
         if (r > S.floor) {
             rs = r;
-            y = 0.5 * log(x1 / x2);
+            x1 = a;
+            x2 = b;
+            ey = sqrt(a / b);
             tries = t;
             return;
         }
@@ -85,11 +109,20 @@ __device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointR
     tries = S.max_tries;
 }
 
+// Photon momenta of one point held in shared memory: component (a, m) at
+// p[(4 a + m) * stride].  stride = points of the tile (point-minor layout, so
+// consecutive threads touch consecutive words), or 1 for an AoS row.
+struct MomView {
+    double* p;
+    int stride;
+    __device__ __forceinline__ double& operator()(int a, int m) const { return p[(4 * a + m) * stride]; }
+};
+
 // RAMBO: n massless momenta with total (rs, 0, 0, 0).  Photon i uses draws
 // 4i..4i+3 of the RAMBO stream: cos(theta) = 2 r0 - 1, phi = 2 pi r1,
 // q0 = -ln(r2 r3); the isotropic q_i are boosted and scaled onto the total.
 template <int N>
-__device__ __forceinline__ void rambo(const PointRng& rng, double rs, double (&p)[N][4]) {
+__device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomView& v) {
     double Q0 = 0, Q1 = 0, Q2 = 0, Q3 = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -101,14 +134,15 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, double (&p
         double sp, cp;
         sincospi(2.0 * r1, &sp, &cp);
         const double q0 = -log(r2 * r3);
-        p[i][0] = q0;
-        p[i][1] = q0 * s * cp;
-        p[i][2] = q0 * s * sp;
-        p[i][3] = q0 * c;
-        Q0 += p[i][0];
-        Q1 += p[i][1];
-        Q2 += p[i][2];
-        Q3 += p[i][3];
+        const double q1 = q0 * s * cp, q2 = q0 * s * sp, q3 = q0 * c;
+        v(i, 0) = q0;
+        v(i, 1) = q1;
+        v(i, 2) = q2;
+        v(i, 3) = q3;
+        Q0 += q0;
+        Q1 += q1;
+        Q2 += q2;
+        Q3 += q3;
     }
     const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
     const double iM = 1.0 / M;
@@ -116,69 +150,90 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, double (&p
     const double g = Q0 * iM;
     const double a = 1.0 / (1.0 + g);
     const double x = rs * iM;
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < N; ++i) {
-        const double bq = b1 * p[i][1] + b2 * p[i][2] + b3 * p[i][3];
-        const double q0 = p[i][0];
-        p[i][0] = x * (g * q0 + bq);
-        p[i][1] = x * (p[i][1] + b1 * q0 + a * bq * b1);
-        p[i][2] = x * (p[i][2] + b2 * q0 + a * bq * b2);
-        p[i][3] = x * (p[i][3] + b3 * q0 + a * bq * b3);
+        const double q0 = v(i, 0), q1 = v(i, 1), q2 = v(i, 2), q3 = v(i, 3);
+        const double bq = b1 * q1 + b2 * q2 + b3 * q3;
+        v(i, 0) = x * (g * q0 + bq);
+        v(i, 1) = x * (q1 + b1 * q0 + a * bq * b1);
+        v(i, 2) = x * (q2 + b2 * q0 + a * bq * b2);
+        v(i, 3) = x * (q3 + b3 * q0 + a * bq * b3);
     }
 }
 
-// Photon cuts, strict: pT > pt_min, |eta + y| < eta_max with
+// v < a * w, decided on squares (w >= 0): no square root.
+__device__ __forceinline__ bool lt_scaled(double v, double a, double w2) {
+    // v < a w  with w = sqrt(w2)
+    if (a >= 0) return v < 0 || v * v < a * a * w2;
+    return v < 0 && v * v > a * a * w2;
+}
+
+// Photon cuts, strict (Sec. 2.2): pT > pt_min, |eta + y| < eta_max with
 // eta = asinh(pz / pT), and Delta R = sqrt(Delta eta^2 + Delta phi^2) > dr_min
-// for every pair (Delta phi folded into [0, pi]); dr_min <= 0 disables it.
+// for every pair (Delta phi in [0, pi]); dr_min <= 0 disables Delta R.
+// Evaluated without per-photon transcendentals:
+//   eta + y in (-E, E)  <=>  pz / pT in (sinh(-E - y), sinh(E - y)),
+//     sinh(E -+ y) = sinh E cosh y -+ cosh E sinh y with e^y = sqrt(x1/x2);
+//   sinh(eta_i - eta_j) = (pz_i |p_j| - pz_j |p_i|) / (pT_i pT_j),
+//   cos(phi_i - phi_j)  = (px_i px_j + py_i py_j) / (pT_i pT_j);
+// a pair passes at once if |Delta eta| > R or Delta phi > R, and only the
+// remaining close pairs evaluate asinh and atan2.
 template <int N>
-__device__ __forceinline__ int pass_cuts(const double (&p)[N][4], double y, const Physics& ph) {
-    double eta[N], phi[N];
-#pragma unroll
+__device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Physics& ph) {
+    const double iey = 1.0 / ey;
+    const double shy = 0.5 * (ey - iey), chy = 0.5 * (ey + iey);
+    const double s_hi = ph.sinh_eta * chy - ph.cosh_eta * shy;    // sinh(E - y)
+    const double s_lo = -ph.sinh_eta * chy - ph.cosh_eta * shy;   // sinh(-E - y)
+    const double pt2min = ph.pt_min * ph.pt_min;
+#pragma unroll 1
     for (int i = 0; i < N; ++i) {
-        const double pt = sqrt(p[i][1] * p[i][1] + p[i][2] * p[i][2]);
-        if (!(pt > ph.pt_min)) return 0;
-        eta[i] = asinh(p[i][3] / pt) + y;
-        if (!(fabs(eta[i]) < ph.eta_max)) return 0;
-        phi[i] = atan2(p[i][2], p[i][1]);
+        const double pz = p(i, 3);
+        const double pt2 = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
+        if (!(pt2 > pt2min)) return 0;
+        // s_lo pT < pz < s_hi pT
+        if (!lt_scaled(pz, s_hi, pt2)) return 0;
+        if (!lt_scaled(-pz, -s_lo, pt2)) return 0;
     }
     if (ph.dr_min > 0) {
-        const double pi = 3.141592653589793238462643;
+        double pt[N], pa[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double pt2 = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
+            pt[i] = sqrt(pt2);
+            pa[i] = sqrt(pt2 + p(i, 3) * p(i, 3));
+        }
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
             for (int j = i + 1; j < N; ++j) {
-                double dphi = fabs(phi[i] - phi[j]);
-                if (dphi > pi) dphi = 2.0 * pi - dphi;
-                const double deta = eta[i] - eta[j];
-                if (!(sqrt(deta * deta + dphi * dphi) > ph.dr_min)) return 0;
+                const double xi = p(i, 1), yi = p(i, 2), zi = p(i, 3);
+                const double xj = p(j, 1), yj = p(j, 2), zj = p(j, 3);
+                const double ptt = pt[i] * pt[j];
+                const double sh = zi * pa[j] - zj * pa[i];   // sinh(d eta) pT_i pT_j
+                if (fabs(sh) > ph.sinh_dr * ptt) continue;
+                const double dot = xi * xj + yi * yj;   // cos(d phi) pT_i pT_j
+                if (dot < ph.cos_dr * ptt) continue;
+                const double deta = asinh(sh / ptt);
+                const double dphi = atan2(fabs(xi * yj - yi * xj), dot);
+                if (!(deta * deta + dphi * dphi > ph.dr_min * ph.dr_min)) return 0;
             }
     }
     return 1;
 }
 
-// (4 pi alpha Q^2)^n
-__device__ __forceinline__ double coupling_pow(const Physics& ph, int n) {
-    const double g2 = 4.0 * 3.141592653589793238462643 * ph.alpha * ph.q * ph.q;
-    double r = 1;
-    for (int i = 0; i < n; ++i) r *= g2;
-    return r;
-}
-
-// One generated event in GeV.
-template <int N>
-struct Event {
-    double p[N][4];
-    double rs, y;
+// Scalars of one generated event; its photon momenta (GeV) live in a MomView.
+struct EventInfo {
+    double rs, ey, x1, x2;
     int tries, ok, mask;
 };
 
 template <int N>
-__device__ __forceinline__ void generate_event(uint64_t seed, uint64_t i, const SamplerArgs& S,
-                                               const Physics& ph, Event<N>& ev) {
+__device__ __forceinline__ void generate_event(uint64_t seed, uint64_t i, const SamplerArgs& S, const Physics& ph,
+                                               const MomView& v, EventInfo& ev) {
     const PointRng rng(seed, i);
-    sample_sqrt_s(S, rng, ev.rs, ev.y, ev.tries, ev.ok);
-    rambo<N>(rng, ev.rs, ev.p);
-    ev.mask = ev.ok ? pass_cuts<N>(ev.p, ev.y, ph) : 0;
+    sample_sqrt_s(S, rng, ev.rs, ev.ey, ev.x1, ev.x2, ev.tries, ev.ok);
+    rambo<N>(rng, ev.rs, v);
+    ev.mask = ev.ok ? pass_cuts<N>(v, ev.ey, ph) : 0;
 }
 
 // Flat phase-space weight Phi_n(s) of eq. (4).
@@ -189,45 +244,45 @@ __device__ __forceinline__ double phase_space_weight(double s) {
     return phase_space_const(N) * sn2;
 }
 
-// Event -> point record.  Event weight per unit sum_h |M_h|^2 (Sec. 2.1
-// eq. (2)): (1/2s)(1/4)(1/9) 3 (1/n!) Phi_n(s), GeV^-2 -> fb.
-template <int N>
-__device__ __forceinline__ void event_to_rec(const Event<N>& ev, const Physics& ph, PointRec<N>& rec) {
-    const double s = ev.rs * ev.rs;
+// Invariants of the record from FP64 photon momenta (GeV) and the scale
+// 1/s-hat; p2 = E2 (1, 0, 0, -1).
+template <class R, int N>
+__device__ __forceinline__ void fill_invariants(const MomView& p, double E2, double is, bool massless,
+                                                PointRec<R, N>& rec) {
+#pragma unroll 1
+    for (int i = 0; i < N; ++i) {
+        const double e = p(i, 0), x = p(i, 1), y = p(i, 2), z = p(i, 3);
+        rec.m2[i] = massless ? 0.0 : (e * e - x * x - y * y - z * z) * is;
+        rec.s2[i] = 2.0 * E2 * (e + z) * is;
+#pragma unroll 1
+        for (int j = i + 1; j < N; ++j)
+            rec.sij[pair_index<N>(i, j)] = 2.0 * (e * p(j, 0) - x * p(j, 1) - y * p(j, 2) - z * p(j, 3)) * is;
+    }
+}
+
+// Event -> point record.  Weight per unit of the scaled |M|^2 sum (Sec. 2.1
+// eq. (2)): (1/2s)(1/4)(1/9) 3 (1/n!) Phi_n(s) fac = wconst / s, with
+// wconst = (4 pi alpha Q^2)^n c_n / (24 n!) GeV^-2 -> fb from the host.
+template <class R, int N>
+__device__ __forceinline__ void event_to_rec(const MomView& v, const EventInfo& ev, const Physics& ph,
+                                             PointRec<R, N>& rec) {
     const double irs = 1.0 / ev.rs;
-#pragma unroll
+    const double is = irs * irs;
+#pragma unroll 1
     for (int a = 0; a < N; ++a)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) rec.k[a][m] = ev.p[a][m] * irs;
-    rec.e1 = 0.5;
-    rec.e2 = 0.5;
+        for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
+    fill_invariants<R, N>(v, 0.5 * ev.rs, is, true, rec);
+    rec.e2 = R(0.5);
+    rec.n1 = R(1);
+    rec.n2 = R(1);
     double sp = 1;  // s^(2-n)
-    for (int a = 2; a < N; ++a) sp /= s;
-    rec.fac = coupling_pow(ph, N) * sp;
-    double nfact = 1;
-    for (int a = 2; a <= N; ++a) nfact *= a;
-    rec.wfac = ev.mask ? (1.0 / (2.0 * s)) * (1.0 / 12.0) / nfact * phase_space_weight<N>(s) * 0.3893793721e12
-                       : 0.0;
+    for (int a = 2; a < N; ++a) sp *= is;
+    rec.fac = ph.cpl * sp;
+    rec.wfac = ev.mask ? ph.wconst * is : 0.0;   // w = wfac * (scaled |M|^2 sum)
     rec.valid = ev.ok;
     rec.mask = ev.mask;
     rec.tries = ev.tries;
-    rec.pad = 0;
-}
-
-// GeV momenta of an event in the API layout [n+2][4]: p1, p2, k1..kn.
-template <int N>
-__device__ __forceinline__ void store_event_momenta(const Event<N>& ev, double* __restrict__ dst) {
-    double2* o = reinterpret_cast<double2*>(dst);
-    const double h = 0.5 * ev.rs;
-    o[0] = make_double2(h, 0.0);
-    o[1] = make_double2(0.0, h);
-    o[2] = make_double2(h, 0.0);
-    o[3] = make_double2(0.0, -h);
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-        o[4 + 2 * a] = make_double2(ev.p[a][0], ev.p[a][1]);
-        o[5 + 2 * a] = make_double2(ev.p[a][2], ev.p[a][3]);
-    }
 }
 
 }  // namespace heget

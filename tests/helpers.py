@@ -54,6 +54,47 @@ def helicity_index(s1, s2, lams):
     return h
 
 
+def propagator_condition(mom):
+    """s-hat / min_T |t_T| over all proper photon subsets T, t_T = (p1 - K_T)^2.
+
+    Input momenta conserve momentum only to FP64 rounding (~1e-16 sqrt(s));
+    two exact-arithmetic-equivalent forms of a denominator, (p1 - K_T)^2 and
+    (K_{T^c} - p2)^2, then differ by ~1e-16 s-hat, i.e. relatively by
+    ~1e-16 s-hat/|t_T|.  This is the factor by which input rounding reaches
+    |M|^2 through the propagators."""
+    mom = np.asarray(mom, dtype=np.float64)
+    n = mom.shape[-2] - 2
+    p1, p2, ks = mom[..., 0, :], mom[..., 1, :], mom[..., 2:, :]
+    s = mdot(p1 + p2, p1 + p2)
+    tmin = np.full(s.shape, np.inf)
+    for T in range(1, (1 << n) - 1):
+        sel = [i for i in range(n) if T >> i & 1]
+        q = p1 - ks[..., sel, :].sum(axis=-2)
+        tmin = np.minimum(tmin, np.abs(mdot(q, q)))
+    return s / tmin
+
+
+def momentum_violation(mom):
+    """max(u_64, |sum k - p1 - p2|_inf / sqrt(s-hat)): how well the input
+    conserves momentum (RAMBO's boost amplifies rounding at small n)."""
+    mom = np.asarray(mom, dtype=np.float64)
+    p1, p2, ks = mom[..., 0, :], mom[..., 1, :], mom[..., 2:, :]
+    rs = np.sqrt(np.abs(mdot(p1 + p2, p1 + p2)))
+    d = np.max(np.abs(ks.sum(axis=-2) - p1 - p2), axis=-1) / rs
+    return np.maximum(2.22e-16, d)
+
+
+def fp64_tolerance(mom, floor=2e-12):
+    """Per-point relative tolerance of an FP64 |M|^2 against the oracle:
+    a floor for rounding-order differences over the ordering and helicity
+    sums, plus 16 n times the momentum-conservation violation of the input
+    times the propagator condition number (the two sides evaluate equivalent
+    but differently rounded forms of each denominator)."""
+    mom = np.asarray(mom, dtype=np.float64)
+    n = mom.shape[-2] - 2
+    return floor + 16 * n * momentum_violation(mom) * propagator_condition(mom)
+
+
 def mask_words(n, hels):
     """uint32 word array with the bits of the helicities in `hels` set."""
     words = np.zeros(max(1, (1 << (n + 2)) // 32), dtype=np.uint32)

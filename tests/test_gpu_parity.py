@@ -1,16 +1,18 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances: FP64 chain <= 1e-11 relative per point (rounding-order
-differences over up to n! * 2^(n+2) terms); FP32 chain median <= 1e-4 and
-max <= 1e-3 relative; phase space to FP64 rounding; integer outputs (cut
-mask, sampler attempts) bit-exact.
+Tolerances: FP64 chain within helpers.fp64_tolerance per point (a 2e-12
+floor for rounding-order differences over up to n! 2^(n+2) terms, plus input
+rounding amplified by the smallest propagator denominator); FP32 chain median
+<= 1e-4 and max <= 1e-3 relative; phase-space momenta within 1e-12 sqrt(s)
+(FP64 rounding amplified by the RAMBO boost); integer outputs (cut mask,
+sampler attempts) bit-exact.
 """
 import math
 
 import numpy as np
 import pytest
 
-from helpers import helicity_index, mask_words, mdot
+from helpers import fp64_tolerance, helicity_index, mask_words, mdot
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +76,7 @@ def test_phase_space_matches_oracle(oracle, heget_lib, gpu, n, kind):
     np.testing.assert_allclose(rs.cpu().numpy(), ref["sqrt_s"], rtol=1e-15)
     np.testing.assert_allclose(y.cpu().numpy(), ref["y"], rtol=0, atol=1e-14)
     scale = ref["sqrt_s"][:, None, None]
-    np.testing.assert_allclose(mom.cpu().numpy() / scale, ref["momenta"] / scale, rtol=0, atol=2e-14)
+    np.testing.assert_allclose(mom.cpu().numpy() / scale, ref["momenta"] / scale, rtol=0, atol=1e-12)
     np.testing.assert_allclose(w.cpu().numpy(), ref["weight"], rtol=1e-13)
     np.testing.assert_array_equal(mask.cpu().numpy(), ref["mask"])
 
@@ -87,7 +89,7 @@ def test_phase_space_fixed_entry_point(oracle, heget_lib, gpu):
     heget_lib.heget_phase_space(gpu, SEED, N, n, 500.0, mom, w)
     torch.cuda.synchronize()
     ref = oracle.phase_space(n, SEED, 0, N, oracle.fixed(500.0))
-    np.testing.assert_allclose(mom.cpu().numpy() / 500.0, ref["momenta"] / 500.0, rtol=0, atol=2e-14)
+    np.testing.assert_allclose(mom.cpu().numpy() / 500.0, ref["momenta"] / 500.0, rtol=0, atol=1e-12)
     np.testing.assert_allclose(w.cpu().numpy(), ref["weight"], rtol=1e-13)
 
 
@@ -107,7 +109,7 @@ def test_amp2_fp64_matches_oracle(oracle, heget_lib, gpu, n):
     mom = oracle_points(oracle, n, N_BY_N[n], SEED + 10 + n)
     ref = oracle.amp2(n, mom)
     got = gpu_amp2(heget_lib, gpu, n, mom, heget_lib.HEGET_FP64)
-    assert np.max(rel(got, ref)) < 1e-11
+    assert np.all(rel(got, ref) < fp64_tolerance(mom))
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7])
@@ -126,7 +128,7 @@ def test_amp2_n8_full_sum(oracle, heget_lib, gpu):
     ref = oracle.amp2(n, mom)
     got64 = gpu_amp2(heget_lib, gpu, n, mom, heget_lib.HEGET_FP64)
     got32 = gpu_amp2(heget_lib, gpu, n, mom, heget_lib.HEGET_FP32)
-    assert np.max(rel(got64, ref)) < 1e-11
+    assert np.all(rel(got64, ref) < fp64_tolerance(mom))
     assert np.max(rel(got32, ref)) < 1e-3
 
 
@@ -152,7 +154,7 @@ def test_amp2_mhv_closed_form(oracle, heget_lib, gpu, n):
         pref = (2 * e2 * Q * Q) ** n * s ** (n - 2) / np.prod(s1 * s2, axis=1)
         a, b = (s1, s2) if minority < 0 else (s2, s1)
         ref = pref * np.sum(a ** 3 * b, axis=1)
-        assert np.max(rel(got64, ref)) < 1e-11
+        assert np.all(rel(got64, ref) < fp64_tolerance(mom))
         assert np.max(rel(got32, ref)) < 1e-3
 
 
@@ -166,7 +168,7 @@ def test_amp2_helicity_masks(oracle, heget_lib, gpu, n):
         ref = oracle.amp2(n, mom, hel_mask=mask)
         got = gpu_amp2(heget_lib, gpu, n, mom, heget_lib.HEGET_FP64, mask)
         scale = oracle.amp2(n, mom)
-        assert np.max(np.abs(got - ref) / scale) < 1e-11
+        assert np.all(np.abs(got - ref) / scale < fp64_tolerance(mom))
 
 
 def test_amp2_rejects_bad_points(oracle, heget_lib, gpu):
@@ -178,7 +180,7 @@ def test_amp2_rejects_bad_points(oracle, heget_lib, gpu):
     assert np.isnan(got[5]) and np.isnan(got[17])
     good = np.ones(40, dtype=bool)
     good[[5, 17]] = False
-    np.testing.assert_allclose(got[good], oracle.amp2(n, mom[good]), rtol=1e-11)
+    assert np.all(rel(got[good], oracle.amp2(n, mom[good])) < fp64_tolerance(mom[good]))
     with pytest.raises(heget_lib.HegetError) as ei:
         heget_lib.heget_check(gpu)
     assert ei.value.status == heget_lib.HEGET_EINVAL
