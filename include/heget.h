@@ -188,6 +188,36 @@ int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
  * The measured denominator of the FMA-pipe roofline.  Synchronizes. */
 int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
 
+/* heget_xsec_async for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a service of this library.  Such callers
+ * include code that runs while a stream is being captured into a CUDA graph
+ * (an allocation cannot be captured), applications whose device memory is
+ * owned by a framework arena or a custom allocator that a library must not
+ * bypass, and latency-critical paths that cannot afford the implicit
+ * synchronisation of cudaMalloc.
+ *
+ * No context is needed and nothing is allocated: no cudaMalloc, no cudaFree,
+ * no allocating library routine.  The per-block partial sums that
+ * heget_xsec_async keeps in the context workspace live here in a static
+ * array of 4096 entries (256 KiB) that every GPU loading the library holds
+ * until the process exits.  The caller passes the inputs and result_dev
+ * (device array of sizeof(heget_xsec_result) bytes) as for
+ * heget_xsec_async; params (host, may be NULL for the defaults) replaces the
+ * context's parameters; `device` selects the GPU.
+ *
+ * Limit: a call needs one partial per block of its launch; if that exceeds
+ * 4096 the call fails with HEGET_EINVAL and a message giving the largest N
+ * for this n (4096 x the tile: 1,048,576 points for n <= 4, 16,384 for n = 8).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array per device and leaves its contents
+ * behind; nothing in it needs clearing, but calls that overlap on the GPU
+ * (concurrent streams) race on it and must not be issued. */
+int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, int64_t N,
+                       const heget_sampler* smp, const heget_params* params,
+                       int precision, heget_xsec_result* result_dev,
+                       void* stream);
+
 /* Compensated sums of x[0..N-1] (the accumulator of heget_xsec, exposed):
  * out_dev[0] = sum x, out_dev[1] = sum x^2, each rounded once from a
  * double-double accumulation in a fixed order.  out_dev: 2 doubles. */

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "heget_kernels.cuh"
@@ -201,8 +202,7 @@ struct heget_ctx {
 // Launch constants for n photons: couplings (4 pi alpha Q^2)^n, the event
 // weight constant (1/2)(1/2^2)(1/3^2) 3 (1/n!) c_n (4 pi alpha Q^2)^n in fb
 // (Sec. 2.1 eq. (2); Phi_n = c_n s^(n-2)), and the cut constants.
-static Physics physics_of(const heget_ctx* c, int n) {
-    const heget_params& p = c->params;
+static Physics physics_of(const heget_params& p, int n) {
     Physics ph{};
     ph.alpha = p.alpha;
     ph.q = p.q_charge;
@@ -221,6 +221,8 @@ static Physics physics_of(const heget_ctx* c, int n) {
     ph.cos_dr = p.dr_min > 0 ? std::cos(p.dr_min) : 1.0;
     return ph;
 }
+
+static Physics physics_of(const heget_ctx* c, int n) { return physics_of(c->params, n); }
 
 namespace {
 struct DeviceGuard {
@@ -515,3 +517,80 @@ int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev, void*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// heget_xsec_noalloc: the cross section without any device allocation.
+//
+// Its only scratch -- the per-block partial sums that heget_xsec_async keeps
+// in the context workspace -- lives in the file-scope array below, which
+// every GPU that loads this library holds until the process exits.  Host
+// code cannot hand the array's name to a kernel (in host code it names a
+// host-side stand-in), so the first call on each device looks up the device
+// address with cudaGetSymbolAddress while that device is current and caches
+// it.  Each call's blocks overwrite exactly the entries its own finalize
+// reads, so nothing has to be cleared between calls.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocMaxBlocks = 4096;   // 4096 partials x 64 B = 256 KiB per device
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) Partial g_noalloc_partials[kNoAllocMaxBlocks];
+
+std::mutex g_noalloc_mu;
+Partial* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+int noalloc_scratch(int device, Partial** out) {
+    if (device < 0 || device >= kNoAllocMaxDevices) return fail(HEGET_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);   // caller made `device` current
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_ptr[device] = static_cast<Partial*>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return HEGET_OK;
+}
+}  // namespace
+
+extern "C" int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, int64_t N,
+                                  const heget_sampler* smp, const heget_params* params, int precision,
+                                  heget_xsec_result* result_dev, void* stream) {
+    if (n < kMinN || n > kMaxN) return fail(HEGET_EINVAL, "n = %d outside [2, 8]", n);
+    if (N < 0 || i0 < 0) return fail(HEGET_EINVAL, "N and i0 must be >= 0");
+    int r = check_precision(precision);
+    if (r) return r;
+    if ((r = check_sampler(smp))) return r;
+    if (!result_dev) return fail(HEGET_EINVAL, "result_dev is NULL");
+    heget_params p = params ? *params : heget_params{1.0 / 137.035999, 2.0 / 3.0, 20.0, 2.5, 0.4};
+    if (!(p.alpha > 0) || !(p.eta_max > 0) || !(p.pt_min >= 0)) return fail(HEGET_EINVAL, "bad params");
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(HEGET_EINVAL, "device %d not present", device);
+    DeviceGuard g(device);
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    AmpLaunch L;
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true)))
+        return cuda_fail((cudaError_t)r, "occupancy");
+    if (N > 0 && L.grid > kNoAllocMaxBlocks)
+        return fail(HEGET_EINVAL,
+                    "N = %lld needs %d block partials; the no-allocation path holds %d (N <= %lld at n = %d)",
+                    (long long)N, L.grid, kNoAllocMaxBlocks, (long long)kNoAllocMaxBlocks * L.tile, n);
+    Partial* scratch = nullptr;
+    if ((r = noalloc_scratch(device, &scratch))) return r;
+    const Physics ph = physics_of(p, n);
+    const SamplerArgs S = sampler_args(smp);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N > 0) {
+        r = precision == HEGET_FP32 ? launch_xsec_f32(n, seed, i0, N, S, ph, scratch, nullptr, L, st)
+                                    : launch_xsec_f64(n, seed, i0, N, S, ph, scratch, nullptr, L, st);
+        if (r) return cuda_fail((cudaError_t)r, "xsec_kernel");
+    }
+    finalize_kernel<<<1, 256, 0, st>>>(scratch, N > 0 ? L.grid : 0, S.kind, 0, result_dev, nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "finalize_kernel");
+    return HEGET_OK;
+}

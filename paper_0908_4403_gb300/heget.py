@@ -79,6 +79,8 @@ SIGNATURES = {
     "heget_xsec_launch": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), I32, P, P]),
     "heget_xsec_finalize": (I32, [P, P, P]),
     "heget_measure_fma_peak": (I32, [P, I32, C.POINTER(C.c_double)]),
+    "heget_xsec_noalloc": (I32, [I32, I32, U64, I64, I64, C.POINTER(heget_sampler), C.POINTER(heget_params),
+                                 I32, P, P]),
     "heget_sum": (I32, [P, P, I64, P, P]),
 }
 
@@ -193,6 +195,13 @@ def heget_measure_fma_peak(ctx, precision=HEGET_FP32) -> float:
     v = C.c_double()
     _check(load().heget_measure_fma_peak(ctx, precision, C.byref(v)))
     return v.value
+
+
+def heget_xsec_noalloc(device, n, seed, i0, N, sampler, precision, result_dev, params=None, stream=None):
+    """heget_xsec_async for callers that cannot allocate device memory (no context needed)."""
+    pp = C.byref(params) if params is not None else None
+    _check(load().heget_xsec_noalloc(device, n, seed, i0, N, C.byref(sampler), pp, precision, _ptr(result_dev),
+                                     _stream(stream)))
 
 
 def heget_sum(ctx, x, N, out_dev, stream=None):
