@@ -182,6 +182,15 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0,
 int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
                         void* stream);
 
+/* Launch shape (this library's knob; the paper's analogue is the register /
+ * block-size scan of Sec. 6.1): points per block tile used by heget_amp2
+ * (kind 0) or heget_xsec* (kind 1) for n photons at `precision`.  tile = 0
+ * restores the default; otherwise tile must be a positive multiple of
+ * 256 / 2^n and at most 4096.  A tile whose shared memory exceeds the device
+ * limit makes the next launch fail with HEGET_ECUDA. */
+int heget_set_tile(heget_ctx* ctx, int n, int precision, int kind, int tile);
+int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind);
+
 /* Device FMA throughput: runs independent FMA chains (8 per thread) in
  * every thread of a grid that fills the GPU and reports the achieved rate in
  * TFLOP/s (2 flops per FMA) in *tflops.  precision: HEGET_FP32 or HEGET_FP64.
@@ -207,7 +216,9 @@ int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
  *
  * Limit: a call needs one partial per block of its launch; if that exceeds
  * 4096 the call fails with HEGET_EINVAL and a message giving the largest N
- * for this n (4096 x the tile: 1,048,576 points for n <= 4, 16,384 for n = 8).
+ * for this n and precision.  FP32 at n <= 4 launches one resident wave of
+ * blocks and has no limit; otherwise N may be at most 4096 x the xsec tile
+ * (for example 131,072 points at n = 6 and 16,384 at n = 8 in FP32).
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the one array per device and leaves its contents

@@ -66,6 +66,18 @@ __device__ __forceinline__ Row<R> row_times(const Row<R>& r, const Row<R>& m0, c
     return o;
 }
 
+// Barrier of the threads that run the amplitude rounds: the whole block
+// (BAR = 0, __syncthreads) or, in a warp-specialised block, the BLOCK
+// consumer threads on named barrier BAR.
+template <int BAR, int BLOCK>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (BAR == 0) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(BLOCK) : "memory");
+    }
+}
+
 template <class R> __device__ __forceinline__ R recip(R x);
 template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
@@ -108,7 +120,7 @@ struct RoundTables {
 // Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Two phases
 // separated by barriers; all threads of the block must call it.  Everything
 // here runs in R: the FP64 content (invariants) is already in the records.
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, int BAR = 0>
 __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, const PointRec<R, N>* recs,
                                             int cnt) {
     using RT = RoundTables<R, N, BLOCK>;
@@ -144,7 +156,6 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
             if (p >= cnt || T == 0 || T == NS - 1) continue;
             const PointRec<R, N>& rc = recs[p];
             R q0 = -rc.e2, q1 = R(0), q2 = R(0), q3 = rc.e2;
-            double t = 0.0;   // FP64 sum of FP64 invariants, rounded once
 #pragma unroll
             for (int i = 0; i < N; ++i)
                 if (T >> i & 1) {
@@ -152,12 +163,8 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
                     q1 += rc.k[i][1];
                     q2 += rc.k[i][2];
                     q3 += rc.k[i][3];
-                    t += rc.m2[i] - rc.s2[i];
-#pragma unroll
-                    for (int j = i + 1; j < N; ++j)
-                        if (T >> j & 1) t += rc.sij[pair_index<N>(i, j)];
                 }
-            const R it_ = recip<R>(R(t));
+            const R it_ = recip<R>(rc.t[T]);   // t_T from FP64, rounded once
             Row<R> d;
             d.ar = (q0 + q3) * it_;
             d.ai = (q0 - q3) * it_;
@@ -166,7 +173,7 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
             tb.SD[p * NS + T] = d;
         }
     }
-    __syncthreads();
+    group_sync<BAR, BLOCK>();
     // (b) step matrices M(j, T) = E_j^lambda Qbar_T, closures and first rows
     const R rs2 = R(0.70710678118654752440);
     for (int it = tid; it < P * K * 2; it += BLOCK) {
@@ -209,7 +216,7 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
             st_row(tb.R1 + oc, Row<R>{n2 * m1.ar, n2 * m1.ai, n2 * m1.br, n2 * m1.bi});
         }
     }
-    __syncthreads();
+    group_sync<BAR, BLOCK>();
 }
 
 // Per-lane view of the round tables.
@@ -280,7 +287,7 @@ __device__ __forceinline__ float lane_weight(const uint32_t* mask, unsigned h) {
 // Amplitude rounds over recs[0 .. cnt-1].  For each point the lane group's
 // reduction yields S = sum_h w_h |A_h|^2 (scaled units); emit(p, S) is called
 // by exactly one thread per point (the group's first thread).
-template <class R, int N, int BLOCK, class Emit>
+template <class R, int N, int BLOCK, int BAR = 0, class Emit>
 __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, const PointRec<R, N>* recs, int cnt,
                                                  float wh, Emit emit) {
     using RT = RoundTables<R, N, BLOCK>;
@@ -292,7 +299,7 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, cons
     LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * slot, (unsigned)(tid & (NS - 1))};
     for (int base = 0; base < cnt; base += P) {
         const int rc = min(P, cnt - base);
-        setup_round<R, N, BLOCK>(tb, recs + base, rc);
+        setup_round<R, N, BLOCK, BAR>(tb, recs + base, rc);
         R are = R(0), aim = R(0);
         const bool active = slot < rc && recs[base + slot].valid;
         if (active) tree_amplitude<R, N, BLOCK>(L, are, aim);
@@ -304,14 +311,14 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, cons
             if ((tid & (NS - 1)) == 0 && slot < rc) emit(base + slot, (double)v);
         } else {
             if ((tid & 31) == 0) tb.RED[tid >> 5] = (double)v;
-            __syncthreads();
+            group_sync<BAR, BLOCK>();
             if ((tid & (NS - 1)) == 0 && slot < rc) {
                 double s = 0;
                 for (int w = 0; w < NS / 32; ++w) s += tb.RED[(tid >> 5) + w];
                 emit(base + slot, s);
             }
         }
-        __syncthreads();
+        group_sync<BAR, BLOCK>();
     }
 }
 

@@ -35,14 +35,14 @@ int cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // Momenta are generated into shared memory (point-minor) and written out
 // cooperatively, so the [N][n+2][4] stores are coalesced.
-constexpr int kPsBlock = 128;
+constexpr int kPsBlock = 64;
 
 template <int N>
 __global__ void __launch_bounds__(kPsBlock)
 phase_space_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, double* __restrict__ mom,
                    double* __restrict__ w, double* __restrict__ rs_out, double* __restrict__ y_out,
                    uint8_t* __restrict__ mask_out, int32_t* __restrict__ tries_out) {
-    __shared__ double stage[N * 4 * kPsBlock];
+    __shared__ double stage[N * kMomSlots * kPsBlock];
     __shared__ double rs_s[kPsBlock];
     constexpr int ROW = (N + 2) * 4;
     for (long long j0 = (long long)blockIdx.x * kPsBlock; j0 < npts; j0 += (long long)gridDim.x * kPsBlock) {
@@ -50,7 +50,7 @@ phase_space_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, P
         const int t = threadIdx.x;
         if (t < cnt) {
             const long long j = j0 + t;
-            const MomView v{stage + t, kPsBlock};
+            const MomView v{stage + t, kPsBlock, kMomSlots};
             EventInfo ev;
             generate_event<N>(seed, (uint64_t)(i0 + j), S, ph, v, ev);
             rs_s[t] = ev.rs;
@@ -67,7 +67,7 @@ phase_space_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, P
                 const int p = e / ROW, c = e - p * ROW, a = c >> 2, m = c & 3;
                 double val;
                 if (a >= 2) {
-                    val = stage[(4 * (a - 2) + m) * kPsBlock + p];
+                    val = stage[(kMomSlots * (a - 2) + m) * kPsBlock + p];
                 } else {   // p1 = (rs/2)(1,0,0,1), p2 = (rs/2)(1,0,0,-1)
                     const double h = 0.5 * rs_s[p];
                     val = m == 0 ? h : (m == 3 ? (a == 0 ? h : -h) : 0.0);
@@ -154,17 +154,36 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int iters, double* __rest
 // ---------------------------------------------------------------------------
 // launch shapes
 // ---------------------------------------------------------------------------
-int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec) {
-    L->block = kBlockThreads;
+int default_tile(int n, bool xsec) {
     // Points per block tile.  amp2: four rounds of block/2^n points (keeps the
-    // staged rows and records small); xsec: one point per thread in the
-    // generation phase while that stays cheap against the tree (n <= 4), then
-    // small tiles so that large-n grids still cover every SM many times.
+    // staged rows and records small); xsec: 128 points (half the threads
+    // generate, three blocks fit an SM) up to n = 4, then small tiles so that
+    // large-n grids still cover every SM many times.
     static const int amp2_tile[9] = {0, 0, 256, 128, 64, 32, 16, 8, 4};
-    static const int xsec_tile[9] = {0, 0, 256, 256, 256, 64, 32, 8, 4};
-    L->tile = xsec ? xsec_tile[n] : amp2_tile[n];
+    static const int xsec_tile[9] = {0, 0, 128, 128, 128, 64, 32, 8, 4};
+    return xsec ? xsec_tile[n] : amp2_tile[n];
+}
+
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile) {
+    L->ws = use_ws(n, precision, xsec);
     int bpsm = 1;
     size_t smem = 0;
+    if (L->ws) {
+        // warp-specialised: fixed stage size, one resident wave of blocks that
+        // each pipeline many stages
+        L->block = kWsThreads;
+        L->tile = kWsStage;
+        const int e = occupancy_ws_f32(n, &bpsm, &smem);
+        if (e) return e;
+        if (bpsm < 1) bpsm = 1;
+        L->smem = smem;
+        const long long tiles = (npts + L->tile - 1) / L->tile;
+        const long long wave = (long long)num_sms * bpsm;
+        L->grid = (int)(tiles < wave ? (tiles < 1 ? 1 : tiles) : wave);
+        return 0;
+    }
+    L->block = kBlockThreads;
+    L->tile = tile > 0 ? tile : default_tile(n, xsec);
     const int e = precision == HEGET_FP32 ? occupancy_f32(n, L->tile, &bpsm, &smem)
                                           : occupancy_f64(n, L->tile, &bpsm, &smem);
     if (e) return e;
@@ -176,7 +195,6 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     L->grid = (int)grid;
-    (void)num_sms;
     return 0;
 }
 
@@ -197,6 +215,7 @@ struct heget_ctx {
     heget_xsec_result* res_host = nullptr;  // pinned
     int last_parts = 0;               // block partials of the last heget_xsec_launch
     int last_kind = 0;                // its sampler kind
+    int tiles[2][2][kMaxN + 1] = {};  // [amp2|xsec][fp32|fp64][n] tile overrides (0 = default)
 };
 
 // Launch constants for n photons: couplings (4 pi alpha Q^2)^n, the event
@@ -321,6 +340,25 @@ void heget_destroy(heget_ctx* c) {
     delete c;
 }
 
+int heget_set_tile(heget_ctx* ctx, int n, int precision, int kind, int tile) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (n < kMinN || n > kMaxN) return fail(HEGET_EINVAL, "n = %d outside [2, 8]", n);
+    int r = check_precision(precision);
+    if (r) return r;
+    if (kind != 0 && kind != 1) return fail(HEGET_EINVAL, "kind must be 0 (amp2) or 1 (xsec)");
+    const int unit = kBlockThreads >> n;
+    if (tile < 0 || tile > 4096 || (tile > 0 && tile % unit != 0))
+        return fail(HEGET_EINVAL, "tile %d must be 0 or a multiple of %d up to 4096", tile, unit);
+    ctx->tiles[kind][precision == HEGET_FP64][n] = tile;
+    return HEGET_OK;
+}
+
+int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind) {
+    if (!ctx || n < kMinN || n > kMaxN || (kind != 0 && kind != 1)) return -1;
+    const int t = ctx->tiles[kind][precision == HEGET_FP64][n];
+    return t > 0 ? t : default_tile(n, kind == 1);
+}
+
 int heget_set_params(heget_ctx* ctx, const heget_params* p) {
     if (!ctx || !p) return fail(HEGET_EINVAL, "NULL argument");
     if (!(p->alpha > 0) || !std::isfinite(p->alpha) || !std::isfinite(p->q_charge) || p->q_charge == 0)
@@ -383,7 +421,7 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta, const ui
     if (((uintptr_t)momenta & 15) != 0) return fail(HEGET_EINVAL, "momenta must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, false))) return cuda_fail((cudaError_t)r, "occupancy");
+    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, false, ctx->tiles[0][precision == HEGET_FP64][n]))) return cuda_fail((cudaError_t)r, "occupancy");
     const Physics ph = physics_of(ctx, n);
     cudaStream_t st = (cudaStream_t)stream;
     r = precision == HEGET_FP32 ? launch_amp2_f32(n, momenta, N, hel_mask, amp2, ph, ctx->flag, L, st)
@@ -419,7 +457,7 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L, true)))
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L, true, ctx->tiles[1][precision == HEGET_FP64][n])))
         return cuda_fail((cudaError_t)r, "occupancy");
     const Physics ph = physics_of(ctx, n);
     const SamplerArgs S = sampler_args(smp);
@@ -573,7 +611,7 @@ extern "C" int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, 
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true)))
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true, 0)))
         return cuda_fail((cudaError_t)r, "occupancy");
     if (N > 0 && L.grid > kNoAllocMaxBlocks)
         return fail(HEGET_EINVAL,

@@ -25,4 +25,10 @@ int occupancy_f32(int n, int tile, int* bpsm, size_t* smem) {
 #undef CALL
 }
 
+int occupancy_ws_f32(int n, int* bpsm, size_t* smem) {
+#define CALL(N) occupancy_ws_n<N>(bpsm, smem)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
 }  // namespace heget

@@ -28,7 +28,7 @@ __host__ __device__ constexpr size_t amp2_region_bytes(int tile) {
 }
 template <class R, int N, int BLOCK>
 __host__ __device__ constexpr size_t xsec_region_bytes(int tile) {
-    const size_t st = align16((size_t)tile * N * 4 * sizeof(double));
+    const size_t st = align16((size_t)tile * N * kMomSlots * sizeof(double));
     return table_bytes<R, N, BLOCK>() > st ? table_bytes<R, N, BLOCK>() : st;
 }
 template <class R, int N, int BLOCK>
@@ -56,12 +56,12 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
     const double s = ok ? 2.0 * (E1 * E2 - row[3] * row[7]) : 1.0;
     const double is = 1.0 / s;
     const double irs = sqrt(is);
-    const MomView v{const_cast<double*>(row) + 8, 1};
+    const MomView v{const_cast<double*>(row) + 8, 1, 4};
 #pragma unroll 1
     for (int a = 0; a < N; ++a)
 #pragma unroll
         for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
-    fill_invariants<R, N>(v, E2, is, false, rec);
+    fill_denominators<R, N>(v, E2, is, false, rec);
     rec.e2 = R(E2 * irs);
     rec.n1 = R(sqrt(2.0 * E1 * irs));
     rec.n2 = R(sqrt(2.0 * E2 * irs));
@@ -146,7 +146,7 @@ xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
         for (int t = threadIdx.x; t < cnt; t += BLOCK) {
-            const MomView v{stage + t, tile};
+            const MomView v{stage + t, tile, kMomSlots};
             EventInfo ev;
             generate_event<N>(seed, (uint64_t)(i0 + t0 + t), S, ph, v, ev);
             event_to_rec<R, N>(v, ev, ph, recs[t]);
@@ -168,13 +168,119 @@ xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
 }
 
 // ---------------------------------------------------------------------------
+// Warp-specialised fused kernel (FP32 chain, n <= 4).
+//
+// GB300 runs FP64 at ~1/64 of the FP32 rate and with long latency, so at small
+// n the FP64 event generation (RAMBO, cuts, denominators) costs more than the
+// FP32 tree and needs many warps in flight.  Each block therefore splits into
+// roles that run concurrently:
+//   warps 0..7  (256 threads): consumers -- the amplitude rounds of the tree;
+//   warps 8..11 (128 threads): producers -- one event per thread per stage.
+// Producers fill a double-buffered ring of kWsStage point records in shared
+// memory; the two roles hand stages over through named barriers
+//   FULL[s]  (bar.arrive by producers, bar.sync by consumers) and
+//   EMPTY[s] (bar.arrive by consumers, bar.sync by producers),
+// while the consumers' own rounds synchronise on barrier kBarRounds.  Every
+// thread of both roles runs the same number of stages, so each barrier
+// instance collects exactly kWsThreads arrivals.  A block walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the grid is sized to the resident
+// blocks so that each block pipelines many stages.
+// ---------------------------------------------------------------------------
+constexpr int kWsConsumers = 256;
+constexpr int kWsStage = 128;                        // producers = points per stage
+constexpr int kWsThreads = kWsConsumers + kWsStage;
+constexpr int kBarRounds = 1, kBarFull = 2, kBarEmpty = 4;   // named barrier ids (2,3 / 4,5)
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <class R, int N>
+__host__ __device__ constexpr size_t ws_recs_offset() {
+    return table_bytes<R, N, kWsConsumers>();
+}
+template <class R, int N>
+__host__ __device__ constexpr size_t ws_stage_offset() {
+    return ws_recs_offset<R, N>() + 2 * align16((size_t)kWsStage * sizeof(PointRec<R, N>));
+}
+template <class R, int N>
+__host__ __device__ constexpr size_t ws_smem_bytes() {
+    return ws_stage_offset<R, N>() + align16((size_t)kWsStage * N * kMomSlots * sizeof(double));
+}
+
+template <class R, int N>
+__global__ void __launch_bounds__(kWsThreads, 2)
+xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph,
+               Partial* __restrict__ partials, double* __restrict__ w_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N>());
+    constexpr size_t ring_stride = align16((size_t)kWsStage * sizeof(PointRec<R, N>)) / sizeof(PointRec<R, N>);
+    double* stage = reinterpret_cast<double*>(smem + ws_stage_offset<R, N>());
+    const int tid = threadIdx.x;
+    const long long tiles = (npts + kWsStage - 1) / kWsStage;
+    const int count = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    Partial acc = zero_partial();
+    if (tid >= kWsConsumers) {
+        // producers
+        const int g = tid - kWsConsumers;
+        const MomView v{stage + g, kWsStage, kMomSlots};
+        for (int k = 0; k < count; ++k) {
+            const int s = k & 1;
+            if (k >= 2) named_sync(kBarEmpty + s, kWsThreads);
+            const long long t0 = ((long long)blockIdx.x + (long long)k * gridDim.x) * kWsStage;
+            const int cnt = (int)min((long long)kWsStage, npts - t0);
+            if (g < cnt) {
+                PointRec<R, N>& rec = ring[s * ring_stride + g];
+                EventInfo ev;
+                generate_event<N>(seed, (uint64_t)(i0 + t0 + g), S, ph, v, ev);
+                event_to_rec<R, N>(v, ev, ph, rec);
+                acc.npass += rec.mask;
+                acc.ntotal += 1;
+                acc.ntries += rec.tries;
+            }
+            __threadfence_block();
+            named_arrive(kBarFull + s, kWsThreads);
+        }
+    } else {
+        // consumers
+        const float wh = lane_weight<N>(nullptr, 0);
+        for (int k = 0; k < count; ++k) {
+            const int s = k & 1;
+            named_sync(kBarFull + s, kWsThreads);
+            const long long t0 = ((long long)blockIdx.x + (long long)k * gridDim.x) * kWsStage;
+            const int cnt = (int)min((long long)kWsStage, npts - t0);
+            const PointRec<R, N>* recs = ring + s * ring_stride;
+            amplitude_rounds<R, N, kWsConsumers, kBarRounds>(smem, recs, cnt, wh, [&](int p, double Ssum) {
+                const double w = recs[p].valid ? Ssum * recs[p].wfac : 0.0;
+                acc.sw = dd_add_d(acc.sw, w);
+                acc.sw2 = dd_add_d(acc.sw2, w * w);
+                if (w_out) w_out[t0 + p] = w;
+            });
+            if (k + 2 < count) {
+                __threadfence_block();
+                named_arrive(kBarEmpty + s, kWsThreads);
+            }
+        }
+    }
+    __syncthreads();
+    const Partial r = block_reduce_partial<kWsThreads>(acc, reinterpret_cast<Partial*>(smem));
+    if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launch descriptors (defined per precision in heget_f32.cu /
 // heget_f64.cu).
 // ---------------------------------------------------------------------------
 struct AmpLaunch {
     int block, tile, grid;
     size_t smem;
+    bool ws;   // warp-specialised xsec kernel (FP32, n <= 4)
 };
+
+constexpr bool use_ws(int n, int precision, bool xsec) { return xsec && precision == HEGET_FP32 && n <= 4; }
 
 // Returns cudaError_t as int.
 int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
@@ -187,7 +293,9 @@ int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const Sa
 int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
                     const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
                     cudaStream_t st);
+int occupancy_ws_f32(int n, int* bpsm, size_t* smem);
 // Default launch shape and the maximum resident blocks per SM.
-int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec);
+int default_tile(int n, bool xsec);
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile);
 
 }  // namespace heget

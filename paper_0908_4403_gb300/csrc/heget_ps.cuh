@@ -16,20 +16,15 @@ namespace heget {
 // Point record staged in shared memory between event generation (or input
 // loading) and the amplitude rounds.  Momenta are divided by sqrt(s-hat) so
 // that the FP32 chain works on O(1) numbers; the mass dimension 4 - 2n of
-// |M|^2 is restored by `fac`.  The Lorentz invariants stay in FP64; the
-// propagator denominators
-//   t_T = (sum_{i in T} k_i - p2)^2
-//       = sum_{i in T} k_i^2 + sum_{i<j in T} 2 k_i.k_j - sum_{i in T} 2 k_i.p2
-// are summed from them in FP64 and rounded once to R, so an FP32 chain sees
-// denominators with FP64 accuracy.
+// |M|^2 is restored by `fac`.  The propagator denominators
+//   t_T = (sum_{i in T} k_i - p2)^2 / s-hat,   T a proper photon subset,
+// are computed in FP64 when the record is built (see fill_denominators) and
+// rounded once to R, so an FP32 chain sees denominators with FP64 accuracy.
 template <class R, int N>
 struct alignas(16) PointRec {
-    static constexpr int NP = N * (N - 1) / 2;
     double fac;       // (4 pi alpha Q^2)^n s-hat^(2-n): scaled sum -> |M|^2
     double wfac;      // scaled sum -> event weight (fb); 0 if masked
-    double sij[NP];   // 2 k_i.k_j / s-hat, i < j, index pair_index<N>(i, j)
-    double m2[N];     // k_i^2 / s-hat
-    double s2[N];     // 2 k_i.p2 / s-hat
+    R t[1 << N];      // t_T by subset bitmask T (entries 0 and 2^n - 1 unused)
     R k[N][4];        // photon momenta / sqrt(s-hat)
     R e2;             // energy of p2 / sqrt(s-hat)  (p2 = e2 (1, 0, 0, -1))
     R n1, n2;         // sqrt(2 e1), sqrt(2 e2): spinor normalisations
@@ -109,13 +104,19 @@ __device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointR
     tries = S.max_tries;
 }
 
-// Photon momenta of one point held in shared memory: component (a, m) at
-// p[(4 a + m) * stride].  stride = points of the tile (point-minor layout, so
-// consecutive threads touch consecutive words), or 1 for an AoS row.
+// Photon momenta of one point held in shared memory: slot (a, m) at
+// p[(slots a + m) * stride], m = 0..3 the components (E, px, py, pz).
+// Generated points use slots = kMomSlots, whose m = 4, 5 are scratch for pT
+// and |p| of the cuts, with stride = points of the tile (point-minor layout:
+// consecutive threads touch consecutive words); input rows use slots = 4,
+// stride = 1.
+constexpr int kMomSlots = 6;
+
 struct MomView {
     double* p;
     int stride;
-    __device__ __forceinline__ double& operator()(int a, int m) const { return p[(4 * a + m) * stride]; }
+    int slots;
+    __device__ __forceinline__ double& operator()(int a, int m) const { return p[(slots * a + m) * stride]; }
 };
 
 // RAMBO: n massless momenta with total (rs, 0, 0, 0).  Photon i uses draws
@@ -124,7 +125,7 @@ struct MomView {
 template <int N>
 __device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomView& v) {
     double Q0 = 0, Q1 = 0, Q2 = 0, Q3 = 0;
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < N; ++i) {
         double r0, r1, r2, r3;
         rng.pair(kStreamRambo, 2 * i, r0, r1);
@@ -195,21 +196,20 @@ __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Phys
         if (!lt_scaled(-pz, -s_lo, pt2)) return 0;
     }
     if (ph.dr_min > 0) {
-        double pt[N], pa[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
+#pragma unroll 1
+        for (int i = 0; i < N; ++i) {   // pT and |p| into the view's scratch slots
             const double pt2 = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
-            pt[i] = sqrt(pt2);
-            pa[i] = sqrt(pt2 + p(i, 3) * p(i, 3));
+            p(i, 4) = sqrt(pt2);
+            p(i, 5) = sqrt(pt2 + p(i, 3) * p(i, 3));
         }
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < N; ++i)
-#pragma unroll
+#pragma unroll 1
             for (int j = i + 1; j < N; ++j) {
                 const double xi = p(i, 1), yi = p(i, 2), zi = p(i, 3);
                 const double xj = p(j, 1), yj = p(j, 2), zj = p(j, 3);
-                const double ptt = pt[i] * pt[j];
-                const double sh = zi * pa[j] - zj * pa[i];   // sinh(d eta) pT_i pT_j
+                const double ptt = p(i, 4) * p(j, 4);
+                const double sh = zi * p(j, 5) - zj * p(i, 5);   // sinh(d eta) pT_i pT_j
                 if (fabs(sh) > ph.sinh_dr * ptt) continue;
                 const double dot = xi * xj + yi * yj;   // cos(d phi) pT_i pT_j
                 if (dot < ph.cos_dr * ptt) continue;
@@ -244,19 +244,53 @@ __device__ __forceinline__ double phase_space_weight(double s) {
     return phase_space_const(N) * sn2;
 }
 
-// Invariants of the record from FP64 photon momenta (GeV) and the scale
-// 1/s-hat; p2 = E2 (1, 0, 0, -1).
+// Propagator denominators t_T / s-hat of the record, in FP64, from photon
+// momenta in GeV, p2 = E2 (1, 0, 0, -1) and is = 1/s-hat.  For n <= 5 they
+// are sums of the Lorentz invariants
+//   t_T = sum_{i in T} k_i^2 + sum_{i<j in T} 2 k_i.k_j - sum_{i in T} 2 k_i.p2,
+// held in registers and summed in a fully unrolled loop over the sets; for
+// larger n (where the tree dwarfs this) t_T = (sum_{i in T} k_i - p2)^2 by
+// components, set by set.
 template <class R, int N>
-__device__ __forceinline__ void fill_invariants(const MomView& p, double E2, double is, bool massless,
-                                                PointRec<R, N>& rec) {
+__device__ __forceinline__ void fill_denominators(const MomView& p, double E2, double is, bool massless,
+                                                  PointRec<R, N>& rec) {
+    if constexpr (N <= 5) {
+        double d[N], sij[N * (N - 1) / 2 > 0 ? N * (N - 1) / 2 : 1];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double e = p(i, 0), x = p(i, 1), y = p(i, 2), z = p(i, 3);
+            d[i] = (massless ? 0.0 : e * e - x * x - y * y - z * z) - 2.0 * E2 * (e + z);
+#pragma unroll
+            for (int j = i + 1; j < N; ++j)
+                sij[pair_index<N>(i, j)] = 2.0 * (e * p(j, 0) - x * p(j, 1) - y * p(j, 2) - z * p(j, 3));
+        }
+#pragma unroll
+        for (int T = 1; T < (1 << N) - 1; ++T) {
+            double t = 0.0;
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+                if (T >> i & 1) {
+                    t += d[i];
+#pragma unroll
+                    for (int j = i + 1; j < N; ++j)
+                        if (T >> j & 1) t += sij[pair_index<N>(i, j)];
+                }
+            rec.t[T] = R(t * is);
+        }
+    } else {
 #pragma unroll 1
-    for (int i = 0; i < N; ++i) {
-        const double e = p(i, 0), x = p(i, 1), y = p(i, 2), z = p(i, 3);
-        rec.m2[i] = massless ? 0.0 : (e * e - x * x - y * y - z * z) * is;
-        rec.s2[i] = 2.0 * E2 * (e + z) * is;
+        for (int T = 1; T < (1 << N) - 1; ++T) {
+            double q0 = -E2, q1 = 0.0, q2 = 0.0, q3 = E2;
 #pragma unroll 1
-        for (int j = i + 1; j < N; ++j)
-            rec.sij[pair_index<N>(i, j)] = 2.0 * (e * p(j, 0) - x * p(j, 1) - y * p(j, 2) - z * p(j, 3)) * is;
+            for (int i = 0; i < N; ++i)
+                if (T >> i & 1) {
+                    q0 += p(i, 0);
+                    q1 += p(i, 1);
+                    q2 += p(i, 2);
+                    q3 += p(i, 3);
+                }
+            rec.t[T] = R((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) * is);
+        }
     }
 }
 
@@ -272,7 +306,7 @@ __device__ __forceinline__ void event_to_rec(const MomView& v, const EventInfo& 
     for (int a = 0; a < N; ++a)
 #pragma unroll
         for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
-    fill_invariants<R, N>(v, 0.5 * ev.rs, is, true, rec);
+    fill_denominators<R, N>(v, 0.5 * ev.rs, is, true, rec);
     rec.e2 = R(0.5);
     rec.n1 = R(1);
     rec.n2 = R(1);

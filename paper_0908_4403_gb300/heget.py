@@ -79,6 +79,8 @@ SIGNATURES = {
     "heget_xsec_launch": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), I32, P, P]),
     "heget_xsec_finalize": (I32, [P, P, P]),
     "heget_measure_fma_peak": (I32, [P, I32, C.POINTER(C.c_double)]),
+    "heget_set_tile": (I32, [P, I32, I32, I32, I32]),
+    "heget_get_tile": (I32, [P, I32, I32, I32]),
     "heget_xsec_noalloc": (I32, [I32, I32, U64, I64, I64, C.POINTER(heget_sampler), C.POINTER(heget_params),
                                  I32, P, P]),
     "heget_sum": (I32, [P, P, I64, P, P]),
@@ -195,6 +197,14 @@ def heget_measure_fma_peak(ctx, precision=HEGET_FP32) -> float:
     v = C.c_double()
     _check(load().heget_measure_fma_peak(ctx, precision, C.byref(v)))
     return v.value
+
+
+def heget_set_tile(ctx, n, precision, kind, tile):
+    _check(load().heget_set_tile(ctx, n, precision, kind, tile))
+
+
+def heget_get_tile(ctx, n, precision, kind) -> int:
+    return load().heget_get_tile(ctx, n, precision, kind)
 
 
 def heget_xsec_noalloc(device, n, seed, i0, N, sampler, precision, result_dev, params=None, stream=None):
