@@ -98,14 +98,14 @@ struct RoundTables {
     static constexpr size_t bytes = (2 * m_elems + 2 * c_elems) * sizeof(Row<R>)   // M0, M1, CL, R1
                                   + (size_t)P * N * sizeof(Row<R>)                 // photon data
                                   + (size_t)P * NS * sizeof(Row<R>)                // set data
-                                  + (size_t)(BLOCK / 32) * sizeof(double) + 16;    // reduction
+                                  + (size_t)(BLOCK / 32) * sizeof(R) + 16;         // reduction
     Row<R>* M0;
     Row<R>* M1;
     Row<R>* CL;
     Row<R>* R1;
     Row<R>* PH;   // [P][N]: (sin th, cos th, cos ph, sin ph)
     Row<R>* SD;   // [P][2^N]: (A, D, Bre, Bim) = ((q0+q3), (q0-q3), q1, q2) / q^2
-    double* RED;  // [BLOCK/32]
+    R* RED;       // [BLOCK/32]
     __device__ __forceinline__ explicit RoundTables(unsigned char* base) {
         M0 = reinterpret_cast<Row<R>*>(base);
         M1 = M0 + m_elems;
@@ -113,7 +113,7 @@ struct RoundTables {
         R1 = CL + c_elems;
         PH = R1 + c_elems;
         SD = PH + (size_t)P * N;
-        RED = reinterpret_cast<double*>(SD + (size_t)P * NS);
+        RED = reinterpret_cast<R*>(SD + (size_t)P * NS);
     }
 };
 
@@ -285,11 +285,12 @@ __device__ __forceinline__ float lane_weight(const uint32_t* mask, unsigned h) {
 }
 
 // Amplitude rounds over recs[0 .. cnt-1].  For each point the lane group's
-// reduction yields S = sum_h w_h |A_h|^2 (scaled units); emit(p, S) is called
-// by exactly one thread per point (the group's first thread).
-template <class R, int N, int BLOCK, int BAR = 0, class Emit>
-__device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, const PointRec<R, N>* recs, int cnt,
-                                                 float wh, Emit emit) {
+// reduction yields S = sum_h w_h |A_h|^2 (scaled units), stored by the
+// group's first thread in recs[p].ssum; the FP64 normalisation and the
+// accumulation are left to whole warps afterwards (one lane per point), so
+// no FP64 instruction here runs with one or two active lanes.
+template <class R, int N, int BLOCK, int BAR = 0>
+__device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, PointRec<R, N>* recs, int cnt, float wh) {
     using RT = RoundTables<R, N, BLOCK>;
     constexpr int P = RT::P;
     constexpr int NS = 1 << N;
@@ -308,14 +309,14 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, cons
 #pragma unroll
         for (int off = 1; off < G; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if constexpr (NS <= 32) {
-            if ((tid & (NS - 1)) == 0 && slot < rc) emit(base + slot, (double)v);
+            if ((tid & (NS - 1)) == 0 && slot < rc) recs[base + slot].ssum = v;
         } else {
-            if ((tid & 31) == 0) tb.RED[tid >> 5] = (double)v;
+            if ((tid & 31) == 0) tb.RED[tid >> 5] = v;
             group_sync<BAR, BLOCK>();
             if ((tid & (NS - 1)) == 0 && slot < rc) {
-                double s = 0;
+                R s = R(0);
                 for (int w = 0; w < NS / 32; ++w) s += tb.RED[(tid >> 5) + w];
-                emit(base + slot, s);
+                recs[base + slot].ssum = s;
             }
         }
         group_sync<BAR, BLOCK>();

@@ -95,9 +95,11 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         __syncthreads();
-        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh, [&](int p, double S) {
-            out[t0 + p] = recs[p].valid ? S * recs[p].fac : __longlong_as_double(0x7ff8000000000000ll);
-        });
+        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh);
+        // one thread per point: FP64 normalisation and a coalesced store
+        for (int t = threadIdx.x; t < cnt; t += BLOCK)
+            out[t0 + t] = recs[t].valid ? (double)recs[t].ssum * recs[t].fac
+                                        : __longlong_as_double(0x7ff8000000000000ll);
     }
 }
 
@@ -155,12 +157,15 @@ xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
             acc.ntries += recs[t].tries;
         }
         __syncthreads();
-        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh, [&](int p, double Ssum) {
-            const double w = recs[p].valid ? Ssum * recs[p].wfac : 0.0;
+        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh);
+        // one thread per point (the thread that generated it): weight and
+        // double-double accumulation with every lane active
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) {
+            const double w = recs[t].valid ? (double)recs[t].ssum * recs[t].wfac : 0.0;
             acc.sw = dd_add_d(acc.sw, w);
             acc.sw2 = dd_add_d(acc.sw2, w * w);
-            if (w_out) w_out[t0 + p] = w;
-        });
+            if (w_out) w_out[t0 + t] = w;
+        }
     }
     // the round tables are free now: reuse them as reduction scratch
     const Partial r = block_reduce_partial<BLOCK>(acc, reinterpret_cast<Partial*>(smem));
@@ -223,14 +228,30 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
     const long long tiles = (npts + kWsStage - 1) / kWsStage;
     const int count = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
     Partial acc = zero_partial();
+    auto stage_t0 = [&](int k) { return ((long long)blockIdx.x + (long long)k * gridDim.x) * kWsStage; };
+    // the producer owning slot g of stage k folds that point's weight into its
+    // accumulator once the consumers have released the stage
+    auto harvest = [&](int k, int g) {
+        const long long t0 = stage_t0(k);
+        if (g < (int)min((long long)kWsStage, npts - t0)) {
+            const PointRec<R, N>& rec = ring[(k & 1) * ring_stride + g];
+            const double w = rec.valid ? (double)rec.ssum * rec.wfac : 0.0;
+            acc.sw = dd_add_d(acc.sw, w);
+            acc.sw2 = dd_add_d(acc.sw2, w * w);
+            if (w_out) w_out[t0 + g] = w;
+        }
+    };
     if (tid >= kWsConsumers) {
         // producers
         const int g = tid - kWsConsumers;
         const MomView v{stage + g, kWsStage, kMomSlots};
         for (int k = 0; k < count; ++k) {
             const int s = k & 1;
-            if (k >= 2) named_sync(kBarEmpty + s, kWsThreads);
-            const long long t0 = ((long long)blockIdx.x + (long long)k * gridDim.x) * kWsStage;
+            if (k >= 2) {
+                named_sync(kBarEmpty + s, kWsThreads);
+                harvest(k - 2, g);
+            }
+            const long long t0 = stage_t0(k);
             const int cnt = (int)min((long long)kWsStage, npts - t0);
             if (g < cnt) {
                 PointRec<R, N>& rec = ring[s * ring_stride + g];
@@ -250,21 +271,18 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
         for (int k = 0; k < count; ++k) {
             const int s = k & 1;
             named_sync(kBarFull + s, kWsThreads);
-            const long long t0 = ((long long)blockIdx.x + (long long)k * gridDim.x) * kWsStage;
-            const int cnt = (int)min((long long)kWsStage, npts - t0);
-            const PointRec<R, N>* recs = ring + s * ring_stride;
-            amplitude_rounds<R, N, kWsConsumers, kBarRounds>(smem, recs, cnt, wh, [&](int p, double Ssum) {
-                const double w = recs[p].valid ? Ssum * recs[p].wfac : 0.0;
-                acc.sw = dd_add_d(acc.sw, w);
-                acc.sw2 = dd_add_d(acc.sw2, w * w);
-                if (w_out) w_out[t0 + p] = w;
-            });
+            const int cnt = (int)min((long long)kWsStage, npts - stage_t0(k));
+            amplitude_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, wh);
             if (k + 2 < count) {
                 __threadfence_block();
                 named_arrive(kBarEmpty + s, kWsThreads);
             }
         }
     }
+    __syncthreads();
+    // the last (up to) two stages were never reclaimed: harvest them now
+    if (tid >= kWsConsumers)
+        for (int k = count - 2 < 0 ? 0 : count - 2; k < count; ++k) harvest(k, tid - kWsConsumers);
     __syncthreads();
     const Partial r = block_reduce_partial<kWsThreads>(acc, reinterpret_cast<Partial*>(smem));
     if (threadIdx.x == 0) partials[blockIdx.x] = r;

@@ -28,6 +28,7 @@ struct alignas(16) PointRec {
     R k[N][4];        // photon momenta / sqrt(s-hat)
     R e2;             // energy of p2 / sqrt(s-hat)  (p2 = e2 (1, 0, 0, -1))
     R n1, n2;         // sqrt(2 e1), sqrt(2 e2): spinor normalisations
+    R ssum;           // result of the tree: sum_h w_h |A_h|^2 in scaled units
     int valid;        // 0: amplitude not evaluated (bad input / sampler failure)
     int mask;         // passes the cuts
     int tries;        // outer sampler attempts
@@ -51,16 +52,44 @@ __host__ __device__ inline double phase_space_const(int n) {
     return c / (f1 * f2);
 }
 
+// FP32 estimate of the uniform u01_from_words(lo, hi) from its top 24 bits:
+// |result - u| <= 2^-24.
+__device__ __forceinline__ float u01_estimate(uint32_t hi) {
+    return (__uint2float_rn(hi >> 8) + 0.5f) * 0x1p-24f;
+}
+
 // Toy-PDF momentum fraction: proposal x = u^2 (density ~ x^-1/2), accepted
-// with probability (1-x)^3; one Philox block per try.  Returns -1 when the
-// bound is hit.
+// if v < (1-x)^3 (both uniforms from one Philox block per try).  Returns -1
+// when the bound is hit.
+//
+// The acceptance test is the FP64 comparison v < (1 - u^2)^3, with the
+// products and the difference rounded separately.  Most tries are settled
+// first in FP32 from the same random bits: with |u_f - u|, |v_f - v| <= 2^-24,
+// the FP32 value t_f of t = (1-u^2)^3 satisfies |t_f - t| <= 5.1 2^-24 (the
+// input error through 3(1-u^2)^2 (2u + u^2 + 1/2) <= 3.1, plus two roundings
+// of the cube), so |v_f - t_f| > 2^-20 = 16 2^-24 decides the comparison the
+// same way; the FP64 test runs only inside that band (about 2e-6 of the
+// tries).
 __device__ __forceinline__ double toy_pdf_x(const PointRng& rng, uint32_t& blk, int max_tries) {
     for (int t = 0; t < max_tries; ++t) {
-        double u, v;
-        rng.pair(kStreamSqrtS, blk++, u, v);
-        const double x = u * u;
-        const double om = 1.0 - x;
-        if (v < om * om * om) return x;
+        const U4 w = philox4x32_10(U4{rng.ilo, rng.ihi, blk++, kStreamSqrtS}, rng.k0, rng.k1);
+        const float uf = u01_estimate(w.y), vf = u01_estimate(w.w);
+        const float of = 1.0f - uf * uf;
+        const float tf = of * of * of;
+        bool accept;
+        if (vf < tf - 0x1p-20f) {
+            accept = true;
+        } else if (vf > tf + 0x1p-20f) {
+            accept = false;
+        } else {
+            const double u = u01_from_words(w.x, w.y), v = u01_from_words(w.z, w.w);
+            const double om = __dsub_rn(1.0, __dmul_rn(u, u));
+            accept = v < __dmul_rn(__dmul_rn(om, om), om);
+        }
+        if (accept) {
+            const double u = u01_from_words(w.x, w.y);
+            return __dmul_rn(u, u);
+        }
     }
     return -1.0;
 }
