@@ -170,6 +170,33 @@ int heget_xsec(heget_ctx* ctx, int n, int64_t N, uint64_t seed,
                const heget_sampler* smp, int precision,
                heget_xsec_result* out, void* stream);
 
+/* One request of a mixed-n batch (heget_xsec_batch): points i0 .. i0+N-1 of
+ * stream `seed` for n photons at `precision` with sampler `sampler`;
+ * result_dev (device, sizeof(heget_xsec_result) bytes) receives the result,
+ * w_out (device, optional) the N per-event weights. */
+typedef struct {
+    int n;
+    int precision;
+    uint64_t seed;
+    int64_t i0;
+    int64_t N;
+    heget_sampler sampler;
+    heget_xsec_result* result_dev;
+    double* w_out;
+} heget_xsec_request;
+
+/* Many cross sections in one fused launch per precision (batching of the
+ * serving path; the paper runs one process per kernel call, Sec. 3.1).
+ * Every request is cut into the same point tiles heget_xsec uses on the
+ * plain (non-warp-specialised) path; the tiles of all requests, whatever
+ * their n and N, form one work list that a single kernel walks, and each
+ * request's tile partials are combined in tile order, so a request's result
+ * does not depend on what else is in the batch.  reqs: host array of `count`
+ * requests.  Grows the context workspace on demand, and synchronizes
+ * `stream` before returning. */
+int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, int count,
+                     void* stream);
+
 /* heget_xsec_async in two halves: heget_xsec_launch enqueues only the fused
  * event kernel, leaving its block partials in the context workspace;
  * heget_xsec_finalize enqueues the fixed-order combination of the partials of
@@ -190,6 +217,99 @@ int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
  * limit makes the next launch fail with HEGET_ECUDA. */
 int heget_set_tile(heget_ctx* ctx, int n, int precision, int kind, int tile);
 int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind);
+
+/* Autotuner (this library's; the paper scans registers x block size by hand,
+ * Sec. 6.1 / Fig. 3): times heget_amp2 (kind 0) or heget_xsec (kind 1) for
+ * n photons at `precision` on `probe_points` synthetic points for every
+ * candidate tile (the default shape -- warp-specialised where it applies --
+ * and 256/2^n x 2^k up to 1024), keeps the fastest in the context and returns
+ * it (*best_tile, 0 = default) with its time (*best_ms).  Allocates and frees
+ * temporary probe buffers; synchronizes.  heget_autotune_save /
+ * heget_autotune_load store and restore the context's tuned tiles in a text
+ * file keyed by GPU name (other GPUs' lines are kept). */
+int heget_autotune(heget_ctx* ctx, int n, int precision, int kind,
+                   int64_t probe_points, int* best_tile, double* best_ms);
+int heget_autotune_save(const heget_ctx* ctx, const char* path);
+int heget_autotune_load(heget_ctx* ctx, const char* path);
+
+/* CUDA graph of one cross-section step: heget_xsec_launch +
+ * heget_xsec_finalize for n, N, sampler and precision as given, captured
+ * once; heget_graph_launch replays it for a new (seed, i0) by updating the
+ * captured event kernel's arguments.  result_dev receives each replay's
+ * result.  A graph uses its context's workspace: replays of graphs of one
+ * context must be ordered on one stream. */
+typedef struct heget_graph heget_graph;
+int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp,
+                     int precision, heget_xsec_result* result_dev,
+                     heget_graph** out);
+int heget_graph_launch(heget_graph* g, uint64_t seed, int64_t i0, void* stream);
+void heget_graph_destroy(heget_graph* g);
+
+/* Request server (continuous batching).  The paper has no counterpart: it
+ * runs one cross section per process (Sec. 3.1); this is a service of this
+ * library for many concurrent cross-section requests of mixed n.
+ *
+ * heget_server_start starts a worker thread that owns one stream on ctx's
+ * device.  Submitted requests wait in arrival order until fewer than
+ * max_inflight are admitted and the device arena (arena_bytes, default
+ * min(256 MiB, free HBM x (1 - hbm_reserve_frac))) has room for their tile
+ * partials (64 bytes per tile of heget_xsec's tile size, plus the result).  Each launch of the mixed-n batch kernel takes tiles round-robin
+ * from every admitted request until about max_launch_work FP32-flop
+ * equivalents are filled, so requests arriving while others run share the
+ * next launch with them; up to two launches are in flight.  A request's
+ * result is bitwise the heget_xsec_batch result of the same request, whatever
+ * else shared its launches.  Zero fields of cfg (or cfg = NULL) take the
+ * defaults: max_inflight 256, max_launch_work 2e11, hbm_reserve_frac 0.1.
+ * ctx must outlive the server and must not change its parameters or tiles
+ * while requests are in flight. */
+typedef struct heget_server heget_server;
+typedef struct {
+    int max_inflight;        /* admitted requests at once (>= 1) */
+    double max_launch_work;  /* FP32-flop equivalents per launch */
+    double hbm_reserve_frac; /* share of free HBM the arena leaves alone */
+    uint64_t arena_bytes;    /* device arena size; 0 = default */
+} heget_server_cfg;
+
+/* One request: points i0 .. i0+N-1 (N >= 1) of stream `seed`, n photons at
+ * `precision` with `sampler`, as for heget_xsec_async. */
+typedef struct {
+    int n;
+    int precision;
+    uint64_t seed;
+    int64_t i0;
+    int64_t N;
+    heget_sampler sampler;
+} heget_request;
+
+/* A finished request: status HEGET_OK with `result`, HEGET_ECUDA if a launch
+ * failed (the server then stops taking work), HEGET_EBUSY if the server
+ * stopped before the request was admitted.  Times are seconds on a
+ * monotonic host clock: submission, admission, result available on host. */
+typedef struct {
+    heget_xsec_result result;
+    double t_submit, t_admit, t_done;
+    int status;
+    int reserved;
+} heget_result;
+
+int heget_server_start(heget_ctx* ctx, const heget_server_cfg* cfg,
+                       heget_server** out);
+/* Queues a request (host struct, copied) and returns its ticket.  Fails with
+ * HEGET_EINVAL on a bad request, HEGET_ENOMEM if it could never fit in the
+ * arena, HEGET_EBUSY once the server is stopping.  Thread-safe. */
+int heget_submit(heget_server* s, const heget_request* q, uint64_t* ticket);
+/* HEGET_OK and *out if the request is finished (the ticket is then
+ * released), HEGET_EBUSY if not yet, HEGET_ENOTFOUND for an unknown or
+ * already released ticket.  Never blocks. */
+int heget_poll(heget_server* s, uint64_t ticket, heget_result* out);
+/* As heget_poll, but waits up to timeout_s seconds; HEGET_ETIMEOUT if the
+ * request is still running then (the ticket stays valid). */
+int heget_wait(heget_server* s, uint64_t ticket, double timeout_s,
+               heget_result* out);
+/* Cancels requests not yet admitted (they finish with HEGET_EBUSY), lets
+ * admitted ones run to completion, joins the worker and frees everything;
+ * unclaimed results are dropped.  Returns HEGET_ECUDA if a launch failed. */
+int heget_server_stop(heget_server* s);
 
 /* Device FMA throughput: runs independent FMA chains (8 per thread) in
  * every thread of a grid that fills the GPU and reports the achieved rate in

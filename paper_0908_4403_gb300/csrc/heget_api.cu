@@ -3,8 +3,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "heget_kernels.cuh"
 #include "heget_internal.h"
@@ -27,6 +29,10 @@ int fail(int code, const char* fmt, ...) {
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
+    // The status reports this error; take it out of the runtime's per-thread
+    // record so that it does not surface again in the caller's next error
+    // check (a sticky error stays sticky regardless).
+    cudaGetLastError();
     return fail(HEGET_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -96,13 +102,12 @@ __global__ void __launch_bounds__(256) sum_kernel(const double* __restrict__ x, 
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
 }
 
-// Combines nparts block partials in index order.  mode 0: write the
-// heget_xsec_result (toy-PDF scale when kind == TOY_PDF); mode 1: write
-// (sum, sum of squares) to sums.
-__global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict__ partials, int nparts, int kind,
-                                                       int mode, heget_xsec_result* __restrict__ res,
-                                                       double* __restrict__ sums) {
-    __shared__ Partial scratch[8];
+// Combines nparts block partials in index order (called by one whole block).
+// mode 0: write the heget_xsec_result (toy-PDF scale when kind == TOY_PDF);
+// mode 1: write (sum, sum of squares) to sums.
+__device__ __forceinline__ void finalize_block(const Partial* __restrict__ partials, int nparts, int kind, int mode,
+                                               heget_xsec_result* __restrict__ res, double* __restrict__ sums,
+                                               Partial* scratch) {
     Partial a = zero_partial();
     for (int b = threadIdx.x; b < nparts; b += 256) a = partial_add(a, partials[b]);
     const Partial r = block_reduce_partial<256>(a, scratch);
@@ -130,6 +135,26 @@ __global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict
     o.n_tries = r.ntries;
     o.n_escalated = r.nesc;
     *res = o;
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(const Partial* __restrict__ partials, int nparts, int kind,
+                                                       int mode, heget_xsec_result* __restrict__ res,
+                                                       double* __restrict__ sums) {
+    __shared__ Partial scratch[8];
+    finalize_block(partials, nparts, kind, mode, res, sums, scratch);
+}
+
+// One block per batch request: its tile partials, in order, into its result.
+__global__ void __launch_bounds__(256) finalize_batch_kernel(const BatchReq* __restrict__ reqs) {
+    __shared__ Partial scratch[8];
+    const BatchReq& r = reqs[blockIdx.x];
+    finalize_block(r.parts, r.ntiles, r.S.kind, 0, r.result, nullptr, scratch);
+}
+
+int launch_batch_finalize(const BatchReq* reqs, int nreqs, cudaStream_t st) {
+    if (nreqs <= 0) return 0;
+    finalize_batch_kernel<<<nreqs, 256, 0, st>>>(reqs);
+    return (int)cudaGetLastError();
 }
 
 // FMA-throughput probe: kPeakChains independent chains per thread, so the
@@ -165,7 +190,7 @@ int default_tile(int n, bool xsec) {
 }
 
 int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile) {
-    L->ws = use_ws(n, precision, xsec);
+    L->ws = use_ws(n, precision, xsec) && tile <= 0;   // an explicit tile selects the plain kernel
     int bpsm = 1;
     size_t smem = 0;
     if (L->ws) {
@@ -202,26 +227,12 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
 
 using namespace heget;
 
-// ---------------------------------------------------------------------------
-// context
-// ---------------------------------------------------------------------------
-struct heget_ctx {
-    int device = 0;
-    int num_sms = 0;
-    heget_params params{};
-    Partial* partials = nullptr;      // kMaxGrid block partials
-    int* flag = nullptr;              // device input-check flag
-    heget_xsec_result* res_dev = nullptr;
-    heget_xsec_result* res_host = nullptr;  // pinned
-    int last_parts = 0;               // block partials of the last heget_xsec_launch
-    int last_kind = 0;                // its sampler kind
-    int tiles[2][2][kMaxN + 1] = {};  // [amp2|xsec][fp32|fp64][n] tile overrides (0 = default)
-};
+namespace heget {
 
 // Launch constants for n photons: couplings (4 pi alpha Q^2)^n, the event
 // weight constant (1/2)(1/2^2)(1/3^2) 3 (1/n!) c_n (4 pi alpha Q^2)^n in fb
 // (Sec. 2.1 eq. (2); Phi_n = c_n s^(n-2)), and the cut constants.
-static Physics physics_of(const heget_params& p, int n) {
+Physics physics_of(const heget_params& p, int n) {
     Physics ph{};
     ph.alpha = p.alpha;
     ph.q = p.q_charge;
@@ -241,19 +252,7 @@ static Physics physics_of(const heget_params& p, int n) {
     return ph;
 }
 
-static Physics physics_of(const heget_ctx* c, int n) { return physics_of(c->params, n); }
-
-namespace {
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
+Physics physics_of(const heget_ctx* c, int n) { return physics_of(c->params, n); }
 
 int check_sampler(const heget_sampler* s) {
     if (!s) return fail(HEGET_EINVAL, "sampler is NULL");
@@ -298,7 +297,7 @@ int check_precision(int p) {
     if (p != HEGET_FP32 && p != HEGET_FP64) return fail(HEGET_EINVAL, "precision must be 32 or 64, got %d", p);
     return HEGET_OK;
 }
-}  // namespace
+}  // namespace heget
 
 extern "C" {
 
@@ -333,6 +332,10 @@ int heget_create(int device, heget_ctx** out) {
 void heget_destroy(heget_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
+    if (c->batch_copied) cudaEventSynchronize(c->batch_copied), cudaEventDestroy(c->batch_copied);
+    if (c->batch_host) cudaFreeHost(c->batch_host);
+    if (c->batch_dev) cudaFree(c->batch_dev);
+    if (c->batch_partials) cudaFree(c->batch_partials);
     if (c->partials) cudaFree(c->partials);
     if (c->flag) cudaFree(c->flag);
     if (c->res_dev) cudaFree(c->res_dev);
@@ -468,6 +471,7 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
     }
     ctx->last_parts = N > 0 ? L.grid : 0;
     ctx->last_kind = S.kind;
+    ctx->last_ws = L.ws;
     return HEGET_OK;
 }
 
@@ -555,6 +559,123 @@ int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev, void*
 }
 
 }  // extern "C"
+
+namespace {
+template <class R>
+size_t batch_tile_smem(int n, int tile) {
+    switch (n) {
+        case 2: return xsec_smem_bytes<R, 2, kBatchThreads>(tile);
+        case 3: return xsec_smem_bytes<R, 3, kBatchThreads>(tile);
+        case 4: return xsec_smem_bytes<R, 4, kBatchThreads>(tile);
+        case 5: return xsec_smem_bytes<R, 5, kBatchThreads>(tile);
+        case 6: return xsec_smem_bytes<R, 6, kBatchThreads>(tile);
+        case 7: return xsec_smem_bytes<R, 7, kBatchThreads>(tile);
+        default: return xsec_smem_bytes<R, 8, kBatchThreads>(tile);
+    }
+}
+
+// Grows a workspace buffer to at least `need` bytes (device or pinned host).
+int grow(void** p, size_t* cap, size_t need, bool pinned) {
+    if (*cap >= need) return HEGET_OK;
+    size_t c = *cap ? *cap : 4096;
+    while (c < need) c *= 2;
+    void* q = nullptr;
+    cudaError_t e = pinned ? cudaMallocHost(&q, c) : cudaMalloc(&q, c);
+    if (e != cudaSuccess) return fail(HEGET_ENOMEM, "workspace growth to %zu bytes failed: %s", c, cudaGetErrorString(e));
+    if (*p) pinned ? cudaFreeHost(*p) : cudaFree(*p);
+    *p = q;
+    *cap = c;
+    return HEGET_OK;
+}
+}  // namespace
+
+extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, int count, void* stream) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (count < 0 || (count > 0 && !reqs)) return fail(HEGET_EINVAL, "bad request array");
+    for (int i = 0; i < count; ++i) {
+        const heget_xsec_request& q = reqs[i];
+        int r = check_common(ctx, q.n, q.N);
+        if (!r) r = check_precision(q.precision);
+        if (!r) r = check_sampler(&q.sampler);
+        if (r) return fail(r, "request %d: %s", i, heget_last_error());
+        if (q.i0 < 0 || !q.result_dev) return fail(HEGET_EINVAL, "request %d: i0 < 0 or result_dev NULL", i);
+    }
+    if (count == 0) return HEGET_OK;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (!ctx->batch_copied) {
+        e = cudaEventCreateWithFlags(&ctx->batch_copied, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+    for (int prec : {HEGET_FP32, HEGET_FP64}) {
+        std::vector<BatchReq> br;
+        std::vector<WorkItem> items;
+        size_t smem = 0;
+        for (int i = 0; i < count; ++i) {
+            const heget_xsec_request& q = reqs[i];
+            if (q.precision != prec) continue;
+            const int tile_o = ctx->tiles[1][prec == HEGET_FP64][q.n];
+            const int tile = tile_o > 0 ? tile_o : default_tile(q.n, true);
+            BatchReq b{};
+            b.seed = q.seed;
+            b.i0 = q.i0;
+            b.S = sampler_args(&q.sampler);
+            b.ph = physics_of(ctx, q.n);
+            b.w_out = q.w_out;
+            b.result = q.result_dev;
+            b.n = q.n;
+            b.tile = tile;
+            b.parts = nullptr;   // set once the partial buffer is sized
+            b.pad = (int)items.size();   // first item, until then
+            for (long long start = 0; start < q.N; start += tile)
+                items.push_back(WorkItem{(int)br.size(), q.n, (int)std::min<long long>(tile, q.N - start), 0, start});
+            b.ntiles = (int)items.size() - b.pad;
+            br.push_back(b);
+            const size_t sm = prec == HEGET_FP32 ? batch_tile_smem<float>(q.n, tile) : batch_tile_smem<double>(q.n, tile);
+            smem = std::max(smem, sm);
+        }
+        if (br.empty()) continue;
+        const size_t items_bytes = align16(items.size() * sizeof(WorkItem));
+        const size_t bytes = items_bytes + br.size() * sizeof(BatchReq);
+        // the previous batch's upload must have left the staging area
+        e = cudaEventSynchronize(ctx->batch_copied);
+        if (e != cudaSuccess) return cuda_fail(e, "batch staging");
+        int r = grow((void**)&ctx->batch_host, &ctx->batch_cap, bytes, true);
+        if (r) return r;
+        const size_t dcap = ctx->batch_cap;   // device buffer mirrors the pinned one
+        if (!ctx->batch_dev || dcap > ctx->batch_dev_cap) {
+            if (ctx->batch_dev) cudaFree(ctx->batch_dev);
+            e = cudaMalloc(&ctx->batch_dev, dcap);
+            if (e != cudaSuccess) return fail(HEGET_ENOMEM, "batch workspace: %s", cudaGetErrorString(e));
+            ctx->batch_dev_cap = dcap;
+        }
+        r = grow((void**)&ctx->batch_partials, &ctx->batch_partials_cap, items.size() * sizeof(Partial), false);
+        if (r) return r;
+        for (auto& b : br) {
+            b.parts = ctx->batch_partials + b.pad;
+            b.pad = 0;
+        }
+        std::memcpy(ctx->batch_host, items.data(), items.size() * sizeof(WorkItem));
+        std::memcpy(ctx->batch_host + items_bytes, br.data(), br.size() * sizeof(BatchReq));
+        e = cudaMemcpyAsync(ctx->batch_dev, ctx->batch_host, bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->batch_copied, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+        const WorkItem* items_d = reinterpret_cast<const WorkItem*>(ctx->batch_dev);
+        const BatchReq* reqs_d = reinterpret_cast<const BatchReq*>(ctx->batch_dev + items_bytes);
+        const int nitems = (int)items.size();
+        const int grid = std::max(1, std::min(nitems, 8 * ctx->num_sms));
+        r = prec == HEGET_FP32 ? launch_batch_f32(items_d, nitems, reqs_d, smem, grid, st)
+                               : launch_batch_f64(items_d, nitems, reqs_d, smem, grid, st);
+        if (r) return cuda_fail((cudaError_t)r, "xsec_batch_kernel");
+        r = launch_batch_finalize(reqs_d, (int)br.size(), st);
+        if (r) return cuda_fail((cudaError_t)r, "finalize_batch_kernel");
+        // the next precision's batch reuses the workspace: keep the order
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "heget_xsec_batch");
+    }
+    return HEGET_OK;
+}
 
 // ---------------------------------------------------------------------------
 // heget_xsec_noalloc: the cross section without any device allocation.

@@ -31,4 +31,9 @@ int occupancy_ws_f32(int n, int* bpsm, size_t* smem) {
 #undef CALL
 }
 
+int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+                     cudaStream_t st) {
+    return launch_batch_t<float>(items, nitems, reqs, smem, grid, st);
+}
+
 }  // namespace heget

@@ -25,4 +25,9 @@ int occupancy_f64(int n, int tile, int* bpsm, size_t* smem) {
 #undef CALL
 }
 
+int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+                     cudaStream_t st) {
+    return launch_batch_t<double>(items, nitems, reqs, smem, grid, st);
+}
+
 }  // namespace heget

@@ -1,10 +1,14 @@
-// heget_internal.h -- host-side constants and error helpers shared by the
-// C-ABI translation units.
+// heget_internal.h -- host-side state and helpers shared by the C-ABI
+// translation units (the context, argument checks, launch constants).
+// Include after heget_kernels.cuh.
 #pragma once
 
 #include <cstdarg>
 
 #include <cuda_runtime.h>
+
+#include "heget.h"
+#include "heget_common.cuh"
 
 namespace heget {
 
@@ -15,4 +19,47 @@ constexpr int kMaxGrid = 65536;      // block partials held by a context
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Makes `dev` current for the scope and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace heget
+
+// The library context (opaque in the C ABI).
+struct heget_ctx {
+    int device = 0;
+    int num_sms = 0;
+    heget_params params{};
+    heget::Partial* partials = nullptr;      // kMaxGrid block partials
+    int* flag = nullptr;              // device input-check flag
+    heget_xsec_result* res_dev = nullptr;
+    heget_xsec_result* res_host = nullptr;  // pinned
+    int last_parts = 0;               // block partials of the last heget_xsec_launch
+    int last_kind = 0;                // its sampler kind
+    bool last_ws = false;             // it used the warp-specialised kernel
+    int tiles[2][2][heget::kMaxN + 1] = {};  // [amp2|xsec][fp32|fp64][n] tile overrides (0 = default)
+    // mixed-n batch workspace (grown on demand)
+    unsigned char* batch_host = nullptr;   // pinned staging of work items + request table
+    unsigned char* batch_dev = nullptr;
+    size_t batch_cap = 0, batch_dev_cap = 0;
+    heget::Partial* batch_partials = nullptr;
+    size_t batch_partials_cap = 0;
+    cudaEvent_t batch_copied = nullptr;    // staging may be rewritten once this has fired
+};
+
+namespace heget {
+Physics physics_of(const heget_params& p, int n);
+Physics physics_of(const heget_ctx* c, int n);
+int check_sampler(const heget_sampler* s);
+SamplerArgs sampler_args(const heget_sampler* s);
+int check_common(const heget_ctx* ctx, int n, long long N);
+int check_precision(int p);
 }  // namespace heget

@@ -11,6 +11,8 @@ namespace heget {
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+constexpr int kBatchThreads = 256;   // threads of the mixed-n batch kernel
+
 template <class R, int N, int BLOCK>
 __host__ __device__ constexpr size_t table_bytes() {
     return align16(RoundTables<R, N, BLOCK>::bytes);
@@ -136,40 +138,110 @@ __device__ __forceinline__ Partial zero_partial() {
     return p;
 }
 
+// One tile of the fused path: points first .. first+cnt-1 (cnt <= tile) of
+// stream `seed` are generated (one thread per point), their amplitudes
+// computed in rounds, and their weights folded into acc by the thread that
+// generated each point.  w_out (may be NULL) receives the tile's weights.
+template <class R, int N, int BLOCK>
+__device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_t seed, long long first, int cnt,
+                                          const SamplerArgs& S, const Physics& ph, Partial& acc,
+                                          double* __restrict__ w_out) {
+    double* stage = reinterpret_cast<double*>(smem);
+    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK>(tile));
+    for (int t = threadIdx.x; t < cnt; t += BLOCK) {
+        const MomView v{stage + t, tile, kMomSlots};
+        EventInfo ev;
+        generate_event<N>(seed, (uint64_t)(first + t), S, ph, v, ev);
+        event_to_rec<R, N>(v, ev, ph, recs[t]);
+        acc.npass += recs[t].mask;
+        acc.ntotal += 1;
+        acc.ntries += recs[t].tries;
+    }
+    __syncthreads();
+    amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, lane_weight<N>(nullptr, 0));
+    // one thread per point (the thread that generated it): weight and
+    // double-double accumulation with every lane active
+    for (int t = threadIdx.x; t < cnt; t += BLOCK) {
+        const double w = recs[t].valid ? (double)recs[t].ssum * recs[t].wfac : 0.0;
+        acc.sw = dd_add_d(acc.sw, w);
+        acc.sw2 = dd_add_d(acc.sw2, w * w);
+        if (w_out) w_out[t] = w;
+    }
+}
+
 template <class R, int N, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, int tile,
             Partial* __restrict__ partials, double* __restrict__ w_out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double* stage = reinterpret_cast<double*>(smem);
-    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK>(tile));
-    const float wh = lane_weight<N>(nullptr, 0);
     Partial acc = zero_partial();
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
-        for (int t = threadIdx.x; t < cnt; t += BLOCK) {
-            const MomView v{stage + t, tile, kMomSlots};
-            EventInfo ev;
-            generate_event<N>(seed, (uint64_t)(i0 + t0 + t), S, ph, v, ev);
-            event_to_rec<R, N>(v, ev, ph, recs[t]);
-            acc.npass += recs[t].mask;
-            acc.ntotal += 1;
-            acc.ntries += recs[t].tries;
-        }
-        __syncthreads();
-        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh);
-        // one thread per point (the thread that generated it): weight and
-        // double-double accumulation with every lane active
-        for (int t = threadIdx.x; t < cnt; t += BLOCK) {
-            const double w = recs[t].valid ? (double)recs[t].ssum * recs[t].wfac : 0.0;
-            acc.sw = dd_add_d(acc.sw, w);
-            acc.sw2 = dd_add_d(acc.sw2, w * w);
-            if (w_out) w_out[t0 + t] = w;
-        }
+        xsec_tile<R, N, BLOCK>(smem, tile, seed, i0 + t0, cnt, S, ph, acc, w_out ? w_out + t0 : nullptr);
     }
     // the round tables are free now: reuse them as reduction scratch
     const Partial r = block_reduce_partial<BLOCK>(acc, reinterpret_cast<Partial*>(smem));
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-n batch: one launch over a work list of tiles drawn from several
+// requests (any n in 2..8, any N).  Each block takes work items in a
+// grid-stride loop; the item's n selects the code path (uniform per block),
+// and every item leaves one partial, in its request's partial array at the
+// tile's index.  A request's tiles do not depend on the rest of the batch,
+// and its partials are combined in tile order, so a request gives the same
+// result, bit for bit, alone or in any mix.
+// ---------------------------------------------------------------------------
+struct BatchReq {
+    uint64_t seed;
+    long long i0;
+    SamplerArgs S;
+    Physics ph;
+    double* w_out;
+    heget_xsec_result* result;
+    Partial* parts;   // this request's tile partials, tile k at parts[k]
+    int n, tile, ntiles, pad;
+};
+
+struct WorkItem {
+    int req;          // index into the request table
+    int n;            // photons of that request
+    int count;        // points in this tile
+    int pad;
+    long long start;  // first point of the tile, relative to the request
+};
+
+template <class R>
+__global__ void __launch_bounds__(kBatchThreads)
+xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq* __restrict__ reqs) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const BatchReq& rq = reqs[w.req];
+        Partial acc = zero_partial();
+        double* wo = rq.w_out ? rq.w_out + w.start : nullptr;
+        const long long first = rq.i0 + w.start;
+        switch (w.n) {
+#define HEGET_BATCH_CASE(NN)                                                                                   \
+    case NN:                                                                                                   \
+        xsec_tile<R, NN, kBatchThreads>(smem, rq.tile, rq.seed, first, w.count, rq.S, rq.ph, acc, wo); \
+        break;
+            HEGET_BATCH_CASE(2)
+            HEGET_BATCH_CASE(3)
+            HEGET_BATCH_CASE(4)
+            HEGET_BATCH_CASE(5)
+            HEGET_BATCH_CASE(6)
+            HEGET_BATCH_CASE(7)
+            HEGET_BATCH_CASE(8)
+#undef HEGET_BATCH_CASE
+            default:
+                break;
+        }
+        const Partial r = block_reduce_partial<kBatchThreads>(acc, reinterpret_cast<Partial*>(smem));
+        if (threadIdx.x == 0) rq.parts[w.start / rq.tile] = r;
+        __syncthreads();   // the scratch is the next item's staging area
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -312,6 +384,13 @@ int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const Sa
                     const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
                     cudaStream_t st);
 int occupancy_ws_f32(int n, int* bpsm, size_t* smem);
+// Mixed-n batch launch (one launch per precision); smem sized for the tiles.
+int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+                     cudaStream_t st);
+int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+                     cudaStream_t st);
+// One block per request: its tile partials, in order, into its result.
+int launch_batch_finalize(const BatchReq* reqs, int nreqs, cudaStream_t st);
 // Default launch shape and the maximum resident blocks per SM.
 int default_tile(int n, bool xsec);
 int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile);

@@ -67,6 +67,16 @@ static int occupancy_ws_n(int* blocks_per_sm, size_t* smem_out) {
     }
 }
 
+template <class R>
+static int launch_batch_t(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+                          cudaStream_t st) {
+    auto k = xsec_batch_kernel<R>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k<<<grid, kBatchThreads, smem, st>>>(items, nitems, reqs);
+    return (int)cudaGetLastError();
+}
+
 #define HEGET_DISPATCH_N(n, CALL)       \
     switch (n) {                        \
         case 2: return CALL(2);         \

@@ -1,0 +1,225 @@
+// heget_runtime.cu -- launch machinery around the kernels: CUDA-graph capture
+// of the cross-section step and the launch-shape autotuner.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "heget_kernels.cuh"
+#include "heget_internal.h"
+
+using namespace heget;
+
+// A captured heget_xsec_launch + heget_xsec_finalize.  Replays update only the
+// first two arguments of the event kernel, which every variant of it takes as
+// (uint64_t seed, long long i0, ...).
+struct heget_graph {
+    heget_ctx* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;   // the event kernel (the graph's only root)
+    cudaKernelNodeParams kp{};         // its captured parameters
+    int nargs = 0;
+};
+
+namespace {
+int graph_fail(heget_graph* g, int code) {
+    if (g) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+    }
+    return code;
+}
+}  // namespace
+
+extern "C" {
+
+int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp, int precision,
+                     heget_xsec_result* result_dev, heget_graph** out) {
+    if (!out) return fail(HEGET_EINVAL, "out is NULL");
+    *out = nullptr;
+    int r = check_common(ctx, n, N);
+    if (r) return r;
+    if ((r = check_precision(precision))) return r;
+    if ((r = check_sampler(smp))) return r;
+    if (N < 1 || !result_dev) return fail(HEGET_EINVAL, "a graph needs N >= 1 and result_dev");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    heget_graph* g = new heget_graph();
+    g->ctx = ctx;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return graph_fail(g, cuda_fail(e, "cudaStreamBeginCapture"));
+    }
+    r = heget_xsec_launch(ctx, n, 0, 0, N, smp, precision, nullptr, st);
+    if (!r) r = heget_xsec_finalize(ctx, result_dev, st);
+    e = cudaStreamEndCapture(st, &g->graph);
+    cudaStreamDestroy(st);
+    if (r) return graph_fail(g, r);
+    if (e != cudaSuccess) return graph_fail(g, cuda_fail(e, "cudaStreamEndCapture"));
+    g->nargs = ctx->last_ws ? 7 : 8;
+    size_t nroots = 1;
+    e = cudaGraphGetRootNodes(g->graph, &g->knode, &nroots);
+    if (e != cudaSuccess || nroots != 1) return graph_fail(g, fail(HEGET_ECUDA, "unexpected captured graph shape"));
+    e = cudaGraphKernelNodeGetParams(g->knode, &g->kp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) return graph_fail(g, cuda_fail(e, "graph instantiate"));
+    *out = g;
+    return HEGET_OK;
+}
+
+int heget_graph_launch(heget_graph* g, uint64_t seed, int64_t i0, void* stream) {
+    if (!g) return fail(HEGET_EINVAL, "graph is NULL");
+    if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
+    DeviceGuard dg(g->ctx->device);
+    void* args[8];
+    for (int k = 0; k < g->nargs; ++k) args[k] = g->kp.kernelParams[k];
+    long long i0v = i0;
+    args[0] = &seed;
+    args[1] = &i0v;
+    cudaKernelNodeParams p = g->kp;
+    p.kernelParams = args;
+    p.extra = nullptr;
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(g->exec, g->knode, &p);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "heget_graph_launch");
+    return HEGET_OK;
+}
+
+void heget_graph_destroy(heget_graph* g) {
+    if (!g) return;
+    DeviceGuard dg(g->ctx->device);
+    graph_fail(g, 0);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+
+int heget_autotune(heget_ctx* ctx, int n, int precision, int kind, int64_t probe_points, int* best_tile,
+                   double* best_ms) {
+    int r = check_common(ctx, n, probe_points);
+    if (r) return r;
+    if ((r = check_precision(precision))) return r;
+    if (kind != 0 && kind != 1) return fail(HEGET_EINVAL, "kind must be 0 (amp2) or 1 (xsec)");
+    if (probe_points < 1) return fail(HEGET_EINVAL, "probe_points must be >= 1");
+    DeviceGuard dg(ctx->device);
+    const int unit = kBlockThreads >> n;
+    std::vector<int> cands;
+    if (kind == 1) cands.push_back(0);   // default shape (warp-specialised where it applies)
+    for (int t = unit; t <= 1024; t *= 2) cands.push_back(t);
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double* mom = nullptr;
+    double* amp = nullptr;
+    heget_xsec_result* res = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && kind == 0) e = cudaMalloc(&mom, sizeof(double) * 4 * (n + 2) * probe_points);
+    if (e == cudaSuccess && kind == 0) e = cudaMalloc(&amp, sizeof(double) * probe_points);
+    if (e == cudaSuccess && kind == 1) e = cudaMalloc(&res, sizeof(heget_xsec_result));
+    heget_sampler toy{HEGET_SAMPLER_TOY_PDF, 0, 0, 0, 7000.0, 100.0, 64};
+    if (e == cudaSuccess && kind == 0)
+        r = heget_phase_space_ex(ctx, 0x0908440300000777ull, 0, probe_points, n, &toy, mom, nullptr, nullptr,
+                                 nullptr, nullptr, nullptr, st);
+    const int saved = ctx->tiles[kind][precision == HEGET_FP64][n];
+    int best = -1;
+    float best_t = 1e30f;
+    for (int c : cands) {
+        if (e != cudaSuccess || r) break;
+        ctx->tiles[kind][precision == HEGET_FP64][n] = c;
+        auto run = [&]() {
+            return kind == 0 ? heget_amp2(ctx, n, probe_points, mom, nullptr, precision, amp, st)
+                             : heget_xsec_async(ctx, n, 0x0908440300000778ull, 0, probe_points, &toy, precision, res,
+                                                nullptr, st);
+        };
+        if (run() != HEGET_OK) continue;   // e.g. shared memory of this tile exceeds the device limit
+        float tmin = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaEventRecord(e0, st);
+            ok = run() == HEGET_OK;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0;
+            if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) tmin = std::min(tmin, ms);
+        }
+        if (ok && tmin < best_t) {
+            best_t = tmin;
+            best = c;
+        }
+    }
+    if (mom) cudaFree(mom);
+    if (amp) cudaFree(amp);
+    if (res) cudaFree(res);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        ctx->tiles[kind][precision == HEGET_FP64][n] = saved;
+        return cuda_fail(e, "heget_autotune");
+    }
+    if (r || best < 0) {
+        ctx->tiles[kind][precision == HEGET_FP64][n] = saved;
+        return r ? r : fail(HEGET_ECUDA, "no launch shape ran");
+    }
+    ctx->tiles[kind][precision == HEGET_FP64][n] = best;
+    if (best_tile) *best_tile = best;
+    if (best_ms) *best_ms = best_t;
+    return HEGET_OK;
+}
+
+int heget_autotune_save(const heget_ctx* ctx, const char* path) {
+    if (!ctx || !path) return fail(HEGET_EINVAL, "NULL argument");
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    std::string gpu(prop.name);
+    std::replace(gpu.begin(), gpu.end(), ' ', '_');
+    // keep other GPUs' lines, replace this GPU's
+    std::vector<std::string> keep;
+    if (FILE* f = std::fopen(path, "r")) {
+        char line[512];
+        while (std::fgets(line, sizeof line, f))
+            if (std::strncmp(line, gpu.c_str(), gpu.size()) != 0 || line[gpu.size()] != ' ') keep.emplace_back(line);
+        std::fclose(f);
+    }
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(HEGET_EINVAL, "cannot write %s", path);
+    for (const auto& l : keep) std::fputs(l.c_str(), f);
+    for (int kind = 0; kind < 2; ++kind)
+        for (int p = 0; p < 2; ++p)
+            for (int n = kMinN; n <= kMaxN; ++n)
+                if (ctx->tiles[kind][p][n] > 0)
+                    std::fprintf(f, "%s %d %d %d %d\n", gpu.c_str(), n, p ? HEGET_FP64 : HEGET_FP32, kind,
+                                 ctx->tiles[kind][p][n]);
+    std::fclose(f);
+    return HEGET_OK;
+}
+
+int heget_autotune_load(heget_ctx* ctx, const char* path) {
+    if (!ctx || !path) return fail(HEGET_EINVAL, "NULL argument");
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    std::string gpu(prop.name);
+    std::replace(gpu.begin(), gpu.end(), ' ', '_');
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(HEGET_EINVAL, "cannot read %s", path);
+    char name[256];
+    int n, prec, kind, tile;
+    while (std::fscanf(f, "%255s %d %d %d %d", name, &n, &prec, &kind, &tile) == 5) {
+        if (gpu != name) continue;
+        heget_set_tile(ctx, n, prec, kind, tile);
+    }
+    std::fclose(f);
+    return HEGET_OK;
+}
+
+}  // extern "C"

@@ -59,6 +59,27 @@ def sampler_toy_pdf(e_beam: float = 7000.0, floor: float = 100.0, max_tries: int
     return heget_sampler(HEGET_SAMPLER_TOY_PDF, 0.0, 0.0, 0.0, e_beam, floor, max_tries)
 
 
+class heget_xsec_request(C.Structure):
+    _fields_ = [("n", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64), ("i0", C.c_int64),
+                ("N", C.c_int64), ("sampler", heget_sampler), ("result_dev", C.c_void_p),
+                ("w_out", C.c_void_p)]
+
+
+class heget_server_cfg(C.Structure):
+    _fields_ = [("max_inflight", C.c_int), ("max_launch_work", C.c_double), ("hbm_reserve_frac", C.c_double),
+                ("arena_bytes", C.c_uint64)]
+
+
+class heget_request(C.Structure):
+    _fields_ = [("n", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64), ("i0", C.c_int64),
+                ("N", C.c_int64), ("sampler", heget_sampler)]
+
+
+class heget_result(C.Structure):
+    _fields_ = [("result", heget_xsec_result), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("status", C.c_int), ("reserved", C.c_int)]
+
+
 _lib = None
 P, I32, I64, U64, D = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
 
@@ -79,11 +100,23 @@ SIGNATURES = {
     "heget_xsec_launch": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), I32, P, P]),
     "heget_xsec_finalize": (I32, [P, P, P]),
     "heget_measure_fma_peak": (I32, [P, I32, C.POINTER(C.c_double)]),
+    "heget_xsec_batch": (I32, [P, C.POINTER(heget_xsec_request), I32, P]),
+    "heget_autotune": (I32, [P, I32, I32, I32, I64, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "heget_autotune_save": (I32, [P, C.c_char_p]),
+    "heget_autotune_load": (I32, [P, C.c_char_p]),
+    "heget_graph_xsec": (I32, [P, I32, I64, C.POINTER(heget_sampler), I32, P, C.POINTER(P)]),
+    "heget_graph_launch": (I32, [P, U64, I64, P]),
+    "heget_graph_destroy": (None, [P]),
     "heget_set_tile": (I32, [P, I32, I32, I32, I32]),
     "heget_get_tile": (I32, [P, I32, I32, I32]),
     "heget_xsec_noalloc": (I32, [I32, I32, U64, I64, I64, C.POINTER(heget_sampler), C.POINTER(heget_params),
                                  I32, P, P]),
     "heget_sum": (I32, [P, P, I64, P, P]),
+    "heget_server_start": (I32, [P, C.POINTER(heget_server_cfg), C.POINTER(P)]),
+    "heget_submit": (I32, [P, C.POINTER(heget_request), C.POINTER(U64)]),
+    "heget_poll": (I32, [P, U64, C.POINTER(heget_result)]),
+    "heget_wait": (I32, [P, U64, D, C.POINTER(heget_result)]),
+    "heget_server_stop": (I32, [P]),
 }
 
 
@@ -199,6 +232,46 @@ def heget_measure_fma_peak(ctx, precision=HEGET_FP32) -> float:
     return v.value
 
 
+def heget_xsec_batch(ctx, requests, stream=None):
+    """requests: list of dicts with n, precision, seed, i0, N, sampler, result_dev (tensor), w_out (tensor|None)."""
+    arr = (heget_xsec_request * len(requests))()
+    for a, r in zip(arr, requests):
+        a.n, a.precision, a.seed, a.i0, a.N = r["n"], r["precision"], r["seed"], r.get("i0", 0), r["N"]
+        a.sampler = r["sampler"]
+        a.result_dev = _ptr(r["result_dev"])
+        a.w_out = _ptr(r.get("w_out"))
+    _check(load().heget_xsec_batch(ctx, arr, len(requests), _stream(stream)))
+
+
+def heget_autotune(ctx, n, precision, kind, probe_points):
+    """Returns (best_tile, best_ms); the context keeps the best tile."""
+    t, ms = C.c_int(), C.c_double()
+    _check(load().heget_autotune(ctx, n, precision, kind, probe_points, C.byref(t), C.byref(ms)))
+    return t.value, ms.value
+
+
+def heget_autotune_save(ctx, path):
+    _check(load().heget_autotune_save(ctx, str(path).encode()))
+
+
+def heget_autotune_load(ctx, path):
+    _check(load().heget_autotune_load(ctx, str(path).encode()))
+
+
+def heget_graph_xsec(ctx, n, N, sampler, precision, result_dev):
+    g = P()
+    _check(load().heget_graph_xsec(ctx, n, N, C.byref(sampler), precision, _ptr(result_dev), C.byref(g)))
+    return g
+
+
+def heget_graph_launch(graph, seed, i0=0, stream=None):
+    _check(load().heget_graph_launch(graph, seed, i0, _stream(stream)))
+
+
+def heget_graph_destroy(graph):
+    load().heget_graph_destroy(graph)
+
+
 def heget_set_tile(ctx, n, precision, kind, tile):
     _check(load().heget_set_tile(ctx, n, precision, kind, tile))
 
@@ -216,6 +289,40 @@ def heget_xsec_noalloc(device, n, seed, i0, N, sampler, precision, result_dev, p
 
 def heget_sum(ctx, x, N, out_dev, stream=None):
     _check(load().heget_sum(ctx, _ptr(x), N, _ptr(out_dev), _stream(stream)))
+
+
+def heget_server_start(ctx, max_inflight=0, max_launch_work=0.0, hbm_reserve_frac=0.0, arena_bytes=0):
+    cfg = heget_server_cfg(max_inflight, max_launch_work, hbm_reserve_frac, arena_bytes)
+    s = P()
+    _check(load().heget_server_start(ctx, C.byref(cfg), C.byref(s)))
+    return s
+
+
+def heget_submit(server, n, seed, N, sampler, precision=HEGET_FP32, i0=0) -> int:
+    q = heget_request(n, precision, seed, i0, N, sampler)
+    t = U64()
+    _check(load().heget_submit(server, C.byref(q), C.byref(t)))
+    return t.value
+
+
+def heget_poll(server, ticket):
+    """The finished heget_result, or None while the request runs."""
+    r = heget_result()
+    st = load().heget_poll(server, ticket, C.byref(r))
+    if st == HEGET_EBUSY:
+        return None
+    _check(st)
+    return r
+
+
+def heget_wait(server, ticket, timeout_s=60.0) -> heget_result:
+    r = heget_result()
+    _check(load().heget_wait(server, ticket, timeout_s, C.byref(r)))
+    return r
+
+
+def heget_server_stop(server):
+    _check(load().heget_server_stop(server))
 
 
 def result_from_tensor(t) -> heget_xsec_result:
