@@ -60,3 +60,43 @@ def test_binding_fails_loudly_without_library(tmp_path):
             heget.load(str(tmp_path / "missing.so"))
     finally:
         heget._lib = saved
+
+
+STRUCTS = ["heget_params", "heget_sampler", "heget_xsec_result", "heget_xsec_request", "heget_server_cfg",
+           "heget_request", "heget_result"]
+
+
+def test_binding_structs_match_the_c_layout(heget_lib, tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets the C
+    compiler gives the header's struct."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "heget.h"', 'int main(void) {']
+    for name in STRUCTS:
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in getattr(heget_lib, name)._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for name in STRUCTS:
+        cls = getattr(heget_lib, name)
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+
+
+def test_server_calls_reject_null_arguments_without_gpu(heget_lib):
+    lib = heget_lib.load()
+    h = ctypes.c_void_p()
+    assert lib.heget_server_start(None, None, ctypes.byref(h)) == heget_lib.HEGET_EINVAL
+    q = heget_lib.heget_request(4, 32, 1, 0, 10, heget_lib.sampler_toy_pdf())
+    t = ctypes.c_uint64()
+    assert lib.heget_submit(None, ctypes.byref(q), ctypes.byref(t)) == heget_lib.HEGET_EINVAL
+    r = heget_lib.heget_result()
+    assert lib.heget_poll(None, 1, ctypes.byref(r)) == heget_lib.HEGET_EINVAL
+    assert lib.heget_wait(None, 1, 0.01, ctypes.byref(r)) == heget_lib.HEGET_EINVAL
+    assert lib.heget_server_stop(None) == heget_lib.HEGET_EINVAL
