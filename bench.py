@@ -38,6 +38,39 @@ WORKLOAD = ("u ubar -> 4 gamma, 1,048,576 points/step/GPU, toy-PDF sqrt(s-hat) =
             "prefix tree, FP32 chain + FP64 RAMBO/cuts/denominators + double-double sigma accumulation")
 
 
+# Peaks derived from unit counts and the maximum SM clock (GB300: 152 SMs at
+# 2.07 GHz; per SM and clock 128 FP32 FMA lanes and 2 FP64 FMA lanes), in
+# TFLOP/s (an FMA counts 2 flops).
+SMS, SM_GHZ = 152, 2.07
+FP32_PEAK = SMS * 128 * 2 * SM_GHZ / 1e3
+FP64_PEAK = SMS * 2 * 2 * SM_GHZ / 1e3
+# FP64 flops executed per point by the fused n = 4 FP32 step (DFMA x 2 +
+# DADD + DMUL, thread-level predicated-on counts from ncu on 262,144 points
+# of this workload): RNG, toy-PDF sampler, RAMBO, cuts, denominators, weights
+# and the double-double sums.
+FP64_FLOPS_PER_POINT = {4: 1087}
+
+
+def roofline(n, N, kern_s, peak32_meas, peak64_meas):
+    """Roofline of the fused step's kernel.  At n <= 4 the FP64 pipe binds
+    (the phase space is FP64 by design; one SM retires 2 DFMA per clock
+    against 128 FFMA), above that the FP32 tree does."""
+    tree = tree_flops_per_point(n) * N / kern_s / 1e12
+    fp32 = {"pipe": "fp32 fma", "achieved": tree, "peak": FP32_PEAK, "frac": tree / FP32_PEAK,
+            "flops_per_point": tree_flops_per_point(n), "measured_peak": peak32_meas,
+            "frac_of_measured": tree / peak32_meas}
+    kern = f"xsec_ws_kernel<float,{n}>" if n <= 4 else f"xsec_kernel<float,{n},256>"
+    if n in FP64_FLOPS_PER_POINT:
+        a64 = FP64_FLOPS_PER_POINT[n] * N / kern_s / 1e12
+        return {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": FP64_PEAK, "unit": "TFLOP/s",
+                "frac": a64 / FP64_PEAK, "traffic": 108544 if n == 4 else None, "kernel": kern,
+                "flops_per_point": FP64_FLOPS_PER_POINT[n],
+                "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                "measured_peak": peak64_meas, "frac_of_measured": a64 / peak64_meas, "fp32_tree": fp32}
+    return {"bound": "alu", **fp32, "unit": "TFLOP/s", "traffic": None, "kernel": kern,
+            "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz"}
+
+
 def tree_flops_per_point(n: int) -> int:
     """FP32 flops of the ordering tree per point: 2^n helicity lanes, each doing
     sum_{l=2}^{n-1} n!/(n-l)! chain steps (28 flops: r . M, 2x2 complex) and n!
@@ -102,24 +135,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(n, seconds=12.0):
+def cpu_baseline(n, seconds=12.0, sampler=None, cut=None, seed=SEED, N_cap=None):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of
-    the same workload (consecutive point indices of the same seed)."""
+    the same workload (consecutive point indices of the same seed).  Returns
+    the baseline record and the sample's weights (for the error columns of
+    --matrix)."""
     import oracle as O
     O.build()
     threads = os.cpu_count() or 1
-    S, Cc = O.toy_pdf(), O.cuts()
+    S = sampler if sampler is not None else O.toy_pdf()
+    Cc = cut if cut is not None else O.cuts()
+    import numpy as np
+    probe = threads if n >= 7 else 256
     t0 = time.perf_counter()
-    probe = 256
-    O.event_weights(n, SEED, 0, probe, S, Cc, threads=threads)
+    w, _, _ = O.event_weights(n, seed, 0, probe, S, Cc, threads=threads)
     dt = time.perf_counter() - t0
-    N = max(probe, int(probe * seconds / max(dt, 1e-3)))
-    t0 = time.perf_counter()
-    O.event_weights(n, SEED, probe, N, S, Cc, threads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": N / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
-            "sample": f"{N} consecutive points of the n={n} workload (seed {SEED:#x}), weights incl. |M|^2 "
-                      f"of cut-passing points, {threads} OpenMP threads, {dt:.1f} s"}
+    N = probe
+    if dt < 0.5 * seconds:   # extend the sample to about `seconds` of work
+        more = max(probe, int(probe * (seconds - dt) / max(dt, 1e-3)))
+        if N_cap:
+            more = max(0, min(more, N_cap - probe))
+        if more:
+            t1 = time.perf_counter()
+            w2, _, _ = O.event_weights(n, seed, probe, more, S, Cc, threads=threads)
+            dt += time.perf_counter() - t1
+            w = np.concatenate([w, w2])
+            N += more
+    rec = {"value": N / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
+           "sample": f"points 0..{N - 1} of the n={n} workload (seed {seed:#x}), weights incl. |M|^2 "
+                     f"of cut-passing points, {threads} OpenMP threads, {dt:.1f} s"}
+    return rec, w
 
 
 def run_reference(args):
@@ -150,6 +195,171 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, flush=None):
+    """Device time per step (ms) of heget_xsec_launch + heget_xsec_finalize,
+    CUDA events on the launching stream, L2 flushed between steps."""
+    import torch
+    res = torch.zeros(80, dtype=torch.uint8, device="cuda")
+    for w in range(2):
+        H.heget_xsec_launch(ctx, n, seed + 77 + w, i0, N, sampler, precision, stream=stream)
+        H.heget_xsec_finalize(ctx, res, stream=stream)
+    stream.synchronize()
+    total = 0.0
+    for k in range(steps):
+        if flush is not None:
+            flush.add_(1)
+            stream.wait_stream(torch.cuda.current_stream())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        H.heget_xsec_launch(ctx, n, seed + k, i0, N, sampler, precision, stream=stream)
+        H.heget_xsec_finalize(ctx, res, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    return total / steps
+
+
+# ---------------------------------------------------------------------------
+# serving: a Poisson trace of mixed requests through the request server
+# ---------------------------------------------------------------------------
+
+def serving_trace(R, rate, seed=0x5E4E):
+    """R requests arriving as a Poisson process of `rate` per second: n uniform
+    in 2..8, precision FP32 or FP64 with equal odds, toy-PDF sampler, and N
+    log-uniform in [1e3, 1e6] divided by 8^(n-4) for n > 4 (the per-point cost
+    grows ~10x per photon above n = 4; unscaled, the n = 8 requests alone would
+    ask for ~100x what one GPU delivers).  Returns a list of dicts."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, R))
+    n = rng.integers(2, 9, R)
+    N = np.exp(rng.uniform(math.log(1e3), math.log(1e6), R)) / 8.0 ** np.maximum(0, n - 4)
+    N = np.maximum(1, N.astype(np.int64))
+    prec = np.where(rng.random(R) < 0.5, 32, 64)
+    return [dict(t=float(t[k]), n=int(n[k]), N=int(N[k]), precision=int(prec[k]), seed=SEED + 0x1000 + k)
+            for k in range(R)]
+
+
+def run_serving(H, ctx, trace, open_loop=True, timeout=300.0):
+    """Submits the trace (at its arrival times, or all at once), waits for every
+    result; latencies from the library's own submit/done stamps."""
+    import threading
+    S = H.sampler_toy_pdf()
+    srv = H.heget_server_start(ctx)
+    tickets = [None] * len(trace)
+    try:
+        def submitter():
+            t0 = time.monotonic()
+            for k, q in enumerate(trace):
+                if open_loop:
+                    dt = q["t"] - (time.monotonic() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                tickets[k] = H.heget_submit(srv, q["n"], q["seed"], q["N"], S, q["precision"])
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join(timeout)
+        results = [H.heget_wait(srv, t, timeout) for t in tickets]
+    finally:
+        H.heget_server_stop(srv)
+    lat = sorted((r.t_done - r.t_submit) * 1e3 for r in results)
+    span = max(r.t_done for r in results) - min(r.t_submit for r in results)
+    pts = sum(q["N"] for q in trace)
+    assert all(r.status == H.HEGET_OK for r in results)
+    return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "max_ms": lat[-1], "points_per_s": pts / span, "span_s": span}
+
+
+def run_sequential(H, ctx, trace, precision=None):
+    """The same requests one after another, each a synchronous heget_xsec call
+    (the plain per-request launch) at `precision` (None: the request's own)."""
+    S = H.sampler_toy_pdf()
+    t0 = time.perf_counter()
+    for q in trace:
+        H.heget_xsec(ctx, q["n"], q["N"], q["seed"], S, precision or q["precision"])
+    dt = time.perf_counter() - t0
+    return {"points_per_s": sum(q["N"] for q in trace) / dt, "span_s": dt}
+
+
+def serving_section(H, ctx, R=400, rate=200.0):
+    trace = serving_trace(R, rate)
+    warm = serving_trace(40, 2000.0, seed=0x3A11)
+    run_serving(H, ctx, warm, open_loop=False)
+    H.heget_xsec(ctx, 8, 16, 1, H.sampler_toy_pdf(), 64)
+    closed = run_serving(H, ctx, trace, open_loop=False)
+    open_ = run_serving(H, ctx, trace, open_loop=True)
+    # the same requests arriving at 70 % of the saturated request rate
+    cap = len(trace) / closed["span_s"]
+    slow = [dict(q, t=q["t"] * rate / (0.7 * cap)) for q in trace]
+    open_07 = run_serving(H, ctx, slow, open_loop=True)
+    open_07["rate_per_s"] = 0.7 * cap
+    seq64 = run_sequential(H, ctx, trace, precision=H.HEGET_FP64)
+    seq_own = run_sequential(H, ctx, trace)
+    return {"trace": f"{R} requests, Poisson {rate:g}/s, n uniform 2..8, FP32/FP64 1:1, toy PDF, "
+                     "N log-uniform 1e3..1e6 / 8^(n-4) for n > 4",
+            "points": sum(q["N"] for q in trace),
+            "open_loop": open_, "saturated": closed, "open_loop_at_0.7_capacity": open_07,
+            "sequential_fp64_plain": seq64, "sequential_own_precision": seq_own,
+            "saturated_vs_sequential_fp64": closed["points_per_s"] / seq64["points_per_s"]}
+
+
+# ---------------------------------------------------------------------------
+# per-configuration table (--matrix)
+# ---------------------------------------------------------------------------
+
+MATRIX = [
+    # name, n, N, sampler (kind, args), cuts (pt, eta, dr), fp64 timing points
+    ("n=2, sqrt(s-hat) = 500 GeV fixed, 65,536 points, cuts pT>20 |eta|<2.5", 2, 65_536, ("fixed", 500.0),
+     (20.0, 2.5, 0.0), 65_536),
+    ("n=4, toy PDF, 1,048,576 points, cuts pT>20 |eta|<2.5 dR>0.4", 4, 1 << 20, ("toy",), (20.0, 2.5, 0.4),
+     1 << 20),
+    ("n=6, toy PDF, 1,048,576 points, same cuts", 6, 1 << 20, ("toy",), (20.0, 2.5, 0.4), 1 << 17),
+    ("n=8, sqrt(s-hat) uniform 200 GeV..2 TeV, 65,536 points, same cuts", 8, 65_536, ("uniform", 200.0, 2000.0),
+     (20.0, 2.5, 0.4), 2048),
+]
+
+
+def matrix_section(H, ctx, stream, peak32, peak64, flush):
+    import numpy as np
+    import torch
+    import oracle as O
+    out = []
+    for name, n, N, smp, cut, n64 in MATRIX:
+        S = {"fixed": lambda a: H.sampler_fixed(a[0]), "toy": lambda a: H.sampler_toy_pdf(),
+             "uniform": lambda a: H.sampler_uniform(a[0], a[1])}[smp[0]](smp[1:])
+        OS = {"fixed": lambda a: O.fixed(a[0]), "toy": lambda a: O.toy_pdf(),
+              "uniform": lambda a: O.uniform(a[0], a[1])}[smp[0]](smp[1:])
+        H.heget_set_params(ctx, pt_min=cut[0], eta_max=cut[1], dr_min=cut[2])
+        ms32 = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3 if n < 8 else 1, stream, flush=flush)
+        ms64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 3 if n < 8 else 1, stream, flush=flush)
+        base, w_or = cpu_baseline(n, seconds=8.0, sampler=OS, cut=O.cuts(*cut), N_cap=4096)
+        M = len(w_or)
+        errs = {}
+        for prec in (H.HEGET_FP32, H.HEGET_FP64):
+            w = torch.zeros(M, dtype=torch.float64, device="cuda")
+            r = torch.zeros(80, dtype=torch.uint8, device="cuda")
+            H.heget_xsec_async(ctx, n, SEED, 0, M, S, prec, r, w_out=w, stream=stream)
+            stream.synchronize()
+            wg = w.cpu().numpy()
+            nz = w_or != 0
+            rel = np.abs(wg[nz] - w_or[nz]) / np.abs(w_or[nz])
+            errs[prec] = (float(np.median(rel)) if rel.size else 0.0, float(rel.max()) if rel.size else 0.0,
+                          int((wg != 0).sum() == nz.sum()))
+        tf = tree_flops_per_point(n)
+        out.append({"config": name, "n": n, "points": N,
+                    "fp32_points_per_s": N / (ms32 * 1e-3), "fp64_plain_points_per_s": n64 / (ms64 * 1e-3),
+                    "fp64_timed_points": n64,
+                    "fp32_rel_err_median_max": errs[H.HEGET_FP32][:2],
+                    "fp64_rel_err_median_max": errs[H.HEGET_FP64][:2],
+                    "masks_agree": bool(errs[H.HEGET_FP32][2] and errs[H.HEGET_FP64][2]),
+                    "err_sample_points": M,
+                    "fp32_tree_frac_of_fp32_fma_peak": tf * N / (ms32 * 1e-3) / (peak32 * 1e12),
+                    "fp64_tree_frac_of_fp64_fma_peak": tf * n64 / (ms64 * 1e-3) / (peak64 * 1e12),
+                    "oracle": base})
+    H.heget_set_params(ctx)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -158,7 +368,11 @@ def main():
     ap.add_argument("--impl", default="heget", choices=["heget", "reference"])
     ap.add_argument("--ref-points", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--n", type=int, default=N_PHOTONS, help="photons (profiling of smaller cases)")
+    ap.add_argument("--points", type=int, default=POINTS, help="points per step per GPU")
+    ap.add_argument("--matrix", action="store_true", help="also print the per-configuration table")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -177,11 +391,12 @@ def main():
     B.build()
     ctx = H.heget_create(local)
     stream = torch.cuda.Stream()
-    n, N = N_PHOTONS, POINTS
+    n, N = args.n, args.points
     i0 = rank * N
     sampler = H.sampler_toy_pdf()
     res = torch.zeros(80, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    flush.random_(0, 255)
 
     peak32 = H.heget_measure_fma_peak(ctx, H.HEGET_FP32)
     peak64 = H.heget_measure_fma_peak(ctx, H.HEGET_FP64)
@@ -201,7 +416,7 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
-        flush.random_(0, 255) if k == 0 else flush.add_(1)   # evict L2 between timed steps (untimed)
+        flush.add_(1)   # evict L2 between timed steps (untimed)
         stream.wait_stream(torch.cuda.current_stream())
         a, b, c = evs[k]
         a.record(stream)
@@ -222,67 +437,68 @@ def main():
         step_ms, kern_ms = t.tolist()
     r = H.result_from_tensor(res)
 
-    # end to end through the public API with host buffers: pinned momenta H2D,
-    # heget_amp2 (FP32), |M|^2 D2H, every step
-    mom_dev = torch.empty((N, n + 2, 4), dtype=torch.float64, device="cuda")
-    H.heget_phase_space_ex(ctx, SEED, i0, N, n, sampler, momenta=mom_dev)
-    torch.cuda.synchronize()
-    mom_host = mom_dev.cpu().pin_memory()
-    amp_host = torch.empty(N, dtype=torch.float64).pin_memory()
-    amp_dev = torch.empty(N, dtype=torch.float64, device="cuda")
-    del mom_dev
-    mom_in = torch.empty((N, n + 2, 4), dtype=torch.float64, device="cuda")
+    # the plain FP64 GPU kernel on the same workload (the comparison the
+    # workload is quoted with)
+    fp64_steps = max(3, min(20, args.steps // 20))
+    ms64 = time_xsec(H, ctx, n, N, sampler, H.HEGET_FP64, fp64_steps, stream, seed=SEED + 5000, i0=i0,
+                     flush=flush)
+
+    # end to end through the public API: heget_xsec per step (launch, fused
+    # RNG -> sampler -> RAMBO -> cuts -> |M|^2 -> sums, result read back to a
+    # host struct, synchronised); the step's inputs are its arguments
+    e2e_seed = SEED + 9000 + (rank << 32)
     for w in range(3):
-        mom_in.copy_(mom_host, non_blocking=True)
-        H.heget_amp2(ctx, n, N, mom_in, amp_dev, precision=H.HEGET_FP32, stream=torch.cuda.current_stream())
-        amp_host.copy_(amp_dev, non_blocking=True)
-    torch.cuda.synchronize()
+        H.heget_xsec(ctx, n, N, e2e_seed + w, sampler, H.HEGET_FP32)
     if ws > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     for k in range(args.e2e_steps):
-        mom_in.copy_(mom_host, non_blocking=True)
-        H.heget_amp2(ctx, n, N, mom_in, amp_dev, precision=H.HEGET_FP32, stream=torch.cuda.current_stream())
-        amp_host.copy_(amp_dev, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        H.heget_xsec(ctx, n, N, e2e_seed + k, sampler, H.HEGET_FP32)
     e2e_s = time.perf_counter() - t0
     if ws > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = t.item()
-    H.heget_check(ctx)
+
+    serving = None
+    if rank == 0 and ws == 1 and not args.no_serving:
+        serving = serving_section(H, ctx)
 
     if rank == 0:
         total_points = N * ws * args.steps
         value = total_points / (step_ms * 1e-3)
+        kern_s = kern_ms / args.steps * 1e-3
         flops = tree_flops_per_point(n) * N
-        achieved = flops / (kern_ms / args.steps * 1e-3) / 1e12
+        achieved = flops / kern_s / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 chain + f64 phase space/accumulation",
             "data": "synthetic (on-device Philox4x32-10 counter RNG from a seed; toy PDF)",
-            "config": {"workload": WORKLOAD, "n": n, "points_per_step": N * ws, "precision": "fp32",
+            "config": {"workload": WORKLOAD if (n, N) == (N_PHOTONS, POINTS) else f"n={n}, {N} points/step, toy PDF",
+                       "n": n, "points_per_step": N * ws, "precision": "fp32",
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": f"dp{ws} (point shards)"},
-            "roofline": {"bound": "alu", "pipe": "fp32 fma", "achieved": achieved, "peak": peak32,
-                         "unit": "TFLOP/s", "frac": achieved / peak32, "traffic": None,
-                         "kernel": "xsec_kernel<float,4,256>",
-                         "flops_per_point": tree_flops_per_point(n),
-                         "peak_source": "measured FFMA throughput (heget_measure_fma_peak, 8 chains/thread)",
-                         "fp64_peak_tflops": peak64},
+            "roofline": roofline(n, N, kern_s, peak32, peak64),
             "gpu_launches": 2 * args.steps,
-            "e2e": {"value": N * ws * args.e2e_steps / e2e_s, "unit": "points/s",
-                    "h2d_bytes_per_step": N * (n + 2) * 4 * 8, "d2h_bytes_per_step": N * 8,
-                    "path": "heget_amp2 (FP32) on pinned host momenta: H2D + kernel + D2H per step"},
+            "e2e": {"value": N * ws * args.e2e_steps / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 80,
+                    "path": "heget_xsec (synchronous public call): inputs (n, N, seed, sampler) travel as launch "
+                            "arguments, the 80-byte result is copied to a host struct every step"},
+            "fp64_plain": {"value": N / (ms64 * 1e-3), "unit": "points/s", "ms_per_step": ms64,
+                           "steps": fp64_steps, "kernel": f"xsec_kernel<double,{n},256>"},
             "kernel_ms_per_step": kern_ms / args.steps,
             "result_last_step": {"sigma_fb": r.sigma_fb, "err_fb": r.err_fb, "n_pass": r.n_pass,
                                  "accept": r.accept},
         }
         if clock_info:
             line["clocks"] = clock_info
+        if serving:
+            line["serving"] = serving
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(n)
+            line["cpu_baseline"] = cpu_baseline(n)[0]
+        if args.matrix:
+            line["matrix"] = matrix_section(H, ctx, stream, peak32, peak64, flush)
         print(json.dumps(line), flush=True)
     H.heget_destroy(ctx)
     if ws > 1:
