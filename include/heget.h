@@ -146,6 +146,19 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta,
                const uint32_t* hel_mask, int precision, double* amp2,
                void* stream);
 
+/* Gauge (Ward) check of the amplitude (the photon wave functions of Sec. 4
+ * are fixed in the light-cone gauge; gauge invariance of the summed
+ * orderings is what the validation of Sec. 5 relies on): for each point,
+ *   ratio[i] = max_h |M_h(eps*_photon -> k_photon / k_photon^0)| / max_h |M_h|
+ * with h over all helicities and the same n! orderings, evaluated in
+ * `precision` from the same records as heget_amp2.  For momenta that conserve
+ * momentum the numerator vanishes up to rounding, so ratio is ~1e-16 in FP64
+ * and ~1e-7 in FP32; a larger value flags broken kinematics or arithmetic.
+ * photon in [0, n); momenta [N][n+2][4]; ratio [N] FP64.  Input checks and
+ * errors as for heget_amp2 (a bad point gets NaN). */
+int heget_ward(heget_ctx* ctx, int n, int64_t N, const double* momenta,
+               int photon, int precision, double* ratio, void* stream);
+
 /* Synchronizes `stream` and reports (then clears) the device-side input
  * flag raised by heget_amp2 / heget_ward: HEGET_EINVAL if set. */
 int heget_check(heget_ctx* ctx, void* stream);

@@ -120,9 +120,11 @@ struct RoundTables {
 // Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Two phases
 // separated by barriers; all threads of the block must call it.  Everything
 // here runs in R: the FP64 content (invariants) is already in the records.
+// ward >= 0 replaces the polarisation of that photon by k/k^0 in every step,
+// closure and first row (the gauge check; both lambda entries then agree).
 template <class R, int N, int BLOCK, int BAR = 0>
 __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, const PointRec<R, N>* recs,
-                                            int cnt) {
+                                            int cnt, int ward = -1) {
     using RT = RoundTables<R, N, BLOCK>;
     constexpr int P = RT::P, K = RT::K, NS = RT::NS;
     const int tid = threadIdx.x;
@@ -189,11 +191,20 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
         const Row<R> sd = tb.SD[p * NS + T];
         // E = eps*(k, lambda) . sigma = (1/sqrt2) [[-l s, -(1 - l c) e^{-i phi}],
         //                                         [(1 + l c) e^{i phi}, l s]]
-        const R e00 = -lam * ph.ar * rs2;
-        const R e11 = -e00;
+        R e00 = -lam * ph.ar * rs2;
+        R e11 = -e00;
         const R am = (R(1) - lam * ph.ai) * rs2, ap = (R(1) + lam * ph.ai) * rs2;
-        const R e01r = -am * ph.br, e01i = am * ph.bi;   // -(1 - l c) e^{-i phi}
-        const R e10r = ap * ph.br, e10i = ap * ph.bi;    //  (1 + l c) e^{+i phi}
+        R e01r = -am * ph.br, e01i = am * ph.bi;   // -(1 - l c) e^{-i phi}
+        R e10r = ap * ph.br, e10i = ap * ph.bi;    //  (1 + l c) e^{+i phi}
+        if (j == ward) {
+            // (k/k^0) . sigma = [[1 - c, -s e^{-i phi}], [-s e^{i phi}, 1 + c]]
+            e00 = R(1) - ph.ai;
+            e11 = R(1) + ph.ai;
+            e01r = -ph.ar * ph.br;
+            e01i = ph.ar * ph.bi;
+            e10r = -ph.ar * ph.br;
+            e10i = -ph.ar * ph.bi;
+        }
         // Qbar = [[A, B*], [B, D]], B = Bre + i Bim
         const R A = sd.ar, D = sd.ai, Br = sd.br, Bi = sd.bi;
         Row<R> m0, m1;
@@ -320,6 +331,51 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, Poin
             }
         }
         group_sync<BAR, BLOCK>();
+    }
+}
+
+// Gauge check rounds over recs[0 .. cnt-1]: for each point the largest
+// |A_h|^2 over the 2^N photon-helicity lanes (s1 = +) of the ordinary tree
+// and of the tree with photon `ward` replaced by k/k^0; stores
+// sqrt(max |W_h|^2 / max |A_h|^2) in recs[p].ssum.  |M_h|^2 of the s1 = -
+// configurations equal those of s1 = + by parity, so the maxima cover all
+// helicities.
+template <class R, int N, int BLOCK>
+__device__ __forceinline__ void ward_rounds(unsigned char* table_smem, PointRec<R, N>* recs, int cnt, int ward) {
+    using RT = RoundTables<R, N, BLOCK>;
+    constexpr int P = RT::P;
+    constexpr int NS = 1 << N;
+    const RT tb(table_smem);
+    const int tid = threadIdx.x;
+    const int slot = tid >> N;
+    LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * slot, (unsigned)(tid & (NS - 1))};
+    for (int base = 0; base < cnt; base += P) {
+        const int rc = min(P, cnt - base);
+        R best[2];
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            setup_round<R, N, BLOCK>(tb, recs + base, rc, pass ? ward : -1);
+            R are = R(0), aim = R(0);
+            const bool active = slot < rc && recs[base + slot].valid;
+            if (active) tree_amplitude<R, N, BLOCK>(L, are, aim);
+            R v = are * are + aim * aim;
+            constexpr int G = NS < 32 ? NS : 32;
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+            if constexpr (NS > 32) {
+                if ((tid & 31) == 0) tb.RED[tid >> 5] = v;
+                __syncthreads();
+                if ((tid & (NS - 1)) == 0)
+                    for (int w = 1; w < NS / 32; ++w) v = fmax(v, tb.RED[(tid >> 5) + w]);
+                __syncthreads();
+            }
+            best[pass] = v;
+        }
+        if ((tid & (NS - 1)) == 0 && slot < rc) {
+            const R a = best[0], w = best[1];
+            recs[base + slot].ssum = a > R(0) ? sqrt(w / a) : (w > R(0) ? R(INFINITY) : R(0));
+        }
+        __syncthreads();
     }
 }
 

@@ -433,6 +433,27 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta, const ui
     return HEGET_OK;
 }
 
+int heget_ward(heget_ctx* ctx, int n, int64_t N, const double* momenta, int photon, int precision, double* ratio,
+               void* stream) {
+    int r = check_common(ctx, n, N);
+    if (r) return r;
+    if ((r = check_precision(precision))) return r;
+    if (photon < 0 || photon >= n) return fail(HEGET_EINVAL, "photon must be in [0, n)");
+    if (N == 0) return HEGET_OK;
+    if (!momenta || !ratio) return fail(HEGET_EINVAL, "momenta and ratio must be non-NULL");
+    if (((uintptr_t)momenta & 15) != 0) return fail(HEGET_EINVAL, "momenta must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    AmpLaunch L;
+    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, false, ctx->tiles[0][precision == HEGET_FP64][n])))
+        return cuda_fail((cudaError_t)r, "occupancy");
+    const Physics ph = physics_of(ctx, n);
+    cudaStream_t st = (cudaStream_t)stream;
+    r = precision == HEGET_FP32 ? launch_ward_f32(n, momenta, N, photon, ratio, ph, ctx->flag, L, st)
+                                : launch_ward_f64(n, momenta, N, photon, ratio, ph, ctx->flag, L, st);
+    if (r) return cuda_fail((cudaError_t)r, "ward_kernel");
+    return HEGET_OK;
+}
+
 int heget_check(heget_ctx* ctx, void* stream) {
     if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
     DeviceGuard g(ctx->device);

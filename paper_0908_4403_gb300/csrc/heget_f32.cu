@@ -11,6 +11,13 @@ int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* ma
 #undef CALL
 }
 
+int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph,
+                    int* flag, const AmpLaunch& L, cudaStream_t st) {
+#define CALL(N) launch_ward_n<float, N>(mom, npts, ward, out, ph, flag, L, st)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
 int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
                     const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
                     cudaStream_t st) {

@@ -105,6 +105,32 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
     }
 }
 
+// Gauge check: ratio[i] = max_h |M_h(eps_w -> k_w/k_w^0)| / max_h |M_h| for
+// the input rows (same staging and records as amp2_kernel).
+template <class R, int N, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+ward_kernel(const double* __restrict__ mom, long long npts, int ward, double* __restrict__ out, int tile,
+            Physics ph, int* __restrict__ flag) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* stage = reinterpret_cast<double*>(smem);
+    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK>(tile));
+    constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
+    for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
+        const int cnt = (int)min((long long)tile, npts - t0);
+        const double* src = mom + (size_t)t0 * ROW;
+        for (int e = threadIdx.x; e < cnt * ROW; e += BLOCK) {
+            const int t = e / ROW;
+            stage[t * SROW + (e - t * ROW)] = __ldg(src + e);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
+        __syncthreads();
+        ward_rounds<R, N, BLOCK>(smem, recs, cnt, ward);
+        for (int t = threadIdx.x; t < cnt; t += BLOCK)
+            out[t0 + t] = recs[t].valid ? (double)recs[t].ssum : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
 // Deterministic block reduction of per-thread partials (shuffle tree, then
 // warp leaders in order).  Uses `scratch` (BLOCK/32 Partials of shared
 // memory); result valid in thread 0.
@@ -377,6 +403,10 @@ int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* ma
                     const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st);
 int launch_amp2_f64(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
                     const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st);
+int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
+                    const AmpLaunch& L, cudaStream_t st);
+int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
+                    const AmpLaunch& L, cudaStream_t st);
 int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
                     const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
                     cudaStream_t st);

@@ -21,6 +21,17 @@ static int launch_amp2_n(const double* mom, long long npts, const uint32_t* mask
 }
 
 template <class R, int N>
+static int launch_ward_n(const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
+                         const AmpLaunch& L, cudaStream_t st) {
+    auto k = ward_kernel<R, N, kBlock>;
+    const size_t smem = amp2_smem_bytes<R, N, kBlock>(L.tile);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k<<<L.grid, kBlock, smem, st>>>(mom, npts, ward, out, L.tile, ph, flag);
+    return (int)cudaGetLastError();
+}
+
+template <class R, int N>
 static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
                          Partial* partials, double* w_out, const AmpLaunch& L, cudaStream_t st) {
     if constexpr (N <= 4 && sizeof(R) == sizeof(float)) {
