@@ -1,0 +1,86 @@
+"""Host logic of the multi-process path: point shards and the one exchange.
+
+Point i of a run depends only on (seed, i), so ranks take contiguous,
+disjoint point ranges and need no communication while they compute.  The
+only exchange is the combination of the per-rank Monte Carlo sums into the
+job's cross section (the summation step of the paper's program, Sec. 3.1,
+spread over processes).  It gathers eight numbers per rank and combines them
+in rank order with error-free transformations, so every rank gets the same
+bits whatever the process timing.
+"""
+from __future__ import annotations
+
+import math
+
+from . import heget as H
+
+
+def shard(N: int, world: int, rank: int) -> tuple[int, int]:
+    """(first point, point count) of `rank` among `world` ranks: contiguous
+    ranges, the first N % world ranks take one extra point."""
+    if world < 1 or not 0 <= rank < world or N < 0:
+        raise ValueError("bad shard request")
+    q, r = divmod(N, world)
+    return rank * q + min(rank, r), q + (1 if rank < r else 0)
+
+
+def _two_sum(a: float, b: float) -> tuple[float, float]:
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def _dd_sum(values) -> float:
+    hi, lo = 0.0, 0.0
+    for v in values:
+        hi, e = _two_sum(hi, v)
+        lo += e
+    return hi + lo
+
+
+def combine(results, sampler_kind: int) -> H.heget_xsec_result:
+    """Merge per-shard results (in the given order) as if one call had
+    processed all their points: sums combined with TwoSum and rounded once,
+    counts added, sigma and its error recomputed with the formulas of
+    heget_xsec (scale 2 x acceptance for the toy PDF)."""
+    sw = _dd_sum(r.sum_w for r in results)
+    sw2 = _dd_sum(r.sum_w2 for r in results)
+    n_total = sum(int(r.n_total) for r in results)
+    n_tries = sum(int(r.n_tries) for r in results)
+    out = H.heget_xsec_result()
+    N = float(n_total)
+    mean = sw / N if n_total > 0 else 0.0
+    var = max(0.0, (sw2 - sw * mean) / (N - 1.0)) if n_total > 1 else 0.0
+    accept = N / n_tries if n_tries > 0 else 1.0
+    scale = 2.0 * accept if sampler_kind == H.HEGET_SAMPLER_TOY_PDF else 1.0
+    out.sigma_fb = scale * mean
+    out.err_fb = scale * math.sqrt(var / N) if n_total > 0 else 0.0
+    out.sum_w, out.sum_w2, out.accept = sw, sw2, accept
+    out.n_pass = sum(int(r.n_pass) for r in results)
+    out.n_total, out.n_tries = n_total, n_tries
+    out.n_escalated = sum(int(r.n_escalated) for r in results)
+    return out
+
+
+def allreduce_result(res: H.heget_xsec_result, sampler_kind: int, group=None) -> H.heget_xsec_result:
+    """The job's result on every rank: all-gather of each rank's sums and
+    counts (8 values) over `group` (any torch.distributed backend), combined
+    in rank order."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    backend = dist.get_backend(group)
+    device = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+    mine = torch.tensor([res.sum_w, res.sum_w2], dtype=torch.float64, device=device)
+    cnt = torch.tensor([res.n_pass, res.n_total, res.n_tries, res.n_escalated], dtype=torch.int64, device=device)
+    fs = [torch.empty_like(mine) for _ in range(world)]
+    cs = [torch.empty_like(cnt) for _ in range(world)]
+    dist.all_gather(fs, mine, group=group)
+    dist.all_gather(cs, cnt, group=group)
+    parts = []
+    for f, c in zip(fs, cs):
+        r = H.heget_xsec_result()
+        r.sum_w, r.sum_w2 = float(f[0]), float(f[1])
+        r.n_pass, r.n_total, r.n_tries, r.n_escalated = (int(x) for x in c.tolist())
+        parts.append(r)
+    return combine(parts, sampler_kind)
