@@ -85,19 +85,45 @@ template <class R> __device__ __forceinline__ R rsq(R x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 
-// Shared-memory tables of one round: P = BLOCK / 2^N points.
+// Lane layout of the tree (a compile-time shape):
+//   * each lane carries H = 2^HB photon-helicity configurations ("rows"), which
+//     differ in the helicities of the top HB photons NB..N-1 (NB = N - HB); one
+//     lane's rows share every table load and all index arithmetic, so the
+//     per-step overhead is spread over H row updates;
+//   * a point's 2^NB lanes form a group; G groups per point split the n(n-1)
+//     depth-2 prefixes between them (a group must fill whole warps, so that a
+//     warp walks one subtree and its table reads stay broadcasts) and add their
+//     partial amplitudes before squaring;
+//   * P = BLOCK / (2^NB G) points share one round of tables.
+// (HB, G) = (0, 1) is one helicity configuration per lane, one group.
+template <int N, int BLOCK, int HB, int G>
+struct TreeShape {
+    static constexpr int H = 1 << HB;
+    static constexpr int NB = N - HB;
+    static constexpr int NSL = 1 << NB;      // lanes of a group
+    static constexpr int LPP = NSL * G;      // lanes of a point
+    static constexpr int P = BLOCK / LPP;    // points per round
+    static_assert(HB >= 0 && HB <= 2 && HB < N, "1, 2 or 4 rows per lane");
+    static_assert(P >= 1 && BLOCK % LPP == 0, "a round holds whole points");
+    static_assert(G == 1 || (NSL >= 32 && N >= 3), "subtree groups fill whole warps");
+};
+
+// Shared-memory tables of one round.
 // Entry layout [index][point][lambda] so that the lanes of a warp, which read
-// one index for up to 32/2^N points and both lambdas, hit distinct banks.
-template <class R, int N, int BLOCK>
+// one index for one or a few points and both lambdas, hit distinct banks.
+template <class R, int N, int BLOCK, int HB = 0, int G = 1>
 struct RoundTables {
-    static constexpr int P = BLOCK >> N;
+    using S = TreeShape<N, BLOCK, HB, G>;
+    static constexpr int P = S::P;
     static constexpr int K = num_pairs(N);
     static constexpr int NS = 1 << N;
     static constexpr size_t m_elems = (size_t)K * P * 2;
     static constexpr size_t c_elems = (size_t)N * P * 2;
+    static constexpr size_t x_elems = G > 1 ? (size_t)BLOCK * S::H * 2 : 0;
     static constexpr size_t bytes = (2 * m_elems + 2 * c_elems) * sizeof(Row<R>)   // M0, M1, CL, R1
                                   + (size_t)P * N * sizeof(Row<R>)                 // photon data
                                   + (size_t)P * NS * sizeof(Row<R>)                // set data
+                                  + x_elems * sizeof(R)                            // group exchange
                                   + (size_t)(BLOCK / 32) * sizeof(R) + 16;         // reduction
     Row<R>* M0;
     Row<R>* M1;
@@ -105,6 +131,7 @@ struct RoundTables {
     Row<R>* R1;
     Row<R>* PH;   // [P][N]: (sin th, cos th, cos ph, sin ph)
     Row<R>* SD;   // [P][2^N]: (A, D, Bre, Bim) = ((q0+q3), (q0-q3), q1, q2) / q^2
+    R* XCH;       // [BLOCK][H][2]: partial amplitudes of the subtree groups
     R* RED;       // [BLOCK/32]
     __device__ __forceinline__ explicit RoundTables(unsigned char* base) {
         M0 = reinterpret_cast<Row<R>*>(base);
@@ -113,7 +140,8 @@ struct RoundTables {
         R1 = CL + c_elems;
         PH = R1 + c_elems;
         SD = PH + (size_t)P * N;
-        RED = reinterpret_cast<R*>(SD + (size_t)P * NS);
+        XCH = reinterpret_cast<R*>(SD + (size_t)P * NS);
+        RED = XCH + x_elems;
     }
 };
 
@@ -122,10 +150,10 @@ struct RoundTables {
 // here runs in R: the FP64 content (invariants) is already in the records.
 // ward >= 0 replaces the polarisation of that photon by k/k^0 in every step,
 // closure and first row (the gauge check; both lambda entries then agree).
-template <class R, int N, int BLOCK, int BAR = 0>
-__device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, const PointRec<R, N>* recs,
+template <class R, int N, int BLOCK, int BAR = 0, int HB = 0, int G = 1>
+__device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G>& tb, const PointRec<R, N>* recs,
                                             int cnt, int ward = -1) {
-    using RT = RoundTables<R, N, BLOCK>;
+    using RT = RoundTables<R, N, BLOCK, HB, G>;
     constexpr int P = RT::P, K = RT::K, NS = RT::NS;
     const int tid = threadIdx.x;
     // (a) photon angles, and propagator data per photon set T:
@@ -231,30 +259,114 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK>& tb, 
 }
 
 // Per-lane view of the round tables.
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, int HB = 0, int G = 1>
 struct LaneTables {
-    static constexpr int P = BLOCK >> N;
+    using S = TreeShape<N, BLOCK, HB, G>;
     const Row<R>* M0;
     const Row<R>* M1;
     const Row<R>* CL;
     const Row<R>* R1;
     int pp;       // 2 * point slot
-    unsigned h;   // photon helicity bits of this lane
-    __device__ __forceinline__ int lam(int j) const { return (h >> j) & 1; }
+    unsigned hl;  // helicity bits of photons 0 .. NB-1 (lambda = bit set -> +1)
 };
 
+// Rows r[b] . M, photon j below NB: every row of the lane has the same lambda.
+template <class R, int H>
+__device__ __forceinline__ void step_same(Row<R> (&o)[H], const Row<R> (&r)[H], const Row<R>& m0, const Row<R>& m1) {
+#pragma unroll
+    for (int b = 0; b < H; ++b) o[b] = row_times(r[b], m0, m1);
+}
+
+// Rows r[b] . M^{lambda_b}, photon NB + JB: row b takes lambda = bit JB of b.
+template <class R, int H, int JB>
+__device__ __forceinline__ void step_split(Row<R> (&o)[H], const Row<R> (&r)[H], const Row<R>& a0, const Row<R>& a1,
+                                           const Row<R>& b0, const Row<R>& b1) {
+#pragma unroll
+    for (int b = 0; b < H; ++b) o[b] = ((b >> JB) & 1) ? row_times(r[b], b0, b1) : row_times(r[b], a0, a1);
+}
+
+// Attach photon j to the rows (table entry index idx).
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ void attach(const LaneTables<R, N, BLOCK, HB, G>& L, int j, int idx,
+                                       const Row<R> (&r)[1 << HB], Row<R> (&o)[1 << HB]) {
+    using S = TreeShape<N, BLOCK, HB, G>;
+    constexpr int H = S::H, NB = S::NB, P = S::P;
+    const int base = idx * P * 2 + L.pp;
+    if (HB == 0 || j < NB) {
+        const int e = base + ((L.hl >> j) & 1);
+        step_same<R, H>(o, r, ld_row(L.M0 + e), ld_row(L.M1 + e));
+    } else {
+        const Row<R> a0 = ld_row(L.M0 + base), a1 = ld_row(L.M1 + base);
+        const Row<R> b0 = ld_row(L.M0 + base + 1), b1 = ld_row(L.M1 + base + 1);
+        if constexpr (HB == 1) {
+            step_split<R, H, 0>(o, r, a0, a1, b0, b1);
+        } else if constexpr (HB == 2) {
+            if (j == NB) step_split<R, H, 0>(o, r, a0, a1, b0, b1);
+            else step_split<R, H, 1>(o, r, a0, a1, b0, b1);
+        }
+    }
+}
+
+// acc[b] += r[b] . c, c = (ca, cb) a column 2-spinor
+template <class R>
+__device__ __forceinline__ void close_row(const Row<R>& r, const Row<R>& c, R& are, R& aim) {
+    are += r.ar * c.ar - r.ai * c.ai + r.br * c.br - r.bi * c.bi;
+    aim += r.ar * c.ai + r.ai * c.ar + r.br * c.bi + r.bi * c.br;
+}
+
+// Closure with the last photon j (iovxx0 against u(p1)).
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ void close_rows(const LaneTables<R, N, BLOCK, HB, G>& L, int j, const Row<R> (&r)[1 << HB],
+                                           R (&are)[1 << HB], R (&aim)[1 << HB]) {
+    using S = TreeShape<N, BLOCK, HB, G>;
+    constexpr int H = S::H, NB = S::NB, P = S::P;
+    const int base = j * P * 2 + L.pp;
+    if (HB == 0 || j < NB) {
+        const Row<R> c = ld_row(L.CL + base + ((L.hl >> j) & 1));
+#pragma unroll
+        for (int b = 0; b < H; ++b) close_row(r[b], c, are[b], aim[b]);
+    } else {
+        const Row<R> c0 = ld_row(L.CL + base), c1 = ld_row(L.CL + base + 1);
+        if (HB == 1 || j == NB) {
+#pragma unroll
+            for (int b = 0; b < H; ++b) close_row(r[b], (b & 1) ? c1 : c0, are[b], aim[b]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < H; ++b) close_row(r[b], ((b >> 1) & 1) ? c1 : c0, are[b], aim[b]);
+        }
+    }
+}
+
+// First rows vbar(p2) . M(j, {j}) for the lane's helicities.
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ void first_rows(const LaneTables<R, N, BLOCK, HB, G>& L, int j, Row<R> (&r)[1 << HB]) {
+    using S = TreeShape<N, BLOCK, HB, G>;
+    constexpr int H = S::H, NB = S::NB, P = S::P;
+    const int base = j * P * 2 + L.pp;
+    if (HB == 0 || j < NB) {
+        const Row<R> a = ld_row(L.R1 + base + ((L.hl >> j) & 1));
+#pragma unroll
+        for (int b = 0; b < H; ++b) r[b] = a;
+    } else {
+        const Row<R> a0 = ld_row(L.R1 + base), a1 = ld_row(L.R1 + base + 1);
+        if (HB == 1 || j == NB) {
+#pragma unroll
+            for (int b = 0; b < H; ++b) r[b] = (b & 1) ? a1 : a0;
+        } else {
+#pragma unroll
+            for (int b = 0; b < H; ++b) r[b] = ((b >> 1) & 1) ? a1 : a0;
+        }
+    }
+}
+
 // Depth-first walk of the ordering tree below a node at depth D (D photons
-// attached, set T, current row r), adding the closures to acc.
-template <class R, int N, int D, int BLOCK>
-__device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK>& L, const Row<R>& r, unsigned T,
-                                        R& acc_re, R& acc_im) {
+// attached, set T, current rows r), adding the closures to acc.
+template <class R, int N, int D, int BLOCK, int HB, int G>
+__device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK, HB, G>& L, const Row<R> (&r)[1 << HB],
+                                        unsigned T, R (&are)[1 << HB], R (&aim)[1 << HB]) {
     constexpr unsigned FULL = (1u << N) - 1;
-    constexpr int P = BLOCK >> N;
     if constexpr (D == N - 1) {
-        const int j = __ffs(FULL & ~T) - 1;
-        const Row<R> c = ld_row(L.CL + (j * P * 2 + L.pp + L.lam(j)));
-        acc_re += r.ar * c.ar - r.ai * c.ai + r.br * c.br - r.bi * c.bi;
-        acc_im += r.ar * c.ai + r.ai * c.ar + r.br * c.bi + r.bi * c.br;
+        close_rows<R, N, BLOCK, HB, G>(L, __ffs(FULL & ~T) - 1, r, are, aim);
     } else {
         unsigned rem = FULL & ~T;
 #pragma unroll 1
@@ -262,28 +374,60 @@ __device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK>& L, const 
             const int j = __ffs(rem) - 1;
             rem &= rem - 1;
             const int idx = c_tables.child[child_offset(N) + T * N + j];
-            const int o = idx * P * 2 + L.pp + L.lam(j);
-            const Row<R> r2 = row_times(r, ld_row(L.M0 + o), ld_row(L.M1 + o));
-            descend<R, N, D + 1, BLOCK>(L, r2, T | (1u << j), acc_re, acc_im);
+            Row<R> r2[1 << HB];
+            attach<R, N, BLOCK, HB, G>(L, j, idx, r, r2);
+            descend<R, N, D + 1, BLOCK, HB, G>(L, r2, T | (1u << j), are, aim);
         }
     }
 }
 
-// The full tree for one lane: sum over all n! orderings of the helicity
-// amplitude (up to normalisation) for photon helicities h, s1 = +.
-template <class R, int N, int BLOCK>
-__device__ __forceinline__ void tree_amplitude(const LaneTables<R, N, BLOCK>& L, R& acc_re, R& acc_im) {
-    constexpr int P = BLOCK >> N;
-    acc_re = R(0);
-    acc_im = R(0);
+// Subtrees below the depth-2 prefixes k = GI, GI + G, ... of the n(n-1)
+// prefixes (j1, j2) in lexicographic order.  GI is a template argument so
+// that every loop bound and table index below stays warp-uniform.
+template <class R, int N, int BLOCK, int HB, int G, int GI>
+__device__ __forceinline__ void tree_group(const LaneTables<R, N, BLOCK, HB, G>& L, R (&are)[1 << HB],
+                                           R (&aim)[1 << HB]) {
+    constexpr int H = 1 << HB;
 #pragma unroll 1
-    for (int j = 0; j < N; ++j) {
-        const Row<R> r1 = ld_row(L.R1 + (j * P * 2 + L.pp + L.lam(j)));
-        descend<R, N, 1, BLOCK>(L, r1, 1u << j, acc_re, acc_im);
+    for (int k = GI; k < N * (N - 1); k += G) {
+        const int j1 = k / (N - 1), t = k - j1 * (N - 1), j2 = t + (t >= j1);
+        Row<R> r1[H], r2[H];
+        first_rows<R, N, BLOCK, HB, G>(L, j1, r1);
+        attach<R, N, BLOCK, HB, G>(L, j2, c_tables.child[child_offset(N) + (1u << j1) * N + j2], r1, r2);
+        descend<R, N, 2, BLOCK, HB, G>(L, r2, (1u << j1) | (1u << j2), are, aim);
     }
 }
 
-// Parity-folded helicity weight of lane h (see file comment).
+// The orderings of group g for one lane: with one group all n! orderings,
+// otherwise the group's share of the depth-2 subtrees (a group is a whole
+// number of warps, so the switch below never diverges inside a warp).  Sums,
+// per row, the helicity amplitude (up to normalisation) for s1 = +.
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ void tree_amplitude(const LaneTables<R, N, BLOCK, HB, G>& L, int g, R (&are)[1 << HB],
+                                               R (&aim)[1 << HB]) {
+    constexpr int H = 1 << HB;
+#pragma unroll
+    for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
+    if constexpr (G == 1) {
+#pragma unroll 1
+        for (int j = 0; j < N; ++j) {
+            Row<R> r1[H];
+            first_rows<R, N, BLOCK, HB, G>(L, j, r1);
+            descend<R, N, 1, BLOCK, HB, G>(L, r1, 1u << j, are, aim);
+        }
+    } else {
+        static_assert(G == 2 || G == 4, "2 or 4 subtree groups");
+        switch (g) {
+            case 0: tree_group<R, N, BLOCK, HB, G, 0>(L, are, aim); break;
+            case 1: tree_group<R, N, BLOCK, HB, G, 1>(L, are, aim); break;
+            case 2: if constexpr (G > 2) tree_group<R, N, BLOCK, HB, G, 2>(L, are, aim); break;
+            default: if constexpr (G > 3) tree_group<R, N, BLOCK, HB, G, 3>(L, are, aim); break;
+        }
+    }
+}
+
+// Parity-folded helicity weight of photon-helicity configuration h (see file
+// comment): w_h = [mask(+,-,h)] + [mask(-,+,~h)], 2 without a mask.
 template <int N>
 __device__ __forceinline__ float lane_weight(const uint32_t* mask, unsigned h) {
     if (!mask) return 2.0f;
@@ -295,48 +439,113 @@ __device__ __forceinline__ float lane_weight(const uint32_t* mask, unsigned h) {
     return (float)(bp + bm);
 }
 
-// Amplitude rounds over recs[0 .. cnt-1].  For each point the lane group's
-// reduction yields S = sum_h w_h |A_h|^2 (scaled units), stored by the
-// group's first thread in recs[p].ssum; the FP64 normalisation and the
-// accumulation are left to whole warps afterwards (one lane per point), so
-// no FP64 instruction here runs with one or two active lanes.
-template <class R, int N, int BLOCK, int BAR = 0>
-__device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, PointRec<R, N>* recs, int cnt, float wh) {
-    using RT = RoundTables<R, N, BLOCK>;
-    constexpr int P = RT::P;
-    constexpr int NS = 1 << N;
+// Lane coordinates in a round: point slot, subtree group, group-local lane.
+template <int N, int BLOCK, int HB, int G>
+struct LaneId {
+    using S = TreeShape<N, BLOCK, HB, G>;
+    int slot, g, hl;
+    __device__ __forceinline__ explicit LaneId(int tid)
+        : slot(tid / S::LPP), g((tid % S::LPP) / S::NSL), hl(tid % S::NSL) {}
+};
+
+// The complete amplitudes of the lane's rows: with several subtree groups,
+// every group leaves its partial sums in shared memory and group 0 adds them
+// (the other groups' amplitudes become 0).  All threads must call it.
+template <class R, int N, int BLOCK, int BAR, int HB, int G>
+__device__ __forceinline__ void combine_groups(const RoundTables<R, N, BLOCK, HB, G>& tb, const LaneId<N, BLOCK, HB, G>& id,
+                                               R (&are)[1 << HB], R (&aim)[1 << HB]) {
+    if constexpr (G > 1) {
+        using S = TreeShape<N, BLOCK, HB, G>;
+        constexpr int H = S::H;
+        R* x = tb.XCH + (size_t)threadIdx.x * H * 2;
+#pragma unroll
+        for (int b = 0; b < H; ++b) {
+            x[2 * b] = are[b];
+            x[2 * b + 1] = aim[b];
+        }
+        group_sync<BAR, BLOCK>();
+        if (id.g == 0) {
+#pragma unroll
+            for (int gg = 1; gg < G; ++gg) {
+                const R* y = tb.XCH + (size_t)(threadIdx.x + gg * S::NSL) * H * 2;
+#pragma unroll
+                for (int b = 0; b < H; ++b) {
+                    are[b] += y[2 * b];
+                    aim[b] += y[2 * b + 1];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
+        }
+    }
+}
+
+// Sum (MAX = false) or maximum (MAX = true) of v over the lanes of each point;
+// the result is valid in the point's first lane.  All threads must call it.
+template <class R, int N, int BLOCK, int BAR, int HB, int G, bool MAX>
+__device__ __forceinline__ R point_reduce(const RoundTables<R, N, BLOCK, HB, G>& tb, R v) {
+    using S = TreeShape<N, BLOCK, HB, G>;
+    constexpr int W = S::LPP < 32 ? S::LPP : 32;
+#pragma unroll
+    for (int off = 1; off < W; off <<= 1) {
+        const R o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = MAX ? fmax(v, o) : v + o;
+    }
+    if constexpr (S::LPP > 32) {
+        const int tid = threadIdx.x;
+        if ((tid & 31) == 0) tb.RED[tid >> 5] = v;
+        group_sync<BAR, BLOCK>();
+        if (tid % S::LPP == 0)
+            for (int w = 1; w < S::LPP / 32; ++w) {
+                const R o = tb.RED[(tid >> 5) + w];
+                v = MAX ? fmax(v, o) : v + o;
+            }
+    }
+    return v;
+}
+
+// Amplitude rounds over recs[0 .. cnt-1].  For each point the lanes' reduction
+// yields S = sum_h w_h |A_h|^2 (scaled units), stored by the point's first
+// lane in recs[p].ssum; the FP64 normalisation and the accumulation are left
+// to whole warps afterwards (one lane per point), so no FP64 instruction here
+// runs with one or two active lanes.  mask: helicity mask (NULL = all).
+template <class R, int N, int BLOCK, int BAR = 0, int HB = 0, int G = 1>
+__device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, PointRec<R, N>* recs, int cnt,
+                                                 const uint32_t* mask) {
+    using RT = RoundTables<R, N, BLOCK, HB, G>;
+    using S = TreeShape<N, BLOCK, HB, G>;
+    constexpr int P = S::P, H = S::H;
     const RT tb(table_smem);
-    const int tid = threadIdx.x;
-    const int slot = tid >> N;
-    LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * slot, (unsigned)(tid & (NS - 1))};
+    const LaneId<N, BLOCK, HB, G> id(threadIdx.x);
+    const LaneTables<R, N, BLOCK, HB, G> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl};
+    float wh[H];
+#pragma unroll
+    for (int b = 0; b < H; ++b) wh[b] = lane_weight<N>(mask, (unsigned)id.hl | ((unsigned)b << S::NB));
     for (int base = 0; base < cnt; base += P) {
         const int rc = min(P, cnt - base);
-        setup_round<R, N, BLOCK, BAR>(tb, recs + base, rc);
-        R are = R(0), aim = R(0);
-        const bool active = slot < rc && recs[base + slot].valid;
-        if (active) tree_amplitude<R, N, BLOCK>(L, are, aim);
-        R v = (are * are + aim * aim) * R(wh);
-        constexpr int G = NS < 32 ? NS : 32;
-#pragma unroll
-        for (int off = 1; off < G; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if constexpr (NS <= 32) {
-            if ((tid & (NS - 1)) == 0 && slot < rc) recs[base + slot].ssum = v;
+        setup_round<R, N, BLOCK, BAR, HB, G>(tb, recs + base, rc);
+        R are[H], aim[H];
+        const bool active = id.slot < rc && recs[base + id.slot].valid;
+        if (active) {
+            tree_amplitude<R, N, BLOCK, HB, G>(L, id.g, are, aim);
         } else {
-            if ((tid & 31) == 0) tb.RED[tid >> 5] = v;
-            group_sync<BAR, BLOCK>();
-            if ((tid & (NS - 1)) == 0 && slot < rc) {
-                R s = R(0);
-                for (int w = 0; w < NS / 32; ++w) s += tb.RED[(tid >> 5) + w];
-                recs[base + slot].ssum = s;
-            }
+#pragma unroll
+            for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
         }
+        combine_groups<R, N, BLOCK, BAR, HB, G>(tb, id, are, aim);
+        R v = R(0);
+#pragma unroll
+        for (int b = 0; b < H; ++b) v += (are[b] * are[b] + aim[b] * aim[b]) * R(wh[b]);
+        v = point_reduce<R, N, BLOCK, BAR, HB, G, false>(tb, v);
+        if (threadIdx.x % S::LPP == 0 && id.slot < rc) recs[base + id.slot].ssum = v;
         group_sync<BAR, BLOCK>();
     }
 }
 
 // Gauge check rounds over recs[0 .. cnt-1]: for each point the largest
-// |A_h|^2 over the 2^N photon-helicity lanes (s1 = +) of the ordinary tree
-// and of the tree with photon `ward` replaced by k/k^0; stores
+// |A_h|^2 over the 2^N photon-helicity configurations (s1 = +) of the
+// ordinary tree and of the tree with photon `ward` replaced by k/k^0; stores
 // sqrt(max |W_h|^2 / max |A_h|^2) in recs[p].ssum.  |M_h|^2 of the s1 = -
 // configurations equal those of s1 = + by parity, so the maxima cover all
 // helicities.
@@ -344,36 +553,23 @@ template <class R, int N, int BLOCK>
 __device__ __forceinline__ void ward_rounds(unsigned char* table_smem, PointRec<R, N>* recs, int cnt, int ward) {
     using RT = RoundTables<R, N, BLOCK>;
     constexpr int P = RT::P;
-    constexpr int NS = 1 << N;
     const RT tb(table_smem);
-    const int tid = threadIdx.x;
-    const int slot = tid >> N;
-    LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * slot, (unsigned)(tid & (NS - 1))};
+    const LaneId<N, BLOCK, 0, 1> id(threadIdx.x);
+    const LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl};
     for (int base = 0; base < cnt; base += P) {
         const int rc = min(P, cnt - base);
         R best[2];
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             setup_round<R, N, BLOCK>(tb, recs + base, rc, pass ? ward : -1);
-            R are = R(0), aim = R(0);
-            const bool active = slot < rc && recs[base + slot].valid;
-            if (active) tree_amplitude<R, N, BLOCK>(L, are, aim);
-            R v = are * are + aim * aim;
-            constexpr int G = NS < 32 ? NS : 32;
-#pragma unroll
-            for (int off = 1; off < G; off <<= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-            if constexpr (NS > 32) {
-                if ((tid & 31) == 0) tb.RED[tid >> 5] = v;
-                __syncthreads();
-                if ((tid & (NS - 1)) == 0)
-                    for (int w = 1; w < NS / 32; ++w) v = fmax(v, tb.RED[(tid >> 5) + w]);
-                __syncthreads();
-            }
-            best[pass] = v;
+            R are[1] = {R(0)}, aim[1] = {R(0)};
+            if (id.slot < rc && recs[base + id.slot].valid) tree_amplitude<R, N, BLOCK, 0, 1>(L, 0, are, aim);
+            best[pass] = point_reduce<R, N, BLOCK, 0, 0, 1, true>(tb, are[0] * are[0] + aim[0] * aim[0]);
+            __syncthreads();
         }
-        if ((tid & (NS - 1)) == 0 && slot < rc) {
+        if (threadIdx.x % (1 << N) == 0 && id.slot < rc) {
             const R a = best[0], w = best[1];
-            recs[base + slot].ssum = a > R(0) ? sqrt(w / a) : (w > R(0) ? R(INFINITY) : R(0));
+            recs[base + id.slot].ssum = a > R(0) ? sqrt(w / a) : (w > R(0) ? R(INFINITY) : R(0));
         }
         __syncthreads();
     }

@@ -13,9 +13,55 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 
 constexpr int kBatchThreads = 256;   // threads of the mixed-n batch kernel
 
+// Tree shape per precision and photon count: 2^HB helicity configurations
+// per lane and G subtree groups per point (see TreeShape).  FP64 keeps one
+// configuration per lane: its DFMA pipe, not instruction issue, is the limit.
+// The FP32 defaults are the fastest of a sweep on GB300 (n = 6, 7: two rows
+// per lane and two subtree groups, +10-18 % over one configuration per lane;
+// n = 5: one configuration per lane, since 16-lane groups share warps).
+// The FP32 shapes can be overridden at build time
+// (-DHEGET_F32_HB_<n>=.. -DHEGET_F32_G_<n>=..).
+#ifndef HEGET_F32_HB_5
+#define HEGET_F32_HB_5 0
+#endif
+#ifndef HEGET_F32_G_5
+#define HEGET_F32_G_5 1
+#endif
+#ifndef HEGET_F32_HB_6
+#define HEGET_F32_HB_6 1
+#endif
+#ifndef HEGET_F32_G_6
+#define HEGET_F32_G_6 2
+#endif
+#ifndef HEGET_F32_HB_7
+#define HEGET_F32_HB_7 1
+#endif
+#ifndef HEGET_F32_G_7
+#define HEGET_F32_G_7 2
+#endif
+#ifndef HEGET_F32_HB_8
+#define HEGET_F32_HB_8 1
+#endif
+#ifndef HEGET_F32_G_8
+#define HEGET_F32_G_8 2
+#endif
+template <int HB_, int G_>
+struct ShapeOf {
+    static constexpr int HB = HB_, G = G_;
+};
+template <class R, int N> struct DefaultShape : ShapeOf<0, 1> {};
+template <> struct DefaultShape<float, 5> : ShapeOf<HEGET_F32_HB_5, HEGET_F32_G_5> {};
+template <> struct DefaultShape<float, 6> : ShapeOf<HEGET_F32_HB_6, HEGET_F32_G_6> {};
+template <> struct DefaultShape<float, 7> : ShapeOf<HEGET_F32_HB_7, HEGET_F32_G_7> {};
+template <> struct DefaultShape<float, 8> : ShapeOf<HEGET_F32_HB_8, HEGET_F32_G_8> {};
+
+// Round-table bytes of the default shape (at least those of one
+// configuration per lane, which the gauge check uses).
 template <class R, int N, int BLOCK>
 __host__ __device__ constexpr size_t table_bytes() {
-    return align16(RoundTables<R, N, BLOCK>::bytes);
+    using SH = DefaultShape<R, N>;
+    constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = RoundTables<R, N, BLOCK>::bytes;
+    return align16(a > b ? a : b);
 }
 
 // Shared memory: [region][records].  The region holds the round tables during
@@ -84,7 +130,7 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
     extern __shared__ __align__(16) unsigned char smem[];
     double* stage = reinterpret_cast<double*>(smem);
     PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK>(tile));
-    const float wh = lane_weight<N>(mask, threadIdx.x & ((1u << N) - 1));
+    using SH = DefaultShape<R, N>;
     constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
@@ -97,7 +143,7 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         __syncthreads();
-        amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, wh);
+        amplitude_rounds<R, N, BLOCK, 0, SH::HB, SH::G>(smem, recs, cnt, mask);
         // one thread per point: FP64 normalisation and a coalesced store
         for (int t = threadIdx.x; t < cnt; t += BLOCK)
             out[t0 + t] = recs[t].valid ? (double)recs[t].ssum * recs[t].fac
@@ -184,7 +230,8 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         acc.ntries += recs[t].tries;
     }
     __syncthreads();
-    amplitude_rounds<R, N, BLOCK>(smem, recs, cnt, lane_weight<N>(nullptr, 0));
+    using SH = DefaultShape<R, N>;
+    amplitude_rounds<R, N, BLOCK, 0, SH::HB, SH::G>(smem, recs, cnt, nullptr);
     // one thread per point (the thread that generated it): weight and
     // double-double accumulation with every lane active
     for (int t = threadIdx.x; t < cnt; t += BLOCK) {
@@ -365,12 +412,11 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
         }
     } else {
         // consumers
-        const float wh = lane_weight<N>(nullptr, 0);
         for (int k = 0; k < count; ++k) {
             const int s = k & 1;
             named_sync(kBarFull + s, kWsThreads);
             const int cnt = (int)min((long long)kWsStage, npts - stage_t0(k));
-            amplitude_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, wh);
+            amplitude_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, nullptr);
             if (k + 2 < count) {
                 __threadfence_block();
                 named_arrive(kBarEmpty + s, kWsThreads);
