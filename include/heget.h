@@ -222,6 +222,22 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0,
 int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
                         void* stream);
 
+/* Ordering-sum algorithm of a context (amp2, xsec, batch, graphs, server).
+ *  HEGET_ALG_TREE (default): the paper's method -- every ordering of the
+ *    photons along the fermion line (Sec. 2.1 eqs. (6)-(8), the permutation
+ *    program of Appendix A.2), each shared ordered prefix computed once.
+ *  HEGET_ALG_SUBSET: the same sum regrouped by the SET of photons attached so
+ *    far (a step's propagator depends on the set, not the order), so that the
+ *    current of each set and helicity assignment is computed once:
+ *    sum_k C(n,k) k 2^k chain steps per point instead of
+ *    2^n sum_l n!/(n-l)!.  Not in the paper; same |M|^2 up to rounding.
+ * heget_ward and heget_xsec_noalloc always use the tree.  EINVAL for an
+ * unknown algorithm; heget_get_algorithm returns -1 for a NULL context. */
+#define HEGET_ALG_TREE 0
+#define HEGET_ALG_SUBSET 1
+int heget_set_algorithm(heget_ctx* ctx, int alg);
+int heget_get_algorithm(const heget_ctx* ctx);
+
 /* Launch shape (this library's knob; the paper's analogue is the register /
  * block-size scan of Sec. 6.1): points per block tile used by heget_amp2
  * (kind 0) or heget_xsec* (kind 1) for n photons at `precision`.  tile = 0

@@ -145,19 +145,14 @@ struct RoundTables {
     }
 };
 
-// Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Two phases
-// separated by barriers; all threads of the block must call it.  Everything
-// here runs in R: the FP64 content (invariants) is already in the records.
-// ward >= 0 replaces the polarisation of that photon by k/k^0 in every step,
-// closure and first row (the gauge check; both lambda entries then agree).
-template <class R, int N, int BLOCK, int BAR = 0, int HB = 0, int G = 1>
-__device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G>& tb, const PointRec<R, N>* recs,
-                                            int cnt, int ward = -1) {
-    using RT = RoundTables<R, N, BLOCK, HB, G>;
-    constexpr int P = RT::P, K = RT::K, NS = RT::NS;
+// Photon data PH[p][j] = (sin th, cos th, cos ph, sin ph) and set data
+// SD[p][T] = (q0+q3, q0-q3, q1, q2) / t_T, q_T = sum_{i in T} k_i - p2, for
+// the points recs[0 .. cnt-1] (P slots).  Everything runs in R: the FP64
+// content (denominators) is already in the records.
+template <class R, int N, int BLOCK, int P>
+__device__ __forceinline__ void setup_photons_and_sets(Row<R>* PH, Row<R>* SD, const PointRec<R, N>* recs, int cnt) {
+    constexpr int NS = 1 << N;
     const int tid = threadIdx.x;
-    // (a) photon angles, and propagator data per photon set T:
-    //     Qbar_T / t_T with t_T summed from the invariants
     constexpr int n_ph = P * N, n_sd = P * NS;
     for (int it = tid; it < n_ph + n_sd; it += BLOCK) {
         if (it < n_ph) {
@@ -179,7 +174,7 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
                 d.br = R(1);
                 d.bi = R(0);
             }
-            tb.PH[p * N + j] = d;
+            PH[p * N + j] = d;
         } else {
             const int r = it - n_ph;
             const int p = r / NS, T = r - p * NS;
@@ -200,12 +195,71 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
             d.ai = (q0 - q3) * it_;
             d.br = q1 * it_;
             d.bi = q2 * it_;
-            tb.SD[p * NS + T] = d;
+            SD[p * NS + T] = d;
         }
     }
+}
+
+// Step matrix M = E Qbar of photon (ph) into set (sd) for lambda = +-1
+// (lam_bit 1/0), with E = eps*(k, lambda) . sigma, or (k/k^0) . sigma for the
+// gauge check; also returns E's first column (the closure against u_R).
+template <class R>
+struct StepMat {
+    Row<R> m0, m1;   // rows (M00, M01), (M10, M11)
+    R e00, e10r, e10i;
+};
+
+template <class R>
+__device__ __forceinline__ StepMat<R> step_matrix(const Row<R>& ph, const Row<R>& sd, int lam_bit, bool ward) {
+    const R rs2 = R(0.70710678118654752440);
+    const R lam = lam_bit ? R(1) : R(-1);
+    // E = eps*(k, lambda) . sigma = (1/sqrt2) [[-l s, -(1 - l c) e^{-i phi}],
+    //                                         [(1 + l c) e^{i phi}, l s]]
+    R e00 = -lam * ph.ar * rs2;
+    R e11 = -e00;
+    const R am = (R(1) - lam * ph.ai) * rs2, ap = (R(1) + lam * ph.ai) * rs2;
+    R e01r = -am * ph.br, e01i = am * ph.bi;   // -(1 - l c) e^{-i phi}
+    R e10r = ap * ph.br, e10i = ap * ph.bi;    //  (1 + l c) e^{+i phi}
+    if (ward) {
+        // (k/k^0) . sigma = [[1 - c, -s e^{-i phi}], [-s e^{i phi}, 1 + c]]
+        e00 = R(1) - ph.ai;
+        e11 = R(1) + ph.ai;
+        e01r = -ph.ar * ph.br;
+        e01i = ph.ar * ph.bi;
+        e10r = -ph.ar * ph.br;
+        e10i = -ph.ar * ph.bi;
+    }
+    // Qbar = [[A, B*], [B, D]], B = Bre + i Bim
+    const R A = sd.ar, D = sd.ai, Br = sd.br, Bi = sd.bi;
+    StepMat<R> o;
+    o.m0.ar = e00 * A + e01r * Br - e01i * Bi;   // M00 = e00 A + e01 B
+    o.m0.ai = e01r * Bi + e01i * Br;
+    o.m0.br = e00 * Br + e01r * D;               // M01 = e00 B* + e01 D
+    o.m0.bi = -e00 * Bi + e01i * D;
+    o.m1.ar = e10r * A + e11 * Br;               // M10 = e10 A + e11 B
+    o.m1.ai = e10i * A + e11 * Bi;
+    o.m1.br = e10r * Br + e10i * Bi + e11 * D;   // M11 = e10 B* + e11 D
+    o.m1.bi = e10i * Br - e10r * Bi;
+    o.e00 = e00;
+    o.e10r = e10r;
+    o.e10i = e10i;
+    return o;
+}
+
+// Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Two phases
+// separated by barriers; all threads of the block must call it.  Everything
+// here runs in R: the FP64 content (invariants) is already in the records.
+// ward >= 0 replaces the polarisation of that photon by k/k^0 in every step,
+// closure and first row (the gauge check; both lambda entries then agree).
+template <class R, int N, int BLOCK, int BAR = 0, int HB = 0, int G = 1>
+__device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G>& tb, const PointRec<R, N>* recs,
+                                            int cnt, int ward = -1) {
+    using RT = RoundTables<R, N, BLOCK, HB, G>;
+    constexpr int P = RT::P, K = RT::K, NS = RT::NS;
+    const int tid = threadIdx.x;
+    setup_photons_and_sets<R, N, BLOCK, P>(tb.PH, tb.SD, recs, cnt);
     group_sync<BAR, BLOCK>();
     // (b) step matrices M(j, T) = E_j^lambda Qbar_T, closures and first rows
-    const R rs2 = R(0.70710678118654752440);
     for (int it = tid; it < P * K * 2; it += BLOCK) {
         const int lam_bit = it & 1;
         const int q = it >> 1;
@@ -214,36 +268,10 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
         if (p >= cnt) continue;
         const uint16_t pr = c_tables.pair[pair_offset(N) + idx];
         const int T = pr & 0xFF, j = pr >> 8;
-        const R lam = lam_bit ? R(1) : R(-1);
-        const Row<R> ph = tb.PH[p * N + j];
-        const Row<R> sd = tb.SD[p * NS + T];
-        // E = eps*(k, lambda) . sigma = (1/sqrt2) [[-l s, -(1 - l c) e^{-i phi}],
-        //                                         [(1 + l c) e^{i phi}, l s]]
-        R e00 = -lam * ph.ar * rs2;
-        R e11 = -e00;
-        const R am = (R(1) - lam * ph.ai) * rs2, ap = (R(1) + lam * ph.ai) * rs2;
-        R e01r = -am * ph.br, e01i = am * ph.bi;   // -(1 - l c) e^{-i phi}
-        R e10r = ap * ph.br, e10i = ap * ph.bi;    //  (1 + l c) e^{+i phi}
-        if (j == ward) {
-            // (k/k^0) . sigma = [[1 - c, -s e^{-i phi}], [-s e^{i phi}, 1 + c]]
-            e00 = R(1) - ph.ai;
-            e11 = R(1) + ph.ai;
-            e01r = -ph.ar * ph.br;
-            e01i = ph.ar * ph.bi;
-            e10r = -ph.ar * ph.br;
-            e10i = -ph.ar * ph.bi;
-        }
-        // Qbar = [[A, B*], [B, D]], B = Bre + i Bim
-        const R A = sd.ar, D = sd.ai, Br = sd.br, Bi = sd.bi;
-        Row<R> m0, m1;
-        m0.ar = e00 * A + e01r * Br - e01i * Bi;   // M00 = e00 A + e01 B
-        m0.ai = e01r * Bi + e01i * Br;
-        m0.br = e00 * Br + e01r * D;               // M01 = e00 B* + e01 D
-        m0.bi = -e00 * Bi + e01i * D;
-        m1.ar = e10r * A + e11 * Br;               // M10 = e10 A + e11 B
-        m1.ai = e10i * A + e11 * Bi;
-        m1.br = e10r * Br + e10i * Bi + e11 * D;   // M11 = e10 B* + e11 D
-        m1.bi = e10i * Br - e10r * Bi;
+        const StepMat<R> sm = step_matrix<R>(tb.PH[p * N + j], tb.SD[p * NS + T], lam_bit, j == ward);
+        const Row<R>& m0 = sm.m0;
+        const Row<R>& m1 = sm.m1;
+        const R e00 = sm.e00, e10r = sm.e10r, e10i = sm.e10i;
         const size_t o = ((size_t)idx * P + p) * 2 + lam_bit;
         st_row(tb.M0 + o, m0);
         st_row(tb.M1 + o, m1);

@@ -252,7 +252,11 @@ Physics physics_of(const heget_params& p, int n) {
     return ph;
 }
 
-Physics physics_of(const heget_ctx* c, int n) { return physics_of(c->params, n); }
+Physics physics_of(const heget_ctx* c, int n) {
+    Physics ph = physics_of(c->params, n);
+    ph.alg = c->alg;
+    return ph;
+}
 
 int check_sampler(const heget_sampler* s) {
     if (!s) return fail(HEGET_EINVAL, "sampler is NULL");
@@ -355,6 +359,15 @@ int heget_set_tile(heget_ctx* ctx, int n, int precision, int kind, int tile) {
     ctx->tiles[kind][precision == HEGET_FP64][n] = tile;
     return HEGET_OK;
 }
+
+int heget_set_algorithm(heget_ctx* ctx, int alg) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (alg != HEGET_ALG_TREE && alg != HEGET_ALG_SUBSET) return fail(HEGET_EINVAL, "unknown algorithm %d", alg);
+    ctx->alg = alg;
+    return HEGET_OK;
+}
+
+int heget_get_algorithm(const heget_ctx* ctx) { return ctx ? ctx->alg : -1; }
 
 int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind) {
     if (!ctx || n < kMinN || n > kMaxN || (kind != 0 && kind != 1)) return -1;

@@ -46,6 +46,7 @@ struct heget_ctx {
     int last_kind = 0;                // its sampler kind
     bool last_ws = false;             // it used the warp-specialised kernel
     int tiles[2][2][heget::kMaxN + 1] = {};  // [amp2|xsec][fp32|fp64][n] tile overrides (0 = default)
+    int alg = 0;                      // ordering sum: HEGET_ALG_TREE or HEGET_ALG_SUBSET
     // mixed-n batch workspace (grown on demand)
     unsigned char* batch_host = nullptr;   // pinned staging of work items + request table
     unsigned char* batch_dev = nullptr;

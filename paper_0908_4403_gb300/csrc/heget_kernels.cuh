@@ -5,7 +5,7 @@
 // plus the launch-shape bookkeeping shared with the host code.
 #pragma once
 
-#include "heget_amp.cuh"
+#include "heget_subset.cuh"
 
 namespace heget {
 
@@ -61,7 +61,22 @@ template <class R, int N, int BLOCK>
 __host__ __device__ constexpr size_t table_bytes() {
     using SH = DefaultShape<R, N>;
     constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = RoundTables<R, N, BLOCK>::bytes;
-    return align16(a > b ? a : b);
+    constexpr size_t c = SubsetTables<R, N, BLOCK>::bytes;
+    constexpr size_t ab = a > b ? a : b;
+    return align16(ab > c ? ab : c);
+}
+
+// The amplitude rounds of the context's ordering-sum algorithm (uniform per
+// launch): the prefix tree of the paper's method, or the subset recursion.
+template <class R, int N, int BLOCK, int BAR = 0>
+__device__ __forceinline__ void amp_rounds(unsigned char* smem, PointRec<R, N>* recs, int cnt, const uint32_t* mask,
+                                           int alg) {
+    if (alg == kAlgSubset) {
+        amplitude_rounds_subset<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
+    } else {
+        using SH = DefaultShape<R, N>;
+        amplitude_rounds<R, N, BLOCK, BAR, SH::HB, SH::G>(smem, recs, cnt, mask);
+    }
 }
 
 // Shared memory: [region][records].  The region holds the round tables during
@@ -130,7 +145,6 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
     extern __shared__ __align__(16) unsigned char smem[];
     double* stage = reinterpret_cast<double*>(smem);
     PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK>(tile));
-    using SH = DefaultShape<R, N>;
     constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
@@ -143,7 +157,7 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         __syncthreads();
-        amplitude_rounds<R, N, BLOCK, 0, SH::HB, SH::G>(smem, recs, cnt, mask);
+        amp_rounds<R, N, BLOCK>(smem, recs, cnt, mask, ph.alg);
         // one thread per point: FP64 normalisation and a coalesced store
         for (int t = threadIdx.x; t < cnt; t += BLOCK)
             out[t0 + t] = recs[t].valid ? (double)recs[t].ssum * recs[t].fac
@@ -230,8 +244,7 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         acc.ntries += recs[t].tries;
     }
     __syncthreads();
-    using SH = DefaultShape<R, N>;
-    amplitude_rounds<R, N, BLOCK, 0, SH::HB, SH::G>(smem, recs, cnt, nullptr);
+    amp_rounds<R, N, BLOCK>(smem, recs, cnt, nullptr, ph.alg);
     // one thread per point (the thread that generated it): weight and
     // double-double accumulation with every lane active
     for (int t = threadIdx.x; t < cnt; t += BLOCK) {
@@ -416,7 +429,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             const int s = k & 1;
             named_sync(kBarFull + s, kWsThreads);
             const int cnt = (int)min((long long)kWsStage, npts - stage_t0(k));
-            amplitude_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, nullptr);
+            amp_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, nullptr, ph.alg);
             if (k + 2 < count) {
                 __threadfence_block();
                 named_arrive(kBarEmpty + s, kWsThreads);

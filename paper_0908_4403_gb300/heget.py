@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libheget.so")
 HEGET_OK, HEGET_EINVAL, HEGET_ENOMEM, HEGET_ECUDA, HEGET_ETIMEOUT, HEGET_EBUSY, HEGET_ENOTFOUND = range(7)
 HEGET_FP32, HEGET_FP64 = 32, 64
 HEGET_SAMPLER_FIXED, HEGET_SAMPLER_UNIFORM, HEGET_SAMPLER_TOY_PDF = 0, 1, 2
+HEGET_ALG_TREE, HEGET_ALG_SUBSET = 0, 1
 
 STATUS_NAMES = {0: "HEGET_OK", 1: "HEGET_EINVAL", 2: "HEGET_ENOMEM", 3: "HEGET_ECUDA",
                 4: "HEGET_ETIMEOUT", 5: "HEGET_EBUSY", 6: "HEGET_ENOTFOUND"}
@@ -109,6 +110,8 @@ SIGNATURES = {
     "heget_graph_launch": (I32, [P, U64, I64, P]),
     "heget_graph_destroy": (None, [P]),
     "heget_set_tile": (I32, [P, I32, I32, I32, I32]),
+    "heget_set_algorithm": (I32, [P, I32]),
+    "heget_get_algorithm": (I32, [P]),
     "heget_get_tile": (I32, [P, I32, I32, I32]),
     "heget_xsec_noalloc": (I32, [I32, I32, U64, I64, I64, C.POINTER(heget_sampler), C.POINTER(heget_params),
                                  I32, P, P]),
@@ -275,6 +278,14 @@ def heget_graph_launch(graph, seed, i0=0, stream=None):
 
 def heget_graph_destroy(graph):
     load().heget_graph_destroy(graph)
+
+
+def heget_set_algorithm(ctx, alg):
+    _check(load().heget_set_algorithm(ctx, alg))
+
+
+def heget_get_algorithm(ctx) -> int:
+    return load().heget_get_algorithm(ctx)
 
 
 def heget_set_tile(ctx, n, precision, kind, tile):
