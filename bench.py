@@ -59,7 +59,7 @@ def roofline(n, N, kern_s, peak32_meas, peak64_meas):
     fp32 = {"pipe": "fp32 fma", "achieved": tree, "peak": FP32_PEAK, "frac": tree / FP32_PEAK,
             "flops_per_point": tree_flops_per_point(n), "measured_peak": peak32_meas,
             "frac_of_measured": tree / peak32_meas}
-    kern = f"xsec_ws_kernel<float,{n}>" if n <= 4 else f"xsec_kernel<float,{n},256>"
+    kern = f"xsec_ws_kernel<float,{n}>" if n <= 5 else f"xsec_kernel<float,{n},256>"
     if n in FP64_FLOPS_PER_POINT:
         a64 = FP64_FLOPS_PER_POINT[n] * N / kern_s / 1e12
         return {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": FP64_PEAK, "unit": "TFLOP/s",
@@ -69,6 +69,13 @@ def roofline(n, N, kern_s, peak32_meas, peak64_meas):
                 "measured_peak": peak64_meas, "frac_of_measured": a64 / peak64_meas, "fp32_tree": fp32}
     return {"bound": "alu", **fp32, "unit": "TFLOP/s", "traffic": None, "kernel": kern,
             "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz"}
+
+
+def subset_flops_per_point(n: int) -> int:
+    """FP32 flops of the subset recursion per point: sum_k C(n,k) k 2^k chain
+    steps (acc += r . M, 16 FMA = 32 flops) and n 2^n closure terms (8 FMA)."""
+    steps = sum(math.comb(n, k) * k * (1 << k) for k in range(2, n))
+    return 32 * steps + 16 * n * (1 << n)
 
 
 def tree_flops_per_point(n: int) -> int:
@@ -281,7 +288,15 @@ def run_sequential(H, ctx, trace, precision=None):
     return {"points_per_s": sum(q["N"] for q in trace) / dt, "span_s": dt}
 
 
-def serving_section(H, ctx, R=400, rate=200.0):
+def serving_section(H, ctx, R=400, rate=200.0, alg=0):
+    H.heget_set_algorithm(ctx, alg)
+    try:
+        return _serving_section(H, ctx, R, rate)
+    finally:
+        H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
+
+
+def _serving_section(H, ctx, R, rate):
     trace = serving_trace(R, rate)
     warm = serving_trace(40, 2000.0, seed=0x3A11)
     run_serving(H, ctx, warm, open_loop=False)
@@ -332,6 +347,10 @@ def matrix_section(H, ctx, stream, peak32, peak64, flush):
         H.heget_set_params(ctx, pt_min=cut[0], eta_max=cut[1], dr_min=cut[2])
         ms32 = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3 if n < 8 else 1, stream, flush=flush)
         ms64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 3 if n < 8 else 1, stream, flush=flush)
+        H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
+        ms32s = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3, stream, flush=flush)
+        ms64s = time_xsec(H, ctx, n, N, S, H.HEGET_FP64, 3, stream, flush=flush)
+        H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
         base, w_or = cpu_baseline(n, seconds=8.0, sampler=OS, cut=O.cuts(*cut), N_cap=4096)
         M = len(w_or)
         errs = {}
@@ -355,6 +374,9 @@ def matrix_section(H, ctx, stream, peak32, peak64, flush):
                     "err_sample_points": M,
                     "fp32_tree_frac_of_fp32_fma_peak": tf * N / (ms32 * 1e-3) / (peak32 * 1e12),
                     "fp64_tree_frac_of_fp64_fma_peak": tf * n64 / (ms64 * 1e-3) / (peak64 * 1e12),
+                    "subset_fp32_points_per_s": N / (ms32s * 1e-3), "subset_fp64_points_per_s": N / (ms64s * 1e-3),
+                    "subset_flops_per_point": subset_flops_per_point(n),
+                    "subset_fp32_frac_of_fp32_peak": subset_flops_per_point(n) * N / (ms32s * 1e-3) / (FP32_PEAK * 1e12),
                     "oracle": base})
     H.heget_set_params(ctx)
     return out
@@ -446,6 +468,14 @@ def main():
     ms64 = time_xsec(H, ctx, n, N, sampler, H.HEGET_FP64, fp64_steps, stream, seed=SEED + 5000, i0=i0,
                      flush=flush)
 
+    # the same workload with the subset recursion (not the paper's method)
+    H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
+    ms_sub = time_xsec(H, ctx, n, N, sampler, H.HEGET_FP32, max(5, min(50, args.steps // 8)), stream,
+                       seed=SEED + 7000, i0=i0, flush=flush)
+    ms_sub64 = time_xsec(H, ctx, n, N, sampler, H.HEGET_FP64, fp64_steps, stream, seed=SEED + 7500, i0=i0,
+                         flush=flush)
+    H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
+
     # end to end through the public API: heget_xsec per step (launch, fused
     # RNG -> sampler -> RAMBO -> cuts -> |M|^2 -> sums, result read back to a
     # host struct, synchronised); the step's inputs are its arguments
@@ -466,6 +496,7 @@ def main():
     serving = None
     if rank == 0 and ws == 1 and not args.no_serving:
         serving = serving_section(H, ctx)
+        serving["subset_recursion"] = serving_section(H, ctx, alg=H.HEGET_ALG_SUBSET)
 
     if rank == 0:
         total_points = N * ws * args.steps
@@ -490,6 +521,10 @@ def main():
                             "arguments, the 80-byte result is copied to a host struct every step"},
             "fp64_plain": {"value": N / (ms64 * 1e-3), "unit": "points/s", "ms_per_step": ms64,
                            "steps": fp64_steps, "kernel": f"xsec_kernel<double,{n},256>"},
+            "subset_recursion": {"fp32_points_per_s": N * ws / (ms_sub * 1e-3),
+                                 "fp64_points_per_s": N * ws / (ms_sub64 * 1e-3),
+                                 "note": "HEGET_ALG_SUBSET on the same workload: the ordering sum regrouped by "
+                                         "photon set (not the paper's method; same |M|^2)"},
             "kernel_ms_per_step": kern_ms / args.steps,
             "result_last_step": {"sigma_fb": r.sigma_fb, "err_fb": r.err_fb, "n_pass": r.n_pass,
                                  "accept": r.accept},

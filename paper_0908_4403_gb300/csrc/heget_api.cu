@@ -189,15 +189,16 @@ int default_tile(int n, bool xsec) {
     return xsec ? xsec_tile[n] : amp2_tile[n];
 }
 
-int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile) {
-    L->ws = use_ws(n, precision, xsec) && tile <= 0;   // an explicit tile selects the plain kernel
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile,
+                       int alg) {
+    L->ws = use_ws(n, precision, xsec, alg) && tile <= 0;   // an explicit tile selects the plain kernel
     int bpsm = 1;
     size_t smem = 0;
     if (L->ws) {
         // warp-specialised: fixed stage size, one resident wave of blocks that
         // each pipeline many stages
-        L->block = kWsThreads;
-        L->tile = kWsStage;
+        L->block = kWsConsumers + ws_stage(n);
+        L->tile = ws_stage(n);
         const int e = occupancy_ws_f32(n, &bpsm, &smem);
         if (e) return e;
         if (bpsm < 1) bpsm = 1;
@@ -494,7 +495,8 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L, true, ctx->tiles[1][precision == HEGET_FP64][n])))
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L, true, ctx->tiles[1][precision == HEGET_FP64][n],
+                                ctx->alg)))
         return cuda_fail((cudaError_t)r, "occupancy");
     const Physics ph = physics_of(ctx, n);
     const SamplerArgs S = sampler_args(smp);
@@ -766,7 +768,9 @@ extern "C" int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, 
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true, 0)))
+    // warp-specialised only up to n = 4 (one resident wave, any N); above, the
+    // tile kernel with its default tile, whose grid bounds N
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true, n <= 4 ? 0 : default_tile(n, true))))
         return cuda_fail((cudaError_t)r, "occupancy");
     if (N > 0 && L.grid > kNoAllocMaxBlocks)
         return fail(HEGET_EINVAL,

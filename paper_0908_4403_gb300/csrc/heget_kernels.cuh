@@ -331,28 +331,32 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 }
 
 // ---------------------------------------------------------------------------
-// Warp-specialised fused kernel (FP32 chain, n <= 4).
+// Warp-specialised fused kernel (FP32 chain).
 //
-// GB300 runs FP64 at ~1/64 of the FP32 rate and with long latency, so at small
-// n the FP64 event generation (RAMBO, cuts, denominators) costs more than the
-// FP32 tree and needs many warps in flight.  Each block therefore splits into
+// GB300 runs FP64 at ~1/64 of the FP32 rate and with long latency, so the FP64
+// event generation (RAMBO, cuts, denominators) costs more than the FP32
+// amplitudes at small n (and at every n with the subset recursion) and needs
+// many events in flight while the amplitudes run.  Each block therefore splits into
 // roles that run concurrently:
 //   warps 0..7  (256 threads): consumers -- the amplitude rounds of the tree;
-//   warps 8..11 (128 threads): producers -- one event per thread per stage.
-// Producers fill a double-buffered ring of kWsStage point records in shared
+//   warps 8..   (ws_stage(n) threads): producers -- one event per thread per stage.
+// Producers fill a double-buffered ring of ws_stage(n) point records in shared
 // memory; the two roles hand stages over through named barriers
 //   FULL[s]  (bar.arrive by producers, bar.sync by consumers) and
 //   EMPTY[s] (bar.arrive by consumers, bar.sync by producers),
 // while the consumers' own rounds synchronise on barrier kBarRounds.  Every
 // thread of both roles runs the same number of stages, so each barrier
-// instance collects exactly kWsThreads arrivals.  A block walks tiles
+// instance collects exactly 256 + ws_stage(n) arrivals.  A block walks tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the grid is sized to the resident
 // blocks so that each block pipelines many stages.
 // ---------------------------------------------------------------------------
 constexpr int kWsConsumers = 256;
-constexpr int kWsStage = 128;                        // producers = points per stage
-constexpr int kWsThreads = kWsConsumers + kWsStage;
 constexpr int kBarRounds = 1, kBarFull = 2, kBarEmpty = 4;   // named barrier ids (2,3 / 4,5)
+
+// Points per stage (= producer threads, a multiple of 32): as many as the
+// shared memory of the ring, the producers' staging and the round tables
+// allows at two (n <= 6) or one (n >= 7) resident blocks per SM.
+__host__ __device__ constexpr int ws_stage(int n) { return n <= 4 ? 128 : n == 5 ? 64 : 32; }
 
 __device__ __forceinline__ void named_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -367,17 +371,23 @@ __host__ __device__ constexpr size_t ws_recs_offset() {
 }
 template <class R, int N>
 __host__ __device__ constexpr size_t ws_stage_offset() {
-    return ws_recs_offset<R, N>() + 2 * align16((size_t)kWsStage * sizeof(PointRec<R, N>));
+    return ws_recs_offset<R, N>() + 2 * align16((size_t)ws_stage(N) * sizeof(PointRec<R, N>));
 }
 template <class R, int N>
 __host__ __device__ constexpr size_t ws_smem_bytes() {
-    return ws_stage_offset<R, N>() + align16((size_t)kWsStage * N * kMomSlots * sizeof(double));
+    return ws_stage_offset<R, N>() + align16((size_t)ws_stage(N) * N * kMomSlots * sizeof(double));
+}
+template <class R, int N>
+__host__ __device__ constexpr int ws_min_blocks() {
+    return ws_smem_bytes<R, N>() <= 113 * 1024 ? 2 : 1;
 }
 
 template <class R, int N>
-__global__ void __launch_bounds__(kWsThreads, 2)
+__global__ void __launch_bounds__(kWsConsumers + ws_stage(N), ws_min_blocks<R, N>())
 xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph,
                Partial* __restrict__ partials, double* __restrict__ w_out) {
+    constexpr int kWsStage = ws_stage(N);
+    constexpr int kWsThreads = kWsConsumers + kWsStage;
     extern __shared__ __align__(16) unsigned char smem[];
     PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N>());
     constexpr size_t ring_stride = align16((size_t)kWsStage * sizeof(PointRec<R, N>)) / sizeof(PointRec<R, N>);
@@ -452,10 +462,16 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
 struct AmpLaunch {
     int block, tile, grid;
     size_t smem;
-    bool ws;   // warp-specialised xsec kernel (FP32, n <= 4)
+    bool ws;   // warp-specialised xsec kernel (FP32)
 };
 
-constexpr bool use_ws(int n, int precision, bool xsec) { return xsec && precision == HEGET_FP32 && n <= 4; }
+// The warp-specialised kernel runs FP32 cross sections where the FP64 event
+// generation is a large share of the work: n <= 5 with the tree, every n with
+// the subset recursion.  The tree at n >= 6 spends nearly all its time in the
+// amplitudes and runs faster on the tile kernel, at more blocks per SM.
+constexpr bool use_ws(int n, int precision, bool xsec, int alg) {
+    return xsec && precision == HEGET_FP32 && (n <= 5 || alg == kAlgSubset);
+}
 
 // Returns cudaError_t as int.
 int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
@@ -482,6 +498,7 @@ int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, si
 int launch_batch_finalize(const BatchReq* reqs, int nreqs, cudaStream_t st);
 // Default launch shape and the maximum resident blocks per SM.
 int default_tile(int n, bool xsec);
-int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile);
+int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile,
+                       int alg = kAlgTree);
 
 }  // namespace heget

@@ -34,13 +34,13 @@ static int launch_ward_n(const double* mom, long long npts, int ward, double* ou
 template <class R, int N>
 static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
                          Partial* partials, double* w_out, const AmpLaunch& L, cudaStream_t st) {
-    if constexpr (N <= 4 && sizeof(R) == sizeof(float)) {
+    if constexpr (sizeof(R) == sizeof(float)) {
         if (L.ws) {
             auto k = xsec_ws_kernel<R, N>;
             const size_t smem = ws_smem_bytes<R, N>();
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return (int)e;
-            k<<<L.grid, kWsThreads, smem, st>>>(seed, i0, npts, S, ph, partials, w_out);
+            k<<<L.grid, kWsConsumers + ws_stage(N), smem, st>>>(seed, i0, npts, S, ph, partials, w_out);
             return (int)cudaGetLastError();
         }
     }
@@ -64,18 +64,12 @@ static int occupancy_n(int tile, int* blocks_per_sm, size_t* smem_out) {
 
 template <int N>
 static int occupancy_ws_n(int* blocks_per_sm, size_t* smem_out) {
-    if constexpr (N <= 4) {
-        const size_t smem = ws_smem_bytes<float, N>();
-        *smem_out = smem;
-        auto k = xsec_ws_kernel<float, N>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return (int)e;
-        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kWsThreads, smem);
-    } else {
-        *blocks_per_sm = 0;
-        *smem_out = 0;
-        return (int)cudaErrorInvalidValue;
-    }
+    const size_t smem = ws_smem_bytes<float, N>();
+    *smem_out = smem;
+    auto k = xsec_ws_kernel<float, N>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kWsConsumers + ws_stage(N), smem);
 }
 
 template <class R>
