@@ -512,6 +512,8 @@ def main():
             "config": {"workload": WORKLOAD if (n, N) == (N_PHOTONS, POINTS) else f"n={n}, {N} points/step, toy PDF",
                        "n": n, "points_per_step": N * ws, "precision": "fp32",
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "compaction": "value counts every generated point; |M|^2 is evaluated for the points that "
+                                     "pass the cuts (the others have weight 0), see pass_fraction",
                        "parallelism": f"dp{ws} (point shards)"},
             "roofline": roofline(n, N, kern_s, peak32, peak64),
             "gpu_launches": 2 * args.steps,
@@ -527,7 +529,7 @@ def main():
                                          "photon set (not the paper's method; same |M|^2)"},
             "kernel_ms_per_step": kern_ms / args.steps,
             "result_last_step": {"sigma_fb": r.sigma_fb, "err_fb": r.err_fb, "n_pass": r.n_pass,
-                                 "accept": r.accept},
+                                 "accept": r.accept, "pass_fraction": r.n_pass / max(1, r.n_total)},
         }
         if clock_info:
             line["clocks"] = clock_info

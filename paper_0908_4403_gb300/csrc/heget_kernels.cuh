@@ -224,34 +224,74 @@ __device__ __forceinline__ Partial zero_partial() {
     return p;
 }
 
+// Ordered compaction: the position of this thread's flagged item among the
+// flagged items of the calling threads (in thread order), and their total.
+// All THREADS threads (whole warps, local ids 0 .. THREADS-1) must call it;
+// they synchronise on __syncthreads (bar = 0) or on named barrier `bar`.
+// cnts: THREADS/32 ints of shared memory.
+template <int THREADS>
+__device__ __forceinline__ int compact_pos(bool flag, int local, int* cnts, int bar, int& total) {
+    const unsigned b = __ballot_sync(0xffffffffu, flag);
+    const int warp = local >> 5, lane = local & 31;
+    if (lane == 0) cnts[warp] = __popc(b);
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(THREADS) : "memory");
+    int before = 0;
+    total = 0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) {
+        const int c = cnts[w];
+        before += w < warp ? c : 0;
+        total += c;
+    }
+    if (bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(THREADS) : "memory");
+    return before + __popc(b & ((1u << lane) - 1u));
+}
+
 // One tile of the fused path: points first .. first+cnt-1 (cnt <= tile) of
-// stream `seed` are generated (one thread per point), their amplitudes
-// computed in rounds, and their weights folded into acc by the thread that
-// generated each point.  w_out (may be NULL) receives the tile's weights.
+// stream `seed` are generated (one thread per point).  Only points that pass
+// the cuts get a record, compacted in point order (a point that fails has
+// weight 0 and needs no amplitude); their amplitudes are computed in rounds
+// and their weights folded into acc.  w_out (may be NULL) receives the
+// tile's weights (0 for points that fail the cuts).
 template <class R, int N, int BLOCK>
 __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_t seed, long long first, int cnt,
                                           const SamplerArgs& S, const Physics& ph, Partial& acc,
                                           double* __restrict__ w_out) {
+    __shared__ int s_cnt[BLOCK / 32];
     double* stage = reinterpret_cast<double*>(smem);
     PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK>(tile));
-    for (int t = threadIdx.x; t < cnt; t += BLOCK) {
+    int npass = 0;
+    for (int t0 = 0; t0 < cnt; t0 += BLOCK) {
+        const int t = t0 + (int)threadIdx.x;
         const MomView v{stage + t, tile, kMomSlots};
         EventInfo ev;
-        generate_event<N>(seed, (uint64_t)(first + t), S, ph, v, ev);
-        event_to_rec<R, N>(v, ev, ph, recs[t]);
-        acc.npass += recs[t].mask;
-        acc.ntotal += 1;
-        acc.ntries += recs[t].tries;
+        bool pass = false;
+        if (t < cnt) {
+            generate_event<N>(seed, (uint64_t)(first + t), S, ph, v, ev);
+            pass = ev.ok && ev.mask;
+            acc.npass += ev.mask;
+            acc.ntotal += 1;
+            acc.ntries += ev.tries;
+            if (w_out && !pass) w_out[t] = 0.0;
+        }
+        int tot;
+        const int pos = compact_pos<BLOCK>(pass, threadIdx.x, s_cnt, 0, tot);
+        if (pass) {
+            event_to_rec<R, N>(v, ev, ph, recs[npass + pos]);
+            recs[npass + pos].idx = t;
+        }
+        npass += tot;
     }
     __syncthreads();
-    amp_rounds<R, N, BLOCK>(smem, recs, cnt, nullptr, ph.alg);
-    // one thread per point (the thread that generated it): weight and
-    // double-double accumulation with every lane active
-    for (int t = threadIdx.x; t < cnt; t += BLOCK) {
-        const double w = recs[t].valid ? (double)recs[t].ssum * recs[t].wfac : 0.0;
+    amp_rounds<R, N, BLOCK>(smem, recs, npass, nullptr, ph.alg);
+    // one thread per record: weight and double-double accumulation
+    for (int c = threadIdx.x; c < npass; c += BLOCK) {
+        const double w = (double)recs[c].ssum * recs[c].wfac;
         acc.sw = dd_add_d(acc.sw, w);
         acc.sw2 = dd_add_d(acc.sw2, w * w);
-        if (w_out) w_out[t] = w;
+        if (w_out) w_out[recs[c].idx] = w;
     }
 }
 
@@ -352,6 +392,7 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 // ---------------------------------------------------------------------------
 constexpr int kWsConsumers = 256;
 constexpr int kBarRounds = 1, kBarFull = 2, kBarEmpty = 4;   // named barrier ids (2,3 / 4,5)
+constexpr int kBarProducers = 6;                              // producers' stage compaction
 
 // Points per stage (= producer threads, a multiple of 32): as many as the
 // shared memory of the ring, the producers' staging and the round tables
@@ -392,6 +433,8 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
     PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N>());
     constexpr size_t ring_stride = align16((size_t)kWsStage * sizeof(PointRec<R, N>)) / sizeof(PointRec<R, N>);
     double* stage = reinterpret_cast<double*>(smem + ws_stage_offset<R, N>());
+    __shared__ int s_cnt[kWsStage / 32];
+    __shared__ int stage_n[2];   // records (cut-passing points) of the stage in each ring slot
     const int tid = threadIdx.x;
     const long long tiles = (npts + kWsStage - 1) / kWsStage;
     const int count = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
@@ -400,13 +443,12 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
     // the producer owning slot g of stage k folds that point's weight into its
     // accumulator once the consumers have released the stage
     auto harvest = [&](int k, int g) {
-        const long long t0 = stage_t0(k);
-        if (g < (int)min((long long)kWsStage, npts - t0)) {
+        if (g < stage_n[k & 1]) {
             const PointRec<R, N>& rec = ring[(k & 1) * ring_stride + g];
-            const double w = rec.valid ? (double)rec.ssum * rec.wfac : 0.0;
+            const double w = (double)rec.ssum * rec.wfac;
             acc.sw = dd_add_d(acc.sw, w);
             acc.sw2 = dd_add_d(acc.sw2, w * w);
-            if (w_out) w_out[t0 + g] = w;
+            if (w_out) w_out[stage_t0(k) + rec.idx] = w;
         }
     };
     if (tid >= kWsConsumers) {
@@ -421,15 +463,25 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             }
             const long long t0 = stage_t0(k);
             const int cnt = (int)min((long long)kWsStage, npts - t0);
+            EventInfo ev;
+            bool pass = false;
             if (g < cnt) {
-                PointRec<R, N>& rec = ring[s * ring_stride + g];
-                EventInfo ev;
                 generate_event<N>(seed, (uint64_t)(i0 + t0 + g), S, ph, v, ev);
-                event_to_rec<R, N>(v, ev, ph, rec);
-                acc.npass += rec.mask;
+                pass = ev.ok && ev.mask;
+                acc.npass += ev.mask;
                 acc.ntotal += 1;
-                acc.ntries += rec.tries;
+                acc.ntries += ev.tries;
+                if (w_out && !pass) w_out[t0 + g] = 0.0;
             }
+            // records only for points that pass the cuts, compacted in point order
+            int tot;
+            const int pos = compact_pos<kWsStage>(pass, g, s_cnt, kBarProducers, tot);
+            if (pass) {
+                PointRec<R, N>& rec = ring[s * ring_stride + pos];
+                event_to_rec<R, N>(v, ev, ph, rec);
+                rec.idx = g;
+            }
+            if (g == 0) stage_n[s] = tot;
             __threadfence_block();
             named_arrive(kBarFull + s, kWsThreads);
         }
@@ -438,7 +490,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
         for (int k = 0; k < count; ++k) {
             const int s = k & 1;
             named_sync(kBarFull + s, kWsThreads);
-            const int cnt = (int)min((long long)kWsStage, npts - stage_t0(k));
+            const int cnt = stage_n[s];
             amp_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, nullptr, ph.alg);
             if (k + 2 < count) {
                 __threadfence_block();

@@ -32,6 +32,7 @@ struct alignas(16) PointRec {
     int valid;        // 0: amplitude not evaluated (bad input / sampler failure)
     int mask;         // passes the cuts
     int tries;        // outer sampler attempts
+    int idx;          // the point's index within its tile or stage (records are compacted)
 };
 
 template <int N>
