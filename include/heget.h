@@ -159,6 +159,13 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta,
 int heget_ward(heget_ctx* ctx, int n, int64_t N, const double* momenta,
                int photon, int precision, double* ratio, void* stream);
 
+/* The device logarithm of the RAMBO energies q0 = -ln(r r'), Sec. 2.1
+ * eq. (4) (Tang's table-driven method, ACM TOMS 16 (1990) 378), exposed so
+ * that its accuracy can be checked: y[i] = ln x[i] for N device doubles,
+ * each a positive normal number (other inputs give unspecified values).
+ * Runs on the current device; EINVAL for N < 0 or NULL arrays. */
+int heget_log_table(const double* x, double* y, int64_t N, void* stream);
+
 /* Synchronizes `stream` and reports (then clears) the device-side input
  * flag raised by heget_amp2 / heget_ward: HEGET_EINVAL if set. */
 int heget_check(heget_ctx* ctx, void* stream);

@@ -85,6 +85,12 @@ phase_space_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, P
     }
 }
 
+__global__ void __launch_bounds__(256) log_table_kernel(const double* __restrict__ x, double* __restrict__ y,
+                                                        long long n) {
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+        y[i] = log_table(x[i]);
+}
+
 // ---------------------------------------------------------------------------
 // fixed-order reductions
 // ---------------------------------------------------------------------------
@@ -465,6 +471,17 @@ int heget_ward(heget_ctx* ctx, int n, int64_t N, const double* momenta, int phot
     r = precision == HEGET_FP32 ? launch_ward_f32(n, momenta, N, photon, ratio, ph, ctx->flag, L, st)
                                 : launch_ward_f64(n, momenta, N, photon, ratio, ph, ctx->flag, L, st);
     if (r) return cuda_fail((cudaError_t)r, "ward_kernel");
+    return HEGET_OK;
+}
+
+int heget_log_table(const double* x, double* y, int64_t N, void* stream) {
+    if (N < 0) return fail(HEGET_EINVAL, "N < 0");
+    if (N == 0) return HEGET_OK;
+    if (!x || !y) return fail(HEGET_EINVAL, "x and y must be non-NULL");
+    const long long blocks = std::min<long long>((N + 255) / 256, 65536);
+    log_table_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(x, y, N);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "log_table_kernel");
     return HEGET_OK;
 }
 

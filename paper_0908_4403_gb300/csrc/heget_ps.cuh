@@ -10,6 +10,7 @@
 #pragma once
 
 #include "heget_common.cuh"
+#include "heget_logtab.h"
 
 namespace heget {
 
@@ -136,11 +137,10 @@ __device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointR
 
 // Photon momenta of one point held in shared memory: slot (a, m) at
 // p[(slots a + m) * stride], m = 0..3 the components (E, px, py, pz).
-// Generated points use slots = kMomSlots, whose m = 4, 5 are scratch for pT
-// and |p| of the cuts, with stride = points of the tile (point-minor layout:
-// consecutive threads touch consecutive words); input rows use slots = 4,
-// stride = 1.
-constexpr int kMomSlots = 6;
+// Generated points use slots = kMomSlots with stride = points of the tile
+// (point-minor layout: consecutive threads touch consecutive words); input
+// rows use slots = 4, stride = 1.
+constexpr int kMomSlots = 4;
 
 struct MomView {
     double* p;
@@ -148,6 +148,35 @@ struct MomView {
     int slots;
     __device__ __forceinline__ double& operator()(int a, int m) const { return p[(slots * a + m) * stride]; }
 };
+
+// Natural logarithm of a positive normal double by Tang's table-driven method
+// (P. T. P. Tang, ACM TOMS 16 (1990) 378): x = 2^e m with m in [1, 2), F the
+// nearest breakpoint 1 + j/64, f = m - F (exact, |f| <= 1/128), r = f / F,
+//   ln x = e ln 2 + ln F + ln(1 + r),
+// with ln F and ln 2 from double-double tables (heget_logtab.h) and ln(1 + r)
+// by its series to r^8 (|r| <= 2^-7: truncation below 2^-56 relative).  A
+// handful of FP64 operations instead of a general-purpose logarithm, for the
+// RAMBO energies.
+__device__ __forceinline__ double log_table(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int e = ((hi >> 20) & 0x7FF) - 1023;
+    const double m = __hiloint2double((hi & 0x000FFFFF) | 0x3FF00000, lo);
+    const int j = (((hi >> 13) & 0x7F) + 1) >> 1;   // nearest breakpoint, 0 .. 64
+    const double f = m - (1.0 + j * 0.015625);       // exact
+    const double r = f * __ldg(&kLogTab[j][2]);
+    // ln(1 + r) - r = r^2 (-1/2 + r (1/3 + r (-1/4 + r (1/5 + r (-1/6 + r (1/7 - r/8))))))
+    double q = -0.125;
+    q = fma(q, r, 1.0 / 7.0);
+    q = fma(q, r, -1.0 / 6.0);
+    q = fma(q, r, 0.2);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double p = r * r * q;
+    const double lhi = fma((double)e, kLn2Hi, __ldg(&kLogTab[j][0]));
+    const double llo = fma((double)e, kLn2Lo, __ldg(&kLogTab[j][1]));
+    return lhi + (r + (p + llo));
+}
 
 // RAMBO: n massless momenta with total (rs, 0, 0, 0).  Photon i uses draws
 // 4i..4i+3 of the RAMBO stream: cos(theta) = 2 r0 - 1, phi = 2 pi r1,
@@ -164,7 +193,7 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomV
         const double s = sqrt(1.0 - c * c);
         double sp, cp;
         sincospi(2.0 * r1, &sp, &cp);
-        const double q0 = -log(r2 * r3);
+        const double q0 = -log_table(r2 * r3);   // r2 r3 in [2^-106, 1): normal
         const double q1 = q0 * s * cp, q2 = q0 * s * sp, q3 = q0 * c;
         v(i, 0) = q0;
         v(i, 1) = q1;
@@ -205,10 +234,10 @@ __device__ __forceinline__ bool lt_scaled(double v, double a, double w2) {
 // Evaluated without per-photon transcendentals:
 //   eta + y in (-E, E)  <=>  pz / pT in (sinh(-E - y), sinh(E - y)),
 //     sinh(E -+ y) = sinh E cosh y -+ cosh E sinh y with e^y = sqrt(x1/x2);
-//   sinh(eta_i - eta_j) = (pz_i |p_j| - pz_j |p_i|) / (pT_i pT_j),
+//   sinh(eta_i - eta_j) = (pz_i E_j - pz_j E_i) / (pT_i pT_j)   (|p| = E),
 //   cos(phi_i - phi_j)  = (px_i px_j + py_i py_j) / (pT_i pT_j);
-// a pair passes at once if |Delta eta| > R or Delta phi > R, and only the
-// remaining close pairs evaluate asinh and atan2.
+// a pair passes at once if |Delta eta| > R or Delta phi > R (compared on
+// squares), and only the remaining close pairs evaluate asinh and atan2.
 template <int N>
 __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Physics& ph) {
     const double iey = 1.0 / ey;
@@ -226,23 +255,22 @@ __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Phys
         if (!lt_scaled(-pz, -s_lo, pt2)) return 0;
     }
     if (ph.dr_min > 0) {
-#pragma unroll 1
-        for (int i = 0; i < N; ++i) {   // pT and |p| into the view's scratch slots
-            const double pt2 = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
-            p(i, 4) = sqrt(pt2);
-            p(i, 5) = sqrt(pt2 + p(i, 3) * p(i, 3));
-        }
+        // squares only: |p| = E for massless photons, and the sinh / cos
+        // comparisons are decided on squares; pT_i pT_j (a square root) is
+        // formed only for the close pairs that need asinh and atan2
+        const double sdr2 = ph.sinh_dr * ph.sinh_dr;
 #pragma unroll 1
         for (int i = 0; i < N; ++i)
 #pragma unroll 1
             for (int j = i + 1; j < N; ++j) {
                 const double xi = p(i, 1), yi = p(i, 2), zi = p(i, 3);
                 const double xj = p(j, 1), yj = p(j, 2), zj = p(j, 3);
-                const double ptt = p(i, 4) * p(j, 4);
-                const double sh = zi * p(j, 5) - zj * p(i, 5);   // sinh(d eta) pT_i pT_j
-                if (fabs(sh) > ph.sinh_dr * ptt) continue;
-                const double dot = xi * xj + yi * yj;   // cos(d phi) pT_i pT_j
-                if (dot < ph.cos_dr * ptt) continue;
+                const double pp2 = (xi * xi + yi * yi) * (xj * xj + yj * yj);   // (pT_i pT_j)^2
+                const double sh = zi * p(j, 0) - zj * p(i, 0);   // sinh(d eta) pT_i pT_j
+                if (sh * sh > sdr2 * pp2) continue;
+                const double dot = xi * xj + yi * yj;            // cos(d phi) pT_i pT_j
+                if (lt_scaled(dot, ph.cos_dr, pp2)) continue;
+                const double ptt = sqrt(pp2);
                 const double deta = asinh(sh / ptt);
                 const double dphi = atan2(fabs(xi * yj - yi * xj), dot);
                 if (!(deta * deta + dphi * dphi > ph.dr_min * ph.dr_min)) return 0;
