@@ -279,10 +279,16 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         int tot;
         const int pos = compact_pos<BLOCK>(pass, threadIdx.x, s_cnt, 0, tot);
         if (pass) {
-            event_to_rec<R, N>(v, ev, ph, recs[npass + pos]);
             recs[npass + pos].idx = t;
+            recs[npass + pos].fac = ev.rs;   // sqrt(s-hat) until the record is built
         }
         npass += tot;
+    }
+    __syncthreads();
+    // records built one per thread in compacted order: every lane busy
+    for (int c = threadIdx.x; c < npass; c += BLOCK) {
+        PointRec<R, N>& rec = recs[c];
+        pass_to_rec<R, N>(MomView{stage + rec.idx, tile, kMomSlots}, rec.fac, ph, rec);
     }
     __syncthreads();
     amp_rounds<R, N, BLOCK>(smem, recs, npass, nullptr, ph.alg);
@@ -476,11 +482,19 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             // records only for points that pass the cuts, compacted in point order
             int tot;
             const int pos = compact_pos<kWsStage>(pass, g, s_cnt, kBarProducers, tot);
+            PointRec<R, N>* rs_ring = ring + s * ring_stride;
             if (pass) {
-                PointRec<R, N>& rec = ring[s * ring_stride + pos];
-                event_to_rec<R, N>(v, ev, ph, rec);
-                rec.idx = g;
+                rs_ring[pos].idx = g;
+                rs_ring[pos].fac = ev.rs;   // sqrt(s-hat) until the record is built
             }
+            named_sync(kBarProducers, kWsStage);
+            // records built one per producer in compacted order: every lane busy
+            if (g < tot)
+                pass_to_rec<R, N>(MomView{stage + rs_ring[g].idx, kWsStage, kMomSlots}, rs_ring[g].fac, ph,
+                                  rs_ring[g]);
+            // every producer has read the staged momenta it needed before any
+            // of them generates the next stage into its column
+            named_sync(kBarProducers, kWsStage);
             if (g == 0) stage_n[s] = tot;
             __threadfence_block();
             named_arrive(kBarFull + s, kWsThreads);

@@ -61,8 +61,8 @@ __device__ __forceinline__ float u01_estimate(uint32_t hi) {
 }
 
 // Toy-PDF momentum fraction: proposal x = u^2 (density ~ x^-1/2), accepted
-// if v < (1-x)^3 (both uniforms from one Philox block per try).  Returns -1
-// when the bound is hit.
+// if v < (1-x)^3 (both uniforms from one Philox block per try); false when
+// the bound of tries is hit.
 //
 // The acceptance test is the FP64 comparison v < (1 - u^2)^3, with the
 // products and the difference rounded separately.  Most tries are settled
@@ -72,7 +72,12 @@ __device__ __forceinline__ float u01_estimate(uint32_t hi) {
 // of the cube), so |v_f - t_f| > 2^-20 = 16 2^-24 decides the comparison the
 // same way; the FP64 test runs only inside that band (about 2e-6 of the
 // tries).
-__device__ __forceinline__ double toy_pdf_x(const PointRng& rng, uint32_t& blk, int max_tries) {
+//
+// The loop itself is integer and FP32 work (plus the rare FP64 tie-break);
+// it returns the accepted try's random words, and the caller converts them to
+// x = u^2 in FP64 after the loop, where the lanes of a warp have converged.
+__device__ __forceinline__ bool toy_pdf_draw(const PointRng& rng, uint32_t& blk, int max_tries, uint32_t& wx,
+                                             uint32_t& wy) {
     for (int t = 0; t < max_tries; ++t) {
         const U4 w = philox4x32_10(U4{rng.ilo, rng.ihi, blk++, kStreamSqrtS}, rng.k0, rng.k1);
         const float uf = u01_estimate(w.y), vf = u01_estimate(w.w);
@@ -89,11 +94,17 @@ __device__ __forceinline__ double toy_pdf_x(const PointRng& rng, uint32_t& blk, 
             accept = v < __dmul_rn(__dmul_rn(om, om), om);
         }
         if (accept) {
-            const double u = u01_from_words(w.x, w.y);
-            return __dmul_rn(u, u);
+            wx = w.x;
+            wy = w.y;
+            return true;
         }
     }
-    return -1.0;
+    return false;
+}
+
+__device__ __forceinline__ double toy_pdf_x_of(uint32_t wx, uint32_t wy) {
+    const double u = u01_from_words(wx, wy);
+    return __dmul_rn(u, u);
 }
 
 // sqrt(s-hat), the boost factor e^y = sqrt(x1/x2) of the partonic frame and
@@ -117,9 +128,10 @@ __device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointR
     }
     uint32_t blk = 0;
     for (int t = 1; t <= S.max_tries; ++t) {
-        const double a = toy_pdf_x(rng, blk, S.max_tries);
-        const double b = a < 0 ? -1.0 : toy_pdf_x(rng, blk, S.max_tries);
-        if (a < 0 || b < 0) break;
+        uint32_t ax, ay, bx, by;
+        if (!toy_pdf_draw(rng, blk, S.max_tries, ax, ay)) break;
+        if (!toy_pdf_draw(rng, blk, S.max_tries, bx, by)) break;
+        const double a = toy_pdf_x_of(ax, ay), b = toy_pdf_x_of(bx, by);
         const double r = 2.0 * S.e_beam * sqrt(a * b);
         if (r > S.floor) {
             rs = r;
@@ -221,11 +233,12 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomV
     }
 }
 
-// v < a * w, decided on squares (w >= 0): no square root.
+// v < a * w, decided on squares (w >= 0): no square root; written with
+// selects, so the lanes of a warp stay together.
 __device__ __forceinline__ bool lt_scaled(double v, double a, double w2) {
-    // v < a w  with w = sqrt(w2)
-    if (a >= 0) return v < 0 || v * v < a * a * w2;
-    return v < 0 && v * v > a * a * w2;
+    const double v2 = v * v, r2 = a * a * w2;
+    const bool neg = v < 0;
+    return a >= 0 ? (neg || v2 < r2) : (neg && v2 > r2);
 }
 
 // Photon cuts, strict (Sec. 2.2): pT > pt_min, |eta + y| < eta_max with
@@ -240,19 +253,21 @@ __device__ __forceinline__ bool lt_scaled(double v, double a, double w2) {
 // squares), and only the remaining close pairs evaluate asinh and atan2.
 template <int N>
 __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Physics& ph) {
+    // every photon and pair is tested without early exits: the FP64 pipe
+    // executes whole warps, so a lane that could stop early saves nothing and
+    // the divergence would cost the others
     const double iey = 1.0 / ey;
     const double shy = 0.5 * (ey - iey), chy = 0.5 * (ey + iey);
     const double s_hi = ph.sinh_eta * chy - ph.cosh_eta * shy;    // sinh(E - y)
     const double s_lo = -ph.sinh_eta * chy - ph.cosh_eta * shy;   // sinh(-E - y)
     const double pt2min = ph.pt_min * ph.pt_min;
-#pragma unroll 1
+    bool ok = true;
+#pragma unroll
     for (int i = 0; i < N; ++i) {
         const double pz = p(i, 3);
         const double pt2 = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
-        if (!(pt2 > pt2min)) return 0;
-        // s_lo pT < pz < s_hi pT
-        if (!lt_scaled(pz, s_hi, pt2)) return 0;
-        if (!lt_scaled(-pz, -s_lo, pt2)) return 0;
+        // pT > pt_min and s_lo pT < pz < s_hi pT
+        ok = ok & (pt2 > pt2min) & lt_scaled(pz, s_hi, pt2) & lt_scaled(-pz, -s_lo, pt2);
     }
     if (ph.dr_min > 0) {
         // squares only: |p| = E for massless photons, and the sinh / cos
@@ -267,16 +282,17 @@ __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Phys
                 const double xj = p(j, 1), yj = p(j, 2), zj = p(j, 3);
                 const double pp2 = (xi * xi + yi * yi) * (xj * xj + yj * yj);   // (pT_i pT_j)^2
                 const double sh = zi * p(j, 0) - zj * p(i, 0);   // sinh(d eta) pT_i pT_j
-                if (sh * sh > sdr2 * pp2) continue;
                 const double dot = xi * xj + yi * yj;            // cos(d phi) pT_i pT_j
-                if (lt_scaled(dot, ph.cos_dr, pp2)) continue;
-                const double ptt = sqrt(pp2);
-                const double deta = asinh(sh / ptt);
-                const double dphi = atan2(fabs(xi * yj - yi * xj), dot);
-                if (!(deta * deta + dphi * dphi > ph.dr_min * ph.dr_min)) return 0;
+                const bool far = (sh * sh > sdr2 * pp2) | lt_scaled(dot, ph.cos_dr, pp2);
+                if (!far && ok) {   // rare: the exact Delta R of a close pair
+                    const double ptt = sqrt(pp2);
+                    const double deta = asinh(sh / ptt);
+                    const double dphi = atan2(fabs(xi * yj - yi * xj), dot);
+                    ok = deta * deta + dphi * dphi > ph.dr_min * ph.dr_min;
+                }
             }
     }
-    return 1;
+    return ok ? 1 : 0;
 }
 
 // Scalars of one generated event; its photon momenta (GeV) live in a MomView.
@@ -350,6 +366,28 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
             rec.t[T] = R((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) * is);
         }
     }
+}
+
+// Record of a point that passed the cuts, from its photon momenta (GeV) and
+// sqrt(s-hat) (the fields of event_to_rec for ok = mask = 1).
+template <class R, int N>
+__device__ __forceinline__ void pass_to_rec(const MomView& v, double rs, const Physics& ph, PointRec<R, N>& rec) {
+    const double irs = 1.0 / rs;
+    const double is = irs * irs;
+#pragma unroll 1
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
+    fill_denominators<R, N>(v, 0.5 * rs, is, true, rec);
+    rec.e2 = R(0.5);
+    rec.n1 = R(1);
+    rec.n2 = R(1);
+    double sp = 1;  // s^(2-n)
+    for (int a = 2; a < N; ++a) sp *= is;
+    rec.fac = ph.cpl * sp;
+    rec.wfac = ph.wconst * is;   // w = wfac * (scaled |M|^2 sum)
+    rec.valid = 1;
+    rec.mask = 1;
 }
 
 // Event -> point record.  Weight per unit of the scaled |M|^2 sum (Sec. 2.1
