@@ -284,11 +284,35 @@ __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Phys
                 const double sh = zi * p(j, 0) - zj * p(i, 0);   // sinh(d eta) pT_i pT_j
                 const double dot = xi * xj + yi * yj;            // cos(d phi) pT_i pT_j
                 const bool far = (sh * sh > sdr2 * pp2) | lt_scaled(dot, ph.cos_dr, pp2);
-                if (!far && ok) {   // rare: the exact Delta R of a close pair
-                    const double ptt = sqrt(pp2);
-                    const double deta = asinh(sh / ptt);
-                    const double dphi = atan2(fabs(xi * yj - yi * xj), dot);
-                    ok = deta * deta + dphi * dphi > ph.dr_min * ph.dr_min;
+                if (!far && ok) {
+                    // a close pair: |d eta|, d phi <= R.  With s = |sinh d eta|
+                    // and t = tan d phi (dot > 0 here when R < pi/2),
+                    //   s^2 (1 - s^2/6)^2 <= d eta^2 <= s^2,
+                    //   t^2 (1 - t^2/3)^2 <= d phi^2 <= t^2
+                    // (asinh and atan lie between their first two Taylor
+                    // terms and their first), which settles all but the pairs
+                    // within about 1 % of R; those take asinh and atan2.
+                    const double cr = xi * yj - yi * xj;
+                    const double R2 = ph.dr_min * ph.dr_min;
+                    bool exact = !(dot > 0);
+                    if (!exact) {
+                        const double s2 = sh * sh / pp2, t2 = cr * cr / (dot * dot);
+                        const double a = 1.0 - s2 * (1.0 / 6.0), b = 1.0 - t2 * (1.0 / 3.0);
+                        const double hi = s2 + t2, lo = s2 * a * a + t2 * b * b;
+                        if (lo > R2 * (1.0 + 1e-12)) {
+                            // Delta R > R: the pair passes
+                        } else if (hi < R2 * (1.0 - 1e-12)) {
+                            ok = false;
+                        } else {
+                            exact = true;
+                        }
+                    }
+                    if (exact) {   // rare
+                        const double ptt = sqrt(pp2);
+                        const double deta = asinh(sh / ptt);
+                        const double dphi = atan2(fabs(cr), dot);
+                        ok = deta * deta + dphi * dphi > R2;
+                    }
                 }
             }
     }
