@@ -203,9 +203,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, flush=None):
+def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, flush=None, result=None):
     """Device time per step (ms) of heget_xsec_launch + heget_xsec_finalize,
-    CUDA events on the launching stream, L2 flushed between steps."""
+    CUDA events on the launching stream, L2 flushed between steps.  result:
+    a list that receives the last step's heget_xsec_result."""
     import torch
     res = torch.zeros(80, dtype=torch.uint8, device="cuda")
     for w in range(2):
@@ -224,6 +225,8 @@ def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, 
         b.record(stream)
         b.synchronize()
         total += a.elapsed_time(b)
+    if result is not None:
+        result.append(H.result_from_tensor(res))
     return total / steps
 
 
@@ -477,6 +480,13 @@ def main():
                          flush=flush)
     H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
 
+    # FP32 -> FP64 escalation at the accuracy target (off by default)
+    H.heget_set_escalation(ctx, 1e-4)
+    esc_res = []
+    ms_esc = time_xsec(H, ctx, n, N, sampler, H.HEGET_FP32, max(5, min(50, args.steps // 8)), stream,
+                       seed=SEED + 8000, i0=i0, flush=flush, result=esc_res)
+    H.heget_set_escalation(ctx, 0.0)
+
     # end to end through the public API: heget_xsec per step (launch, fused
     # RNG -> sampler -> RAMBO -> cuts -> |M|^2 -> sums, result read back to a
     # host struct, synchronised); the step's inputs are its arguments
@@ -528,6 +538,10 @@ def main():
                                  "fp64_points_per_s": N * ws / (ms_sub64 * 1e-3),
                                  "note": "HEGET_ALG_SUBSET on the same workload: the ordering sum regrouped by "
                                          "photon set (not the paper's method; same |M|^2)"},
+            "escalation": {"tau": 1e-4, "points_per_s": N * ws / (ms_esc * 1e-3),
+                           "n_escalated_last_step": esc_res[0].n_escalated, "n_pass_last_step": esc_res[0].n_pass,
+                           "note": "the same step with FP32 points whose error bound exceeds tau recomputed "
+                                   "in FP64 (heget_set_escalation; off in the headline value)"},
             "kernel_ms_per_step": kern_ms / args.steps,
             "result_last_step": {"sigma_fb": r.sigma_fb, "err_fb": r.err_fb, "n_pass": r.n_pass,
                                  "accept": r.accept, "pass_fraction": r.n_pass / max(1, r.n_total)},

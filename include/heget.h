@@ -245,6 +245,27 @@ int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
 int heget_set_algorithm(heget_ctx* ctx, int alg);
 int heget_get_algorithm(const heget_ctx* ctx);
 
+/* FP32 -> FP64 escalation (the FP32 precision policy: FP32 where it is
+ * accurate, FP64 where it is not).  In FP32, heget_amp2 and the fused cross
+ * section (heget_xsec, heget_xsec_async, heget_xsec_launch, graphs) bound
+ * each point's rounding error: with B_h >= sum over orderings |A_pi,h| from
+ * norm bounds of the chain steps, the relative error of sum_h w_h |A_h|^2 is
+ * at most about u32 sqrt(sum_h w_h B_h^2 / sum_h w_h |A_h|^2), u32 = 2^-24.
+ * Points whose bound exceeds tau are recomputed in FP64 by a second kernel
+ * on the same stream (with the subset recursion, whatever the context's
+ * algorithm: the same |M|^2 up to rounding, far cheaper at large n): heget_amp2 overwrites their |M|^2, the cross section
+ * replaces their FP32 weights by the FP64 ones (in w_out too) and counts
+ * them in n_escalated.  tau = 0 (the default) turns it off; 1e-4 is the
+ * threshold of the FP32 accuracy target (the bound is conservative: at
+ * n = 8 it flags a few per cent of points whose actual FP32 error is far
+ * below tau, and their FP64 recomputation is the cost).  Batches,
+ * the server and heget_xsec_noalloc do not escalate (their n_escalated is 0).
+ * heget_amp2_escalated synchronizes `stream` and returns the number of rows
+ * the last FP32 heget_amp2 on ctx recomputed. */
+int heget_set_escalation(heget_ctx* ctx, double tau);
+int heget_get_escalation(const heget_ctx* ctx, double* tau);
+int heget_amp2_escalated(heget_ctx* ctx, void* stream, int64_t* count);
+
 /* Launch shape (this library's knob; the paper's analogue is the register /
  * block-size scan of Sec. 6.1): points per block tile used by heget_amp2
  * (kind 0) or heget_xsec* (kind 1) for n photons at `precision`.  tile = 0

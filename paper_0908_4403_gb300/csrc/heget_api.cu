@@ -262,6 +262,7 @@ Physics physics_of(const heget_params& p, int n) {
 Physics physics_of(const heget_ctx* c, int n) {
     Physics ph = physics_of(c->params, n);
     ph.alg = c->alg;
+    ph.esc_tau = c->esc_tau;
     return ph;
 }
 
@@ -310,6 +311,51 @@ int check_precision(int p) {
 }
 }  // namespace heget
 
+namespace {
+template <class R>
+size_t batch_tile_smem(int n, int tile) {
+    switch (n) {
+        case 2: return xsec_smem_bytes<R, 2, kBatchThreads>(tile);
+        case 3: return xsec_smem_bytes<R, 3, kBatchThreads>(tile);
+        case 4: return xsec_smem_bytes<R, 4, kBatchThreads>(tile);
+        case 5: return xsec_smem_bytes<R, 5, kBatchThreads>(tile);
+        case 6: return xsec_smem_bytes<R, 6, kBatchThreads>(tile);
+        case 7: return xsec_smem_bytes<R, 7, kBatchThreads>(tile);
+        default: return xsec_smem_bytes<R, 8, kBatchThreads>(tile);
+    }
+}
+
+// Grows a workspace buffer to at least `need` bytes (device or pinned host).
+int grow(void** p, size_t* cap, size_t need, bool pinned) {
+    if (*cap >= need) return HEGET_OK;
+    size_t c = *cap ? *cap : 4096;
+    while (c < need) c *= 2;
+    void* q = nullptr;
+    cudaError_t e = pinned ? cudaMallocHost(&q, c) : cudaMalloc(&q, c);
+    if (e != cudaSuccess) return fail(HEGET_ENOMEM, "workspace growth to %zu bytes failed: %s", c, cudaGetErrorString(e));
+    if (*p) pinned ? cudaFreeHost(*p) : cudaFree(*p);
+    *p = q;
+    *cap = c;
+    return HEGET_OK;
+}
+}  // namespace
+
+namespace heget {
+// Entries per block of the escalation lists: every point a block can own.
+int escalation_cap(const AmpLaunch& L, long long N) {
+    const long long tiles = (N + L.tile - 1) / L.tile;
+    return (int)(((tiles + L.grid - 1) / L.grid) * L.tile);
+}
+
+int reserve_escalation(heget_ctx* ctx, const AmpLaunch& L, long long N) {
+    const size_t entries = (size_t)L.grid * (size_t)escalation_cap(L, N);
+    int r = grow((void**)&ctx->esc_idx, &ctx->esc_idx_cap, entries * sizeof(long long), false);
+    if (!r) r = grow((void**)&ctx->esc_w, &ctx->esc_w_cap, entries * sizeof(double), false);
+    if (!r) r = grow((void**)&ctx->esc_cnt, &ctx->esc_cnt_cap, (size_t)L.grid * sizeof(int), false);
+    return r;
+}
+}  // namespace heget
+
 extern "C" {
 
 const char* heget_last_error(void) { return g_err.c_str(); }
@@ -327,7 +373,10 @@ int heget_create(int device, heget_ctx** out) {
     c->device = device;
     c->params = heget_params{1.0 / 137.035999, 2.0 / 3.0, 20.0, 2.5, 0.4};
     e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(Partial) * (size_t)kMaxGrid);
+    // block partials of a launch, followed by those of its escalation launch
+    if (e == cudaSuccess) e = cudaMalloc(&c->partials, 2 * sizeof(Partial) * (size_t)kMaxGrid);
+    if (e == cudaSuccess) e = cudaMalloc(&c->amp_esc_count, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->amp_esc_count, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->res_dev, sizeof(heget_xsec_result));
@@ -348,6 +397,11 @@ void heget_destroy(heget_ctx* c) {
     if (c->batch_dev) cudaFree(c->batch_dev);
     if (c->batch_partials) cudaFree(c->batch_partials);
     if (c->partials) cudaFree(c->partials);
+    if (c->esc_idx) cudaFree(c->esc_idx);
+    if (c->esc_w) cudaFree(c->esc_w);
+    if (c->esc_cnt) cudaFree(c->esc_cnt);
+    if (c->amp_esc_list) cudaFree(c->amp_esc_list);
+    if (c->amp_esc_count) cudaFree(c->amp_esc_count);
     if (c->flag) cudaFree(c->flag);
     if (c->res_dev) cudaFree(c->res_dev);
     if (c->res_host) cudaFreeHost(c->res_host);
@@ -375,6 +429,31 @@ int heget_set_algorithm(heget_ctx* ctx, int alg) {
 }
 
 int heget_get_algorithm(const heget_ctx* ctx) { return ctx ? ctx->alg : -1; }
+
+int heget_set_escalation(heget_ctx* ctx, double tau) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (!(tau >= 0) || !std::isfinite(tau)) return fail(HEGET_EINVAL, "tau must be finite and >= 0");
+    ctx->esc_tau = tau;
+    return HEGET_OK;
+}
+
+int heget_get_escalation(const heget_ctx* ctx, double* tau) {
+    if (!ctx || !tau) return fail(HEGET_EINVAL, "NULL argument");
+    *tau = ctx->esc_tau;
+    return HEGET_OK;
+}
+
+int heget_amp2_escalated(heget_ctx* ctx, void* stream, int64_t* count) {
+    if (!ctx || !count) return fail(HEGET_EINVAL, "NULL argument");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->amp_esc_count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "heget_amp2_escalated");
+    *count = h;
+    return HEGET_OK;
+}
 
 int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind) {
     if (!ctx || n < kMinN || n > kMaxN || (kind != 0 && kind != 1)) return -1;
@@ -447,9 +526,26 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta, const ui
     if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, false, ctx->tiles[0][precision == HEGET_FP64][n]))) return cuda_fail((cudaError_t)r, "occupancy");
     const Physics ph = physics_of(ctx, n);
     cudaStream_t st = (cudaStream_t)stream;
-    r = precision == HEGET_FP32 ? launch_amp2_f32(n, momenta, N, hel_mask, amp2, ph, ctx->flag, L, st)
-                                : launch_amp2_f64(n, momenta, N, hel_mask, amp2, ph, ctx->flag, L, st);
+    const bool esc = precision == HEGET_FP32 && ctx->esc_tau > 0 && N <= INT32_MAX;
+    if (esc) {
+        if ((r = grow((void**)&ctx->amp_esc_list, &ctx->amp_esc_cap, sizeof(int) * (size_t)N, false))) return r;
+        const cudaError_t e = cudaMemsetAsync(ctx->amp_esc_count, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "escalation counter");
+    }
+    r = precision == HEGET_FP32
+            ? launch_amp2_f32(n, momenta, N, hel_mask, amp2, ph, ctx->flag, esc ? ctx->amp_esc_list : nullptr,
+                              esc ? ctx->amp_esc_count : nullptr, L, st)
+            : launch_amp2_f64(n, momenta, N, hel_mask, amp2, ph, ctx->flag, nullptr, nullptr, L, st);
     if (r) return cuda_fail((cudaError_t)r, "amp2_kernel");
+    if (esc) {
+        // the flagged rows in FP64 (grid-stride over the device-side count)
+        const int tile = ctx->tiles[0][1][n] > 0 ? ctx->tiles[0][1][n] : default_tile(n, false);
+        Physics ph64 = ph;
+        ph64.alg = kAlgSubset;   // as for the cross section: same |M|^2, far cheaper at large n
+        r = launch_amp2_list_f64(n, momenta, ctx->amp_esc_list, ctx->amp_esc_count, hel_mask, amp2, ph64, ctx->flag,
+                                 tile, 2 * ctx->num_sms, st);
+        if (r) return cuda_fail((cudaError_t)r, "amp2_list_kernel");
+    }
     return HEGET_OK;
 }
 
@@ -502,6 +598,7 @@ int heget_check(heget_ctx* ctx, void* stream) {
     return HEGET_OK;
 }
 
+
 int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N, const heget_sampler* smp,
                       int precision, double* w_out, void* stream) {
     int r = check_common(ctx, n, N);
@@ -517,14 +614,31 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
         return cuda_fail((cudaError_t)r, "occupancy");
     const Physics ph = physics_of(ctx, n);
     const SamplerArgs S = sampler_args(smp);
+    EscArgs esc{nullptr, nullptr, nullptr, 0, 0};
+    const bool escalate = precision == HEGET_FP32 && ctx->esc_tau > 0 && N > 0;
+    if (escalate) {
+        if ((r = reserve_escalation(ctx, L, N))) return r;
+        esc = EscArgs{ctx->esc_idx, ctx->esc_w, ctx->esc_cnt, escalation_cap(L, N), 0};
+    }
     if (N > 0) {
-        r = precision == HEGET_FP32 ? launch_xsec_f32(n, seed, i0, N, S, ph, ctx->partials, w_out, L, st)
-                                    : launch_xsec_f64(n, seed, i0, N, S, ph, ctx->partials, w_out, L, st);
+        r = precision == HEGET_FP32 ? launch_xsec_f32(n, seed, i0, N, S, ph, ctx->partials, w_out, esc, L, st)
+                                    : launch_xsec_f64(n, seed, i0, N, S, ph, ctx->partials, w_out, esc, L, st);
         if (r) return cuda_fail((cudaError_t)r, "xsec_kernel");
     }
-    ctx->last_parts = N > 0 ? L.grid : 0;
+    if (escalate) {
+        // FP64 recomputation of the flagged points (by the subset recursion,
+        // whatever the context's algorithm: the same |M|^2, far cheaper at
+        // large n); its partials follow the FP32 ones
+        Physics ph64 = ph;
+        ph64.alg = kAlgSubset;
+        r = launch_escalate_f64(n, seed, i0, S, ph64, default_tile(n, true), esc, ctx->partials + L.grid, w_out,
+                                L.grid, st);
+        if (r) return cuda_fail((cudaError_t)r, "xsec_escalate_kernel");
+    }
+    ctx->last_parts = N > 0 ? (escalate ? 2 * L.grid : L.grid) : 0;
     ctx->last_kind = S.kind;
     ctx->last_ws = L.ws;
+    ctx->last_esc = escalate;
     return HEGET_OK;
 }
 
@@ -613,34 +727,6 @@ int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev, void*
 
 }  // extern "C"
 
-namespace {
-template <class R>
-size_t batch_tile_smem(int n, int tile) {
-    switch (n) {
-        case 2: return xsec_smem_bytes<R, 2, kBatchThreads>(tile);
-        case 3: return xsec_smem_bytes<R, 3, kBatchThreads>(tile);
-        case 4: return xsec_smem_bytes<R, 4, kBatchThreads>(tile);
-        case 5: return xsec_smem_bytes<R, 5, kBatchThreads>(tile);
-        case 6: return xsec_smem_bytes<R, 6, kBatchThreads>(tile);
-        case 7: return xsec_smem_bytes<R, 7, kBatchThreads>(tile);
-        default: return xsec_smem_bytes<R, 8, kBatchThreads>(tile);
-    }
-}
-
-// Grows a workspace buffer to at least `need` bytes (device or pinned host).
-int grow(void** p, size_t* cap, size_t need, bool pinned) {
-    if (*cap >= need) return HEGET_OK;
-    size_t c = *cap ? *cap : 4096;
-    while (c < need) c *= 2;
-    void* q = nullptr;
-    cudaError_t e = pinned ? cudaMallocHost(&q, c) : cudaMalloc(&q, c);
-    if (e != cudaSuccess) return fail(HEGET_ENOMEM, "workspace growth to %zu bytes failed: %s", c, cudaGetErrorString(e));
-    if (*p) pinned ? cudaFreeHost(*p) : cudaFree(*p);
-    *p = q;
-    *cap = c;
-    return HEGET_OK;
-}
-}  // namespace
 
 extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, int count, void* stream) {
     if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
@@ -799,8 +885,9 @@ extern "C" int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, 
     const SamplerArgs S = sampler_args(smp);
     cudaStream_t st = (cudaStream_t)stream;
     if (N > 0) {
-        r = precision == HEGET_FP32 ? launch_xsec_f32(n, seed, i0, N, S, ph, scratch, nullptr, L, st)
-                                    : launch_xsec_f64(n, seed, i0, N, S, ph, scratch, nullptr, L, st);
+        const EscArgs no_esc{nullptr, nullptr, nullptr, 0, 0};
+        r = precision == HEGET_FP32 ? launch_xsec_f32(n, seed, i0, N, S, ph, scratch, nullptr, no_esc, L, st)
+                                    : launch_xsec_f64(n, seed, i0, N, S, ph, scratch, nullptr, no_esc, L, st);
         if (r) return cuda_fail((cudaError_t)r, "xsec_kernel");
     }
     finalize_kernel<<<1, 256, 0, st>>>(scratch, N > 0 ? L.grid : 0, S.kind, 0, result_dev, nullptr);

@@ -172,6 +172,7 @@ struct Physics {
     double wconst;              // cpl c_n / (24 n!) GeV^-2 -> fb (weight = wconst S / s)
     double sinh_eta, cosh_eta;  // sinh, cosh of eta_max
     double sinh_dr, cos_dr;     // sinh, cos of dr_min
+    double esc_tau;             // FP32 -> FP64 escalation: relative error bound that triggers it (0 = off)
     int alg;                    // ordering sum: 0 prefix tree, 1 subset recursion
     int pad;
 };

@@ -5,8 +5,8 @@
 namespace heget {
 
 int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
-                    const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st) {
-#define CALL(N) launch_amp2_n<float, N>(mom, npts, mask, out, ph, flag, L, st)
+                    const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st) {
+#define CALL(N) launch_amp2_n<float, N>(mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st)
     HEGET_DISPATCH_N(n, CALL)
 #undef CALL
 }
@@ -19,9 +19,9 @@ int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* 
 }
 
 int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
-                    const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
+                    const Physics& ph, Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
                     cudaStream_t st) {
-#define CALL(N) launch_xsec_n<float, N>(seed, i0, npts, S, ph, partials, w_out, L, st)
+#define CALL(N) launch_xsec_n<float, N>(seed, i0, npts, S, ph, partials, w_out, esc, L, st)
     HEGET_DISPATCH_N(n, CALL)
 #undef CALL
 }

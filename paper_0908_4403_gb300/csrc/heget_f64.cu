@@ -5,8 +5,8 @@
 namespace heget {
 
 int launch_amp2_f64(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
-                    const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st) {
-#define CALL(N) launch_amp2_n<double, N>(mom, npts, mask, out, ph, flag, L, st)
+                    const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st) {
+#define CALL(N) launch_amp2_n<double, N>(mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st)
     HEGET_DISPATCH_N(n, CALL)
 #undef CALL
 }
@@ -19,9 +19,9 @@ int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* 
 }
 
 int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
-                    const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
+                    const Physics& ph, Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
                     cudaStream_t st) {
-#define CALL(N) launch_xsec_n<double, N>(seed, i0, npts, S, ph, partials, w_out, L, st)
+#define CALL(N) launch_xsec_n<double, N>(seed, i0, npts, S, ph, partials, w_out, esc, L, st)
     HEGET_DISPATCH_N(n, CALL)
 #undef CALL
 }
@@ -35,6 +35,20 @@ int occupancy_f64(int n, int tile, int* bpsm, size_t* smem) {
 int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
                      cudaStream_t st) {
     return launch_batch_t<double>(items, nitems, reqs, smem, grid, st);
+}
+
+int launch_escalate_f64(int n, uint64_t seed, long long i0, const SamplerArgs& S, const Physics& ph, int tile,
+                        const EscArgs& esc, Partial* out, double* w_out, int grid, cudaStream_t st) {
+#define CALL(N) launch_escalate_n<N>(seed, i0, S, ph, tile, esc, out, w_out, grid, st)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+int launch_amp2_list_f64(int n, const double* mom, const int* list, const int* count, const uint32_t* mask,
+                         double* out, const Physics& ph, int* flag, int tile, int grid, cudaStream_t st) {
+#define CALL(N) launch_amp2_list_n<N>(mom, list, count, mask, out, ph, flag, tile, grid, st)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
 }
 
 }  // namespace heget

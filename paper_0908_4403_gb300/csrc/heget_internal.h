@@ -45,8 +45,20 @@ struct heget_ctx {
     int last_parts = 0;               // block partials of the last heget_xsec_launch
     int last_kind = 0;                // its sampler kind
     bool last_ws = false;             // it used the warp-specialised kernel
+    bool last_esc = false;            // it launched the FP64 escalation kernel after it
     int tiles[2][2][heget::kMaxN + 1] = {};  // [amp2|xsec][fp32|fp64][n] tile overrides (0 = default)
     int alg = 0;                      // ordering sum: HEGET_ALG_TREE or HEGET_ALG_SUBSET
+    double esc_tau = 0.0;             // FP32 -> FP64 escalation threshold (0 = off)
+    // escalation lists of the fused FP32 launch (grown on demand): entries
+    // [grid][cap] of (point index, FP32 weight) and per-block counts
+    long long* esc_idx = nullptr;
+    double* esc_w = nullptr;
+    int* esc_cnt = nullptr;
+    size_t esc_idx_cap = 0, esc_w_cap = 0, esc_cnt_cap = 0;
+    // escalation list of FP32 heget_amp2 (row indices) and its device counter
+    int* amp_esc_list = nullptr;
+    size_t amp_esc_cap = 0;
+    int* amp_esc_count = nullptr;
     // mixed-n batch workspace (grown on demand)
     unsigned char* batch_host = nullptr;   // pinned staging of work items + request table
     unsigned char* batch_dev = nullptr;
@@ -57,6 +69,9 @@ struct heget_ctx {
 };
 
 namespace heget {
+struct AmpLaunch;
+// Grows the escalation lists of a fused FP32 launch of shape L over N points.
+int reserve_escalation(heget_ctx* ctx, const AmpLaunch& L, long long N);
 Physics physics_of(const heget_params& p, int n);
 Physics physics_of(const heget_ctx* c, int n);
 int check_sampler(const heget_sampler* s);

@@ -68,14 +68,16 @@ __host__ __device__ constexpr size_t table_bytes() {
 
 // The amplitude rounds of the context's ordering-sum algorithm (uniform per
 // launch): the prefix tree of the paper's method, or the subset recursion.
+// kappa: also the condition bound recs[p].kap2 (FP32 escalation).
 template <class R, int N, int BLOCK, int BAR = 0>
 __device__ __forceinline__ void amp_rounds(unsigned char* smem, PointRec<R, N>* recs, int cnt, const uint32_t* mask,
-                                           int alg) {
+                                           int alg, bool kappa = false) {
     if (alg == kAlgSubset) {
-        amplitude_rounds_subset<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
+        amplitude_rounds_subset<R, N, BLOCK, BAR>(smem, recs, cnt, mask, kappa);
     } else {
         using SH = DefaultShape<R, N>;
         amplitude_rounds<R, N, BLOCK, BAR, SH::HB, SH::G>(smem, recs, cnt, mask);
+        if (kappa) kappa_rounds<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
     }
 }
 
@@ -101,6 +103,25 @@ __host__ __device__ constexpr size_t amp2_smem_bytes(int tile) {
 template <class R, int N, int BLOCK>
 __host__ __device__ constexpr size_t xsec_smem_bytes(int tile) {
     return xsec_region_bytes<R, N, BLOCK>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
+}
+
+// FP32 -> FP64 escalation lists of a fused launch: block b appends the
+// points it flags (absolute point index, FP32 weight) in a fixed order to
+// idx/w[b cap ...] and stores their number in cnt[b]; idx == NULL disables
+// the bound and the lists (FP64 launches, batches).
+struct EscArgs {
+    long long* idx;
+    double* w;
+    int* cnt;
+    int cap;
+    int pad;
+};
+
+// A record escalates when its relative error bound u32 sqrt(kap2 / ssum)
+// exceeds tau: kap2 > (tau / u32)^2 ssum.
+__device__ __forceinline__ float esc_threshold(double tau) {
+    const double q = tau * 16777216.0;   // tau / u32, u32 = 2^-24
+    return (float)(q * q);
 }
 
 // Record of one input row (smem, API layout [n+2][4]); p1 must be massless
@@ -138,10 +159,11 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
     if (!ok) atomicOr(flag, 1);
 }
 
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, bool ESC = false>
 __global__ void __launch_bounds__(BLOCK)
 amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __restrict__ mask,
-            double* __restrict__ out, int tile, Physics ph, int* __restrict__ flag) {
+            double* __restrict__ out, int tile, Physics ph, int* __restrict__ flag, int* __restrict__ esc_list,
+            int* __restrict__ esc_count) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* stage = reinterpret_cast<double*>(smem);
     PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK>(tile));
@@ -157,11 +179,16 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         __syncthreads();
-        amp_rounds<R, N, BLOCK>(smem, recs, cnt, mask, ph.alg);
-        // one thread per point: FP64 normalisation and a coalesced store
-        for (int t = threadIdx.x; t < cnt; t += BLOCK)
+        constexpr bool esc = ESC && sizeof(R) == sizeof(float);
+        amp_rounds<R, N, BLOCK>(smem, recs, cnt, mask, ph.alg, esc);
+        const float thr = esc ? esc_threshold(ph.esc_tau) : 0.0f;
+        // one thread per point: FP64 normalisation and a coalesced store; points
+        // whose FP32 error bound exceeds the threshold are listed for FP64
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) {
             out[t0 + t] = recs[t].valid ? (double)recs[t].ssum * recs[t].fac
                                         : __longlong_as_double(0x7ff8000000000000ll);
+            if (esc && recs[t].valid && recs[t].kap2 > thr * recs[t].ssum) esc_list[atomicAdd(esc_count, 1)] = (int)(t0 + t);
+        }
     }
 }
 
@@ -255,10 +282,10 @@ __device__ __forceinline__ int compact_pos(bool flag, int local, int* cnts, int 
 // weight 0 and needs no amplitude); their amplitudes are computed in rounds
 // and their weights folded into acc.  w_out (may be NULL) receives the
 // tile's weights (0 for points that fail the cuts).
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, bool ESC = false>
 __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_t seed, long long first, int cnt,
                                           const SamplerArgs& S, const Physics& ph, Partial& acc,
-                                          double* __restrict__ w_out) {
+                                          double* __restrict__ w_out, const EscArgs& esc, int& esc_n) {
     __shared__ int s_cnt[BLOCK / 32];
     double* stage = reinterpret_cast<double*>(smem);
     PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK>(tile));
@@ -291,29 +318,131 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         pass_to_rec<R, N>(MomView{stage + rec.idx, tile, kMomSlots}, rec.fac, ph, rec);
     }
     __syncthreads();
-    amp_rounds<R, N, BLOCK>(smem, recs, npass, nullptr, ph.alg);
-    // one thread per record: weight and double-double accumulation
-    for (int c = threadIdx.x; c < npass; c += BLOCK) {
-        const double w = (double)recs[c].ssum * recs[c].wfac;
-        acc.sw = dd_add_d(acc.sw, w);
-        acc.sw2 = dd_add_d(acc.sw2, w * w);
-        if (w_out) w_out[recs[c].idx] = w;
+    constexpr bool kEsc = ESC && sizeof(R) == sizeof(float);
+    amp_rounds<R, N, BLOCK>(smem, recs, npass, nullptr, ph.alg, kEsc);
+    // one thread per record: weight and double-double accumulation; records
+    // whose FP32 error bound exceeds the threshold join the escalation list
+    if constexpr (!kEsc) {
+        for (int c = threadIdx.x; c < npass; c += BLOCK) {
+            const double w = (double)recs[c].ssum * recs[c].wfac;
+            acc.sw = dd_add_d(acc.sw, w);
+            acc.sw2 = dd_add_d(acc.sw2, w * w);
+            if (w_out) w_out[recs[c].idx] = w;
+        }
+        return;
+    }
+    const float thr = esc_threshold(ph.esc_tau);
+    for (int c0 = 0; c0 < npass; c0 += BLOCK) {
+        const int c = c0 + (int)threadIdx.x;
+        bool flag = false;
+        double w = 0.0;
+        if (c < npass) {
+            w = (double)recs[c].ssum * recs[c].wfac;
+            acc.sw = dd_add_d(acc.sw, w);
+            acc.sw2 = dd_add_d(acc.sw2, w * w);
+            if (w_out) w_out[recs[c].idx] = w;
+            flag = recs[c].kap2 > thr * recs[c].ssum;
+        }
+        {
+            int tot;
+            const int pos = compact_pos<BLOCK>(flag, threadIdx.x, s_cnt, 0, tot);
+            if (flag && esc_n + pos < esc.cap) {
+                const size_t e = (size_t)blockIdx.x * esc.cap + esc_n + pos;
+                esc.idx[e] = first + recs[c].idx;
+                esc.w[e] = w;
+            }
+            esc_n += tot;
+        }
     }
 }
 
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, bool ESC = false>
 __global__ void __launch_bounds__(BLOCK)
 xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, int tile,
-            Partial* __restrict__ partials, double* __restrict__ w_out) {
+            Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
     extern __shared__ __align__(16) unsigned char smem[];
     Partial acc = zero_partial();
+    int esc_n = 0;
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
-        xsec_tile<R, N, BLOCK>(smem, tile, seed, i0 + t0, cnt, S, ph, acc, w_out ? w_out + t0 : nullptr);
+        xsec_tile<R, N, BLOCK, ESC>(smem, tile, seed, i0 + t0, cnt, S, ph, acc, w_out ? w_out + t0 : nullptr, esc,
+                                    esc_n);
     }
+    if (ESC && threadIdx.x == 0) esc.cnt[blockIdx.x] = min(esc_n, esc.cap);
     // the round tables are free now: reuse them as reduction scratch
     const Partial r = block_reduce_partial<BLOCK>(acc, reinterpret_cast<Partial*>(smem));
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
+}
+
+// FP64 recomputation of the points an FP32 launch flagged (same grid): block
+// b regenerates the events of its list in order, evaluates them in FP64 and
+// leaves the corrections sum (w64 - w32), sum (w64^2 - w32^2) and the count
+// in out[b]; w_out (relative to i0) receives the FP64 weights.  Combined
+// after the FP32 partials in fixed order, they make the flagged points count
+// with their FP64 weights.
+template <int N, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int tile, EscArgs esc,
+                     Partial* __restrict__ out, double* __restrict__ w_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* stage = reinterpret_cast<double*>(smem);
+    PointRec<double, N>* recs =
+        reinterpret_cast<PointRec<double, N>*>(smem + xsec_region_bytes<double, N, BLOCK>(tile));
+    const int nb = esc.cnt[blockIdx.x];
+    const size_t base = (size_t)blockIdx.x * esc.cap;
+    Partial acc = zero_partial();
+    for (int c0 = 0; c0 < nb; c0 += tile) {
+        const int cnt = min(tile, nb - c0);
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) {
+            const MomView v{stage + t, tile, kMomSlots};
+            EventInfo ev;
+            generate_event<N>(seed, (uint64_t)esc.idx[base + c0 + t], S, ph, v, ev);
+            pass_to_rec<double, N>(v, ev.rs, ph, recs[t]);
+            recs[t].idx = t;
+        }
+        __syncthreads();
+        amp_rounds<double, N, BLOCK>(smem, recs, cnt, nullptr, ph.alg);
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) {
+            const double w64 = recs[t].ssum * recs[t].wfac, w32 = esc.w[base + c0 + t];
+            acc.sw = dd_add_d(acc.sw, w64 - w32);
+            acc.sw2 = dd_add_d(acc.sw2, w64 * w64 - w32 * w32);
+            if (w_out) w_out[esc.idx[base + c0 + t] - i0] = w64;
+        }
+        __syncthreads();
+    }
+    Partial r = block_reduce_partial<BLOCK>(acc, reinterpret_cast<Partial*>(smem));
+    if (threadIdx.x == 0) {
+        r.nesc = nb;
+        out[blockIdx.x] = r;
+    }
+}
+
+// FP64 |M|^2 of the rows listed by an FP32 heget_amp2 launch (their number
+// in *count): out[list[k]] is overwritten.
+template <int N, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+amp2_list_kernel(const double* __restrict__ mom, const int* __restrict__ list, const int* __restrict__ count,
+                 const uint32_t* __restrict__ mask, double* __restrict__ out, int tile, Physics ph,
+                 int* __restrict__ flag) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* stage = reinterpret_cast<double*>(smem);
+    PointRec<double, N>* recs =
+        reinterpret_cast<PointRec<double, N>*>(smem + amp2_region_bytes<double, N, BLOCK>(tile));
+    constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
+    const long long npts = *count;
+    for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
+        const int cnt = (int)min((long long)tile, npts - t0);
+        for (int e = threadIdx.x; e < cnt * ROW; e += BLOCK) {
+            const int t = e / ROW;
+            stage[t * SROW + (e - t * ROW)] = __ldg(mom + (size_t)list[t0 + t] * ROW + (e - t * ROW));
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<double, N>(stage + t * SROW, ph, recs[t], flag);
+        __syncthreads();
+        amp_rounds<double, N, BLOCK>(smem, recs, cnt, mask, ph.alg);
+        for (int t = threadIdx.x; t < cnt; t += BLOCK) out[list[t0 + t]] = (double)recs[t].ssum * recs[t].fac;
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -352,12 +481,15 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
         const WorkItem w = items[it];
         const BatchReq& rq = reqs[w.req];
         Partial acc = zero_partial();
+        int esc_n = 0;
+        const EscArgs kNoEsc{nullptr, nullptr, nullptr, 0, 0};
         double* wo = rq.w_out ? rq.w_out + w.start : nullptr;
         const long long first = rq.i0 + w.start;
         switch (w.n) {
 #define HEGET_BATCH_CASE(NN)                                                                                   \
     case NN:                                                                                                   \
-        xsec_tile<R, NN, kBatchThreads>(smem, rq.tile, rq.seed, first, w.count, rq.S, rq.ph, acc, wo); \
+        xsec_tile<R, NN, kBatchThreads>(smem, rq.tile, rq.seed, first, w.count, rq.S, rq.ph, acc, wo, kNoEsc, \
+                                        esc_n);                                                        \
         break;
             HEGET_BATCH_CASE(2)
             HEGET_BATCH_CASE(3)
@@ -429,10 +561,10 @@ __host__ __device__ constexpr int ws_min_blocks() {
     return ws_smem_bytes<R, N>() <= 113 * 1024 ? 2 : 1;
 }
 
-template <class R, int N>
+template <class R, int N, bool ESC = false>
 __global__ void __launch_bounds__(kWsConsumers + ws_stage(N), ws_min_blocks<R, N>())
 xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph,
-               Partial* __restrict__ partials, double* __restrict__ w_out) {
+               Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
     constexpr int kWsStage = ws_stage(N);
     constexpr int kWsThreads = kWsConsumers + kWsStage;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -448,13 +580,29 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
     auto stage_t0 = [&](int k) { return ((long long)blockIdx.x + (long long)k * gridDim.x) * kWsStage; };
     // the producer owning slot g of stage k folds that point's weight into its
     // accumulator once the consumers have released the stage
+    int esc_n = 0;
+    const float thr = ESC ? esc_threshold(ph.esc_tau) : 0.0f;
+    // (called by every producer for the same stages, in order)
     auto harvest = [&](int k, int g) {
+        bool flag = false;
+        double w = 0.0;
+        const PointRec<R, N>& rec = ring[(k & 1) * ring_stride + g];
         if (g < stage_n[k & 1]) {
-            const PointRec<R, N>& rec = ring[(k & 1) * ring_stride + g];
-            const double w = (double)rec.ssum * rec.wfac;
+            w = (double)rec.ssum * rec.wfac;
             acc.sw = dd_add_d(acc.sw, w);
             acc.sw2 = dd_add_d(acc.sw2, w * w);
             if (w_out) w_out[stage_t0(k) + rec.idx] = w;
+            flag = ESC && rec.kap2 > thr * rec.ssum;
+        }
+        if constexpr (ESC) {
+            int tot;
+            const int pos = compact_pos<kWsStage>(flag, g, s_cnt, kBarProducers, tot);
+            if (flag && esc_n + pos < esc.cap) {
+                const size_t e = (size_t)blockIdx.x * esc.cap + esc_n + pos;
+                esc.idx[e] = i0 + stage_t0(k) + rec.idx;
+                esc.w[e] = w;
+            }
+            esc_n += tot;
         }
     };
     if (tid >= kWsConsumers) {
@@ -505,7 +653,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             const int s = k & 1;
             named_sync(kBarFull + s, kWsThreads);
             const int cnt = stage_n[s];
-            amp_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, nullptr, ph.alg);
+            amp_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, nullptr, ph.alg, ESC);
             if (k + 2 < count) {
                 __threadfence_block();
                 named_arrive(kBarEmpty + s, kWsThreads);
@@ -514,8 +662,10 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
     }
     __syncthreads();
     // the last (up to) two stages were never reclaimed: harvest them now
-    if (tid >= kWsConsumers)
+    if (tid >= kWsConsumers) {
         for (int k = count - 2 < 0 ? 0 : count - 2; k < count; ++k) harvest(k, tid - kWsConsumers);
+        if (ESC && tid == kWsConsumers) esc.cnt[blockIdx.x] = min(esc_n, esc.cap);
+    }
     __syncthreads();
     const Partial r = block_reduce_partial<kWsThreads>(acc, reinterpret_cast<Partial*>(smem));
     if (threadIdx.x == 0) partials[blockIdx.x] = r;
@@ -541,18 +691,22 @@ constexpr bool use_ws(int n, int precision, bool xsec, int alg) {
 
 // Returns cudaError_t as int.
 int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
-                    const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st);
+                    const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st);
 int launch_amp2_f64(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
-                    const Physics& ph, int* flag, const AmpLaunch& L, cudaStream_t st);
+                    const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st);
+int launch_amp2_list_f64(int n, const double* mom, const int* list, const int* count, const uint32_t* mask,
+                         double* out, const Physics& ph, int* flag, int tile, int grid, cudaStream_t st);
+int launch_escalate_f64(int n, uint64_t seed, long long i0, const SamplerArgs& S, const Physics& ph, int tile,
+                        const EscArgs& esc, Partial* out, double* w_out, int grid, cudaStream_t st);
 int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
                     const AmpLaunch& L, cudaStream_t st);
 int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
                     const AmpLaunch& L, cudaStream_t st);
 int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
-                    const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
+                    const Physics& ph, Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
                     cudaStream_t st);
 int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
-                    const Physics& ph, Partial* partials, double* w_out, const AmpLaunch& L,
+                    const Physics& ph, Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
                     cudaStream_t st);
 int occupancy_ws_f32(int n, int* bpsm, size_t* smem);
 // Mixed-n batch launch (one launch per precision); smem sized for the tiles.

@@ -30,6 +30,7 @@ struct alignas(16) PointRec {
     R e2;             // energy of p2 / sqrt(s-hat)  (p2 = e2 (1, 0, 0, -1))
     R n1, n2;         // sqrt(2 e1), sqrt(2 e2): spinor normalisations
     R ssum;           // result of the tree: sum_h w_h |A_h|^2 in scaled units
+    R kap2;           // sum_h w_h B_h^2, B_h >= sum over orderings |A_pi,h| (condition bound)
     int valid;        // 0: amplitude not evaluated (bad input / sampler failure)
     int mask;         // passes the cuts
     int tries;        // outer sampler attempts

@@ -11,16 +11,23 @@
 
 using namespace heget;
 
-// A captured heget_xsec_launch + heget_xsec_finalize.  Replays update only the
-// first two arguments of the event kernel, which every variant of it takes as
-// (uint64_t seed, long long i0, ...).
+// A captured heget_xsec_launch + heget_xsec_finalize: a chain of kernel
+// nodes -- the event kernel, the FP64 escalation kernel when the context
+// escalates FP32 points, then the finalisation.  Replays update the first
+// two arguments (uint64_t seed, long long i0) of the event and escalation
+// kernels, which every variant of them takes first.
+struct GraphKernel {
+    cudaGraphNode_t node = nullptr;
+    cudaKernelNodeParams kp{};   // captured parameters
+    int nargs = 0;
+};
+
 struct heget_graph {
     heget_ctx* ctx = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t knode = nullptr;   // the event kernel (the graph's only root)
-    cudaKernelNodeParams kp{};         // its captured parameters
-    int nargs = 0;
+    GraphKernel k[2];   // event kernel, escalation kernel
+    int nk = 0;
 };
 
 namespace {
@@ -46,6 +53,13 @@ int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp,
     if ((r = check_sampler(smp))) return r;
     if (N < 1 || !result_dev) return fail(HEGET_EINVAL, "a graph needs N >= 1 and result_dev");
     DeviceGuard dg(ctx->device);
+    // allocations cannot be captured: grow the escalation lists first
+    if (precision == HEGET_FP32 && ctx->esc_tau > 0) {
+        AmpLaunch L;
+        if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, true, ctx->tiles[1][0][n], ctx->alg)))
+            return cuda_fail((cudaError_t)r, "occupancy");
+        if ((r = reserve_escalation(ctx, L, N))) return r;
+    }
     cudaStream_t st = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
@@ -62,11 +76,21 @@ int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp,
     cudaStreamDestroy(st);
     if (r) return graph_fail(g, r);
     if (e != cudaSuccess) return graph_fail(g, cuda_fail(e, "cudaStreamEndCapture"));
-    g->nargs = ctx->last_ws ? 7 : 8;
-    size_t nroots = 1;
-    e = cudaGraphGetRootNodes(g->graph, &g->knode, &nroots);
-    if (e != cudaSuccess || nroots != 1) return graph_fail(g, fail(HEGET_ECUDA, "unexpected captured graph shape"));
-    e = cudaGraphKernelNodeGetParams(g->knode, &g->kp);
+    // walk the chain from its root: event kernel, [escalation kernel], finalisation
+    g->nk = ctx->last_esc ? 2 : 1;
+    g->k[0].nargs = ctx->last_ws ? 8 : 9;
+    g->k[1].nargs = 8;
+    size_t cnt = 1;
+    e = cudaGraphGetRootNodes(g->graph, &g->k[0].node, &cnt);
+    if (e != cudaSuccess || cnt != 1) return graph_fail(g, fail(HEGET_ECUDA, "unexpected captured graph shape"));
+    for (int j = 0; j < g->nk && e == cudaSuccess; ++j) {
+        e = cudaGraphKernelNodeGetParams(g->k[j].node, &g->k[j].kp);
+        if (e == cudaSuccess && j + 1 < g->nk) {
+            cnt = 1;
+            e = cudaGraphNodeGetDependentNodes(g->k[j].node, &g->k[j + 1].node, nullptr, &cnt);
+            if (e == cudaSuccess && cnt != 1) return graph_fail(g, fail(HEGET_ECUDA, "unexpected captured graph shape"));
+        }
+    }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
     if (e != cudaSuccess) return graph_fail(g, cuda_fail(e, "graph instantiate"));
     *out = g;
@@ -77,15 +101,18 @@ int heget_graph_launch(heget_graph* g, uint64_t seed, int64_t i0, void* stream) 
     if (!g) return fail(HEGET_EINVAL, "graph is NULL");
     if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
     DeviceGuard dg(g->ctx->device);
-    void* args[8];
-    for (int k = 0; k < g->nargs; ++k) args[k] = g->kp.kernelParams[k];
     long long i0v = i0;
-    args[0] = &seed;
-    args[1] = &i0v;
-    cudaKernelNodeParams p = g->kp;
-    p.kernelParams = args;
-    p.extra = nullptr;
-    cudaError_t e = cudaGraphExecKernelNodeSetParams(g->exec, g->knode, &p);
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < g->nk && e == cudaSuccess; ++j) {
+        void* args[9];
+        for (int a = 0; a < g->k[j].nargs; ++a) args[a] = g->k[j].kp.kernelParams[a];
+        args[0] = &seed;
+        args[1] = &i0v;
+        cudaKernelNodeParams p = g->k[j].kp;
+        p.kernelParams = args;
+        p.extra = nullptr;
+        e = cudaGraphExecKernelNodeSetParams(g->exec, g->k[j].node, &p);
+    }
     if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "heget_graph_launch");
     return HEGET_OK;

@@ -112,6 +112,9 @@ SIGNATURES = {
     "heget_graph_destroy": (None, [P]),
     "heget_set_tile": (I32, [P, I32, I32, I32, I32]),
     "heget_set_algorithm": (I32, [P, I32]),
+    "heget_set_escalation": (I32, [P, D]),
+    "heget_get_escalation": (I32, [P, C.POINTER(C.c_double)]),
+    "heget_amp2_escalated": (I32, [P, P, C.POINTER(I64)]),
     "heget_get_algorithm": (I32, [P]),
     "heget_get_tile": (I32, [P, I32, I32, I32]),
     "heget_xsec_noalloc": (I32, [I32, I32, U64, I64, I64, C.POINTER(heget_sampler), C.POINTER(heget_params),
@@ -291,6 +294,22 @@ def heget_set_algorithm(ctx, alg):
 
 def heget_get_algorithm(ctx) -> int:
     return load().heget_get_algorithm(ctx)
+
+
+def heget_set_escalation(ctx, tau):
+    _check(load().heget_set_escalation(ctx, tau))
+
+
+def heget_get_escalation(ctx) -> float:
+    v = C.c_double()
+    _check(load().heget_get_escalation(ctx, C.byref(v)))
+    return v.value
+
+
+def heget_amp2_escalated(ctx, stream=None) -> int:
+    v = I64()
+    _check(load().heget_amp2_escalated(ctx, _stream(stream), C.byref(v)))
+    return v.value
 
 
 def heget_set_tile(ctx, n, precision, kind, tile):
