@@ -52,11 +52,12 @@ FP64_PEAK = SMS * 2 * 2 * SM_GHZ / 1e3
 FP64_FLOPS_PER_POINT = {4: 928}
 
 
-def roofline(n, N, kern_s, peak32_meas, peak64_meas):
+def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None):
     """Roofline of the fused step's kernel.  At n <= 4 the FP64 pipe binds
     (the phase space is FP64 by design; one SM retires 2 DFMA per clock
-    against 128 FFMA), above that the FP32 tree does."""
-    tree = tree_flops_per_point(n) * N / kern_s / 1e12
+    against 128 FFMA), above that the FP32 tree does.  n_eval: points whose
+    amplitudes were evaluated (those that pass the cuts)."""
+    tree = tree_flops_per_point(n) * (N if n_eval is None else n_eval) / kern_s / 1e12
     fp32 = {"pipe": "fp32 fma", "achieved": tree, "peak": FP32_PEAK, "frac": tree / FP32_PEAK,
             "flops_per_point": tree_flops_per_point(n), "measured_peak": peak32_meas,
             "frac_of_measured": tree / peak32_meas}
@@ -349,8 +350,9 @@ def matrix_section(H, ctx, stream, peak32, peak64, flush):
         OS = {"fixed": lambda a: O.fixed(a[0]), "toy": lambda a: O.toy_pdf(),
               "uniform": lambda a: O.uniform(a[0], a[1])}[smp[0]](smp[1:])
         H.heget_set_params(ctx, pt_min=cut[0], eta_max=cut[1], dr_min=cut[2])
-        ms32 = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3 if n < 8 else 1, stream, flush=flush)
-        ms64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 3 if n < 8 else 1, stream, flush=flush)
+        r32, r64 = [], []
+        ms32 = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3 if n < 8 else 1, stream, flush=flush, result=r32)
+        ms64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 3 if n < 8 else 1, stream, flush=flush, result=r64)
         H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
         ms32s = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3, stream, flush=flush)
         ms64s = time_xsec(H, ctx, n, N, S, H.HEGET_FP64, 3, stream, flush=flush)
@@ -376,11 +378,14 @@ def matrix_section(H, ctx, stream, peak32, peak64, flush):
                     "fp64_rel_err_median_max": errs[H.HEGET_FP64][:2],
                     "masks_agree": bool(errs[H.HEGET_FP32][2] and errs[H.HEGET_FP64][2]),
                     "err_sample_points": M,
-                    "fp32_tree_frac_of_fp32_fma_peak": tf * N / (ms32 * 1e-3) / (peak32 * 1e12),
-                    "fp64_tree_frac_of_fp64_fma_peak": tf * n64 / (ms64 * 1e-3) / (peak64 * 1e12),
+                    # amplitudes are evaluated for the points that pass the cuts only
+                    "pass_fraction": r32[0].n_pass / N,
+                    "fp32_tree_frac_of_fp32_fma_peak": tf * r32[0].n_pass / (ms32 * 1e-3) / (FP32_PEAK * 1e12),
+                    "fp64_tree_frac_of_fp64_fma_peak": tf * r64[0].n_pass / (ms64 * 1e-3) / (FP64_PEAK * 1e12),
                     "subset_fp32_points_per_s": N / (ms32s * 1e-3), "subset_fp64_points_per_s": N / (ms64s * 1e-3),
                     "subset_flops_per_point": subset_flops_per_point(n),
-                    "subset_fp32_frac_of_fp32_peak": subset_flops_per_point(n) * N / (ms32s * 1e-3) / (FP32_PEAK * 1e12),
+                    "subset_fp32_frac_of_fp32_peak": subset_flops_per_point(n) * r32[0].n_pass / (ms32s * 1e-3)
+                                                     / (FP32_PEAK * 1e12),
                     "oracle": base})
     H.heget_set_params(ctx)
     return out
@@ -526,7 +531,7 @@ def main():
                        "compaction": "value counts every generated point; |M|^2 is evaluated for the points that "
                                      "pass the cuts (the others have weight 0), see pass_fraction",
                        "parallelism": f"dp{ws} (point shards)"},
-            "roofline": roofline(n, N, kern_s, peak32, peak64),
+            "roofline": roofline(n, N, kern_s, peak32, peak64, n_eval=r.n_pass / max(1, ws)),
             "gpu_launches": 2 * args.steps,
             "e2e": {"value": N * ws * args.e2e_steps / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 80,

@@ -387,6 +387,33 @@ __device__ __forceinline__ void first_rows(const LaneTables<R, N, BLOCK, HB, G>&
     }
 }
 
+// Levels at the bottom of the tree written out without loops: 0, 1 (the
+// last two photons as two chains) or 2 (also the loop over the last three),
+// per precision and photon count.  FP32 values from a GB300 sweep (n = 5
+// +26 %, n = 7 +19 %, n = 8 +23 % over none; n = 4, 6 best without); they
+// can be overridden with -DHEGET_F32_UNROLL_<n>=..
+#ifndef HEGET_F32_UNROLL_4
+#define HEGET_F32_UNROLL_4 0
+#endif
+#ifndef HEGET_F32_UNROLL_5
+#define HEGET_F32_UNROLL_5 2
+#endif
+#ifndef HEGET_F32_UNROLL_6
+#define HEGET_F32_UNROLL_6 0
+#endif
+#ifndef HEGET_F32_UNROLL_7
+#define HEGET_F32_UNROLL_7 1
+#endif
+#ifndef HEGET_F32_UNROLL_8
+#define HEGET_F32_UNROLL_8 1
+#endif
+template <class R, int N>
+__host__ __device__ constexpr int tree_unroll() {
+    if (sizeof(R) != sizeof(float)) return 0;
+    return N == 4 ? HEGET_F32_UNROLL_4 : N == 5 ? HEGET_F32_UNROLL_5 : N == 6 ? HEGET_F32_UNROLL_6
+         : N == 7 ? HEGET_F32_UNROLL_7 : N == 8 ? HEGET_F32_UNROLL_8 : 0;
+}
+
 // Depth-first walk of the ordering tree below a node at depth D (D photons
 // attached, set T, current rows r), adding the closures to acc.
 template <class R, int N, int D, int BLOCK, int HB, int G>
@@ -395,6 +422,27 @@ __device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK, HB, G>& L,
     constexpr unsigned FULL = (1u << N) - 1;
     if constexpr (D == N - 1) {
         close_rows<R, N, BLOCK, HB, G>(L, __ffs(FULL & ~T) - 1, r, are, aim);
+    } else if constexpr (D == N - 2 && tree_unroll<R, N>() >= 1) {
+        // two photons a < b left: the orderings (a, b) and (b, a) as two
+        // independent chains, accumulated in the loop's order
+        const unsigned rem = FULL & ~T;
+        const int a = __ffs(rem) - 1, b = __ffs(rem & (rem - 1)) - 1;
+        Row<R> ra[1 << HB], rb[1 << HB];
+        attach<R, N, BLOCK, HB, G>(L, a, c_tables.child[child_offset(N) + T * N + a], r, ra);
+        attach<R, N, BLOCK, HB, G>(L, b, c_tables.child[child_offset(N) + T * N + b], r, rb);
+        close_rows<R, N, BLOCK, HB, G>(L, b, ra, are, aim);
+        close_rows<R, N, BLOCK, HB, G>(L, a, rb, are, aim);
+    } else if constexpr (D == N - 3 && tree_unroll<R, N>() >= 2) {
+        // three photons left: the loop over them unrolled
+        unsigned rem = FULL & ~T;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int j = __ffs(rem) - 1;
+            rem &= rem - 1;
+            Row<R> r2[1 << HB];
+            attach<R, N, BLOCK, HB, G>(L, j, c_tables.child[child_offset(N) + T * N + j], r, r2);
+            descend<R, N, D + 1, BLOCK, HB, G>(L, r2, T | (1u << j), are, aim);
+        }
     } else {
         unsigned rem = FULL & ~T;
 #pragma unroll 1
