@@ -65,7 +65,7 @@ def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None):
     if n in FP64_FLOPS_PER_POINT:
         a64 = FP64_FLOPS_PER_POINT[n] * N / kern_s / 1e12
         return {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": FP64_PEAK, "unit": "TFLOP/s",
-                "frac": a64 / FP64_PEAK, "traffic": 125440 if n == 4 else None, "kernel": kern,
+                "frac": a64 / FP64_PEAK, "traffic": 125696 if n == 4 else None, "kernel": kern,
                 "flops_per_point": FP64_FLOPS_PER_POINT[n],
                 "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
                 "measured_peak": peak64_meas, "frac_of_measured": a64 / peak64_meas, "fp32_tree": fp32}
