@@ -320,6 +320,89 @@ __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Phys
     return ok ? 1 : 0;
 }
 
+// FP32 prefilter of the cut decisions.  Each test of pass_cuts is decided in
+// FP32 when the FP32 value lies clearly on one side of the boundary, and the
+// point falls back to the FP64 pass_cuts otherwise, so every decision equals
+// the FP64 one.  Error bounds (u = 2^-24): the components convert with
+// relative error u; a product or sum of two such terms carries at most a
+// few u relative to the magnitudes involved.  Margins are 64 u relative for
+// the single-photon tests (no cancellation) and 32 u times the sum of the
+// term magnitudes for the pair quantities sinh(d eta) pT pT and
+// cos(d phi) pT pT, which cancel.  Only the rare close pairs (which need
+// the exact Delta R) and near-boundary tests reach FP64.
+struct Tri {   // a decision: certain (true / false) or undecided
+    bool ok, sure;
+};
+
+// v < a w with w = sqrt(w2) >= 0, from FP32 values v2 = v^2, r2 = a^2 w2
+// carrying relative error <= rel, and exact signs of v and a.
+__device__ __forceinline__ Tri lt_scaled_f(bool vneg, bool apos, float v2, float r2, float rel) {
+    const bool lt = v2 < r2 * (1.0f - rel), gt = v2 > r2 * (1.0f + rel);
+    if (apos) return vneg ? Tri{true, true} : Tri{lt, lt || gt};
+    return vneg ? Tri{gt, lt || gt} : Tri{false, true};
+}
+
+template <int N>
+__device__ __forceinline__ int pass_cuts_fast(const MomView& p, double ey, const Physics& ph) {
+    constexpr float kU = 5.9604645e-8f;   // 2^-24
+    const double iey = 1.0 / ey;
+    const double shy = 0.5 * (ey - iey), chy = 0.5 * (ey + iey);
+    const double s_hi = ph.sinh_eta * chy - ph.cosh_eta * shy;    // sinh(E - y)
+    const double s_lo = -ph.sinh_eta * chy - ph.cosh_eta * shy;   // sinh(-E - y)
+    const float shi_f = (float)s_hi, slo_f = (float)s_lo;
+    const float shi2 = shi_f * shi_f, slo2 = slo_f * slo_f;
+    const float ptmin2 = (float)(ph.pt_min * ph.pt_min);
+    float x[N], y[N], z[N], e[N], pt2[N];
+    bool ok = true, sure = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        e[i] = (float)p(i, 0);
+        x[i] = (float)p(i, 1);
+        y[i] = (float)p(i, 2);
+        z[i] = (float)p(i, 3);
+        pt2[i] = x[i] * x[i] + y[i] * y[i];
+        const bool gt = pt2[i] > ptmin2 * (1.0f + 64.0f * kU), le = pt2[i] < ptmin2 * (1.0f - 64.0f * kU);
+        sure = sure && (gt || le);
+        ok = ok && gt;
+        const float z2 = z[i] * z[i];
+        const Tri hi = lt_scaled_f(z[i] < 0.0f, shi_f >= 0.0f, z2, shi2 * pt2[i], 64.0f * kU);
+        const Tri lo = lt_scaled_f(z[i] > 0.0f, -slo_f >= 0.0f, z2, slo2 * pt2[i], 64.0f * kU);
+        sure = sure && hi.sure && lo.sure;
+        ok = ok && hi.ok && lo.ok;
+    }
+    bool close = false;
+    if (ph.dr_min > 0) {
+        const float sdr2 = (float)(ph.sinh_dr * ph.sinh_dr), cdr = (float)ph.cos_dr;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = i + 1; j < N; ++j) {
+                const float pp2 = pt2[i] * pt2[j];
+                const float sh = z[i] * e[j] - z[j] * e[i];
+                const float esh = 32.0f * kU * (fabsf(z[i] * e[j]) + fabsf(z[j] * e[i]));
+                const float dot = x[i] * x[j] + y[i] * y[j];
+                const float edot = 32.0f * kU * (fabsf(x[i] * x[j]) + fabsf(y[i] * y[j]));
+                const float ash = fabsf(sh);
+                // far in eta: sh^2 > sdr2 pp2, certain if (|sh| - esh)^2 beats it
+                const float T = sdr2 * pp2;
+                const bool eta_far = ash > esh && (ash - esh) * (ash - esh) > T * (1.0f + 64.0f * kU);
+                const bool eta_near = (ash + esh) * (ash + esh) < T * (1.0f - 64.0f * kU);
+                // far in phi: dot < cos_dr pT pT
+                const float c = cdr * sqrtf(pp2);
+                const float ec = 64.0f * kU * fabsf(c);
+                const bool phi_far = dot + edot < c - ec;
+                const bool phi_near = dot - edot > c + ec;
+                const bool far = eta_far || phi_far;
+                sure = sure && (far || (eta_near && phi_near));
+                close = close || (!far && eta_near && phi_near);
+            }
+    }
+    // undecided tests, and the close pairs (which need the exact Delta R),
+    // go to the FP64 decision
+    if (!sure || (ok && close)) return pass_cuts<N>(p, ey, ph);
+    return ok ? 1 : 0;
+}
+
 // Scalars of one generated event; its photon momenta (GeV) live in a MomView.
 struct EventInfo {
     double rs, ey, x1, x2;
@@ -332,7 +415,10 @@ __device__ __forceinline__ void generate_event(uint64_t seed, uint64_t i, const 
     const PointRng rng(seed, i);
     sample_sqrt_s(S, rng, ev.rs, ev.ey, ev.x1, ev.x2, ev.tries, ev.ok);
     rambo<N>(rng, ev.rs, v);
-    ev.mask = ev.ok ? pass_cuts<N>(v, ev.ey, ph) : 0;
+    // the FP32 prefilter keeps 5n floats per photon set live in the producer
+    // threads: a gain up to n = 3 (+22 % at n = 2 on GB300), a loss above
+    if constexpr (N <= 3) ev.mask = ev.ok ? pass_cuts_fast<N>(v, ev.ey, ph) : 0;
+    else ev.mask = ev.ok ? pass_cuts<N>(v, ev.ey, ph) : 0;
 }
 
 // Flat phase-space weight Phi_n(s) of eq. (4).
