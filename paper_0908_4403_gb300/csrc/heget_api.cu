@@ -13,8 +13,33 @@
 
 namespace heget {
 
-int occupancy_f32(int n, int tile, int* bpsm, size_t* smem);
-int occupancy_f64(int n, int tile, int* bpsm, size_t* smem);
+// Launchers dispatched on the ordering-sum algorithm of the launch; each
+// algorithm's kernels are separate instantiations (heget_tree_*.cu,
+// heget_subset_*.cu), so neither shapes the other's registers.
+int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
+                    const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st) {
+    return ph.alg == kAlgSubset
+               ? launch_amp2_alg<float, kAlgSubset>(n, mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st)
+               : launch_amp2_alg<float, kAlgTree>(n, mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st);
+}
+int launch_amp2_f64(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
+                    const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st) {
+    return ph.alg == kAlgSubset
+               ? launch_amp2_alg<double, kAlgSubset>(n, mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st)
+               : launch_amp2_alg<double, kAlgTree>(n, mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st);
+}
+int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                    Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
+    return ph.alg == kAlgSubset
+               ? launch_xsec_alg<float, kAlgSubset>(n, seed, i0, npts, S, ph, partials, w_out, esc, L, st)
+               : launch_xsec_alg<float, kAlgTree>(n, seed, i0, npts, S, ph, partials, w_out, esc, L, st);
+}
+int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                    Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
+    return ph.alg == kAlgSubset
+               ? launch_xsec_alg<double, kAlgSubset>(n, seed, i0, npts, S, ph, partials, w_out, esc, L, st)
+               : launch_xsec_alg<double, kAlgTree>(n, seed, i0, npts, S, ph, partials, w_out, esc, L, st);
+}
 
 static thread_local std::string g_err;
 
@@ -205,7 +230,8 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
         // each pipeline many stages
         L->block = kWsConsumers + ws_stage(n);
         L->tile = ws_stage(n);
-        const int e = occupancy_ws_f32(n, &bpsm, &smem);
+        const int e = alg == kAlgSubset ? occupancy_ws_alg<kAlgSubset>(n, &bpsm, &smem)
+                                        : occupancy_ws_alg<kAlgTree>(n, &bpsm, &smem);
         if (e) return e;
         if (bpsm < 1) bpsm = 1;
         L->smem = smem;
@@ -216,8 +242,12 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
     }
     L->block = kBlockThreads;
     L->tile = tile > 0 ? tile : default_tile(n, xsec);
-    const int e = precision == HEGET_FP32 ? occupancy_f32(n, L->tile, &bpsm, &smem)
-                                          : occupancy_f64(n, L->tile, &bpsm, &smem);
+    const bool sub = alg == kAlgSubset;
+    const int e = precision == HEGET_FP32
+                      ? (sub ? occupancy_alg<float, kAlgSubset>(n, L->tile, &bpsm, &smem)
+                             : occupancy_alg<float, kAlgTree>(n, L->tile, &bpsm, &smem))
+                      : (sub ? occupancy_alg<double, kAlgSubset>(n, L->tile, &bpsm, &smem)
+                             : occupancy_alg<double, kAlgTree>(n, L->tile, &bpsm, &smem));
     if (e) return e;
     if (bpsm < 1) bpsm = 1;
     L->smem = smem;
@@ -523,7 +553,9 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta, const ui
     if (((uintptr_t)momenta & 15) != 0) return fail(HEGET_EINVAL, "momenta must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     AmpLaunch L;
-    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, false, ctx->tiles[0][precision == HEGET_FP64][n]))) return cuda_fail((cudaError_t)r, "occupancy");
+    if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, false, ctx->tiles[0][precision == HEGET_FP64][n],
+                                ctx->alg)))
+        return cuda_fail((cudaError_t)r, "occupancy");
     const Physics ph = physics_of(ctx, n);
     cudaStream_t st = (cudaStream_t)stream;
     const bool esc = precision == HEGET_FP32 && ctx->esc_tau > 0 && N <= INT32_MAX;
@@ -540,9 +572,7 @@ int heget_amp2(heget_ctx* ctx, int n, int64_t N, const double* momenta, const ui
     if (esc) {
         // the flagged rows in FP64 (grid-stride over the device-side count)
         const int tile = ctx->tiles[0][1][n] > 0 ? ctx->tiles[0][1][n] : default_tile(n, false);
-        Physics ph64 = ph;
-        ph64.alg = kAlgSubset;   // as for the cross section: same |M|^2, far cheaper at large n
-        r = launch_amp2_list_f64(n, momenta, ctx->amp_esc_list, ctx->amp_esc_count, hel_mask, amp2, ph64, ctx->flag,
+        r = launch_amp2_list_f64(n, momenta, ctx->amp_esc_list, ctx->amp_esc_count, hel_mask, amp2, ph, ctx->flag,
                                  tile, 2 * ctx->num_sms, st);
         if (r) return cuda_fail((cudaError_t)r, "amp2_list_kernel");
     }
@@ -629,9 +659,7 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
         // FP64 recomputation of the flagged points (by the subset recursion,
         // whatever the context's algorithm: the same |M|^2, far cheaper at
         // large n); its partials follow the FP32 ones
-        Physics ph64 = ph;
-        ph64.alg = kAlgSubset;
-        r = launch_escalate_f64(n, seed, i0, S, ph64, default_tile(n, true), esc, ctx->partials + L.grid, w_out,
+        r = launch_escalate_f64(n, seed, i0, S, ph, default_tile(n, true), esc, ctx->partials + L.grid, w_out,
                                 L.grid, st);
         if (r) return cuda_fail((cudaError_t)r, "xsec_escalate_kernel");
     }

@@ -1,33 +1,13 @@
-// heget_f64.cu -- FP64 ("plain FP64") spinor-chain instantiations.
-
+// heget_f64.cu -- FP64 ("plain FP64") spinor-chain kernels that serve either
+// ordering-sum algorithm (the mixed-n batch), the gauge check (prefix tree)
+// and the FP64 recomputation of escalated FP32 points (subset recursion).
 #include "heget_launch.cuh"
 
 namespace heget {
 
-int launch_amp2_f64(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
-                    const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st) {
-#define CALL(N) launch_amp2_n<double, N>(mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st)
-    HEGET_DISPATCH_N(n, CALL)
-#undef CALL
-}
-
 int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph,
                     int* flag, const AmpLaunch& L, cudaStream_t st) {
 #define CALL(N) launch_ward_n<double, N>(mom, npts, ward, out, ph, flag, L, st)
-    HEGET_DISPATCH_N(n, CALL)
-#undef CALL
-}
-
-int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
-                    const Physics& ph, Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
-                    cudaStream_t st) {
-#define CALL(N) launch_xsec_n<double, N>(seed, i0, npts, S, ph, partials, w_out, esc, L, st)
-    HEGET_DISPATCH_N(n, CALL)
-#undef CALL
-}
-
-int occupancy_f64(int n, int tile, int* bpsm, size_t* smem) {
-#define CALL(N) occupancy_n<double, N>(tile, bpsm, smem)
     HEGET_DISPATCH_N(n, CALL)
 #undef CALL
 }

@@ -55,29 +55,43 @@ template <> struct DefaultShape<float, 6> : ShapeOf<HEGET_F32_HB_6, HEGET_F32_G_
 template <> struct DefaultShape<float, 7> : ShapeOf<HEGET_F32_HB_7, HEGET_F32_G_7> {};
 template <> struct DefaultShape<float, 8> : ShapeOf<HEGET_F32_HB_8, HEGET_F32_G_8> {};
 
-// Round-table bytes of the default shape (at least those of one
-// configuration per lane, which the gauge check uses).
-template <class R, int N, int BLOCK>
+// Round-table bytes of algorithm ALG: the tree's default shape (at least
+// those of one configuration per lane, which the gauge check uses), the
+// subset recursion's level tables, or the larger of the two (kAlgAny).
+template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t table_bytes() {
     using SH = DefaultShape<R, N>;
     constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = RoundTables<R, N, BLOCK>::bytes;
     constexpr size_t c = SubsetTables<R, N, BLOCK>::bytes;
     constexpr size_t ab = a > b ? a : b;
-    return align16(ab > c ? ab : c);
+    return align16(ALG == kAlgTree ? ab : ALG == kAlgSubset ? c : (ab > c ? ab : c));
 }
 
-// The amplitude rounds of the context's ordering-sum algorithm (uniform per
-// launch): the prefix tree of the paper's method, or the subset recursion.
+// The tables a kernel of algorithm ALG lays out: the tree's condition-bound
+// pass (FP32 escalation, kappa_rounds) runs on the subset recursion's tables,
+// so a tree kernel with it reserves both.
+template <int ALG, bool KAPPA>
+__host__ __device__ constexpr int table_alg() {
+    return KAPPA && ALG == kAlgTree ? kAlgAny : ALG;
+}
+
+// The amplitude rounds of the ordering-sum algorithm: the prefix tree of the
+// paper's method or the subset recursion, fixed per kernel by ALG, or (ALG =
+// kAlgAny) chosen by `alg`, uniform per launch.
 // kappa: also the condition bound recs[p].kap2 (FP32 escalation).
-template <class R, int N, int BLOCK, int BAR = 0>
+template <class R, int N, int BLOCK, int BAR = 0, int ALG = kAlgAny>
 __device__ __forceinline__ void amp_rounds(unsigned char* smem, PointRec<R, N>* recs, int cnt, const uint32_t* mask,
                                            int alg, bool kappa = false) {
-    if (alg == kAlgSubset) {
+    if constexpr (ALG == kAlgSubset) {
         amplitude_rounds_subset<R, N, BLOCK, BAR>(smem, recs, cnt, mask, kappa);
-    } else {
+    } else if constexpr (ALG == kAlgTree) {
         using SH = DefaultShape<R, N>;
         amplitude_rounds<R, N, BLOCK, BAR, SH::HB, SH::G>(smem, recs, cnt, mask);
         if (kappa) kappa_rounds<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
+    } else if (alg == kAlgSubset) {
+        amp_rounds<R, N, BLOCK, BAR, kAlgSubset>(smem, recs, cnt, mask, alg, kappa);
+    } else {
+        amp_rounds<R, N, BLOCK, BAR, kAlgTree>(smem, recs, cnt, mask, alg, kappa);
     }
 }
 
@@ -86,23 +100,23 @@ __device__ __forceinline__ void amp_rounds(unsigned char* smem, PointRec<R, N>* 
 // for amp2, generated photons for xsec); the two uses never overlap in time.
 __host__ __device__ constexpr int amp2_row(int N) { return (N + 2) * 4 + 1; }   // odd stride: conflict-free rows
 
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t amp2_region_bytes(int tile) {
     const size_t st = align16((size_t)tile * amp2_row(N) * sizeof(double));
-    return table_bytes<R, N, BLOCK>() > st ? table_bytes<R, N, BLOCK>() : st;
+    return table_bytes<R, N, BLOCK, ALG>() > st ? table_bytes<R, N, BLOCK, ALG>() : st;
 }
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t xsec_region_bytes(int tile) {
     const size_t st = align16((size_t)tile * N * kMomSlots * sizeof(double));
-    return table_bytes<R, N, BLOCK>() > st ? table_bytes<R, N, BLOCK>() : st;
+    return table_bytes<R, N, BLOCK, ALG>() > st ? table_bytes<R, N, BLOCK, ALG>() : st;
 }
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t amp2_smem_bytes(int tile) {
-    return amp2_region_bytes<R, N, BLOCK>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
+    return amp2_region_bytes<R, N, BLOCK, ALG>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
 }
-template <class R, int N, int BLOCK>
+template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t xsec_smem_bytes(int tile) {
-    return xsec_region_bytes<R, N, BLOCK>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
+    return xsec_region_bytes<R, N, BLOCK, ALG>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
 }
 
 // FP32 -> FP64 escalation lists of a fused launch: block b appends the
@@ -159,14 +173,16 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
     if (!ok) atomicOr(flag, 1);
 }
 
-template <class R, int N, int BLOCK, bool ESC = false>
+template <class R, int N, int BLOCK, bool ESC, int ALG>
 __global__ void __launch_bounds__(BLOCK)
 amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __restrict__ mask,
             double* __restrict__ out, int tile, Physics ph, int* __restrict__ flag, int* __restrict__ esc_list,
             int* __restrict__ esc_count) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* stage = reinterpret_cast<double*>(smem);
-    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK>(tile));
+    constexpr bool esc = ESC && sizeof(R) == sizeof(float);
+    PointRec<R, N>* recs =
+        reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK, table_alg<ALG, esc>()>(tile));
     constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
@@ -179,8 +195,7 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         __syncthreads();
-        constexpr bool esc = ESC && sizeof(R) == sizeof(float);
-        amp_rounds<R, N, BLOCK>(smem, recs, cnt, mask, ph.alg, esc);
+        amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, cnt, mask, ph.alg, esc);
         const float thr = esc ? esc_threshold(ph.esc_tau) : 0.0f;
         // one thread per point: FP64 normalisation and a coalesced store; points
         // whose FP32 error bound exceeds the threshold are listed for FP64
@@ -200,7 +215,7 @@ ward_kernel(const double* __restrict__ mom, long long npts, int ward, double* __
             Physics ph, int* __restrict__ flag) {
     extern __shared__ __align__(16) unsigned char smem[];
     double* stage = reinterpret_cast<double*>(smem);
-    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK>(tile));
+    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + amp2_region_bytes<R, N, BLOCK, kAlgTree>(tile));
     constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
@@ -282,13 +297,15 @@ __device__ __forceinline__ int compact_pos(bool flag, int local, int* cnts, int 
 // weight 0 and needs no amplitude); their amplitudes are computed in rounds
 // and their weights folded into acc.  w_out (may be NULL) receives the
 // tile's weights (0 for points that fail the cuts).
-template <class R, int N, int BLOCK, bool ESC = false>
+template <class R, int N, int BLOCK, bool ESC = false, int ALG = kAlgAny>
 __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_t seed, long long first, int cnt,
                                           const SamplerArgs& S, const Physics& ph, Partial& acc,
                                           double* __restrict__ w_out, const EscArgs& esc, int& esc_n) {
     __shared__ int s_cnt[BLOCK / 32];
     double* stage = reinterpret_cast<double*>(smem);
-    PointRec<R, N>* recs = reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK>(tile));
+    constexpr bool kEsc = ESC && sizeof(R) == sizeof(float);
+    PointRec<R, N>* recs =
+        reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK, table_alg<ALG, kEsc>()>(tile));
     int npass = 0;
     for (int t0 = 0; t0 < cnt; t0 += BLOCK) {
         const int t = t0 + (int)threadIdx.x;
@@ -318,8 +335,7 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         pass_to_rec<R, N>(MomView{stage + rec.idx, tile, kMomSlots}, rec.fac, ph, rec);
     }
     __syncthreads();
-    constexpr bool kEsc = ESC && sizeof(R) == sizeof(float);
-    amp_rounds<R, N, BLOCK>(smem, recs, npass, nullptr, ph.alg, kEsc);
+    amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, npass, nullptr, ph.alg, kEsc);
     // one thread per record: weight and double-double accumulation; records
     // whose FP32 error bound exceeds the threshold join the escalation list
     if constexpr (!kEsc) {
@@ -356,7 +372,7 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
     }
 }
 
-template <class R, int N, int BLOCK, bool ESC = false>
+template <class R, int N, int BLOCK, bool ESC, int ALG>
 __global__ void __launch_bounds__(BLOCK)
 xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, int tile,
             Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
@@ -365,8 +381,8 @@ xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
     int esc_n = 0;
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
-        xsec_tile<R, N, BLOCK, ESC>(smem, tile, seed, i0 + t0, cnt, S, ph, acc, w_out ? w_out + t0 : nullptr, esc,
-                                    esc_n);
+        xsec_tile<R, N, BLOCK, ESC, ALG>(smem, tile, seed, i0 + t0, cnt, S, ph, acc, w_out ? w_out + t0 : nullptr, esc,
+                                         esc_n);
     }
     if (ESC && threadIdx.x == 0) esc.cnt[blockIdx.x] = min(esc_n, esc.cap);
     // the round tables are free now: reuse them as reduction scratch
@@ -375,7 +391,8 @@ xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
 }
 
 // FP64 recomputation of the points an FP32 launch flagged (same grid): block
-// b regenerates the events of its list in order, evaluates them in FP64 and
+// b regenerates the events of its list in order, evaluates them in FP64 (with
+// the subset recursion: the same |M|^2 as the tree, far cheaper at large n) and
 // leaves the corrections sum (w64 - w32), sum (w64^2 - w32^2) and the count
 // in out[b]; w_out (relative to i0) receives the FP64 weights.  Combined
 // after the FP32 partials in fixed order, they make the flagged points count
@@ -387,7 +404,7 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
     extern __shared__ __align__(16) unsigned char smem[];
     double* stage = reinterpret_cast<double*>(smem);
     PointRec<double, N>* recs =
-        reinterpret_cast<PointRec<double, N>*>(smem + xsec_region_bytes<double, N, BLOCK>(tile));
+        reinterpret_cast<PointRec<double, N>*>(smem + xsec_region_bytes<double, N, BLOCK, kAlgSubset>(tile));
     const int nb = esc.cnt[blockIdx.x];
     const size_t base = (size_t)blockIdx.x * esc.cap;
     Partial acc = zero_partial();
@@ -401,7 +418,7 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
             recs[t].idx = t;
         }
         __syncthreads();
-        amp_rounds<double, N, BLOCK>(smem, recs, cnt, nullptr, ph.alg);
+        amp_rounds<double, N, BLOCK, 0, kAlgSubset>(smem, recs, cnt, nullptr, kAlgSubset);
         for (int t = threadIdx.x; t < cnt; t += BLOCK) {
             const double w64 = recs[t].ssum * recs[t].wfac, w32 = esc.w[base + c0 + t];
             acc.sw = dd_add_d(acc.sw, w64 - w32);
@@ -417,8 +434,8 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
     }
 }
 
-// FP64 |M|^2 of the rows listed by an FP32 heget_amp2 launch (their number
-// in *count): out[list[k]] is overwritten.
+// FP64 |M|^2 (subset recursion) of the rows listed by an FP32 heget_amp2
+// launch (their number in *count): out[list[k]] is overwritten.
 template <int N, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
 amp2_list_kernel(const double* __restrict__ mom, const int* __restrict__ list, const int* __restrict__ count,
@@ -427,7 +444,7 @@ amp2_list_kernel(const double* __restrict__ mom, const int* __restrict__ list, c
     extern __shared__ __align__(16) unsigned char smem[];
     double* stage = reinterpret_cast<double*>(smem);
     PointRec<double, N>* recs =
-        reinterpret_cast<PointRec<double, N>*>(smem + amp2_region_bytes<double, N, BLOCK>(tile));
+        reinterpret_cast<PointRec<double, N>*>(smem + amp2_region_bytes<double, N, BLOCK, kAlgSubset>(tile));
     constexpr int ROW = (N + 2) * 4, SROW = amp2_row(N);
     const long long npts = *count;
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
@@ -439,7 +456,7 @@ amp2_list_kernel(const double* __restrict__ mom, const int* __restrict__ list, c
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<double, N>(stage + t * SROW, ph, recs[t], flag);
         __syncthreads();
-        amp_rounds<double, N, BLOCK>(smem, recs, cnt, mask, ph.alg);
+        amp_rounds<double, N, BLOCK, 0, kAlgSubset>(smem, recs, cnt, mask, kAlgSubset);
         for (int t = threadIdx.x; t < cnt; t += BLOCK) out[list[t0 + t]] = (double)recs[t].ssum * recs[t].fac;
         __syncthreads();
     }
@@ -544,33 +561,34 @@ __device__ __forceinline__ void named_arrive(int id, int count) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <class R, int N>
+template <class R, int N, int ALG>
 __host__ __device__ constexpr size_t ws_recs_offset() {
-    return table_bytes<R, N, kWsConsumers>();
+    return table_bytes<R, N, kWsConsumers, ALG>();
 }
-template <class R, int N>
+template <class R, int N, int ALG>
 __host__ __device__ constexpr size_t ws_stage_offset() {
-    return ws_recs_offset<R, N>() + 2 * align16((size_t)ws_stage(N) * sizeof(PointRec<R, N>));
+    return ws_recs_offset<R, N, ALG>() + 2 * align16((size_t)ws_stage(N) * sizeof(PointRec<R, N>));
 }
-template <class R, int N>
+template <class R, int N, int ALG>
 __host__ __device__ constexpr size_t ws_smem_bytes() {
-    return ws_stage_offset<R, N>() + align16((size_t)ws_stage(N) * N * kMomSlots * sizeof(double));
+    return ws_stage_offset<R, N, ALG>() + align16((size_t)ws_stage(N) * N * kMomSlots * sizeof(double));
 }
-template <class R, int N>
+template <class R, int N, int ALG>
 __host__ __device__ constexpr int ws_min_blocks() {
-    return ws_smem_bytes<R, N>() <= 113 * 1024 ? 2 : 1;
+    return ws_smem_bytes<R, N, ALG>() <= 113 * 1024 ? 2 : 1;
 }
 
-template <class R, int N, bool ESC = false>
-__global__ void __launch_bounds__(kWsConsumers + ws_stage(N), ws_min_blocks<R, N>())
+template <class R, int N, bool ESC, int ALG>
+__global__ void __launch_bounds__(kWsConsumers + ws_stage(N), ws_min_blocks<R, N, table_alg<ALG, ESC>()>())
 xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph,
                Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
     constexpr int kWsStage = ws_stage(N);
     constexpr int kWsThreads = kWsConsumers + kWsStage;
     extern __shared__ __align__(16) unsigned char smem[];
-    PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N>());
+    constexpr int TAB = table_alg<ALG, ESC>();
+    PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N, TAB>());
     constexpr size_t ring_stride = align16((size_t)kWsStage * sizeof(PointRec<R, N>)) / sizeof(PointRec<R, N>);
-    double* stage = reinterpret_cast<double*>(smem + ws_stage_offset<R, N>());
+    double* stage = reinterpret_cast<double*>(smem + ws_stage_offset<R, N, TAB>());
     __shared__ int s_cnt[kWsStage / 32];
     __shared__ int stage_n[2];   // records (cut-passing points) of the stage in each ring slot
     const int tid = threadIdx.x;
@@ -653,7 +671,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             const int s = k & 1;
             named_sync(kBarFull + s, kWsThreads);
             const int cnt = stage_n[s];
-            amp_rounds<R, N, kWsConsumers, kBarRounds>(smem, ring + s * ring_stride, cnt, nullptr, ph.alg, ESC);
+            amp_rounds<R, N, kWsConsumers, kBarRounds, ALG>(smem, ring + s * ring_stride, cnt, nullptr, ph.alg, ESC);
             if (k + 2 < count) {
                 __threadfence_block();
                 named_arrive(kBarEmpty + s, kWsThreads);
@@ -672,8 +690,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
 }
 
 // ---------------------------------------------------------------------------
-// Host-side launch descriptors (defined per precision in heget_f32.cu /
-// heget_f64.cu).
+// Host-side launch descriptors.
 // ---------------------------------------------------------------------------
 struct AmpLaunch {
     int block, tile, grid;
@@ -689,26 +706,41 @@ constexpr bool use_ws(int n, int precision, bool xsec, int alg) {
     return xsec && precision == HEGET_FP32 && (n <= 5 || alg == kAlgSubset);
 }
 
-// Returns cudaError_t as int.
+// Per-algorithm launchers over n = 2..8 (ALG = kAlgTree or kAlgSubset),
+// defined in heget_launch.cuh and instantiated once per precision and
+// algorithm by the kernel translation units.  Return cudaError_t as int.
+template <class R, int ALG>
+int launch_amp2_alg(int n, const double* mom, long long npts, const uint32_t* mask, double* out, const Physics& ph,
+                    int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st);
+template <class R, int ALG>
+int launch_xsec_alg(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                    Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st);
+template <class R, int ALG>
+int occupancy_alg(int n, int tile, int* bpsm, size_t* smem);
+template <int ALG>
+int occupancy_ws_alg(int n, int* bpsm, size_t* smem);
+
+// The same, dispatched on ph.alg (heget_api.cu).
 int launch_amp2_f32(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
                     const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st);
 int launch_amp2_f64(int n, const double* mom, long long npts, const uint32_t* mask, double* out,
                     const Physics& ph, int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st);
-int launch_amp2_list_f64(int n, const double* mom, const int* list, const int* count, const uint32_t* mask,
-                         double* out, const Physics& ph, int* flag, int tile, int grid, cudaStream_t st);
-int launch_escalate_f64(int n, uint64_t seed, long long i0, const SamplerArgs& S, const Physics& ph, int tile,
-                        const EscArgs& esc, Partial* out, double* w_out, int grid, cudaStream_t st);
-int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
-                    const AmpLaunch& L, cudaStream_t st);
-int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
-                    const AmpLaunch& L, cudaStream_t st);
 int launch_xsec_f32(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
                     const Physics& ph, Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
                     cudaStream_t st);
 int launch_xsec_f64(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S,
                     const Physics& ph, Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
                     cudaStream_t st);
-int occupancy_ws_f32(int n, int* bpsm, size_t* smem);
+// FP64 recomputations of escalated points (subset recursion).
+int launch_amp2_list_f64(int n, const double* mom, const int* list, const int* count, const uint32_t* mask,
+                         double* out, const Physics& ph, int* flag, int tile, int grid, cudaStream_t st);
+int launch_escalate_f64(int n, uint64_t seed, long long i0, const SamplerArgs& S, const Physics& ph, int tile,
+                        const EscArgs& esc, Partial* out, double* w_out, int grid, cudaStream_t st);
+// Gauge check (prefix tree).
+int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
+                    const AmpLaunch& L, cudaStream_t st);
+int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
+                    const AmpLaunch& L, cudaStream_t st);
 // Mixed-n batch launch (one launch per precision); smem sized for the tiles.
 int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
                      cudaStream_t st);

@@ -1,6 +1,8 @@
-// heget_launch.cuh -- per-precision launch wrappers of the amplitude kernels.
-// Included by exactly one .cu per precision, which defines HEGET_REAL and
-// HEGET_SUFFIX before including it.
+// heget_launch.cuh -- launch wrappers of the amplitude kernels.  Included by
+// the kernel translation units only: each instantiates the per-algorithm
+// launchers of one precision and one ordering-sum algorithm
+// (HEGET_INSTANTIATE_ALG), or defines the launchers that serve any algorithm
+// (mixed-n batch, gauge check, FP64 recomputation of escalated points).
 #pragma once
 
 #include "heget_kernels.cuh"
@@ -9,24 +11,87 @@ namespace heget {
 
 constexpr int kBlock = 256;
 
-template <class R, int N>
+template <class R, int N, int ALG>
 static int launch_amp2_n(const double* mom, long long npts, const uint32_t* mask, double* out, const Physics& ph,
                          int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st) {
-    auto k = amp2_kernel<R, N, kBlock, false>;
+    auto k = amp2_kernel<R, N, kBlock, false, ALG>;
+    size_t smem = amp2_smem_bytes<R, N, kBlock, ALG>(L.tile);
     if constexpr (sizeof(R) == sizeof(float))
-        if (esc_list) k = amp2_kernel<R, N, kBlock, true>;
-    const size_t smem = amp2_smem_bytes<R, N, kBlock>(L.tile);
+        if (esc_list) {
+            k = amp2_kernel<R, N, kBlock, true, ALG>;
+            smem = amp2_smem_bytes<R, N, kBlock, table_alg<ALG, true>()>(L.tile);
+        }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     k<<<L.grid, kBlock, smem, st>>>(mom, npts, mask, out, L.tile, ph, flag, esc_list, esc_count);
     return (int)cudaGetLastError();
 }
 
+// The warp-specialised kernel exists where use_ws() can select it: FP32,
+// n <= 5 with the tree, every n with the subset recursion.
+template <class R, int N, int ALG>
+constexpr bool has_ws() {
+    return sizeof(R) == sizeof(float) && (N <= 5 || ALG == kAlgSubset);
+}
+
+template <class R, int N, int ALG>
+static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                         Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
+    if constexpr (has_ws<R, N, ALG>()) {
+        if (L.ws) {
+            auto k = esc.idx ? xsec_ws_kernel<R, N, true, ALG> : xsec_ws_kernel<R, N, false, ALG>;
+            const size_t smem = esc.idx ? ws_smem_bytes<R, N, table_alg<ALG, true>()>() : ws_smem_bytes<R, N, ALG>();
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return (int)e;
+            k<<<L.grid, kWsConsumers + ws_stage(N), smem, st>>>(seed, i0, npts, S, ph, partials, w_out, esc);
+            return (int)cudaGetLastError();
+        }
+    } else {
+        if (L.ws) return (int)cudaErrorInvalidValue;
+    }
+    auto k = xsec_kernel<R, N, kBlock, false, ALG>;
+    size_t smem = xsec_smem_bytes<R, N, kBlock, ALG>(L.tile);
+    if constexpr (sizeof(R) == sizeof(float))
+        if (esc.idx) {
+            k = xsec_kernel<R, N, kBlock, true, ALG>;
+            smem = xsec_smem_bytes<R, N, kBlock, table_alg<ALG, true>()>(L.tile);
+        }
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k<<<L.grid, kBlock, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out, esc);
+    return (int)cudaGetLastError();
+}
+
+template <class R, int N, int ALG>
+static int occupancy_n(int tile, int* blocks_per_sm, size_t* smem_out) {
+    const size_t smem = xsec_smem_bytes<R, N, kBlock, ALG>(tile);
+    *smem_out = smem;
+    auto k = xsec_kernel<R, N, kBlock, false, ALG>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
+}
+
+template <int N, int ALG>
+static int occupancy_ws_n(int* blocks_per_sm, size_t* smem_out) {
+    if constexpr (has_ws<float, N, ALG>()) {
+        const size_t smem = ws_smem_bytes<float, N, ALG>();
+        *smem_out = smem;
+        auto k = xsec_ws_kernel<float, N, false, ALG>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kWsConsumers + ws_stage(N),
+                                                                 smem);
+    } else {
+        return (int)cudaErrorInvalidValue;
+    }
+}
+
 template <int N>
 static int launch_amp2_list_n(const double* mom, const int* list, const int* count, const uint32_t* mask,
                               double* out, const Physics& ph, int* flag, int tile, int grid, cudaStream_t st) {
     auto k = amp2_list_kernel<N, kBlock>;
-    const size_t smem = amp2_smem_bytes<double, N, kBlock>(tile);
+    const size_t smem = amp2_smem_bytes<double, N, kBlock, kAlgSubset>(tile);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     k<<<grid, kBlock, smem, st>>>(mom, list, count, mask, out, tile, ph, flag);
@@ -37,7 +102,7 @@ template <int N>
 static int launch_escalate_n(uint64_t seed, long long i0, const SamplerArgs& S, const Physics& ph, int tile,
                              const EscArgs& esc, Partial* out, double* w_out, int grid, cudaStream_t st) {
     auto k = xsec_escalate_kernel<N, kBlock>;
-    const size_t smem = xsec_smem_bytes<double, N, kBlock>(tile);
+    const size_t smem = xsec_smem_bytes<double, N, kBlock, kAlgSubset>(tile);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     k<<<grid, kBlock, smem, st>>>(seed, i0, S, ph, tile, esc, out, w_out);
@@ -48,54 +113,11 @@ template <class R, int N>
 static int launch_ward_n(const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
                          const AmpLaunch& L, cudaStream_t st) {
     auto k = ward_kernel<R, N, kBlock>;
-    const size_t smem = amp2_smem_bytes<R, N, kBlock>(L.tile);
+    const size_t smem = amp2_smem_bytes<R, N, kBlock, kAlgTree>(L.tile);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     k<<<L.grid, kBlock, smem, st>>>(mom, npts, ward, out, L.tile, ph, flag);
     return (int)cudaGetLastError();
-}
-
-template <class R, int N>
-static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
-                         Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
-    if constexpr (sizeof(R) == sizeof(float)) {
-        if (L.ws) {
-            auto k = esc.idx ? xsec_ws_kernel<R, N, true> : xsec_ws_kernel<R, N, false>;
-            const size_t smem = ws_smem_bytes<R, N>();
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return (int)e;
-            k<<<L.grid, kWsConsumers + ws_stage(N), smem, st>>>(seed, i0, npts, S, ph, partials, w_out, esc);
-            return (int)cudaGetLastError();
-        }
-    }
-    auto k = xsec_kernel<R, N, kBlock, false>;
-    if constexpr (sizeof(R) == sizeof(float))
-        if (esc.idx) k = xsec_kernel<R, N, kBlock, true>;
-    const size_t smem = xsec_smem_bytes<R, N, kBlock>(L.tile);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    k<<<L.grid, kBlock, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out, esc);
-    return (int)cudaGetLastError();
-}
-
-template <class R, int N>
-static int occupancy_n(int tile, int* blocks_per_sm, size_t* smem_out) {
-    const size_t smem = xsec_smem_bytes<R, N, kBlock>(tile);
-    *smem_out = smem;
-    auto k = xsec_kernel<R, N, kBlock>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
-}
-
-template <int N>
-static int occupancy_ws_n(int* blocks_per_sm, size_t* smem_out) {
-    const size_t smem = ws_smem_bytes<float, N>();
-    *smem_out = smem;
-    auto k = xsec_ws_kernel<float, N>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kWsConsumers + ws_stage(N), smem);
 }
 
 template <class R>
@@ -119,5 +141,43 @@ static int launch_batch_t(const WorkItem* items, int nitems, const BatchReq* req
         case 8: return CALL(8);         \
         default: return (int)cudaErrorInvalidValue; \
     }
+
+template <class R, int ALG>
+int launch_amp2_alg(int n, const double* mom, long long npts, const uint32_t* mask, double* out, const Physics& ph,
+                    int* flag, int* esc_list, int* esc_count, const AmpLaunch& L, cudaStream_t st) {
+#define CALL(N) launch_amp2_n<R, N, ALG>(mom, npts, mask, out, ph, flag, esc_list, esc_count, L, st)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+template <class R, int ALG>
+int launch_xsec_alg(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                    Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
+#define CALL(N) launch_xsec_n<R, N, ALG>(seed, i0, npts, S, ph, partials, w_out, esc, L, st)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+template <class R, int ALG>
+int occupancy_alg(int n, int tile, int* bpsm, size_t* smem) {
+#define CALL(N) occupancy_n<R, N, ALG>(tile, bpsm, smem)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+template <int ALG>
+int occupancy_ws_alg(int n, int* bpsm, size_t* smem) {
+#define CALL(N) occupancy_ws_n<N, ALG>(bpsm, smem)
+    HEGET_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+// Explicit instantiation of one precision's launchers for one algorithm.
+#define HEGET_INSTANTIATE_ALG(R, ALG)                                                                               \
+    template int launch_amp2_alg<R, ALG>(int, const double*, long long, const uint32_t*, double*, const Physics&, \
+                                         int*, int*, int*, const AmpLaunch&, cudaStream_t);                       \
+    template int launch_xsec_alg<R, ALG>(int, uint64_t, long long, long long, const SamplerArgs&, const Physics&,  \
+                                         Partial*, double*, const EscArgs&, const AmpLaunch&, cudaStream_t);      \
+    template int occupancy_alg<R, ALG>(int, int, int*, size_t*);
 
 }  // namespace heget

@@ -30,6 +30,7 @@ namespace heget {
 
 constexpr int kAlgTree = 0;
 constexpr int kAlgSubset = 1;
+constexpr int kAlgAny = -1;   // kernel template argument: Physics::alg decides at run time
 
 __host__ __device__ constexpr int binom(int n, int k) {
     if (k < 0 || k > n) return 0;

@@ -1,0 +1,9 @@
+// heget_tree_f32.cu -- prefix-tree kernels (the paper's ordering sum) of the
+// FP32 spinor chain (FP64 phase space, denominators and accumulation):
+// amp2, fused cross section and occupancy launchers for n = 2..8.
+#include "heget_launch.cuh"
+
+namespace heget {
+HEGET_INSTANTIATE_ALG(float, kAlgTree)
+template int occupancy_ws_alg<kAlgTree>(int, int*, size_t*);
+}  // namespace heget
