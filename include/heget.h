@@ -166,6 +166,14 @@ int heget_ward(heget_ctx* ctx, int n, int64_t N, const double* momenta,
  * Runs on the current device; EINVAL for N < 0 or NULL arrays. */
 int heget_log_table(const double* x, double* y, int64_t N, void* stream);
 
+/* The device cosine and sine of the RAMBO azimuth phi = 2 pi r, Sec. 2.1
+ * eq. (4), exposed so that their accuracy can be checked.  words [N][2]
+ * (device uint32: lo, hi) are the two random words of one uniform,
+ * r = (2m + 1) 2^-53 with m = ((hi << 32) | lo) >> 12 (the generator's layout);
+ * cs [N][2] (device doubles) receives (cos phi, sin phi).  Runs on the
+ * current device; EINVAL for N < 0 or NULL arrays. */
+int heget_sincos_2pi(const uint32_t* words, double* cs, int64_t N, void* stream);
+
 /* Synchronizes `stream` and reports (then clears) the device-side input
  * flag raised by heget_amp2 / heget_ward: HEGET_EINVAL if set. */
 int heget_check(heget_ctx* ctx, void* stream);

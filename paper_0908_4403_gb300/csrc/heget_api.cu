@@ -116,6 +116,12 @@ __global__ void __launch_bounds__(256) log_table_kernel(const double* __restrict
         y[i] = log_table(x[i]);
 }
 
+__global__ void __launch_bounds__(256) sincos_kernel(const uint32_t* __restrict__ words, double* __restrict__ cs,
+                                                     long long n) {
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+        sincos_2pi_words(words[2 * i], words[2 * i + 1], cs[2 * i + 1], cs[2 * i]);
+}
+
 // ---------------------------------------------------------------------------
 // fixed-order reductions
 // ---------------------------------------------------------------------------
@@ -608,6 +614,17 @@ int heget_log_table(const double* x, double* y, int64_t N, void* stream) {
     log_table_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(x, y, N);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "log_table_kernel");
+    return HEGET_OK;
+}
+
+int heget_sincos_2pi(const uint32_t* words, double* cs, int64_t N, void* stream) {
+    if (N < 0) return fail(HEGET_EINVAL, "N < 0");
+    if (N == 0) return HEGET_OK;
+    if (!words || !cs) return fail(HEGET_EINVAL, "words and cs must be non-NULL");
+    const long long blocks = std::min<long long>((N + 255) / 256, 65536);
+    sincos_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(words, cs, N);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "sincos_kernel");
     return HEGET_OK;
 }
 

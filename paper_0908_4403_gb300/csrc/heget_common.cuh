@@ -102,10 +102,14 @@ struct PointRng {
     __device__ __forceinline__ PointRng(uint64_t seed, uint64_t i)
         : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), ilo((uint32_t)i),
           ihi((uint32_t)(i >> 32)) {}
+    // the random words of block b of stream `tag`: draw 2b from (x, y), 2b+1 from (z, w)
+    __device__ __forceinline__ U4 words(uint32_t tag, uint32_t b) const {
+        return philox4x32_10(U4{ilo, ihi, b, tag}, k0, k1);
+    }
     // both draws of block b of stream `tag`
     __device__ __forceinline__ void pair(uint32_t tag, uint32_t b, double& u0,
                                          double& u1) const {
-        const U4 w = philox4x32_10(U4{ilo, ihi, b, tag}, k0, k1);
+        const U4 w = words(tag, b);
         u0 = u01_from_words(w.x, w.y);
         u1 = u01_from_words(w.z, w.w);
     }

@@ -159,7 +159,7 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
     for (int a = 0; a < N; ++a)
 #pragma unroll
         for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
-    fill_denominators<R, N>(v, E2, is, false, rec);
+    fill_denominators<R, N, true>(v, E2, is, false, rec);
     rec.e2 = R(E2 * irs);
     rec.n1 = R(sqrt(2.0 * E1 * irs));
     rec.n2 = R(sqrt(2.0 * E2 * irs));
@@ -324,7 +324,7 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         const int pos = compact_pos<BLOCK>(pass, threadIdx.x, s_cnt, 0, tot);
         if (pass) {
             recs[npass + pos].idx = t;
-            recs[npass + pos].fac = ev.rs;   // sqrt(s-hat) until the record is built
+            recs[npass + pos].fac = ev.irs;   // 1/sqrt(s-hat) until the record is built
         }
         npass += tot;
     }
@@ -414,7 +414,7 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
             const MomView v{stage + t, tile, kMomSlots};
             EventInfo ev;
             generate_event<N>(seed, (uint64_t)esc.idx[base + c0 + t], S, ph, v, ev);
-            pass_to_rec<double, N>(v, ev.rs, ph, recs[t]);
+            pass_to_rec<double, N>(v, ev.irs, ph, recs[t]);
             recs[t].idx = t;
         }
         __syncthreads();
@@ -651,7 +651,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             PointRec<R, N>* rs_ring = ring + s * ring_stride;
             if (pass) {
                 rs_ring[pos].idx = g;
-                rs_ring[pos].fac = ev.rs;   // sqrt(s-hat) until the record is built
+                rs_ring[pos].fac = ev.irs;   // 1/sqrt(s-hat) until the record is built
             }
             named_sync(kBarProducers, kWsStage);
             // records built one per producer in compacted order: every lane busy

@@ -11,6 +11,7 @@
 
 #include "heget_common.cuh"
 #include "heget_logtab.h"
+#include "heget_sincostab.h"
 
 namespace heget {
 
@@ -108,26 +109,40 @@ __device__ __forceinline__ double toy_pdf_x_of(uint32_t wx, uint32_t wy) {
     return __dmul_rn(u, u);
 }
 
-// sqrt(s-hat), the boost factor e^y = sqrt(x1/x2) of the partonic frame and
-// the outer attempts for point i.  y itself (a logarithm) is left to callers
-// that output it.
-__device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointRng& rng, double& rs, double& ey,
-                                              double& x1, double& x2, int& tries, int& ok) {
-    ok = 1;
-    ey = 1.0;
-    x1 = x2 = 1.0;
-    tries = 1;
+// Scalars of one generated event; its photon momenta (GeV) live in a MomView.
+// ey, iey: e^y and e^-y of the partonic frame's rapidity y (1 for the fixed
+// and uniform samplers).
+struct EventInfo {
+    double rs, irs, ey, iey, x1, x2;
+    int tries, ok, mask;
+};
+
+// sqrt(s-hat) and its inverse, the momentum fractions, the boost factors
+// e^+-y and the outer attempts for point i.  With sqrt(s-hat) = 2 E sqrt(x1
+// x2), e^y = sqrt(x1 / x2) = 2 E x1 / sqrt(s-hat) and e^-y = 2 E x2 /
+// sqrt(s-hat): one division serves all three.  y itself (a logarithm) is
+// left to callers that output it.
+__device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointRng& rng, EventInfo& ev) {
+    ev.ok = 1;
+    ev.ey = ev.iey = 1.0;
+    ev.x1 = ev.x2 = 1.0;
+    ev.tries = 1;
     if (S.kind == HEGET_SAMPLER_FIXED) {
-        rs = S.sqrt_s;
+        ev.rs = S.sqrt_s;
+        ev.irs = 1.0 / ev.rs;
         return;
     }
     if (S.kind == HEGET_SAMPLER_UNIFORM) {
         double u, unused;
         rng.pair(kStreamSqrtS, 0, u, unused);
-        rs = S.lo + (S.hi - S.lo) * u;
+        ev.rs = S.lo + (S.hi - S.lo) * u;
+        ev.irs = 1.0 / ev.rs;
         return;
     }
     uint32_t blk = 0;
+    ev.ok = 0;
+    ev.rs = S.floor;
+    ev.tries = S.max_tries;
     for (int t = 1; t <= S.max_tries; ++t) {
         uint32_t ax, ay, bx, by;
         if (!toy_pdf_draw(rng, blk, S.max_tries, ax, ay)) break;
@@ -135,17 +150,18 @@ __device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointR
         const double a = toy_pdf_x_of(ax, ay), b = toy_pdf_x_of(bx, by);
         const double r = 2.0 * S.e_beam * sqrt(a * b);
         if (r > S.floor) {
-            rs = r;
-            x1 = a;
-            x2 = b;
-            ey = sqrt(a / b);
-            tries = t;
-            return;
+            ev.rs = r;
+            ev.x1 = a;
+            ev.x2 = b;
+            ev.tries = t;
+            ev.ok = 1;
+            break;
         }
     }
-    ok = 0;
-    rs = S.floor;
-    tries = S.max_tries;
+    ev.irs = 1.0 / ev.rs;
+    const double h = 2.0 * S.e_beam * ev.irs;
+    ev.ey = ev.ok ? ev.x1 * h : 1.0;
+    ev.iey = ev.ok ? ev.x2 * h : 1.0;
 }
 
 // Photon momenta of one point held in shared memory: slot (a, m) at
@@ -191,6 +207,30 @@ __device__ __forceinline__ double log_table(double x) {
     return lhi + (r + (p + llo));
 }
 
+// cos and sin of the RAMBO azimuth phi = 2 pi r for the uniform
+// r = u01_from_words(lo, hi) = (2m + 1) 2^-53, m the top 52 bits of (hi, lo),
+// by a breakpoint table (heget_sincostab.h): j = round(512 r), a = 2 pi j/512
+// and theta = 2 pi (r - j/512), |theta| <= pi/512.  The remainder is exact:
+// r - j/512 = D 2^-53 with the integer D = 2m + 1 - j 2^44, |D| <= 2^43.  With
+// s = sin theta and c' = cos theta - 1 by their Taylor series (truncated below
+// 1e-19),
+//   cos phi = cos a + (c' cos a - s sin a),  sin phi = sin a + (c' sin a + s cos a),
+// within about 2 ulp; 15 FP64 operations and one table load.
+__device__ __forceinline__ void sincos_2pi_words(uint32_t lo, uint32_t hi, double& sp, double& cp) {
+    const unsigned long long m = ((((unsigned long long)hi) << 32) | lo) >> 12;
+    const unsigned long long j = (m + (1ull << 42)) >> 43;   // 0 .. 512
+    const long long D = (long long)(2 * m + 1) - (long long)(j << 44);
+    // D as a double without a conversion: 1.5 2^52 + D has D in its mantissa
+    const double d = __longlong_as_double(0x4338000000000000ll + D) - 0x1.8p52;
+    const double th = d * 0x1.921fb54442d18p-51;   // 2 pi 2^-53
+    const double t2 = th * th;
+    const double s = fma(th * t2, fma(t2, 1.0 / 120.0, -1.0 / 6.0), th);
+    const double cm = t2 * fma(t2, fma(t2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+    const double2 a = __ldg(&kSinCosTab[j & (kSinCosTable - 1)]);
+    cp = a.x + fma(a.x, cm, -(a.y * s));
+    sp = a.y + fma(a.y, cm, a.x * s);
+}
+
 // RAMBO: n massless momenta with total (rs, 0, 0, 0).  Photon i uses draws
 // 4i..4i+3 of the RAMBO stream: cos(theta) = 2 r0 - 1, phi = 2 pi r1,
 // q0 = -ln(r2 r3); the isotropic q_i are boosted and scaled onto the total.
@@ -199,15 +239,16 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomV
     double Q0 = 0, Q1 = 0, Q2 = 0, Q3 = 0;
 #pragma unroll 1
     for (int i = 0; i < N; ++i) {
-        double r0, r1, r2, r3;
-        rng.pair(kStreamRambo, 2 * i, r0, r1);
+        const U4 w = rng.words(kStreamRambo, 2 * i);   // r0 = u(w.x, w.y), r1 = u(w.z, w.w)
+        double r2, r3;
         rng.pair(kStreamRambo, 2 * i + 1, r2, r3);
-        const double c = 2.0 * r0 - 1.0;
+        const double c = 2.0 * u01_from_words(w.x, w.y) - 1.0;
         const double s = sqrt(1.0 - c * c);
         double sp, cp;
-        sincospi(2.0 * r1, &sp, &cp);
+        sincos_2pi_words(w.z, w.w, sp, cp);
         const double q0 = -log_table(r2 * r3);   // r2 r3 in [2^-106, 1): normal
-        const double q1 = q0 * s * cp, q2 = q0 * s * sp, q3 = q0 * c;
+        const double qs = q0 * s;
+        const double q1 = qs * cp, q2 = qs * sp, q3 = q0 * c;
         v(i, 0) = q0;
         v(i, 1) = q1;
         v(i, 2) = q2;
@@ -217,20 +258,24 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomV
         Q2 += q2;
         Q3 += q3;
     }
-    const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
-    const double iM = 1.0 / M;
+    // M = sqrt(Q^2), b = -Q/M, gamma = Q0/M, a = 1/(1 + gamma) = M/(M + Q0),
+    // x = rs/M; then p_i = x (gamma q0 + b.q, q + b (q0 + a b.q)).
+    const double M2 = Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3;
+    const double iM = rsqrt(M2);
+    const double M = M2 * iM;
     const double b1 = -Q1 * iM, b2 = -Q2 * iM, b3 = -Q3 * iM;
-    const double g = Q0 * iM;
-    const double a = 1.0 / (1.0 + g);
+    const double a = M / (M + Q0);
     const double x = rs * iM;
+    const double xg = x * (Q0 * iM), xb1 = x * b1, xb2 = x * b2, xb3 = x * b3;
 #pragma unroll 1
     for (int i = 0; i < N; ++i) {
         const double q0 = v(i, 0), q1 = v(i, 1), q2 = v(i, 2), q3 = v(i, 3);
         const double bq = b1 * q1 + b2 * q2 + b3 * q3;
-        v(i, 0) = x * (g * q0 + bq);
-        v(i, 1) = x * (q1 + b1 * q0 + a * bq * b1);
-        v(i, 2) = x * (q2 + b2 * q0 + a * bq * b2);
-        v(i, 3) = x * (q3 + b3 * q0 + a * bq * b3);
+        const double t = fma(a, bq, q0);
+        v(i, 0) = fma(xg, q0, x * bq);
+        v(i, 1) = fma(xb1, t, x * q1);
+        v(i, 2) = fma(xb2, t, x * q2);
+        v(i, 3) = fma(xb3, t, x * q3);
     }
 }
 
@@ -252,70 +297,84 @@ __device__ __forceinline__ bool lt_scaled(double v, double a, double w2) {
 //   cos(phi_i - phi_j)  = (px_i px_j + py_i py_j) / (pT_i pT_j);
 // a pair passes at once if |Delta eta| > R or Delta phi > R (compared on
 // squares), and only the remaining close pairs evaluate asinh and atan2.
+// ey, iey: e^y and e^-y.
 template <int N>
-__device__ __forceinline__ int pass_cuts(const MomView& p, double ey, const Physics& ph) {
+__device__ __forceinline__ int pass_cuts(const MomView& p, double ey, double iey, const Physics& ph) {
     // every photon and pair is tested without early exits: the FP64 pipe
     // executes whole warps, so a lane that could stop early saves nothing and
     // the divergence would cost the others
-    const double iey = 1.0 / ey;
     const double shy = 0.5 * (ey - iey), chy = 0.5 * (ey + iey);
     const double s_hi = ph.sinh_eta * chy - ph.cosh_eta * shy;    // sinh(E - y)
     const double s_lo = -ph.sinh_eta * chy - ph.cosh_eta * shy;   // sinh(-E - y)
     const double pt2min = ph.pt_min * ph.pt_min;
     bool ok = true;
+    double pt2[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const double pz = p(i, 3);
-        const double pt2 = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
+        pt2[i] = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
         // pT > pt_min and s_lo pT < pz < s_hi pT
-        ok = ok & (pt2 > pt2min) & lt_scaled(pz, s_hi, pt2) & lt_scaled(-pz, -s_lo, pt2);
+        ok = ok & (pt2[i] > pt2min) & lt_scaled(pz, s_hi, pt2[i]) & lt_scaled(-pz, -s_lo, pt2[i]);
     }
     if (ph.dr_min > 0) {
         // squares only: |p| = E for massless photons, and the sinh / cos
         // comparisons are decided on squares; pT_i pT_j (a square root) is
-        // formed only for the close pairs that need asinh and atan2
+        // formed only for the close pairs that need asinh and atan2.  The
+        // pairs are screened first (pair_index bits of `close`), then the
+        // close ones, which are rare, settled one by one.
         const double sdr2 = ph.sinh_dr * ph.sinh_dr;
-#pragma unroll 1
+        unsigned close = 0;
+#pragma unroll
         for (int i = 0; i < N; ++i)
-#pragma unroll 1
+#pragma unroll
             for (int j = i + 1; j < N; ++j) {
-                const double xi = p(i, 1), yi = p(i, 2), zi = p(i, 3);
-                const double xj = p(j, 1), yj = p(j, 2), zj = p(j, 3);
-                const double pp2 = (xi * xi + yi * yi) * (xj * xj + yj * yj);   // (pT_i pT_j)^2
-                const double sh = zi * p(j, 0) - zj * p(i, 0);   // sinh(d eta) pT_i pT_j
-                const double dot = xi * xj + yi * yj;            // cos(d phi) pT_i pT_j
+                const double pp2 = pt2[i] * pt2[j];                      // (pT_i pT_j)^2
+                const double sh = p(i, 3) * p(j, 0) - p(j, 3) * p(i, 0);   // sinh(d eta) pT_i pT_j
+                const double dot = p(i, 1) * p(j, 1) + p(i, 2) * p(j, 2);  // cos(d phi) pT_i pT_j
                 const bool far = (sh * sh > sdr2 * pp2) | lt_scaled(dot, ph.cos_dr, pp2);
-                if (!far && ok) {
-                    // a close pair: |d eta|, d phi <= R.  With s = |sinh d eta|
-                    // and t = tan d phi (dot > 0 here when R < pi/2),
-                    //   s^2 (1 - s^2/6)^2 <= d eta^2 <= s^2,
-                    //   t^2 (1 - t^2/3)^2 <= d phi^2 <= t^2
-                    // (asinh and atan lie between their first two Taylor
-                    // terms and their first), which settles all but the pairs
-                    // within about 1 % of R; those take asinh and atan2.
-                    const double cr = xi * yj - yi * xj;
-                    const double R2 = ph.dr_min * ph.dr_min;
-                    bool exact = !(dot > 0);
-                    if (!exact) {
-                        const double s2 = sh * sh / pp2, t2 = cr * cr / (dot * dot);
-                        const double a = 1.0 - s2 * (1.0 / 6.0), b = 1.0 - t2 * (1.0 / 3.0);
-                        const double hi = s2 + t2, lo = s2 * a * a + t2 * b * b;
-                        if (lo > R2 * (1.0 + 1e-12)) {
-                            // Delta R > R: the pair passes
-                        } else if (hi < R2 * (1.0 - 1e-12)) {
-                            ok = false;
-                        } else {
-                            exact = true;
-                        }
-                    }
-                    if (exact) {   // rare
-                        const double ptt = sqrt(pp2);
-                        const double deta = asinh(sh / ptt);
-                        const double dphi = atan2(fabs(cr), dot);
-                        ok = deta * deta + dphi * dphi > R2;
-                    }
+                close |= (far ? 0u : 1u) << pair_index<N>(i, j);
+            }
+        if (!ok) close = 0;
+        while (close) {
+            int q = __ffs(close) - 1, i = 0;
+            close &= close - 1;
+            while (q >= N - 1 - i) q -= N - 1 - i++;
+            const int j = i + 1 + q;
+            const double xi = p(i, 1), yi = p(i, 2), zi = p(i, 3);
+            const double xj = p(j, 1), yj = p(j, 2), zj = p(j, 3);
+            const double pp2 = (xi * xi + yi * yi) * (xj * xj + yj * yj);
+            const double sh = zi * p(j, 0) - zj * p(i, 0);
+            const double dot = xi * xj + yi * yj;
+            // a close pair: |d eta|, d phi <= R.  With s = |sinh d eta| and
+            // t = tan d phi (dot > 0 here when R < pi/2),
+            //   s^2 (1 - s^2/6)^2 <= d eta^2 <= s^2,
+            //   t^2 (1 - t^2/3)^2 <= d phi^2 <= t^2
+            // (asinh and atan lie between their first two Taylor terms and
+            // their first), which settles all but the pairs within about 1 %
+            // of R; those take asinh and atan2.
+            const double cr = xi * yj - yi * xj;
+            const double R2 = ph.dr_min * ph.dr_min;
+            bool exact = !(dot > 0);
+            if (!exact) {
+                const double s2 = sh * sh / pp2, t2 = cr * cr / (dot * dot);
+                const double a = 1.0 - s2 * (1.0 / 6.0), b = 1.0 - t2 * (1.0 / 3.0);
+                const double hi = s2 + t2, lo = s2 * a * a + t2 * b * b;
+                if (lo > R2 * (1.0 + 1e-12)) {
+                    // Delta R > R: the pair passes
+                } else if (hi < R2 * (1.0 - 1e-12)) {
+                    ok = false;
+                } else {
+                    exact = true;
                 }
             }
+            if (exact) {   // rare
+                const double ptt = sqrt(pp2);
+                const double deta = asinh(sh / ptt);
+                const double dphi = atan2(fabs(cr), dot);
+                ok = ok && deta * deta + dphi * dphi > R2;
+            }
+            if (!ok) close = 0;
+        }
     }
     return ok ? 1 : 0;
 }
@@ -343,9 +402,8 @@ __device__ __forceinline__ Tri lt_scaled_f(bool vneg, bool apos, float v2, float
 }
 
 template <int N>
-__device__ __forceinline__ int pass_cuts_fast(const MomView& p, double ey, const Physics& ph) {
+__device__ __forceinline__ int pass_cuts_fast(const MomView& p, double ey, double iey, const Physics& ph) {
     constexpr float kU = 5.9604645e-8f;   // 2^-24
-    const double iey = 1.0 / ey;
     const double shy = 0.5 * (ey - iey), chy = 0.5 * (ey + iey);
     const double s_hi = ph.sinh_eta * chy - ph.cosh_eta * shy;    // sinh(E - y)
     const double s_lo = -ph.sinh_eta * chy - ph.cosh_eta * shy;   // sinh(-E - y)
@@ -399,26 +457,20 @@ __device__ __forceinline__ int pass_cuts_fast(const MomView& p, double ey, const
     }
     // undecided tests, and the close pairs (which need the exact Delta R),
     // go to the FP64 decision
-    if (!sure || (ok && close)) return pass_cuts<N>(p, ey, ph);
+    if (!sure || (ok && close)) return pass_cuts<N>(p, ey, iey, ph);
     return ok ? 1 : 0;
 }
-
-// Scalars of one generated event; its photon momenta (GeV) live in a MomView.
-struct EventInfo {
-    double rs, ey, x1, x2;
-    int tries, ok, mask;
-};
 
 template <int N>
 __device__ __forceinline__ void generate_event(uint64_t seed, uint64_t i, const SamplerArgs& S, const Physics& ph,
                                                const MomView& v, EventInfo& ev) {
     const PointRng rng(seed, i);
-    sample_sqrt_s(S, rng, ev.rs, ev.ey, ev.x1, ev.x2, ev.tries, ev.ok);
+    sample_sqrt_s(S, rng, ev);
     rambo<N>(rng, ev.rs, v);
     // the FP32 prefilter keeps 5n floats per photon set live in the producer
     // threads: a gain up to n = 3 (+22 % at n = 2 on GB300), a loss above
-    if constexpr (N <= 3) ev.mask = ev.ok ? pass_cuts_fast<N>(v, ev.ey, ph) : 0;
-    else ev.mask = ev.ok ? pass_cuts<N>(v, ev.ey, ph) : 0;
+    if constexpr (N <= 3) ev.mask = ev.ok ? pass_cuts_fast<N>(v, ev.ey, ev.iey, ph) : 0;
+    else ev.mask = ev.ok ? pass_cuts<N>(v, ev.ey, ev.iey, ph) : 0;
 }
 
 // Flat phase-space weight Phi_n(s) of eq. (4).
@@ -429,14 +481,19 @@ __device__ __forceinline__ double phase_space_weight(double s) {
     return phase_space_const(N) * sn2;
 }
 
-// Propagator denominators t_T / s-hat of the record, in FP64, from photon
-// momenta in GeV, p2 = E2 (1, 0, 0, -1) and is = 1/s-hat.  For n <= 5 they
-// are sums of the Lorentz invariants
-//   t_T = sum_{i in T} k_i^2 + sum_{i<j in T} 2 k_i.k_j - sum_{i in T} 2 k_i.p2,
-// held in registers and summed in a fully unrolled loop over the sets; for
-// larger n (where the tree dwarfs this) t_T = (sum_{i in T} k_i - p2)^2 by
-// components, set by set.
-template <class R, int N>
+// Propagator denominators t_T of the record, in FP64, from photon momenta p
+// and p2 = E2 (1, 0, 0, -1), times `is` if SCALE (momenta in GeV, is =
+// 1/s-hat; without SCALE the momenta are already divided by sqrt(s-hat)).
+// For n <= 5 they are sums of the Lorentz invariants
+//   t_T = sum_{i in T} d_i + sum_{i<j in T} s_ij,
+//   d_i = k_i^2 - 2 k_i.p2,  s_ij = 2 k_i.k_j,
+// built up over the sets in increasing order in registers: with h the
+// highest photon of T and U = T - {h},
+//   t_T = t_U + e_h(U),  e_h(U) = d_h + sum_{j in U} s_jh = e_h(U - {l}) + s_lh
+// (l the lowest photon of U): two additions per set.  For larger n (where
+// the tree dwarfs this) t_T = (sum_{i in T} k_i - p2)^2 by components, set
+// by set.
+template <class R, int N, bool SCALE>
 __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, double is, bool massless,
                                                   PointRec<R, N>& rec) {
     if constexpr (N <= 5) {
@@ -444,23 +501,29 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const double e = p(i, 0), x = p(i, 1), y = p(i, 2), z = p(i, 3);
-            d[i] = (massless ? 0.0 : e * e - x * x - y * y - z * z) - 2.0 * E2 * (e + z);
+            d[i] = massless ? -(2.0 * E2 * (e + z)) : (e * e - x * x - y * y - z * z) - 2.0 * E2 * (e + z);
 #pragma unroll
             for (int j = i + 1; j < N; ++j)
                 sij[pair_index<N>(i, j)] = 2.0 * (e * p(j, 0) - x * p(j, 1) - y * p(j, 2) - z * p(j, 3));
         }
+        double t[1 << (N - 1)];   // t_U for the sets U below the current highest photon
+        double e[1 << (N - 1)];   // e_h(U)
 #pragma unroll
-        for (int T = 1; T < (1 << N) - 1; ++T) {
-            double t = 0.0;
+        for (int h = 0; h < N; ++h) {
+            e[0] = d[h];
 #pragma unroll
-            for (int i = 0; i < N; ++i)
-                if (T >> i & 1) {
-                    t += d[i];
+            for (int U = 1; U < (1 << h); ++U) {
+                const int l = __popc((U & -U) - 1);
+                e[U] = e[U & (U - 1)] + sij[pair_index<N>(l, h)];
+            }
 #pragma unroll
-                    for (int j = i + 1; j < N; ++j)
-                        if (T >> j & 1) t += sij[pair_index<N>(i, j)];
-                }
-            rec.t[T] = R(t * is);
+            for (int U = 0; U < (1 << h); ++U) {
+                const int T = U | (1 << h);
+                if (T == (1 << N) - 1) continue;
+                const double tt = U ? t[U] + e[U] : e[0];
+                rec.t[T] = R(SCALE ? tt * is : tt);
+                if (h < N - 1) t[T] = tt;
+            }
         }
     } else {
 #pragma unroll 1
@@ -474,22 +537,28 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
                     q2 += p(i, 2);
                     q3 += p(i, 3);
                 }
-            rec.t[T] = R((q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3) * is);
+            const double tt = q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3;
+            rec.t[T] = R(SCALE ? tt * is : tt);
         }
     }
 }
 
 // Record of a point that passed the cuts, from its photon momenta (GeV) and
-// sqrt(s-hat) (the fields of event_to_rec for ok = mask = 1).
+// irs = 1/sqrt(s-hat) (the fields of event_to_rec for ok = mask = 1).  The
+// momenta are divided by sqrt(s-hat) in place, and the denominators formed
+// from the scaled values.
 template <class R, int N>
-__device__ __forceinline__ void pass_to_rec(const MomView& v, double rs, const Physics& ph, PointRec<R, N>& rec) {
-    const double irs = 1.0 / rs;
+__device__ __forceinline__ void pass_to_rec(const MomView& v, double irs, const Physics& ph, PointRec<R, N>& rec) {
     const double is = irs * irs;
 #pragma unroll 1
     for (int a = 0; a < N; ++a)
 #pragma unroll
-        for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
-    fill_denominators<R, N>(v, 0.5 * rs, is, true, rec);
+        for (int m = 0; m < 4; ++m) {
+            const double k = v(a, m) * irs;
+            v(a, m) = k;
+            rec.k[a][m] = R(k);
+        }
+    fill_denominators<R, N, false>(v, 0.5, 1.0, true, rec);
     rec.e2 = R(0.5);
     rec.n1 = R(1);
     rec.n2 = R(1);
@@ -499,31 +568,6 @@ __device__ __forceinline__ void pass_to_rec(const MomView& v, double rs, const P
     rec.wfac = ph.wconst * is;   // w = wfac * (scaled |M|^2 sum)
     rec.valid = 1;
     rec.mask = 1;
-}
-
-// Event -> point record.  Weight per unit of the scaled |M|^2 sum (Sec. 2.1
-// eq. (2)): (1/2s)(1/4)(1/9) 3 (1/n!) Phi_n(s) fac = wconst / s, with
-// wconst = (4 pi alpha Q^2)^n c_n / (24 n!) GeV^-2 -> fb from the host.
-template <class R, int N>
-__device__ __forceinline__ void event_to_rec(const MomView& v, const EventInfo& ev, const Physics& ph,
-                                             PointRec<R, N>& rec) {
-    const double irs = 1.0 / ev.rs;
-    const double is = irs * irs;
-#pragma unroll 1
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
-    fill_denominators<R, N>(v, 0.5 * ev.rs, is, true, rec);
-    rec.e2 = R(0.5);
-    rec.n1 = R(1);
-    rec.n2 = R(1);
-    double sp = 1;  // s^(2-n)
-    for (int a = 2; a < N; ++a) sp *= is;
-    rec.fac = ph.cpl * sp;
-    rec.wfac = ev.mask ? ph.wconst * is : 0.0;   // w = wfac * (scaled |M|^2 sum)
-    rec.valid = ev.ok;
-    rec.mask = ev.mask;
-    rec.tries = ev.tries;
 }
 
 }  // namespace heget

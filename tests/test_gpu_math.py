@@ -1,8 +1,11 @@
-"""The device logarithm of the RAMBO energies (Tang's table-driven method)
-against the host libm logarithm: within 3 ulp of the result everywhere on the
-inputs RAMBO produces (products of two uniforms in (0, 1)), at every table
+"""Device elementary functions of RAMBO, checked against the host.
+
+The logarithm of the RAMBO energies (Tang's table-driven method) against the
+host libm logarithm: within 3 ulp of the result everywhere on the inputs
+RAMBO produces (products of two uniforms in (0, 1)), at every table
 breakpoint and midpoint, next to 1 (where the ln 2 terms cancel) and at the
-extreme exponents."""
+extreme exponents.  The cosine and sine of the azimuth 2 pi r against
+extended-precision host values: within 2.5 ulp."""
 import numpy as np
 import pytest
 
@@ -50,3 +53,49 @@ def test_log_table_argument_checks(heget_lib, gpu):
     with pytest.raises(H.HegetError):
         H.heget_log_table(None, None, 4)
     H.heget_log_table(None, None, 0)
+
+
+def _two_pi_long():
+    return np.longdouble("6.283185307179586476925286766559005768394")
+
+
+def test_sincos_2pi_within_two_and_a_half_ulp(heget_lib, gpu):
+    """The RAMBO azimuth (table of 2 pi j/512 plus Taylor series of the
+    remainder) against cos and sin of 2 pi r in extended precision: random
+    uniforms, every breakpoint and the midpoints between them (where the
+    table index switches), the quarter turns (exact zeros of one factor) and
+    the ends of (0, 1)."""
+    import torch
+    H = heget_lib
+    rng = np.random.default_rng(2 * 4403)
+    m = list(rng.integers(0, 2**52, size=200_000, dtype=np.uint64))
+    for j in range(513):
+        for off in (-(1 << 42) - 1, -(1 << 42), -1, 0, 1, (1 << 42) - 1, 1 << 42):
+            c = j * (1 << 43) + off
+            if 0 <= c < (1 << 52):
+                m.append(np.uint64(c))
+    m += [np.uint64(v) for v in (0, 1, (1 << 52) - 1, (1 << 52) - 2)]
+    m = np.array(m, dtype=np.uint64)
+    low = rng.integers(0, 1 << 12, size=m.size, dtype=np.uint64)
+    bits = (m << np.uint64(12)) | low
+    words = np.stack([(bits & np.uint64(0xFFFFFFFF)).astype(np.uint32), (bits >> np.uint64(32)).astype(np.uint32)], 1)
+    wd = torch.from_numpy(words.view(np.int32).copy()).cuda()
+    cs = torch.empty((m.size, 2), dtype=torch.float64, device="cuda")
+    H.heget_sincos_2pi(wd, cs, m.size)
+    torch.cuda.synchronize()
+    got = cs.cpu().numpy()
+    r = (2 * m.astype(np.longdouble) + 1) / np.longdouble(2.0**53)
+    phi = _two_pi_long() * r
+    for k, ref in enumerate((np.cos(phi), np.sin(phi))):
+        refd = ref.astype(np.float64)
+        err = np.abs(got[:, k].astype(np.longdouble) - ref) / np.spacing(np.abs(refd)).astype(np.longdouble)
+        err = err.astype(np.float64)
+        assert err.max() <= 2.5, (k, err.max(), m[np.argmax(err)])
+        assert np.mean(err <= 1.0) > 0.99
+
+
+def test_sincos_2pi_argument_checks(heget_lib, gpu):
+    H = heget_lib
+    with pytest.raises(H.HegetError):
+        H.heget_sincos_2pi(None, None, 4)
+    H.heget_sincos_2pi(None, None, 0)
