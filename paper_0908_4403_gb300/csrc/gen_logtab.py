@@ -1,13 +1,14 @@
 #!/usr/bin/env python3
 """Writes heget_logtab.h: the breakpoint table of the table-driven natural
-logarithm in heget_ps.cuh (Tang, ACM TOMS 16 (1990) 378).  For j = 0..64 and
-F_j = 1 + j/64 it stores ln F_j as a double-double (hi + lo, computed with
+logarithm in heget_ps.cuh (Tang, ACM TOMS 16 (1990) 378).  For j = 0..256 and
+F_j = 1 + j/256 it stores ln F_j as a double-double (hi + lo, computed with
 40-digit decimal arithmetic) and 1/F_j rounded to double.  ln 2 itself is
 stored the same way.  Run from anywhere: python gen_logtab.py"""
 import os
 from decimal import Decimal, getcontext
 
 getcontext().prec = 40
+TABLE = 256
 
 
 def dd(v: Decimal):
@@ -19,15 +20,16 @@ def dd(v: Decimal):
 def main():
     lines = [
         "// heget_logtab.h -- generated by gen_logtab.py; do not edit.",
-        "// ln(1 + j/64) = hi + lo (double-double) and 1/(1 + j/64), j = 0..64.",
+        f"// ln(1 + j/{TABLE}) = hi + lo (double-double) and 1/(1 + j/{TABLE}), j = 0..{TABLE}.",
         "#pragma once",
         "",
         "namespace heget {",
         "",
-        "__device__ const double kLogTab[65][3] = {",
+        f"constexpr int kLogTable = {TABLE};",
+        f"__device__ const double kLogTab[{TABLE + 1}][3] = {{",
     ]
-    for j in range(65):
-        F = Decimal(64 + j) / Decimal(64)
+    for j in range(TABLE + 1):
+        F = Decimal(TABLE + j) / Decimal(TABLE)
         hi, lo = dd(F.ln())
         inv = float(Decimal(1) / F)
         lines.append(f"    {{{hi.hex()}, {lo.hex()}, {inv.hex()}}},")

@@ -180,30 +180,31 @@ struct MomView {
 
 // Natural logarithm of a positive normal double by Tang's table-driven method
 // (P. T. P. Tang, ACM TOMS 16 (1990) 378): x = 2^e m with m in [1, 2), F the
-// nearest breakpoint 1 + j/64, f = m - F (exact, |f| <= 1/128), r = f / F,
+// nearest breakpoint 1 + j/256, f = m - F (exact, |f| <= 1/512), r = f / F,
 //   ln x = e ln 2 + ln F + ln(1 + r),
 // with ln F and ln 2 from double-double tables (heget_logtab.h) and ln(1 + r)
-// by its series to r^8 (|r| <= 2^-7: truncation below 2^-56 relative).  A
-// handful of FP64 operations instead of a general-purpose logarithm, for the
-// RAMBO energies.
+// by its series to r^6 (|r| <= 2^-9: truncation below 2^-56 relative).  F and
+// e become doubles through their bit patterns, so the whole costs 15 FP64
+// operations instead of a general-purpose logarithm, for the RAMBO energies.
 __device__ __forceinline__ double log_table(double x) {
     const int hi = __double2hiint(x), lo = __double2loint(x);
     const int e = ((hi >> 20) & 0x7FF) - 1023;
     const double m = __hiloint2double((hi & 0x000FFFFF) | 0x3FF00000, lo);
-    const int j = (((hi >> 13) & 0x7F) + 1) >> 1;   // nearest breakpoint, 0 .. 64
-    const double f = m - (1.0 + j * 0.015625);       // exact
+    const int j = (((hi >> 11) & 0x1FF) + 1) >> 1;            // nearest breakpoint, 0 .. 256
+    const double F = __hiloint2double(0x3FF00000 + (j << 12), 0);   // 1 + j/256
+    const double f = m - F;                                          // exact
     const double r = f * __ldg(&kLogTab[j][2]);
-    // ln(1 + r) - r = r^2 (-1/2 + r (1/3 + r (-1/4 + r (1/5 + r (-1/6 + r (1/7 - r/8))))))
-    double q = -0.125;
-    q = fma(q, r, 1.0 / 7.0);
-    q = fma(q, r, -1.0 / 6.0);
+    // ln(1 + r) - r = r^2 (-1/2 + r (1/3 + r (-1/4 + r (1/5 - r/6))))
+    double q = -1.0 / 6.0;
     q = fma(q, r, 0.2);
     q = fma(q, r, -0.25);
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
     const double p = r * r * q;
-    const double lhi = fma((double)e, kLn2Hi, __ldg(&kLogTab[j][0]));
-    const double llo = fma((double)e, kLn2Lo, __ldg(&kLogTab[j][1]));
+    // e as a double: 2^52 + 2^31 + e carries e in its low mantissa bits
+    const double ed = __hiloint2double(0x43300000, (int)(0x80000000u + (unsigned)e)) - 0x1.00000800p52;
+    const double lhi = fma(ed, kLn2Hi, __ldg(&kLogTab[j][0]));
+    const double llo = fma(ed, kLn2Lo, __ldg(&kLogTab[j][1]));
     return lhi + (r + (p + llo));
 }
 
@@ -279,12 +280,25 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomV
     }
 }
 
+// a < b for doubles a, b >= +0 (squares and their products, never -0 or
+// NaN): their IEEE bit patterns order like the values, so the comparison
+// runs on the integer pipe, not on the FP64 pipe with the arithmetic.
+__device__ __forceinline__ bool lt_nonneg(double a, double b) {
+    return __double_as_longlong(a) < __double_as_longlong(b);
+}
+
+// v < 0 from the bit pattern (false for -0).
+__device__ __forceinline__ bool is_negative(double v) {
+    const long long b = __double_as_longlong(v);
+    return b < 0 && (b << 1) != 0;
+}
+
 // v < a * w, decided on squares (w >= 0): no square root; written with
 // selects, so the lanes of a warp stay together.
 __device__ __forceinline__ bool lt_scaled(double v, double a, double w2) {
     const double v2 = v * v, r2 = a * a * w2;
-    const bool neg = v < 0;
-    return a >= 0 ? (neg || v2 < r2) : (neg && v2 > r2);
+    const bool neg = is_negative(v);
+    return a >= 0 ? (neg || lt_nonneg(v2, r2)) : (neg && lt_nonneg(r2, v2));
 }
 
 // Photon cuts, strict (Sec. 2.2): pT > pt_min, |eta + y| < eta_max with
@@ -314,7 +328,7 @@ __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, double iey
         const double pz = p(i, 3);
         pt2[i] = p(i, 1) * p(i, 1) + p(i, 2) * p(i, 2);
         // pT > pt_min and s_lo pT < pz < s_hi pT
-        ok = ok & (pt2[i] > pt2min) & lt_scaled(pz, s_hi, pt2[i]) & lt_scaled(-pz, -s_lo, pt2[i]);
+        ok = ok & lt_nonneg(pt2min, pt2[i]) & lt_scaled(pz, s_hi, pt2[i]) & lt_scaled(-pz, -s_lo, pt2[i]);
     }
     if (ph.dr_min > 0) {
         // squares only: |p| = E for massless photons, and the sinh / cos
@@ -331,7 +345,7 @@ __device__ __forceinline__ int pass_cuts(const MomView& p, double ey, double iey
                 const double pp2 = pt2[i] * pt2[j];                      // (pT_i pT_j)^2
                 const double sh = p(i, 3) * p(j, 0) - p(j, 3) * p(i, 0);   // sinh(d eta) pT_i pT_j
                 const double dot = p(i, 1) * p(j, 1) + p(i, 2) * p(j, 2);  // cos(d phi) pT_i pT_j
-                const bool far = (sh * sh > sdr2 * pp2) | lt_scaled(dot, ph.cos_dr, pp2);
+                const bool far = lt_nonneg(sdr2 * pp2, sh * sh) | lt_scaled(dot, ph.cos_dr, pp2);
                 close |= (far ? 0u : 1u) << pair_index<N>(i, j);
             }
         if (!ok) close = 0;

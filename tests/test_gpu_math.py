@@ -31,9 +31,10 @@ def test_log_table_within_three_ulp(heget_lib, gpu):
     m = rng.integers(0, 2**52, size=(2, 400_000), dtype=np.uint64)
     u = (m.astype(np.float64) + 0.5) * 2.0**-52          # the uniforms of the RNG layout
     xs = [u[0] * u[1], u[0]]
-    j = np.arange(65)
-    xs.append(1.0 + j / 64.0)
-    xs.append((1.0 + (j + 0.5) / 64.0)[:-1])
+    j = np.arange(257)
+    xs.append(1.0 + j / 256.0)
+    xs.append((1.0 + (j + 0.5) / 256.0)[:-1])
+    xs.append(np.nextafter(1.0 + (j + 0.5) / 256.0, 0.0)[:-1])
     xs.append(np.nextafter(1.0, 0.0) - np.arange(64) * 2.0**-53)
     xs.append(0.5 + np.arange(1, 64) * 2.0**-60)
     xs.append(np.ldexp(1.0 + rng.random(2000), rng.integers(-1021, 1023, 2000)))

@@ -1,7 +1,7 @@
 """The constant tables of the device elementary functions, pinned against an
 independent high-precision evaluation (mpmath at 200 bits): every entry of
 the RAMBO azimuth table (cos, sin of 2 pi j/512) and of the logarithm's
-breakpoint table (ln(1 + j/64) as a double-double, 1/(1 + j/64)) must be the
+breakpoint table (ln(1 + j/256) as a double-double, 1/(1 + j/256)) must be the
 correctly rounded value."""
 import os
 import re
@@ -34,9 +34,9 @@ def test_log_table_is_correctly_rounded():
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.prec = 200
     rows = _rows("heget_logtab.h", 3)
-    assert len(rows) == 65
+    assert len(rows) == 257
     for j, (hi, lo, inv) in enumerate(rows):
-        F = mpmath.mpf(64 + j) / 64
+        F = mpmath.mpf(256 + j) / 256
         ln = mpmath.log(F)
         assert hi == float(ln) and lo == float(ln - mpmath.mpf(hi)), j
         assert inv == float(1 / F), j
