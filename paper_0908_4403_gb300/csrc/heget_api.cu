@@ -331,6 +331,11 @@ SamplerArgs sampler_args(const heget_sampler* s) {
     a.hi = s->hi;
     a.e_beam = s->e_beam;
     a.floor = s->floor;
+    // the FP32 product of the two uniforms' 24-bit estimates is within
+    // 3 2^-24 of u_a u_b; 16 2^-24 on either side of the threshold is left to FP64
+    const double c = s->kind == HEGET_SAMPLER_TOY_PDF ? s->floor / (2.0 * s->e_beam) : 0.0;
+    a.band_lo = (float)(c - 16.0 * 0x1p-24);
+    a.band_hi = (float)(c + 16.0 * 0x1p-24);
     return a;
 }
 

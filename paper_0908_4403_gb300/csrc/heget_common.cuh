@@ -185,6 +185,9 @@ struct SamplerArgs {
     int kind;
     int max_tries;
     double sqrt_s, lo, hi, e_beam, floor;
+    // toy PDF: the floor test sqrt(s-hat) > floor in terms of the uniforms,
+    // u_a u_b > floor / (2 e_beam), settled in FP32 outside [band_lo, band_hi]
+    float band_lo, band_hi;
 };
 
 // Launch shape of the amplitude kernels (chosen per (n, precision)).

@@ -55,24 +55,30 @@ template <> struct DefaultShape<float, 6> : ShapeOf<HEGET_F32_HB_6, HEGET_F32_G_
 template <> struct DefaultShape<float, 7> : ShapeOf<HEGET_F32_HB_7, HEGET_F32_G_7> {};
 template <> struct DefaultShape<float, 8> : ShapeOf<HEGET_F32_HB_8, HEGET_F32_G_8> {};
 
-// Round-table bytes of algorithm ALG: the tree's default shape (at least
-// those of one configuration per lane, which the gauge check uses), the
-// subset recursion's level tables, or the larger of the two (kAlgAny).
-template <class R, int N, int BLOCK, int ALG = kAlgAny>
+// Shared-memory table layouts: the tree's (kAlgTree), the subset
+// recursion's without (kAlgSubset) or with (kTabSubsetKappa) the arrays of
+// the FP32 condition bound, or room for any of them (kAlgAny).
+constexpr int kTabSubsetKappa = 2;
+
+// Round-table bytes of layout TAB: the tree's default shape (at least those
+// of one configuration per lane, which the gauge check uses), the subset
+// recursion's, or the larger of the two.
+template <class R, int N, int BLOCK, int TAB = kAlgAny>
 __host__ __device__ constexpr size_t table_bytes() {
     using SH = DefaultShape<R, N>;
     constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = RoundTables<R, N, BLOCK>::bytes;
-    constexpr size_t c = SubsetTables<R, N, BLOCK>::bytes;
+    constexpr size_t c = SubsetTables<R, N, BLOCK>::bytes_core, ck = SubsetTables<R, N, BLOCK>::bytes;
     constexpr size_t ab = a > b ? a : b;
-    return align16(ALG == kAlgTree ? ab : ALG == kAlgSubset ? c : (ab > c ? ab : c));
+    return align16(TAB == kAlgTree ? ab : TAB == kAlgSubset ? c : TAB == kTabSubsetKappa ? ck : (ab > ck ? ab : ck));
 }
 
-// The tables a kernel of algorithm ALG lays out: the tree's condition-bound
-// pass (FP32 escalation, kappa_rounds) runs on the subset recursion's tables,
-// so a tree kernel with it reserves both.
+// The table layout of a kernel of algorithm ALG: the condition-bound pass
+// (FP32 escalation) needs the subset tables' bound arrays, and the tree's
+// (kappa_rounds) runs on the subset layout, so a tree kernel with it
+// reserves both.
 template <int ALG, bool KAPPA>
 __host__ __device__ constexpr int table_alg() {
-    return KAPPA && ALG == kAlgTree ? kAlgAny : ALG;
+    return !KAPPA ? ALG : ALG == kAlgTree ? kAlgAny : ALG == kAlgSubset ? kTabSubsetKappa : ALG;
 }
 
 // The amplitude rounds of the ordering-sum algorithm: the prefix tree of the
@@ -543,12 +549,21 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 // amplitudes at small n (and at every n with the subset recursion) and needs
 // many events in flight while the amplitudes run.  Each block therefore splits into
 // roles that run concurrently:
-//   warps 0..7  (256 threads): consumers -- the amplitude rounds of the tree;
-//   warps 8..   (ws_stage(n) threads): producers -- one event per thread per stage.
+//   warps 0..7  (256 threads): consumers -- the amplitude rounds of the tree,
+//               and the sampler draws of the stage two ahead;
+//   warps 8..   (ws_stage(n) threads): producers -- one event per thread per
+//               stage from its draws: the FP64 rest (sqrt(s-hat), RAMBO, cuts,
+//               records).
+// The sampler (the toy PDF's rejection loops) is integer and FP32 work whose
+// iteration counts differ from lane to lane; run on the producers it would
+// idle the FP64 pipe, on the consumers it fills their waits.
 // Producers fill a double-buffered ring of ws_stage(n) point records in shared
 // memory; the two roles hand stages over through named barriers
 //   FULL[s]  (bar.arrive by producers, bar.sync by consumers) and
-//   EMPTY[s] (bar.arrive by consumers, bar.sync by producers),
+//   EMPTY[s] (bar.arrive by consumers, bar.sync by producers);
+// the draws of stage k + 2 go into slot s = k & 1 of a second double buffer
+// before the consumers' EMPTY[s] arrival (those of stages 0 and 1 before the
+// roles split),
 // while the consumers' own rounds synchronise on barrier kBarRounds.  Every
 // thread of both roles runs the same number of stages, so each barrier
 // instance collects exactly 256 + ws_stage(n) arrivals.  A block walks tiles
@@ -601,11 +616,20 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
     double* stage = reinterpret_cast<double*>(smem + ws_stage_offset<R, N, TAB>());
     __shared__ int s_cnt[kWsStage / 32];
     __shared__ int stage_n[2];   // records (cut-passing points) of the stage in each ring slot
+    __shared__ SampleDraw s_draw[2][kWsStage];   // sampler draws of the stage in each slot
     const int tid = threadIdx.x;
     const long long tiles = (npts + kWsStage - 1) / kWsStage;
     const int count = tiles > blockIdx.x ? (int)((tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
     Partial acc = zero_partial();
     auto stage_t0 = [&](int k) { return ((long long)blockIdx.x + (long long)k * gridDim.x) * kWsStage; };
+    // draws of stage k into slot s by `nthr` threads (local ids `lid`)
+    auto draw_stage = [&](int k, int s, int lid, int nthr) {
+        const long long t0 = stage_t0(k);
+        for (int p = lid; p < kWsStage; p += nthr)
+            if (t0 + p < npts) s_draw[s][p] = sample_draw(S, PointRng(seed, (uint64_t)(i0 + t0 + p)));
+    };
+    for (int k = 0; k < 2 && k < count; ++k) draw_stage(k, k, tid, kWsThreads);
+    __syncthreads();
     // the producer owning slot g of stage k folds that point's weight into its
     // accumulator once the consumers have released the stage
     int esc_n = 0;
@@ -648,7 +672,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             EventInfo ev;
             bool pass = false;
             if (g < cnt) {
-                generate_event<N>(seed, (uint64_t)(i0 + t0 + g), S, ph, v, ev);
+                generate_from<N>(PointRng(seed, (uint64_t)(i0 + t0 + g)), s_draw[s][g], S, ph, v, ev);
                 pass = ev.ok && ev.mask;
                 acc.npass += ev.mask;
                 acc.ntotal += 1;
@@ -683,6 +707,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             const int cnt = stage_n[s];
             amp_rounds<R, N, kWsConsumers, kBarRounds, ALG>(smem, ring + s * ring_stride, cnt, nullptr, ph.alg, ESC);
             if (k + 2 < count) {
+                draw_stage(k + 2, s, tid, kWsConsumers);   // the producers read slot s after EMPTY[s]
                 __threadfence_block();
                 named_arrive(kBarEmpty + s, kWsThreads);
             }

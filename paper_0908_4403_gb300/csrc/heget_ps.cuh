@@ -117,46 +117,85 @@ struct EventInfo {
     int tries, ok, mask;
 };
 
+// The sampler's random draws for one point, kept apart from the FP64 rest
+// of the event: integer and FP32 work (plus a rare FP64 tie-break), which
+// another set of threads can run ahead of time.  16 bytes: u01_from_words
+// ignores the low 12 bits of its low word, so those of ax carry the outer
+// attempts and the success flag.
+struct alignas(16) SampleDraw {
+    uint32_t ax, ay;   // toy PDF: words of the accepted x1 draw; uniform: the words of sqrt(s-hat)
+    uint32_t bx, by;   // toy PDF: words of the accepted x2 draw
+    __device__ __forceinline__ int tries() const { return (int)((ax >> 1) & 0x7FFu); }
+    __device__ __forceinline__ int ok() const { return (int)(ax & 1u); }
+    __device__ __forceinline__ void set(int tries, int ok) { ax = (ax & ~0xFFFu) | ((uint32_t)tries << 1) | (uint32_t)ok; }
+};
+
+__device__ __forceinline__ SampleDraw sample_draw(const SamplerArgs& S, const PointRng& rng) {
+    SampleDraw d{0u, 0u, 0u, 0u};
+    if (S.kind == HEGET_SAMPLER_FIXED) {
+        d.set(1, 1);
+        return d;
+    }
+    if (S.kind == HEGET_SAMPLER_UNIFORM) {
+        const U4 w = rng.words(kStreamSqrtS, 0);
+        d.ax = w.x;
+        d.ay = w.y;
+        d.set(1, 1);
+        return d;
+    }
+    // The floor test r > floor, r = 2 E sqrt(x1 x2) in FP64, is the test
+    // u_a u_b > floor / (2 E) on the uniforms behind x = u^2; their FP32
+    // estimates (within 2^-24) settle it outside a band of +-16 2^-24 around
+    // the threshold, and the FP64 r decides inside it.  So the loop runs on
+    // integer and FP32 work, and r and the fractions are formed once, by
+    // sample_finish.
+    uint32_t blk = 0;
+    int tries = S.max_tries, ok = 0;
+    for (int t = 1; t <= S.max_tries; ++t) {
+        if (!toy_pdf_draw(rng, blk, S.max_tries, d.ax, d.ay)) break;
+        if (!toy_pdf_draw(rng, blk, S.max_tries, d.bx, d.by)) break;
+        const float p = u01_estimate(d.ay) * u01_estimate(d.by);
+        bool pass = p > S.band_hi;
+        if (!pass && p >= S.band_lo) {   // rare
+            const double a = toy_pdf_x_of(d.ax, d.ay), b = toy_pdf_x_of(d.bx, d.by);
+            pass = 2.0 * S.e_beam * sqrt(a * b) > S.floor;
+        }
+        if (pass) {
+            tries = t;
+            ok = 1;
+            break;
+        }
+    }
+    d.set(tries, ok);
+    return d;
+}
+
 // sqrt(s-hat) and its inverse, the momentum fractions, the boost factors
-// e^+-y and the outer attempts for point i.  With sqrt(s-hat) = 2 E sqrt(x1
-// x2), e^y = sqrt(x1 / x2) = 2 E x1 / sqrt(s-hat) and e^-y = 2 E x2 /
+// e^+-y and the outer attempts from the draws.  With sqrt(s-hat) = 2 E
+// sqrt(x1 x2), e^y = sqrt(x1 / x2) = 2 E x1 / sqrt(s-hat) and e^-y = 2 E x2 /
 // sqrt(s-hat): one division serves all three.  y itself (a logarithm) is
 // left to callers that output it.
-__device__ __forceinline__ void sample_sqrt_s(const SamplerArgs& S, const PointRng& rng, EventInfo& ev) {
-    ev.ok = 1;
+__device__ __forceinline__ void sample_finish(const SamplerArgs& S, const SampleDraw& d, EventInfo& ev) {
+    ev.ok = d.ok();
+    ev.tries = d.tries();
     ev.ey = ev.iey = 1.0;
     ev.x1 = ev.x2 = 1.0;
-    ev.tries = 1;
     if (S.kind == HEGET_SAMPLER_FIXED) {
         ev.rs = S.sqrt_s;
         ev.irs = 1.0 / ev.rs;
         return;
     }
     if (S.kind == HEGET_SAMPLER_UNIFORM) {
-        double u, unused;
-        rng.pair(kStreamSqrtS, 0, u, unused);
-        ev.rs = S.lo + (S.hi - S.lo) * u;
+        ev.rs = S.lo + (S.hi - S.lo) * u01_from_words(d.ax, d.ay);
         ev.irs = 1.0 / ev.rs;
         return;
     }
-    uint32_t blk = 0;
-    ev.ok = 0;
-    ev.rs = S.floor;
-    ev.tries = S.max_tries;
-    for (int t = 1; t <= S.max_tries; ++t) {
-        uint32_t ax, ay, bx, by;
-        if (!toy_pdf_draw(rng, blk, S.max_tries, ax, ay)) break;
-        if (!toy_pdf_draw(rng, blk, S.max_tries, bx, by)) break;
-        const double a = toy_pdf_x_of(ax, ay), b = toy_pdf_x_of(bx, by);
-        const double r = 2.0 * S.e_beam * sqrt(a * b);
-        if (r > S.floor) {
-            ev.rs = r;
-            ev.x1 = a;
-            ev.x2 = b;
-            ev.tries = t;
-            ev.ok = 1;
-            break;
-        }
+    if (ev.ok) {
+        ev.x1 = toy_pdf_x_of(d.ax, d.ay);
+        ev.x2 = toy_pdf_x_of(d.bx, d.by);
+        ev.rs = 2.0 * S.e_beam * sqrt(ev.x1 * ev.x2);
+    } else {
+        ev.rs = S.floor;
     }
     ev.irs = 1.0 / ev.rs;
     const double h = 2.0 * S.e_beam * ev.irs;
@@ -475,16 +514,24 @@ __device__ __forceinline__ int pass_cuts_fast(const MomView& p, double ey, doubl
     return ok ? 1 : 0;
 }
 
+// Event i of stream `seed` from its sampler draws d: sqrt(s-hat), RAMBO
+// momenta into v, cut decision.
 template <int N>
-__device__ __forceinline__ void generate_event(uint64_t seed, uint64_t i, const SamplerArgs& S, const Physics& ph,
-                                               const MomView& v, EventInfo& ev) {
-    const PointRng rng(seed, i);
-    sample_sqrt_s(S, rng, ev);
+__device__ __forceinline__ void generate_from(const PointRng& rng, const SampleDraw& d, const SamplerArgs& S,
+                                              const Physics& ph, const MomView& v, EventInfo& ev) {
+    sample_finish(S, d, ev);
     rambo<N>(rng, ev.rs, v);
     // the FP32 prefilter keeps 5n floats per photon set live in the producer
     // threads: a gain up to n = 3 (+22 % at n = 2 on GB300), a loss above
     if constexpr (N <= 3) ev.mask = ev.ok ? pass_cuts_fast<N>(v, ev.ey, ev.iey, ph) : 0;
     else ev.mask = ev.ok ? pass_cuts<N>(v, ev.ey, ev.iey, ph) : 0;
+}
+
+template <int N>
+__device__ __forceinline__ void generate_event(uint64_t seed, uint64_t i, const SamplerArgs& S, const Physics& ph,
+                                               const MomView& v, EventInfo& ev) {
+    const PointRng rng(seed, i);
+    generate_from<N>(rng, sample_draw(S, rng), S, ph, v, ev);
 }
 
 // Flat phase-space weight Phi_n(s) of eq. (4).

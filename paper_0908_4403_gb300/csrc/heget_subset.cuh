@@ -78,13 +78,15 @@ struct SubsetTables {
     static constexpr int NS = 1 << N;
     static constexpr int JR = subset_level_rows(N);
     static constexpr int MR = subset_level_mats(N);
-    static constexpr size_t bytes = ((size_t)P * N + (size_t)P * NS + (size_t)P * N * 2   // PH, SD, CL
-                                     + 2 * (size_t)P * JR                                   // J ping-pong
-                                     + 2 * (size_t)P * MR) * sizeof(Row<R>)                 // M0K, M1K
-                                    + (size_t)P * NS * sizeof(R)                            // weighted |A|^2
-                                    + (2 * (size_t)P * JR + (size_t)P * MR + (size_t)P * N * 2
-                                       + (size_t)P * NS) * sizeof(R)                       // condition bound
-                                    + 2 * (size_t)NS + 16;                                  // rank, subset list
+    // bytes_core: what the recursion needs; bytes: with the condition-bound
+    // arrays (FP32 escalation), which come last
+    static constexpr size_t bytes_core = ((size_t)P * N + (size_t)P * NS + (size_t)P * N * 2   // PH, SD, CL
+                                          + 2 * (size_t)P * JR                                   // J ping-pong
+                                          + 2 * (size_t)P * MR) * sizeof(Row<R>)                 // M0K, M1K
+                                         + (size_t)P * NS * sizeof(R)                            // weighted |A|^2
+                                         + 2 * (size_t)NS + 16;                                  // rank, subset list
+    static constexpr size_t bytes = bytes_core + (2 * (size_t)P * JR + (size_t)P * MR + (size_t)P * N * 2 +
+                                                  (size_t)P * NS) * sizeof(R);                  // condition bound
     Row<R>* PH;    // [P][N]
     Row<R>* SD;    // [P][2^N]
     Row<R>* CL;    // [P][N][2]: closure columns (eps*_i . sigma) u_R, lambda minor
@@ -92,12 +94,12 @@ struct SubsetTables {
     Row<R>* M0K;   // [P][MR]: level's step matrices, entry (rank(S) k + pos) 2 + lambda
     Row<R>* M1K;
     R* A2;                 // [P][2^N]
+    unsigned char* RANK;   // [2^N]: rank of S among the subsets of its size
+    unsigned char* LIST;   // [2^N]: subsets by size, then rank
     R* JN[2];              // [P][JR]: norm bounds of the currents (condition bound)
     R* NM;                 // [P][MR]: norms of the level's step matrices
     R* CLN;                // [P][N][2]: norms of the closure columns
     R* B2;                 // [P][2^N]: weighted squared bounds
-    unsigned char* RANK;   // [2^N]: rank of S among the subsets of its size
-    unsigned char* LIST;   // [2^N]: subsets by size, then rank
     __device__ __forceinline__ explicit SubsetTables(unsigned char* base) {
         PH = reinterpret_cast<Row<R>*>(base);
         SD = PH + (size_t)P * N;
@@ -107,13 +109,13 @@ struct SubsetTables {
         M0K = J[1] + (size_t)P * JR;
         M1K = M0K + (size_t)P * MR;
         A2 = reinterpret_cast<R*>(M1K + (size_t)P * MR);
-        JN[0] = A2 + (size_t)P * NS;
+        RANK = reinterpret_cast<unsigned char*>(A2 + (size_t)P * NS);
+        LIST = RANK + NS;
+        JN[0] = reinterpret_cast<R*>(base + bytes_core);
         JN[1] = JN[0] + (size_t)P * JR;
         NM = JN[1] + (size_t)P * JR;
         CLN = NM + (size_t)P * MR;
         B2 = CLN + (size_t)P * N * 2;
-        RANK = reinterpret_cast<unsigned char*>(B2 + (size_t)P * NS);
-        LIST = RANK + NS;
     }
 };
 
