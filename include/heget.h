@@ -174,6 +174,13 @@ int heget_log_table(const double* x, double* y, int64_t N, void* stream);
  * current device; EINVAL for N < 0 or NULL arrays. */
 int heget_sincos_2pi(const uint32_t* words, double* cs, int64_t N, void* stream);
 
+/* The device double -> float conversion of the FP32 point records (round to
+ * nearest even by integer operations; results below the normal float range
+ * become signed zeros), exposed so that it can be checked against the
+ * hardware conversion: y[i] = (float) x[i] for N device values.  Runs on the
+ * current device; EINVAL for N < 0 or NULL arrays. */
+int heget_f32_round(const double* x, float* y, int64_t N, void* stream);
+
 /* Synchronizes `stream` and reports (then clears) the device-side input
  * flag raised by heget_amp2 / heget_ward: HEGET_EINVAL if set. */
 int heget_check(heget_ctx* ctx, void* stream);

@@ -122,6 +122,12 @@ __global__ void __launch_bounds__(256) sincos_kernel(const uint32_t* __restrict_
         sincos_2pi_words(words[2 * i], words[2 * i + 1], cs[2 * i + 1], cs[2 * i]);
 }
 
+__global__ void __launch_bounds__(256) f32_round_kernel(const double* __restrict__ x, float* __restrict__ y,
+                                                        long long n) {
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+        y[i] = f32_rn(x[i]);
+}
+
 // ---------------------------------------------------------------------------
 // fixed-order reductions
 // ---------------------------------------------------------------------------
@@ -630,6 +636,17 @@ int heget_sincos_2pi(const uint32_t* words, double* cs, int64_t N, void* stream)
     sincos_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(words, cs, N);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "sincos_kernel");
+    return HEGET_OK;
+}
+
+int heget_f32_round(const double* x, float* y, int64_t N, void* stream) {
+    if (N < 0) return fail(HEGET_EINVAL, "N < 0");
+    if (N == 0) return HEGET_OK;
+    if (!x || !y) return fail(HEGET_EINVAL, "x and y must be non-NULL");
+    const long long blocks = std::min<long long>((N + 255) / 256, 65536);
+    f32_round_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(x, y, N);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "f32_round_kernel");
     return HEGET_OK;
 }
 

@@ -217,6 +217,33 @@ struct MomView {
     __device__ __forceinline__ double& operator()(int a, int m) const { return p[(slots * a + m) * stride]; }
 };
 
+// double -> float, rounded to nearest even, by integer operations on the bit
+// pattern: on GB300 the hardware conversion occupies the FP64 pipe, which
+// the event generation saturates.  Exact for results in the normal float
+// range; results below it become a signed zero (no subnormals), above it
+// +-inf, and NaN stays NaN.
+__device__ __forceinline__ float f32_rn(double x) {
+    // 32-bit words throughout: the round bit is bit 28 of lo, the sticky bits
+    // 0..27, the kept bits start at 29; the exponent field of
+    // (|x| >> 29) mod 2^32 minus (1023 - 127) << 23 is the float's, and a
+    // round-up carry out of the mantissa moves into it
+    const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+    const unsigned int habs = hi & 0x7FFFFFFFu, sign = hi & 0x80000000u;
+    const unsigned int t = __funnelshift_r(lo, habs, 29);          // exponent and top mantissa bits
+    const unsigned int inc = (lo >> 28) & ((lo & 0x2FFFFFFFu) != 0u ? 1u : 0u);   // round bit and (sticky or lsb)
+    unsigned int f = t - (896u << 23) + inc;
+    f = habs < 0x38100000u ? 0u : f;
+    f = habs >= 0x47F00000u ? ((habs > 0x7FF00000u || (habs == 0x7FF00000u && lo != 0u)) ? 0x7FC00000u : 0x7F800000u) : f;
+    return __uint_as_float(f | sign);
+}
+
+// A record field from its FP64 value: f32_rn for FP32 records.
+template <class R>
+__device__ __forceinline__ R rec_value(double x) {
+    if constexpr (sizeof(R) == sizeof(float)) return f32_rn(x);
+    else return x;
+}
+
 // Natural logarithm of a positive normal double by Tang's table-driven method
 // (P. T. P. Tang, ACM TOMS 16 (1990) 378): x = 2^e m with m in [1, 2), F the
 // nearest breakpoint 1 + j/256, f = m - F (exact, |f| <= 1/512), r = f / F,
@@ -283,7 +310,8 @@ __device__ __forceinline__ void rambo(const PointRng& rng, double rs, const MomV
         double r2, r3;
         rng.pair(kStreamRambo, 2 * i + 1, r2, r3);
         const double c = 2.0 * u01_from_words(w.x, w.y) - 1.0;
-        const double s = sqrt(1.0 - c * c);
+        const double s2 = 1.0 - c * c;   // in [2^-51, 1): never 0
+        const double s = s2 * rsqrt(s2);
         double sp, cp;
         sincos_2pi_words(w.z, w.w, sp, cp);
         const double q0 = -log_table(r2 * r3);   // r2 r3 in [2^-106, 1): normal
@@ -460,17 +488,17 @@ __device__ __forceinline__ int pass_cuts_fast(const MomView& p, double ey, doubl
     const double shy = 0.5 * (ey - iey), chy = 0.5 * (ey + iey);
     const double s_hi = ph.sinh_eta * chy - ph.cosh_eta * shy;    // sinh(E - y)
     const double s_lo = -ph.sinh_eta * chy - ph.cosh_eta * shy;   // sinh(-E - y)
-    const float shi_f = (float)s_hi, slo_f = (float)s_lo;
+    const float shi_f = f32_rn(s_hi), slo_f = f32_rn(s_lo);
     const float shi2 = shi_f * shi_f, slo2 = slo_f * slo_f;
-    const float ptmin2 = (float)(ph.pt_min * ph.pt_min);
+    const float ptmin2 = f32_rn(ph.pt_min * ph.pt_min);
     float x[N], y[N], z[N], e[N], pt2[N];
     bool ok = true, sure = true;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        e[i] = (float)p(i, 0);
-        x[i] = (float)p(i, 1);
-        y[i] = (float)p(i, 2);
-        z[i] = (float)p(i, 3);
+        e[i] = f32_rn(p(i, 0));
+        x[i] = f32_rn(p(i, 1));
+        y[i] = f32_rn(p(i, 2));
+        z[i] = f32_rn(p(i, 3));
         pt2[i] = x[i] * x[i] + y[i] * y[i];
         const bool gt = pt2[i] > ptmin2 * (1.0f + 64.0f * kU), le = pt2[i] < ptmin2 * (1.0f - 64.0f * kU);
         sure = sure && (gt || le);
@@ -483,7 +511,7 @@ __device__ __forceinline__ int pass_cuts_fast(const MomView& p, double ey, doubl
     }
     bool close = false;
     if (ph.dr_min > 0) {
-        const float sdr2 = (float)(ph.sinh_dr * ph.sinh_dr), cdr = (float)ph.cos_dr;
+        const float sdr2 = f32_rn(ph.sinh_dr * ph.sinh_dr), cdr = f32_rn(ph.cos_dr);
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -582,7 +610,7 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
                 const int T = U | (1 << h);
                 if (T == (1 << N) - 1) continue;
                 const double tt = U ? t[U] + e[U] : e[0];
-                rec.t[T] = R(SCALE ? tt * is : tt);
+                rec.t[T] = rec_value<R>(SCALE ? tt * is : tt);
                 if (h < N - 1) t[T] = tt;
             }
         }
@@ -599,7 +627,7 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
                     q3 += p(i, 3);
                 }
             const double tt = q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3;
-            rec.t[T] = R(SCALE ? tt * is : tt);
+            rec.t[T] = rec_value<R>(SCALE ? tt * is : tt);
         }
     }
 }
@@ -617,7 +645,7 @@ __device__ __forceinline__ void pass_to_rec(const MomView& v, double irs, const 
         for (int m = 0; m < 4; ++m) {
             const double k = v(a, m) * irs;
             v(a, m) = k;
-            rec.k[a][m] = R(k);
+            rec.k[a][m] = rec_value<R>(k);
         }
     fill_denominators<R, N, false>(v, 0.5, 1.0, true, rec);
     rec.e2 = R(0.5);

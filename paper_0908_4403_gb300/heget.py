@@ -98,6 +98,7 @@ SIGNATURES = {
     "heget_check": (I32, [P, P]),
     "heget_log_table": (I32, [P, P, I64, P]),
     "heget_sincos_2pi": (I32, [P, P, I64, P]),
+    "heget_f32_round": (I32, [P, P, I64, P]),
     "heget_ward": (I32, [P, I32, I64, P, I32, I32, P, P]),
     "heget_xsec_async": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), I32, P, P, P]),
     "heget_xsec": (I32, [P, I32, I64, U64, C.POINTER(heget_sampler), I32, C.POINTER(heget_xsec_result), P]),
@@ -221,6 +222,10 @@ def heget_log_table(x, y, N, stream=None):
 
 def heget_sincos_2pi(words, cs, N, stream=None):
     _check(load().heget_sincos_2pi(_ptr(words), _ptr(cs), N, _stream(stream)))
+
+
+def heget_f32_round(x, y, N, stream=None):
+    _check(load().heget_f32_round(_ptr(x), _ptr(y), N, _stream(stream)))
 
 
 def heget_check(ctx, stream=None):

@@ -5,7 +5,8 @@ host libm logarithm: within 3 ulp of the result everywhere on the inputs
 RAMBO produces (products of two uniforms in (0, 1)), at every table
 breakpoint and midpoint, next to 1 (where the ln 2 terms cancel) and at the
 extreme exponents.  The cosine and sine of the azimuth 2 pi r against
-extended-precision host values: within 2.5 ulp."""
+extended-precision host values: within 2.5 ulp.  The records' integer
+double -> float conversion against the hardware one: bit for bit."""
 import numpy as np
 import pytest
 
@@ -100,3 +101,47 @@ def test_sincos_2pi_argument_checks(heget_lib, gpu):
     with pytest.raises(H.HegetError):
         H.heget_sincos_2pi(None, None, 4)
     H.heget_sincos_2pi(None, None, 0)
+
+
+def test_f32_round_matches_the_hardware_conversion(heget_lib, gpu):
+    """The records' double -> float conversion (integer operations) against
+    the hardware conversion, bit for bit, over the normal float range: random
+    values, ties and near-ties of the dropped 29 bits, carries into the
+    exponent, the largest finite float and the overflow boundary, infinities
+    and NaN; below 2^-126 it gives a signed zero."""
+    import torch
+    H = heget_lib
+    rng = np.random.default_rng(3 * 4403)
+    xs = [rng.standard_normal(100_000) * np.exp2(rng.integers(-120, 120, 100_000)),
+          rng.random(50_000), -rng.random(50_000)]
+    base = np.float32(rng.random(2000) + 1.0).astype(np.float64)
+    ulp = np.spacing(np.float32(base)).astype(np.float64)
+    for f in (0.5, 0.5 - 2.0**-30, 0.5 + 2.0**-30, 1.0 - 2.0**-30, 2.0**-29):
+        xs += [base + f * ulp, -(base + f * ulp)]
+    fmax = float(np.finfo(np.float32).max)
+    xs.append(np.array([0.0, -0.0, 2.0**-126, -(2.0**-126), fmax, -fmax, np.nextafter(2.0**128 - 2.0**103, 0.0),
+                        2.0**128 - 2.0**103, 2.0**129, np.inf, -np.inf, 1.9999999403953552, 0.99999997, 1e30]))
+    x = np.concatenate(xs)
+    x = x[(np.abs(x) >= 2.0**-126) | (x == 0)]   # the hardware keeps subnormals; the records never hold them
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    H.heget_f32_round(xd, yd, x.size)
+    torch.cuda.synchronize()
+    got = yd.cpu().numpy()
+    ref = xd.float().cpu().numpy()
+    np.testing.assert_array_equal(got.view(np.uint32), ref.view(np.uint32))
+    tiny = np.array([1e-39, -1e-40, 2.0**-127], dtype=np.float64)
+    H.heget_f32_round(torch.from_numpy(tiny).cuda(), yd, tiny.size)
+    torch.cuda.synchronize()
+    assert np.all(yd[:3].cpu().numpy() == 0.0) and np.signbit(yd[1].item())
+    nan = torch.tensor([np.nan], dtype=torch.float64, device="cuda")
+    H.heget_f32_round(nan, yd, 1)
+    torch.cuda.synchronize()
+    assert np.isnan(yd[0].item())
+
+
+def test_f32_round_argument_checks(heget_lib, gpu):
+    H = heget_lib
+    with pytest.raises(H.HegetError):
+        H.heget_f32_round(None, None, 4)
+    H.heget_f32_round(None, None, 0)
