@@ -46,10 +46,13 @@ FP32_PEAK = SMS * 128 * 2 * SM_GHZ / 1e3
 FP64_PEAK = SMS * 2 * 2 * SM_GHZ / 1e3
 # FP64 flops executed per point by the fused n = 4 FP32 step (DFMA x 2 +
 # DADD + DMUL, thread-level predicated-on counts from ncu on 262,144 points
-# of this workload): RNG, toy-PDF
-# sampler, RAMBO, cuts, and for the points that pass the cuts the
-# denominators, records, weights and double-double sums.
-FP64_FLOPS_PER_POINT = {4: 928}
+# of this workload): sqrt(s-hat), RAMBO, cuts, and for the points that pass
+# the cuts the denominators, records, weights and double-double sums.
+FP64_FLOPS_PER_POINT = {4: 714}
+# DRAM bytes per launch of that kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum): its inputs come from the counter-based generator,
+# so this is code, constant tables and block partials, the same at any size.
+FP64_STEP_TRAFFIC = {4: 151552}
 
 
 def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None):
@@ -65,7 +68,7 @@ def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None):
     if n in FP64_FLOPS_PER_POINT:
         a64 = FP64_FLOPS_PER_POINT[n] * N / kern_s / 1e12
         return {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": FP64_PEAK, "unit": "TFLOP/s",
-                "frac": a64 / FP64_PEAK, "traffic": 125696 if n == 4 else None, "kernel": kern,
+                "frac": a64 / FP64_PEAK, "traffic": FP64_STEP_TRAFFIC.get(n), "kernel": kern,
                 "flops_per_point": FP64_FLOPS_PER_POINT[n],
                 "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
                 "measured_peak": peak64_meas, "frac_of_measured": a64 / peak64_meas, "fp32_tree": fp32}
