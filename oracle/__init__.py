@@ -95,6 +95,7 @@ def _load():
             lib.oracle_event_weight.argtypes = [i32, d, d, d, i32]
             lib.oracle_event_weight.restype = d
             lib.oracle_event_weights.argtypes = [i32, u64, i64, i64, P, P, d, d, i32, P, P, P]
+            lib.oracle_hist.argtypes = [i32, i64, P, P, P, i32, P, P]
             _lib = lib
     return _lib
 
@@ -199,6 +200,32 @@ def event_weights(n: int, seed: int, i0: int, N: int, sampler: Sampler, cut: Cut
     lib.oracle_event_weights(n, seed, i0, N, C.byref(sampler), C.byref(cut) if cut else None,
                              alpha, Q, th, _ptr(w), _ptr(mask), _ptr(tries))
     return w, mask, tries
+
+
+class HistSpec(C.Structure):
+    """One histogram: observable kind (0 max pT, 1 pT, 2 eta, 3 Delta R of
+    each pair, 4 smallest Delta R, 5 sqrt(s-hat)), nbins uniform bins on
+    [lo, hi) plus an underflow and an overflow bin."""
+    _fields_ = [("kind", C.c_int), ("nbins", C.c_int), ("lo", C.c_double), ("hi", C.c_double)]
+
+
+def hist(n: int, mom, y, w, specs):
+    """Weighted histograms of events (momenta (N, n+2, 4), boost rapidities
+    y (N,), weights w (N,)): a list with one (nbins + 2, 2) array per spec
+    (rows: underflow, the bins, overflow; columns: sum w, sum w^2)."""
+    lib = _load()
+    mm = _f64(mom).reshape(-1)
+    yy, ww = _f64(y), _f64(w)
+    N = ww.size
+    arr = (HistSpec * len(specs))(*[HistSpec(*sp) for sp in specs])
+    total = sum(sp[1] + 2 for sp in specs)
+    out = np.zeros(2 * total)
+    lib.oracle_hist(n, N, _ptr(mm), _ptr(yy), _ptr(ww), len(specs), arr, _ptr(out))
+    res, off = [], 0
+    for sp in specs:
+        res.append(out[2 * off:2 * (off + sp[1] + 2)].reshape(sp[1] + 2, 2))
+        off += sp[1] + 2
+    return res
 
 
 def xsec_from_weights(w, tries=None, sampler_kind: int = 0):

@@ -640,3 +640,118 @@ void oracle_event_weights(int n, uint64_t seed, int64_t i0, int64_t N,
         if (tries_out) tries_out[j] = t;
     }
 }
+
+/*
+ * Weighted histograms of kinematic observables of the generated events
+ * (Sec. 5, Fig. 2: the maximum transverse momentum and the Delta R between
+ * final-state photons).  Observables, with pT = sqrt(px^2 + py^2),
+ * eta = asinh(pz / pT) + y (lab frame, as for the cuts of Sec. 2.2),
+ * phi = atan2(py, px) and Delta phi folded into [0, pi]:
+ *   0 the largest pT of the event's photons   (1 entry per event)
+ *   1 the pT of each photon                   (n entries)
+ *   2 the eta of each photon                  (n entries)
+ *   3 Delta R of each photon pair             (n(n-1)/2 entries)
+ *   4 the smallest Delta R of the event       (1 entry)
+ *   5 sqrt(s-hat) = E1 + E2                   (1 entry)
+ * Bins: 0 takes x < lo (and NaN), 1..nbins the uniform bins of [lo, hi)
+ * (closed on the left), nbins + 1 takes x >= hi; x falls in bin
+ * 1 + floor((x - lo) * (nbins / (hi - lo))).  Each entry adds the event's
+ * weight w to the bin's sum of w and w^2 to its sum of w^2, both summed
+ * with Neumaier's compensation.  out, per spec and bin in order:
+ * (sum w, sum w^2).  mom: [N][n+2][4]; y: [N].
+ */
+typedef struct {
+    int kind, nbins;
+    double lo, hi;
+} oracle_hist_spec;
+
+typedef struct { double s, c; } nsum;   /* Neumaier sum */
+
+static void nsum_add(nsum* a, double x)
+{
+    const double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static int hist_bin(double x, const oracle_hist_spec* H)
+{
+    if (!(x >= H->lo)) return 0;
+    const double t = (x - H->lo) * ((double)H->nbins / (H->hi - H->lo));
+    if (t >= H->nbins) return H->nbins + 1;
+    return 1 + (int)t;
+}
+
+void oracle_hist(int n, int64_t N, const double* mom, const double* y, const double* w,
+                 int nspec, const oracle_hist_spec* specs, double* out)
+{
+    int total = 0;
+    for (int s = 0; s < nspec; ++s) total += specs[s].nbins + 2;
+    nsum* sw = calloc((size_t)total, sizeof(nsum));
+    nsum* sw2 = calloc((size_t)total, sizeof(nsum));
+    for (int64_t j = 0; j < N; ++j) {
+        const double* ev = mom + (size_t)j * (n + 2) * 4;
+        const double* k = ev + 8;
+        double pt[ORACLE_MAXN], eta[ORACLE_MAXN], phi[ORACLE_MAXN];
+        for (int i = 0; i < n; ++i) {
+            pt[i] = sqrt(k[4 * i + 1] * k[4 * i + 1] + k[4 * i + 2] * k[4 * i + 2]);
+            eta[i] = asinh(k[4 * i + 3] / pt[i]) + y[j];
+            phi[i] = atan2(k[4 * i + 2], k[4 * i + 1]);
+        }
+        double dr[ORACLE_MAXN * ORACLE_MAXN];
+        int npair = 0;
+        for (int a = 0; a < n; ++a)
+            for (int b = a + 1; b < n; ++b) {
+                double dphi = fabs(phi[a] - phi[b]);
+                if (dphi > M_PI) dphi = 2 * M_PI - dphi;
+                const double deta = eta[a] - eta[b];
+                dr[npair++] = sqrt(deta * deta + dphi * dphi);
+            }
+        int off = 0;
+        for (int s = 0; s < nspec; ++s) {
+            const oracle_hist_spec* H = &specs[s];
+            double x[ORACLE_MAXN * ORACLE_MAXN];
+            int m = 0;
+            switch (H->kind) {
+                case 0:
+                    x[0] = pt[0];
+                    for (int i = 1; i < n; ++i)
+                        if (pt[i] > x[0]) x[0] = pt[i];
+                    m = 1;
+                    break;
+                case 1:
+                    for (int i = 0; i < n; ++i) x[m++] = pt[i];
+                    break;
+                case 2:
+                    for (int i = 0; i < n; ++i) x[m++] = eta[i];
+                    break;
+                case 3:
+                    for (int p = 0; p < npair; ++p) x[m++] = dr[p];
+                    break;
+                case 4:
+                    x[0] = dr[0];
+                    for (int p = 1; p < npair; ++p)
+                        if (dr[p] < x[0]) x[0] = dr[p];
+                    m = npair > 0 ? 1 : 0;
+                    break;
+                default:
+                    x[0] = ev[0] + ev[4];
+                    m = 1;
+                    break;
+            }
+            for (int e = 0; e < m; ++e) {
+                const int b = off + hist_bin(x[e], H);
+                nsum_add(&sw[b], w[j]);
+                nsum_add(&sw2[b], w[j] * w[j]);
+            }
+            off += H->nbins + 2;
+        }
+    }
+    for (int b = 0; b < total; ++b) {
+        out[2 * b] = sw[b].s + sw[b].c;
+        out[2 * b + 1] = sw2[b].s + sw2[b].c;
+    }
+    free(sw);
+    free(sw2);
+}
