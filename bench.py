@@ -234,6 +234,38 @@ def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, 
     return total / steps
 
 
+HIST_SPECS = [(0, 50, 20.0, 520.0), (1, 50, 20.0, 520.0), (2, 50, -2.5, 2.5), (3, 40, 0.4, 8.4),
+              (4, 40, 0.4, 8.4)]
+
+
+def time_hist(H, ctx, n, N, sampler, stream, seed, i0=0, flush=None, steps=5):
+    """Device time (CUDA events) of heget_hist over the N events of one step,
+    with that step's FP32 weights, L2 flushed between steps; points/s."""
+    import torch
+    res = torch.zeros(80, dtype=torch.uint8, device="cuda")
+    w = torch.empty(N, dtype=torch.float64, device="cuda")
+    out = torch.empty(H.hist_bins(HIST_SPECS), dtype=torch.float64, device="cuda")
+    H.heget_xsec_async(ctx, n, seed, i0, N, sampler, H.HEGET_FP32, res, w, stream=stream)
+    H.heget_hist(ctx, n, seed, i0, N, sampler, w, HIST_SPECS, out, stream=stream)
+    stream.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.add_(1)
+            stream.wait_stream(torch.cuda.current_stream())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        H.heget_hist(ctx, n, seed, i0, N, sampler, w, HIST_SPECS, out, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    ms = total / steps
+    return {"points_per_s": N / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+            "histograms": "max pT, pT, eta (50 bins each), Delta R of every pair, smallest Delta R (40 bins each)",
+            "note": "heget_hist on the events of one step with its FP32 weights: momenta regenerated on the "
+                    "device, double-double bin sums in a fixed order (Sec. 5, Fig. 2)"}
+
+
 # ---------------------------------------------------------------------------
 # serving: a Poisson trace of mixed requests through the request server
 # ---------------------------------------------------------------------------
@@ -495,6 +527,11 @@ def main():
                        seed=SEED + 8000, i0=i0, flush=flush, result=esc_res)
     H.heget_set_escalation(ctx, 0.0)
 
+    # kinematic distributions (Sec. 5, Fig. 2) of the same events: the step's
+    # weights, then heget_hist regenerates the momenta and bins max pT, the
+    # photons' pT and eta, every pair's Delta R and the smallest Delta R
+    dist = time_hist(H, ctx, n, N, sampler, stream, seed=SEED + 8500, i0=i0, flush=flush)
+
     # end to end through the public API: heget_xsec per step (launch, fused
     # RNG -> sampler -> RAMBO -> cuts -> |M|^2 -> sums, result read back to a
     # host struct, synchronised); the step's inputs are its arguments
@@ -550,6 +587,7 @@ def main():
                            "n_escalated_last_step": esc_res[0].n_escalated, "n_pass_last_step": esc_res[0].n_pass,
                            "note": "the same step with FP32 points whose error bound exceeds tau recomputed "
                                    "in FP64 (heget_set_escalation; off in the headline value)"},
+            "distributions": dist,
             "kernel_ms_per_step": kern_ms / args.steps,
             "result_last_step": {"sigma_fb": r.sigma_fb, "err_fb": r.err_fb, "n_pass": r.n_pass,
                                  "accept": r.accept, "pass_fraction": r.n_pass / max(1, r.n_total)},

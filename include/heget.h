@@ -232,6 +232,50 @@ typedef struct {
 int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, int count,
                      void* stream);
 
+/* Kinematic distributions (Sec. 5, Fig. 2: the maximum transverse momentum
+ * and the Delta R of the final-state photons).  Observables, in GeV for
+ * momenta, with pT = sqrt(px^2 + py^2), the lab pseudorapidity
+ * eta = asinh(pz / pT) + y (y the boost rapidity of the toy-PDF sampler, 0
+ * otherwise, as for the cuts of Sec. 2.2), phi = atan2(py, px) and
+ * Delta R = sqrt(Delta eta^2 + Delta phi^2) with Delta phi in [0, pi]. */
+#define HEGET_OBS_PT_MAX 0 /* largest photon pT of the event: 1 entry */
+#define HEGET_OBS_PT 1     /* pT of each photon: n entries */
+#define HEGET_OBS_ETA 2    /* eta of each photon: n entries */
+#define HEGET_OBS_DR 3     /* Delta R of each photon pair: n(n-1)/2 entries */
+#define HEGET_OBS_DR_MIN 4 /* smallest Delta R of the event: 1 entry */
+#define HEGET_OBS_SQRT_S 5 /* sqrt(s-hat): 1 entry */
+
+/* One histogram: `nbins` uniform bins on [lo, hi), closed on the left, plus
+ * an underflow bin (x < lo, and NaN) and an overflow bin (x >= hi).  x falls
+ * in bin 1 + floor((x - lo) * (nbins / (hi - lo))), evaluated in FP64. */
+typedef struct {
+    int32_t observable; /* HEGET_OBS_* */
+    int32_t nbins;      /* >= 1 */
+    double lo, hi;      /* finite, lo < hi */
+} heget_hist_spec;
+
+#define HEGET_HIST_MAX_SPECS 8
+#define HEGET_HIST_MAX_BINS 1024 /* sum over the specs of nbins + 2 */
+
+/* Weighted histograms of the events (seed, i0 .. i0+N-1) of n photons: each
+ * entry of an event adds its weight w[j] to its bin's sum of weights and w[j]^2
+ * to its sum of squares.  The events are those of heget_xsec and
+ * heget_phase_space_ex with the same (n, seed, i0, N, sampler) and the
+ * context's parameters; their momenta are regenerated on the device, so w
+ * is typically the w_out of a heget_xsec_async call on the same points
+ * (0 for the points that fail the cuts).
+ * w: N device doubles.  specs: host array of 1 <= nspec <= HEGET_HIST_MAX_SPECS
+ * histograms with at most HEGET_HIST_MAX_BINS bins in all.  out: device
+ * doubles, for each spec in order its nbins + 2 bins (underflow, the bins,
+ * overflow), each as (sum w, sum w^2): 2 sum (nbins + 2) values, written
+ * (zeros for N = 0).  The sums are double-double accumulations in a fixed
+ * order, so results are bitwise reproducible.  EINVAL for bad specs, n, N,
+ * sampler or NULL arrays (N > 0). */
+int heget_hist(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N,
+               const heget_sampler* sampler, const double* w,
+               const heget_hist_spec* specs, int nspec, double* out,
+               void* stream);
+
 /* heget_xsec_async in two halves: heget_xsec_launch enqueues only the fused
  * event kernel, leaving its block partials in the context workspace;
  * heget_xsec_finalize enqueues the fixed-order combination of the partials of

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libheget.so")
 
 SOURCES = ["heget_api.cu", "heget_f32.cu", "heget_f64.cu", "heget_tree_f32.cu", "heget_subset_f32.cu",
-           "heget_tree_f64.cu", "heget_subset_f64.cu", "heget_runtime.cu", "heget_server.cu"]
+           "heget_tree_f64.cu", "heget_subset_f64.cu", "heget_runtime.cu", "heget_server.cu", "heget_hist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -372,6 +372,9 @@ size_t batch_tile_smem(int n, int tile) {
     }
 }
 
+}  // namespace
+
+namespace heget {
 // Grows a workspace buffer to at least `need` bytes (device or pinned host).
 int grow(void** p, size_t* cap, size_t need, bool pinned) {
     if (*cap >= need) return HEGET_OK;
@@ -385,7 +388,7 @@ int grow(void** p, size_t* cap, size_t need, bool pinned) {
     *cap = c;
     return HEGET_OK;
 }
-}  // namespace
+}  // namespace heget
 
 namespace heget {
 // Entries per block of the escalation lists: every point a block can own.
@@ -452,6 +455,7 @@ void heget_destroy(heget_ctx* c) {
     if (c->flag) cudaFree(c->flag);
     if (c->res_dev) cudaFree(c->res_dev);
     if (c->res_host) cudaFreeHost(c->res_host);
+    if (c->hist_parts) cudaFree(c->hist_parts);
     delete c;
 }
 

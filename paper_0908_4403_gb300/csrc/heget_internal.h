@@ -66,6 +66,9 @@ struct heget_ctx {
     heget::Partial* batch_partials = nullptr;
     size_t batch_partials_cap = 0;
     cudaEvent_t batch_copied = nullptr;    // staging may be rewritten once this has fired
+    // heget_hist: per-block partial histograms (grown on demand)
+    double* hist_parts = nullptr;
+    size_t hist_parts_cap = 0;
 };
 
 namespace heget {
@@ -78,4 +81,6 @@ int check_sampler(const heget_sampler* s);
 SamplerArgs sampler_args(const heget_sampler* s);
 int check_common(const heget_ctx* ctx, int n, long long N);
 int check_precision(int p);
+// Grows a workspace buffer to at least `need` bytes (device, or pinned host).
+int grow(void** p, size_t* cap, size_t need, bool pinned);
 }  // namespace heget

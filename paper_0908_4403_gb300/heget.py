@@ -17,6 +17,8 @@ HEGET_OK, HEGET_EINVAL, HEGET_ENOMEM, HEGET_ECUDA, HEGET_ETIMEOUT, HEGET_EBUSY, 
 HEGET_FP32, HEGET_FP64 = 32, 64
 HEGET_SAMPLER_FIXED, HEGET_SAMPLER_UNIFORM, HEGET_SAMPLER_TOY_PDF = 0, 1, 2
 HEGET_ALG_TREE, HEGET_ALG_SUBSET = 0, 1
+HEGET_OBS_PT_MAX, HEGET_OBS_PT, HEGET_OBS_ETA, HEGET_OBS_DR, HEGET_OBS_DR_MIN, HEGET_OBS_SQRT_S = range(6)
+HEGET_HIST_MAX_SPECS, HEGET_HIST_MAX_BINS = 8, 1024
 
 STATUS_NAMES = {0: "HEGET_OK", 1: "HEGET_EINVAL", 2: "HEGET_ENOMEM", 3: "HEGET_ECUDA",
                 4: "HEGET_ETIMEOUT", 5: "HEGET_EBUSY", 6: "HEGET_ENOTFOUND"}
@@ -81,6 +83,10 @@ class heget_result(C.Structure):
                 ("t_done", C.c_double), ("status", C.c_int), ("reserved", C.c_int)]
 
 
+class heget_hist_spec(C.Structure):
+    _fields_ = [("observable", C.c_int32), ("nbins", C.c_int32), ("lo", C.c_double), ("hi", C.c_double)]
+
+
 _lib = None
 P, I32, I64, U64, D = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
 
@@ -106,6 +112,8 @@ SIGNATURES = {
     "heget_xsec_finalize": (I32, [P, P, P]),
     "heget_measure_fma_peak": (I32, [P, I32, C.POINTER(C.c_double)]),
     "heget_xsec_batch": (I32, [P, C.POINTER(heget_xsec_request), I32, P]),
+    "heget_hist": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), P, C.POINTER(heget_hist_spec), I32, P,
+                         P]),
     "heget_autotune": (I32, [P, I32, I32, I32, I64, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "heget_autotune_save": (I32, [P, C.c_char_p]),
     "heget_autotune_load": (I32, [P, C.c_char_p]),
@@ -256,6 +264,19 @@ def heget_measure_fma_peak(ctx, precision=HEGET_FP32) -> float:
     v = C.c_double()
     _check(load().heget_measure_fma_peak(ctx, precision, C.byref(v)))
     return v.value
+
+
+def hist_bins(specs):
+    """Output length of heget_hist: 2 sum (nbins + 2) doubles."""
+    return 2 * sum(sp[1] + 2 for sp in specs)
+
+
+def heget_hist(ctx, n, seed, i0, N, sampler, w, specs, out, stream=None):
+    """specs: list of (observable, nbins, lo, hi); out: device doubles of
+    length hist_bins(specs), per spec (nbins + 2) rows of (sum w, sum w^2)."""
+    arr = (heget_hist_spec * len(specs))(*[heget_hist_spec(*sp) for sp in specs])
+    _check(load().heget_hist(ctx, n, seed, i0, N, C.byref(sampler), _ptr(w), arr, len(specs), _ptr(out),
+                             _stream(stream)))
 
 
 def heget_xsec_batch(ctx, requests, stream=None):
