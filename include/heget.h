@@ -268,9 +268,11 @@ typedef struct {
  * histograms with at most HEGET_HIST_MAX_BINS bins in all.  out: device
  * doubles, for each spec in order its nbins + 2 bins (underflow, the bins,
  * overflow), each as (sum w, sum w^2): 2 sum (nbins + 2) values, written
- * (zeros for N = 0).  The sums are double-double accumulations in a fixed
- * order, so results are bitwise reproducible.  EINVAL for bad specs, n, N,
- * sampler or NULL arrays (N > 0). */
+ * (zeros for N = 0).  Each block sums its tiles' entries per bin in a fixed
+ * order and folds the tile sums into double-double sums, combined in block
+ * order: results are reproducible bit for bit on a given GPU model (the
+ * grid is one resident wave).  EINVAL for bad specs, n, N, sampler or NULL
+ * arrays (N > 0). */
 int heget_hist(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N,
                const heget_sampler* sampler, const double* w,
                const heget_hist_spec* specs, int nspec, double* out,

@@ -1,9 +1,10 @@
 // heget_hist.cu -- kinematic distributions (Sec. 5, Fig. 2): weighted
 // histograms of photon observables of the generated events.  The events are
-// regenerated from the counter-based generator; every block accumulates its
-// points in a fixed order into double-double bin sums, and the block
-// partials are combined in block order, so results are bitwise
-// reproducible whatever the launch shape.
+// regenerated from the counter-based generator; every block sums each tile's
+// entries per bin in a fixed order and folds the tile sums into double-double
+// bin sums, and the block partials are combined in block order, so results
+// are reproducible bit for bit for a given launch shape (one resident wave,
+// set by the GPU).
 #include <algorithm>
 #include <cmath>
 
@@ -128,21 +129,25 @@ hist_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
             for (int e = m; e < E; ++e) bins[e * kHistBlock + tid] = -1;
             __syncthreads();
             // thread b folds bin b (and b + kHistBlock, ...) of this histogram:
-            // the tile's points in order, each point's entries in order
+            // the tile's points in order, each point's entries in order, into
+            // a plain FP64 tile sum, which joins the block's double-double sum
+            // once per tile.  (An FP64 instruction occupies the pipe for a whole
+            // warp even when one lane runs it, and a match is one lane's work:
+            // two FP64 operations per match instead of a double-double update.)
             const int ne = h.kind == HEGET_OBS_PT || h.kind == HEGET_OBS_ETA ? N : h.kind == HEGET_OBS_DR ? NP : 1;
             for (int b = tid; b < h.nbins + 2; b += kHistBlock) {
-                DD a = hw[h.off + b], a2 = hw2[h.off + b];
+                double t1 = 0.0, t2 = 0.0;
                 for (int p = 0; p < cnt; ++p) {
                     const double wp = wt[p];
                     if (wp == 0.0) continue;
                     for (int e = 0; e < ne; ++e)
                         if (bins[e * kHistBlock + p] == b) {
-                            a = dd_add_d(a, wp);
-                            a2 = dd_add_d(a2, wp * wp);
+                            t1 += wp;
+                            t2 = fma(wp, wp, t2);
                         }
                 }
-                hw[h.off + b] = a;
-                hw2[h.off + b] = a2;
+                hw[h.off + b] = dd_add_d(hw[h.off + b], t1);
+                hw2[h.off + b] = dd_add_d(hw2[h.off + b], t2);
             }
             __syncthreads();
         }
@@ -157,13 +162,40 @@ hist_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
     }
 }
 
-// out[2b], out[2b + 1] = the block partials of bin b combined in block order.
-__global__ void __launch_bounds__(128) hist_finalize_kernel(const double* __restrict__ parts, int nblocks,
+// Block partials combined in block order, in two stages so that many
+// threads share the work: stage 1 folds groups of kHistGroup consecutive
+// blocks (bin-major threads), stage 2 the groups of each bin in order into
+// out[2b], out[2b + 1].
+constexpr int kHistGroup = 32;
+
+__global__ void __launch_bounds__(128) hist_group_kernel(const double* __restrict__ parts, int nblocks, int total,
+                                                         double* __restrict__ groups) {
+    const int ngroups = (nblocks + kHistGroup - 1) / kHistGroup;
+    const long long items = (long long)ngroups * total;
+    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(it / total), b = (int)(it - (long long)g * total);
+        DD a{0.0, 0.0}, a2{0.0, 0.0};
+        const int k1 = min(nblocks, (g + 1) * kHistGroup);
+        for (int k = g * kHistGroup; k < k1; ++k) {
+            const double* o = parts + ((size_t)k * total + b) * 4;
+            a = dd_add(a, DD{o[0], o[1]});
+            a2 = dd_add(a2, DD{o[2], o[3]});
+        }
+        double* q = groups + ((size_t)g * total + b) * 4;
+        q[0] = a.hi;
+        q[1] = a.lo;
+        q[2] = a2.hi;
+        q[3] = a2.lo;
+    }
+}
+
+__global__ void __launch_bounds__(128) hist_finalize_kernel(const double* __restrict__ groups, int ngroups,
                                                             int total, double* __restrict__ out) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < total; b += gridDim.x * blockDim.x) {
         DD a{0.0, 0.0}, a2{0.0, 0.0};
-        for (int k = 0; k < nblocks; ++k) {
-            const double* o = parts + ((size_t)k * total + b) * 4;
+        for (int g = 0; g < ngroups; ++g) {
+            const double* o = groups + ((size_t)g * total + b) * 4;
             a = dd_add(a, DD{o[0], o[1]});
             a2 = dd_add(a2, DD{o[2], o[3]});
         }
@@ -248,11 +280,17 @@ int heget_hist(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N, cons
     }
 #undef OCC
     if (r) return cuda_fail((cudaError_t)r, "hist occupancy");
+    // one resident wave of at most four blocks per SM (16 warps: enough to
+    // keep the FP64 pipe busy) keeps the block partials few
     const long long tiles = (N + kHistBlock - 1) / kHistBlock;
-    const long long wave = (long long)ctx->num_sms * (bpsm > 0 ? bpsm : 1);
+    const long long wave = (long long)ctx->num_sms * std::min(std::max(bpsm, 1), 4);
     const int grid = (int)std::min(tiles, wave);
-    if ((r = grow((void**)&ctx->hist_parts, &ctx->hist_parts_cap, (size_t)grid * total * 4 * sizeof(double), false)))
+    const int ngroups = (grid + kHistGroup - 1) / kHistGroup;
+    const size_t part_bytes = (size_t)grid * total * 4 * sizeof(double);
+    if ((r = grow((void**)&ctx->hist_parts, &ctx->hist_parts_cap,
+                  part_bytes + (size_t)ngroups * total * 4 * sizeof(double), false)))
         return r;
+    double* groups = ctx->hist_parts + (size_t)grid * total * 4;
     const SamplerArgs S = sampler_args(smp);
     const Physics ph = physics_of(ctx, n);
 #define RUN(NN) launch_hist_n<NN>(seed, i0, N, S, ph, w, H, ctx->hist_parts, grid, st)
@@ -267,8 +305,13 @@ int heget_hist(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N, cons
     }
 #undef RUN
     if (r) return cuda_fail((cudaError_t)r, "hist_kernel");
-    hist_finalize_kernel<<<(total + 127) / 128, 128, 0, st>>>(ctx->hist_parts, grid, total, out);
-    const cudaError_t e = cudaGetLastError();
+    const long long items = (long long)ngroups * total;
+    hist_group_kernel<<<(int)std::min<long long>((items + 127) / 128, 4096), 128, 0, st>>>(ctx->hist_parts, grid,
+                                                                                       total, groups);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "hist_group_kernel");
+    hist_finalize_kernel<<<(total + 127) / 128, 128, 0, st>>>(groups, ngroups, total, out);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "hist_finalize_kernel");
     return HEGET_OK;
 }
