@@ -306,6 +306,20 @@ int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
 int heget_set_algorithm(heget_ctx* ctx, int alg);
 int heget_get_algorithm(const heget_ctx* ctx);
 
+/* Helicity sampling (off by default).  The paper's events each carry one
+ * random helicity combination (Sec. 3, program step 4); with sampling on,
+ * the cross-section paths of a context (heget_xsec*, batch, graphs, server)
+ * do the same: point i draws h = floor(2^(n+2) u), u draw 0 of generator
+ * stream 2 (key = seed, counter = (i lo, i hi, 0, 2)), and its weight uses
+ * 2^(n+2) |M_h|^2 instead of the sum over all helicities; h with
+ * sigma1 = sigma2 gives weight 0.  The estimate has the same mean and a
+ * larger variance, at the same cost (the kernels evaluate every helicity of
+ * a point together).  heget_amp2, heget_ward and heget_xsec_noalloc are
+ * unaffected.  EINVAL for a NULL context or on not 0/1; the getter returns -1
+ * for a NULL context. */
+int heget_set_helicity_sampling(heget_ctx* ctx, int on);
+int heget_get_helicity_sampling(const heget_ctx* ctx);
+
 /* FP32 -> FP64 escalation (the FP32 precision policy: FP32 where it is
  * accurate, FP64 where it is not).  In FP32, heget_amp2 and the fused cross
  * section (heget_xsec, heget_xsec_async, heget_xsec_launch, graphs) bound

@@ -515,6 +515,14 @@ __device__ __forceinline__ float lane_weight(const uint32_t* mask, unsigned h) {
     return (float)(bp + bm);
 }
 
+// Weight of lane lam for a point whose record selects `hsel` (PointRec):
+// w (the mask's) for every lane when hsel = -1, else 2^(n+2) for the selected
+// lane only (a sampled helicity counts for all 2^(n+2)).
+template <int N>
+__device__ __forceinline__ float sel_weight(int hsel, unsigned lam, float w) {
+    return hsel == -1 ? w : (int)lam == hsel ? (float)(1 << (N + 2)) : 0.0f;
+}
+
 // Lane coordinates in a round: point slot, subtree group, group-local lane.
 template <int N, int BLOCK, int HB, int G>
 struct LaneId {
@@ -610,9 +618,13 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, Poin
             for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
         }
         combine_groups<R, N, BLOCK, BAR, HB, G>(tb, id, are, aim);
+        const int hsel = id.slot < rc ? recs[base + id.slot].hsel : -1;
         R v = R(0);
 #pragma unroll
-        for (int b = 0; b < H; ++b) v += (are[b] * are[b] + aim[b] * aim[b]) * R(wh[b]);
+        for (int b = 0; b < H; ++b) {
+            const unsigned lam = (unsigned)id.hl | ((unsigned)b << S::NB);
+            v += (are[b] * are[b] + aim[b] * aim[b]) * R(sel_weight<N>(hsel, lam, wh[b]));
+        }
         v = point_reduce<R, N, BLOCK, BAR, HB, G, false>(tb, v);
         if (threadIdx.x % S::LPP == 0 && id.slot < rc) recs[base + id.slot].ssum = v;
         group_sync<BAR, BLOCK>();

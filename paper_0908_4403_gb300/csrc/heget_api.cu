@@ -305,6 +305,7 @@ Physics physics_of(const heget_ctx* c, int n) {
     Physics ph = physics_of(c->params, n);
     ph.alg = c->alg;
     ph.esc_tau = c->esc_tau;
+    ph.hel_sample = c->hel_sample;
     return ph;
 }
 
@@ -480,6 +481,15 @@ int heget_set_algorithm(heget_ctx* ctx, int alg) {
 }
 
 int heget_get_algorithm(const heget_ctx* ctx) { return ctx ? ctx->alg : -1; }
+
+int heget_set_helicity_sampling(heget_ctx* ctx, int on) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (on != 0 && on != 1) return fail(HEGET_EINVAL, "helicity sampling must be 0 or 1, got %d", on);
+    ctx->hel_sample = on;
+    return HEGET_OK;
+}
+
+int heget_get_helicity_sampling(const heget_ctx* ctx) { return ctx ? ctx->hel_sample : -1; }
 
 int heget_set_escalation(heget_ctx* ctx, double tau) {
     if (!ctx) return fail(HEGET_EINVAL, "context is NULL");

@@ -96,6 +96,7 @@ __device__ __forceinline__ double u01_from_words(uint32_t lo, uint32_t hi) {
 // key = seed.  One Philox call yields draws 2b and 2b+1.
 constexpr uint32_t kStreamSqrtS = 0u;
 constexpr uint32_t kStreamRambo = 1u;
+constexpr uint32_t kStreamHelicity = 2u;   // helicity sampling: draw 0
 
 struct PointRng {
     uint32_t k0, k1, ilo, ihi;
@@ -178,7 +179,7 @@ struct Physics {
     double sinh_dr, cos_dr;     // sinh, cos of dr_min
     double esc_tau;             // FP32 -> FP64 escalation: relative error bound that triggers it (0 = off)
     int alg;                    // ordering sum: 0 prefix tree, 1 subset recursion
-    int pad;
+    int hel_sample;             // 1: one sampled helicity per point (Sec. 3), weighted 2^(n+2)
 };
 
 struct SamplerArgs {

@@ -49,6 +49,7 @@ struct heget_ctx {
     int tiles[2][2][heget::kMaxN + 1] = {};  // [amp2|xsec][fp32|fp64][n] tile overrides (0 = default)
     int alg = 0;                      // ordering sum: HEGET_ALG_TREE or HEGET_ALG_SUBSET
     double esc_tau = 0.0;             // FP32 -> FP64 escalation threshold (0 = off)
+    int hel_sample = 0;               // one sampled helicity per point (heget_set_helicity_sampling)
     // escalation lists of the fused FP32 launch (grown on demand): entries
     // [grid][cap] of (point index, FP32 weight) and per-block counts
     long long* esc_idx = nullptr;

@@ -165,6 +165,7 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
     for (int a = 0; a < N; ++a)
 #pragma unroll
         for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
+    rec.hsel = -1;
     fill_denominators<R, N, true>(v, E2, is, false, rec);
     rec.e2 = R(E2 * irs);
     rec.n1 = R(sqrt(2.0 * E1 * irs));
@@ -330,6 +331,7 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         const int pos = compact_pos<BLOCK>(pass, threadIdx.x, s_cnt, 0, tot);
         if (pass) {
             recs[npass + pos].idx = t;
+            recs[npass + pos].hsel = ev.hsel;
             recs[npass + pos].fac = ev.irs;   // 1/sqrt(s-hat) until the record is built
         }
         npass += tot;
@@ -432,6 +434,7 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
             generate_event<N>(seed, (uint64_t)esc.idx[base + c0 + t], S, ph, v, ev);
             pass_to_rec<double, N>(v, ev.irs, ph, recs[t]);
             recs[t].idx = t;
+            recs[t].hsel = ev.hsel;
         }
         __syncthreads();
         amp_rounds<double, N, BLOCK, 0, kAlgSubset>(smem, recs, cnt, nullptr, kAlgSubset);
@@ -685,6 +688,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             PointRec<R, N>* rs_ring = ring + s * ring_stride;
             if (pass) {
                 rs_ring[pos].idx = g;
+                rs_ring[pos].hsel = ev.hsel;
                 rs_ring[pos].fac = ev.irs;   // 1/sqrt(s-hat) until the record is built
             }
             named_sync(kBarProducers, kWsStage);

@@ -32,6 +32,7 @@ struct alignas(16) PointRec {
     R n1, n2;         // sqrt(2 e1), sqrt(2 e2): spinor normalisations
     R ssum;           // result of the tree: sum_h w_h |A_h|^2 in scaled units
     R kap2;           // sum_h w_h B_h^2, B_h >= sum over orderings |A_pi,h| (condition bound)
+    int hsel;         // -1: every helicity; >= 0: only this lane (a sampled helicity); -2: none
     int valid;        // 0: amplitude not evaluated (bad input / sampler failure)
     int mask;         // passes the cuts
     int tries;        // outer sampler attempts
@@ -115,7 +116,22 @@ __device__ __forceinline__ double toy_pdf_x_of(uint32_t wx, uint32_t wy) {
 struct EventInfo {
     double rs, irs, ey, iey, x1, x2;
     int tries, ok, mask;
+    int hsel;   // record's lane selection (PointRec::hsel)
 };
+
+// Helicity sampling (the paper's events carry one random helicity
+// combination, Sec. 3): h = floor(2^(n+2) u) with u draw 0 of the helicity
+// stream, bits as everywhere (bit 0 sigma1, bit 1 sigma2, bit 2 + i lambda_i).
+// The kernels compute the lanes lambda with sigma1 = +, sigma2 = -; h with
+// sigma1 = sigma2 vanishes exactly (-2: no lane), and h with sigma1 = -,
+// sigma2 = + equals its parity image, the lane ~lambda.
+template <int N>
+__device__ __forceinline__ int sampled_lane(const PointRng& rng) {
+    const U4 w = rng.words(kStreamHelicity, 0);
+    const int h = (int)(u01_from_words(w.x, w.y) * (double)(1 << (N + 2)));
+    const int s1 = h & 1, s2 = (h >> 1) & 1, lam = h >> 2;
+    return s1 == s2 ? -2 : s1 ? lam : (~lam & ((1 << N) - 1));
+}
 
 // The sampler's random draws for one point, kept apart from the FP64 rest
 // of the event: integer and FP32 work (plus a rare FP64 tie-break), which
@@ -548,6 +564,7 @@ template <int N>
 __device__ __forceinline__ void generate_from(const PointRng& rng, const SampleDraw& d, const SamplerArgs& S,
                                               const Physics& ph, const MomView& v, EventInfo& ev) {
     sample_finish(S, d, ev);
+    ev.hsel = ph.hel_sample ? sampled_lane<N>(rng) : -1;
     rambo<N>(rng, ev.rs, v);
     // the FP32 prefilter keeps 5n floats per photon set live in the producer
     // threads: a gain up to n = 3 (+22 % at n = 2 on GB300), a loss above

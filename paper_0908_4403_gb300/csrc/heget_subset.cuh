@@ -259,7 +259,7 @@ __device__ __forceinline__ void amplitude_rounds_subset(unsigned char* table_sme
                 close_row(ld_row(Jl + (size_t)p * JR + src), ld_row(tb.CL + (size_t)c), are, aim);
                 if (kappa) b += jn[src] * tb.CLN[c];
             }
-            const R wl = R(lane_weight<N>(mask, (unsigned)lam));
+            const R wl = R(sel_weight<N>(rb[p].hsel, (unsigned)lam, lane_weight<N>(mask, (unsigned)lam)));
             tb.A2[p * NS + lam] = (are * are + aim * aim) * wl;
             if (kappa) tb.B2[p * NS + lam] = b * b * wl;
         }
@@ -394,7 +394,7 @@ __device__ __noinline__ void kappa_rounds(unsigned char* table_smem, PointRec<R,
             for (int i = 0; i < N; ++i)
                 b += Jl[(size_t)p * JR + ((int)tb.RANK[FULL ^ (1u << i)] << (N - 1)) + drop_bit(lam, i)] *
                      tb.CLN[(p * N + i) * 2 + ((lam >> i) & 1)];
-            tb.B2[p * NS + lam] = b * b * R(lane_weight<N>(mask, (unsigned)lam));
+            tb.B2[p * NS + lam] = b * b * R(sel_weight<N>(rb[p].hsel, (unsigned)lam, lane_weight<N>(mask, (unsigned)lam)));
         }
         group_sync<BAR, BLOCK>();
         for (int p = tid >> 5; p < rc; p += BLOCK / 32) {

@@ -112,6 +112,8 @@ SIGNATURES = {
     "heget_xsec_finalize": (I32, [P, P, P]),
     "heget_measure_fma_peak": (I32, [P, I32, C.POINTER(C.c_double)]),
     "heget_xsec_batch": (I32, [P, C.POINTER(heget_xsec_request), I32, P]),
+    "heget_set_helicity_sampling": (I32, [P, I32]),
+    "heget_get_helicity_sampling": (I32, [P]),
     "heget_hist": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), P, C.POINTER(heget_hist_spec), I32, P,
                          P]),
     "heget_autotune": (I32, [P, I32, I32, I32, I64, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -264,6 +266,14 @@ def heget_measure_fma_peak(ctx, precision=HEGET_FP32) -> float:
     v = C.c_double()
     _check(load().heget_measure_fma_peak(ctx, precision, C.byref(v)))
     return v.value
+
+
+def heget_set_helicity_sampling(ctx, on):
+    _check(load().heget_set_helicity_sampling(ctx, int(on)))
+
+
+def heget_get_helicity_sampling(ctx):
+    return load().heget_get_helicity_sampling(ctx)
 
 
 def hist_bins(specs):
