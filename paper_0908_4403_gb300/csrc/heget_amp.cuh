@@ -108,6 +108,29 @@ struct TreeShape {
     static_assert(G == 1 || (NSL >= 32 && N >= 3), "subtree groups fill whole warps");
 };
 
+// Two-ended finish of the tree (sub-current reuse from the u side): with two
+// photons a, b left after an ordered prefix, the two remaining orderings are
+//   r . M(a, all - {b}) . cl_b  +  r . M(b, all - {a}) . cl_a,
+// and the pair columns PC(a -> b) = M(a, all - {b}) . cl_b depend only on
+// (a, b, lambda_a, lambda_b), not on the prefix: computed once per point,
+// they turn the last level of steps (n! per lane) into closures.  Compiled
+// in for n >= 5, where the tree's amplitude work dominates the step; below,
+// their table would cost the warp-specialised kernel a resident block per SM.
+// -DHEGET_TWO_ENDED=0 turns it off.
+#ifndef HEGET_TWO_ENDED
+#define HEGET_TWO_ENDED 1
+#endif
+template <int N>
+__host__ __device__ constexpr bool tree_two_ended() {
+    return HEGET_TWO_ENDED && N >= 5;
+}
+
+// Ordered pair (a, b), a != b, as an index in [0, n(n-1)).
+template <int N>
+__host__ __device__ __forceinline__ int pair_slot(int a, int b) {
+    return a * (N - 1) + b - (b > a);
+}
+
 // Shared-memory tables of one round.
 // Entry layout [index][point][lambda] so that the lanes of a warp, which read
 // one index for one or a few points and both lambdas, hit distinct banks.
@@ -120,7 +143,8 @@ struct RoundTables {
     static constexpr size_t m_elems = (size_t)K * P * 2;
     static constexpr size_t c_elems = (size_t)N * P * 2;
     static constexpr size_t x_elems = G > 1 ? (size_t)BLOCK * S::H * 2 : 0;
-    static constexpr size_t bytes = (2 * m_elems + 2 * c_elems) * sizeof(Row<R>)   // M0, M1, CL, R1
+    static constexpr size_t p_elems = tree_two_ended<N>() ? (size_t)N * (N - 1) * P * 4 : 0;
+    static constexpr size_t bytes = (2 * m_elems + 2 * c_elems + p_elems) * sizeof(Row<R>)   // M0, M1, CL, R1, PC
                                   + (size_t)P * N * sizeof(Row<R>)                 // photon data
                                   + (size_t)P * NS * sizeof(Row<R>)                // set data
                                   + x_elems * sizeof(R)                            // group exchange
@@ -131,6 +155,7 @@ struct RoundTables {
     Row<R>* R1;
     Row<R>* PH;   // [P][N]: (sin th, cos th, cos ph, sin ph)
     Row<R>* SD;   // [P][2^N]: (A, D, Bre, Bim) = ((q0+q3), (q0-q3), q1, q2) / q^2
+    Row<R>* PC;   // [pair_slot(a, b)][P][lambda_a 2 + lambda_b]: pair columns (two-ended finish)
     R* XCH;       // [BLOCK][H][2]: partial amplitudes of the subtree groups
     R* RED;       // [BLOCK/32]
     __device__ __forceinline__ explicit RoundTables(unsigned char* base) {
@@ -138,7 +163,8 @@ struct RoundTables {
         M1 = M0 + m_elems;
         CL = M1 + m_elems;
         R1 = CL + c_elems;
-        PH = R1 + c_elems;
+        PC = R1 + c_elems;
+        PH = PC + p_elems;
         SD = PH + (size_t)P * N;
         XCH = reinterpret_cast<R*>(SD + (size_t)P * NS);
         RED = XCH + x_elems;
@@ -246,6 +272,13 @@ __device__ __forceinline__ StepMat<R> step_matrix(const Row<R>& ph, const Row<R>
     return o;
 }
 
+// acc[b] += r[b] . c, c = (ca, cb) a column 2-spinor
+template <class R>
+__device__ __forceinline__ void close_row(const Row<R>& r, const Row<R>& c, R& are, R& aim) {
+    are += r.ar * c.ar - r.ai * c.ai + r.br * c.br - r.bi * c.bi;
+    aim += r.ar * c.ai + r.ai * c.ar + r.br * c.bi + r.bi * c.br;
+}
+
 // Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Two phases
 // separated by barriers; all threads of the block must call it.  Everything
 // here runs in R: the FP64 content (invariants) is already in the records.
@@ -284,6 +317,27 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
         }
     }
     group_sync<BAR, BLOCK>();
+    if constexpr (tree_two_ended<N>()) {
+        // (c) pair columns PC(a -> b) = M(a, all - {b}) . cl_b
+        constexpr unsigned FULL = (1u << N) - 1;
+        for (int it = tid; it < N * (N - 1) * P * 4; it += BLOCK) {
+            const int lams = it & 3, q = it >> 2;
+            const int p = q % P, k = q / P;
+            if (p >= cnt) continue;
+            const int a = k / (N - 1), t = k - a * (N - 1), b = t + (t >= a);
+            const int la = lams >> 1, lb = lams & 1;
+            const int idx = c_tables.child[child_offset(N) + (FULL & ~((1u << a) | (1u << b))) * N + a];
+            const size_t o = ((size_t)idx * P + p) * 2 + la;
+            const Row<R> m0 = ld_row(tb.M0 + o), m1 = ld_row(tb.M1 + o);
+            const Row<R> c = ld_row(tb.CL + ((size_t)b * P + p) * 2 + lb);
+            Row<R> pc{R(0), R(0), R(0), R(0)};
+            // (M c)_0 = m0 . c, (M c)_1 = m1 . c, as a column (a, b)
+            close_row(m0, c, pc.ar, pc.ai);
+            close_row(m1, c, pc.br, pc.bi);
+            st_row(tb.PC + (size_t)it, pc);
+        }
+        group_sync<BAR, BLOCK>();
+    }
 }
 
 // Per-lane view of the round tables.
@@ -296,6 +350,7 @@ struct LaneTables {
     const Row<R>* R1;
     int pp;       // 2 * point slot
     unsigned hl;  // helicity bits of photons 0 .. NB-1 (lambda = bit set -> +1)
+    const Row<R>* PC;   // pair columns (two-ended finish), else NULL
 };
 
 // Rows r[b] . M, photon j below NB: every row of the lane has the same lambda.
@@ -335,13 +390,6 @@ __device__ __forceinline__ void attach(const LaneTables<R, N, BLOCK, HB, G>& L, 
     }
 }
 
-// acc[b] += r[b] . c, c = (ca, cb) a column 2-spinor
-template <class R>
-__device__ __forceinline__ void close_row(const Row<R>& r, const Row<R>& c, R& are, R& aim) {
-    are += r.ar * c.ar - r.ai * c.ai + r.br * c.br - r.bi * c.bi;
-    aim += r.ar * c.ai + r.ai * c.ar + r.br * c.bi + r.bi * c.br;
-}
-
 // Closure with the last photon j (iovxx0 against u(p1)).
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void close_rows(const LaneTables<R, N, BLOCK, HB, G>& L, int j, const Row<R> (&r)[1 << HB],
@@ -362,6 +410,24 @@ __device__ __forceinline__ void close_rows(const LaneTables<R, N, BLOCK, HB, G>&
 #pragma unroll
             for (int b = 0; b < H; ++b) close_row(r[b], ((b >> 1) & 1) ? c1 : c0, are[b], aim[b]);
         }
+    }
+}
+
+// The two orderings left below a node of depth n - 2 by the pair columns:
+// acc += r . PC(a -> b) + r . PC(b -> a), each row with its own lambdas.
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ void close_pair(const LaneTables<R, N, BLOCK, HB, G>& L, int a, int b,
+                                           const Row<R> (&r)[1 << HB], R (&are)[1 << HB], R (&aim)[1 << HB]) {
+    using S = TreeShape<N, BLOCK, HB, G>;
+    constexpr int H = S::H, NB = S::NB, P = S::P;
+    const Row<R>* ab = L.PC + ((size_t)pair_slot<N>(a, b) * P) * 4 + 2 * L.pp;
+    const Row<R>* ba = L.PC + ((size_t)pair_slot<N>(b, a) * P) * 4 + 2 * L.pp;
+#pragma unroll
+    for (int row = 0; row < H; ++row) {
+        const int la = a < NB ? (int)((L.hl >> a) & 1) : (row >> (a - NB)) & 1;
+        const int lb = b < NB ? (int)((L.hl >> b) & 1) : (row >> (b - NB)) & 1;
+        close_row(r[row], ld_row(ab + la * 2 + lb), are[row], aim[row]);
+        close_row(r[row], ld_row(ba + lb * 2 + la), are[row], aim[row]);
     }
 }
 
@@ -422,6 +488,9 @@ __device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK, HB, G>& L,
     constexpr unsigned FULL = (1u << N) - 1;
     if constexpr (D == N - 1) {
         close_rows<R, N, BLOCK, HB, G>(L, __ffs(FULL & ~T) - 1, r, are, aim);
+    } else if constexpr (D == N - 2 && tree_two_ended<N>()) {
+        const unsigned rem = FULL & ~T;
+        close_pair<R, N, BLOCK, HB, G>(L, __ffs(rem) - 1, __ffs(rem & (rem - 1)) - 1, r, are, aim);
     } else if constexpr (D == N - 2 && tree_unroll<R, N>() >= 1) {
         // two photons a < b left: the orderings (a, b) and (b, a) as two
         // independent chains, accumulated in the loop's order
@@ -602,7 +671,7 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, Poin
     constexpr int P = S::P, H = S::H;
     const RT tb(table_smem);
     const LaneId<N, BLOCK, HB, G> id(threadIdx.x);
-    const LaneTables<R, N, BLOCK, HB, G> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl};
+    const LaneTables<R, N, BLOCK, HB, G> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl, tb.PC};
     float wh[H];
 #pragma unroll
     for (int b = 0; b < H; ++b) wh[b] = lane_weight<N>(mask, (unsigned)id.hl | ((unsigned)b << S::NB));
@@ -643,7 +712,7 @@ __device__ __forceinline__ void ward_rounds(unsigned char* table_smem, PointRec<
     constexpr int P = RT::P;
     const RT tb(table_smem);
     const LaneId<N, BLOCK, 0, 1> id(threadIdx.x);
-    const LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl};
+    const LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl, tb.PC};
     for (int base = 0; base < cnt; base += P) {
         const int rc = min(P, cnt - base);
         R best[2];
