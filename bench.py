@@ -86,10 +86,14 @@ def subset_flops_per_point(n: int) -> int:
 def tree_flops_per_point(n: int) -> int:
     """FP32 flops of the ordering tree per point: 2^n helicity lanes, each doing
     sum_{l=2}^{n-1} n!/(n-l)! chain steps (28 flops: r . M, 2x2 complex) and n!
-    closures (16 flops)."""
+    closures (16 flops).  From n = 5 the walk stops two photons short and
+    closes against per-point pair columns: the steps of level n - 1 go, and
+    n(n-1) 4 pair columns (two 2-vector products, 32 flops) are formed."""
     f = math.factorial(n)
-    steps = sum(f // math.factorial(n - l) for l in range(2, n))
-    return (1 << n) * (28 * steps + 16 * f)
+    last = n - 1 if n >= 5 else n
+    steps = sum(f // math.factorial(n - l) for l in range(2, last))
+    pairs = n * (n - 1) * 4 * 32 if n >= 5 else 0
+    return (1 << n) * (28 * steps + 16 * f) + pairs
 
 
 def dist_info():
