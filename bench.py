@@ -83,16 +83,18 @@ def subset_flops_per_point(n: int) -> int:
     return 32 * steps + 16 * n * (1 << n)
 
 
-def tree_flops_per_point(n: int) -> int:
-    """FP32 flops of the ordering tree per point: 2^n helicity lanes, each doing
+def tree_flops_per_point(n: int, fp64: bool = False) -> int:
+    """Flops of the ordering tree per point: 2^n helicity lanes, each doing
     sum_{l=2}^{n-1} n!/(n-l)! chain steps (28 flops: r . M, 2x2 complex) and n!
-    closures (16 flops).  From n = 5 the walk stops two photons short and
-    closes against per-point pair columns: the steps of level n - 1 go, and
-    n(n-1) 4 pair columns (two 2-vector products, 32 flops) are formed."""
+    closures (16 flops).  From n = 5 (n = 4 in FP64) the walk stops two
+    photons short and closes against per-point pair columns: the steps of
+    level n - 1 go, and n(n-1) 4 pair columns (two 2-vector products, 32
+    flops) are formed."""
     f = math.factorial(n)
-    last = n - 1 if n >= 5 else n
+    two_ended = n >= 5 or (fp64 and n == 4)
+    last = n - 1 if two_ended else n
     steps = sum(f // math.factorial(n - l) for l in range(2, last))
-    pairs = n * (n - 1) * 4 * 32 if n >= 5 else 0
+    pairs = n * (n - 1) * 4 * 32 if two_ended else 0
     return (1 << n) * (28 * steps + 16 * f) + pairs
 
 
@@ -420,7 +422,8 @@ def matrix_section(H, ctx, stream, peak32, peak64, flush):
                     # amplitudes are evaluated for the points that pass the cuts only
                     "pass_fraction": r32[0].n_pass / N,
                     "fp32_tree_frac_of_fp32_fma_peak": tf * r32[0].n_pass / (ms32 * 1e-3) / (FP32_PEAK * 1e12),
-                    "fp64_tree_frac_of_fp64_fma_peak": tf * r64[0].n_pass / (ms64 * 1e-3) / (FP64_PEAK * 1e12),
+                    "fp64_tree_frac_of_fp64_fma_peak": tree_flops_per_point(n, fp64=True) * r64[0].n_pass
+                                                       / (ms64 * 1e-3) / (FP64_PEAK * 1e12),
                     "subset_fp32_points_per_s": N / (ms32s * 1e-3), "subset_fp64_points_per_s": N / (ms64s * 1e-3),
                     "subset_flops_per_point": subset_flops_per_point(n),
                     "subset_fp32_frac_of_fp32_peak": subset_flops_per_point(n) * r32[0].n_pass / (ms32s * 1e-3)

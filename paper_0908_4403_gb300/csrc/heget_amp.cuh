@@ -114,15 +114,16 @@ struct TreeShape {
 // and the pair columns PC(a -> b) = M(a, all - {b}) . cl_b depend only on
 // (a, b, lambda_a, lambda_b), not on the prefix: computed once per point,
 // they turn the last level of steps (n! per lane) into closures.  Compiled
-// in for n >= 5, where the tree's amplitude work dominates the step; below,
-// their table would cost the warp-specialised kernel a resident block per SM.
-// -DHEGET_TWO_ENDED=0 turns it off.
+// in for n >= 5, where the tree's amplitude work dominates the step, and for
+// the FP64 chain at n = 4 (+37 % on GB300); the FP32 table at n = 4 would
+// cost the warp-specialised kernel a resident block per SM, and at n = 3 the
+// table costs more than the level it saves.  -DHEGET_TWO_ENDED=0 turns it off.
 #ifndef HEGET_TWO_ENDED
 #define HEGET_TWO_ENDED 1
 #endif
-template <int N>
+template <class R, int N>
 __host__ __device__ constexpr bool tree_two_ended() {
-    return HEGET_TWO_ENDED && N >= 5;
+    return HEGET_TWO_ENDED && (N >= 5 || (N == 4 && sizeof(R) == sizeof(double)));
 }
 
 // Ordered pair (a, b), a != b, as an index in [0, n(n-1)).
@@ -143,7 +144,7 @@ struct RoundTables {
     static constexpr size_t m_elems = (size_t)K * P * 2;
     static constexpr size_t c_elems = (size_t)N * P * 2;
     static constexpr size_t x_elems = G > 1 ? (size_t)BLOCK * S::H * 2 : 0;
-    static constexpr size_t p_elems = tree_two_ended<N>() ? (size_t)N * (N - 1) * P * 4 : 0;
+    static constexpr size_t p_elems = tree_two_ended<R, N>() ? (size_t)N * (N - 1) * P * 4 : 0;
     static constexpr size_t bytes = (2 * m_elems + 2 * c_elems + p_elems) * sizeof(Row<R>)   // M0, M1, CL, R1, PC
                                   + (size_t)P * N * sizeof(Row<R>)                 // photon data
                                   + (size_t)P * NS * sizeof(Row<R>)                // set data
@@ -317,7 +318,7 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
         }
     }
     group_sync<BAR, BLOCK>();
-    if constexpr (tree_two_ended<N>()) {
+    if constexpr (tree_two_ended<R, N>()) {
         // (c) pair columns PC(a -> b) = M(a, all - {b}) . cl_b
         constexpr unsigned FULL = (1u << N) - 1;
         for (int it = tid; it < N * (N - 1) * P * 4; it += BLOCK) {
@@ -488,7 +489,7 @@ __device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK, HB, G>& L,
     constexpr unsigned FULL = (1u << N) - 1;
     if constexpr (D == N - 1) {
         close_rows<R, N, BLOCK, HB, G>(L, __ffs(FULL & ~T) - 1, r, are, aim);
-    } else if constexpr (D == N - 2 && tree_two_ended<N>()) {
+    } else if constexpr (D == N - 2 && tree_two_ended<R, N>()) {
         const unsigned rem = FULL & ~T;
         close_pair<R, N, BLOCK, HB, G>(L, __ffs(rem) - 1, __ffs(rem & (rem - 1)) - 1, r, are, aim);
     } else if constexpr (D == N - 2 && tree_unroll<R, N>() >= 1) {
