@@ -688,12 +688,18 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, Poin
             for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
         }
         combine_groups<R, N, BLOCK, BAR, HB, G>(tb, id, are, aim);
-        const int hsel = id.slot < rc ? recs[base + id.slot].hsel : -1;
         R v = R(0);
 #pragma unroll
-        for (int b = 0; b < H; ++b) {
-            const unsigned lam = (unsigned)id.hl | ((unsigned)b << S::NB);
-            v += (are[b] * are[b] + aim[b] * aim[b]) * R(sel_weight<N>(hsel, lam, wh[b]));
+        for (int b = 0; b < H; ++b) v += (are[b] * are[b] + aim[b] * aim[b]) * R(wh[b]);
+        // a sampled helicity (PointRec::hsel): only the selected lane counts
+        const int hsel = active ? recs[base + id.slot].hsel : -1;
+        if (hsel != -1) {
+            v = R(0);
+#pragma unroll
+            for (int b = 0; b < H; ++b) {
+                const unsigned lam = (unsigned)id.hl | ((unsigned)b << S::NB);
+                v += (are[b] * are[b] + aim[b] * aim[b]) * R(sel_weight<N>(hsel, lam, wh[b]));
+            }
         }
         v = point_reduce<R, N, BLOCK, BAR, HB, G, false>(tb, v);
         if (threadIdx.x % S::LPP == 0 && id.slot < rc) recs[base + id.slot].ssum = v;

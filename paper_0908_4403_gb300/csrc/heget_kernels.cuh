@@ -331,7 +331,7 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         const int pos = compact_pos<BLOCK>(pass, threadIdx.x, s_cnt, 0, tot);
         if (pass) {
             recs[npass + pos].idx = t;
-            recs[npass + pos].hsel = ev.hsel;
+            recs[npass + pos].hsel = point_hsel<N>(ph, seed, (uint64_t)(first + t));
             recs[npass + pos].fac = ev.irs;   // 1/sqrt(s-hat) until the record is built
         }
         npass += tot;
@@ -434,7 +434,7 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
             generate_event<N>(seed, (uint64_t)esc.idx[base + c0 + t], S, ph, v, ev);
             pass_to_rec<double, N>(v, ev.irs, ph, recs[t]);
             recs[t].idx = t;
-            recs[t].hsel = ev.hsel;
+            recs[t].hsel = point_hsel<N>(ph, seed, (uint64_t)esc.idx[base + c0 + t]);
         }
         __syncthreads();
         amp_rounds<double, N, BLOCK, 0, kAlgSubset>(smem, recs, cnt, nullptr, kAlgSubset);
@@ -688,7 +688,7 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             PointRec<R, N>* rs_ring = ring + s * ring_stride;
             if (pass) {
                 rs_ring[pos].idx = g;
-                rs_ring[pos].hsel = ev.hsel;
+                rs_ring[pos].hsel = point_hsel<N>(ph, seed, (uint64_t)(i0 + t0 + g));
                 rs_ring[pos].fac = ev.irs;   // 1/sqrt(s-hat) until the record is built
             }
             named_sync(kBarProducers, kWsStage);

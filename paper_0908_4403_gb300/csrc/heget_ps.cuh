@@ -116,7 +116,6 @@ __device__ __forceinline__ double toy_pdf_x_of(uint32_t wx, uint32_t wy) {
 struct EventInfo {
     double rs, irs, ey, iey, x1, x2;
     int tries, ok, mask;
-    int hsel;   // record's lane selection (PointRec::hsel)
 };
 
 // Helicity sampling (the paper's events carry one random helicity
@@ -131,6 +130,13 @@ __device__ __forceinline__ int sampled_lane(const PointRng& rng) {
     const int h = (int)(u01_from_words(w.x, w.y) * (double)(1 << (N + 2)));
     const int s1 = h & 1, s2 = (h >> 1) & 1, lam = h >> 2;
     return s1 == s2 ? -2 : s1 ? lam : (~lam & ((1 << N) - 1));
+}
+
+// The record's lane selection (PointRec::hsel) for point i of stream seed:
+// drawn when the record is written, so nothing stays live across RAMBO.
+template <int N>
+__device__ __forceinline__ int point_hsel(const Physics& ph, uint64_t seed, uint64_t i) {
+    return ph.hel_sample ? sampled_lane<N>(PointRng(seed, i)) : -1;
 }
 
 // The sampler's random draws for one point, kept apart from the FP64 rest
@@ -564,7 +570,6 @@ template <int N>
 __device__ __forceinline__ void generate_from(const PointRng& rng, const SampleDraw& d, const SamplerArgs& S,
                                               const Physics& ph, const MomView& v, EventInfo& ev) {
     sample_finish(S, d, ev);
-    ev.hsel = ph.hel_sample ? sampled_lane<N>(rng) : -1;
     rambo<N>(rng, ev.rs, v);
     // the FP32 prefilter keeps 5n floats per photon set live in the producer
     // threads: a gain up to n = 3 (+22 % at n = 2 on GB300), a loss above
