@@ -113,17 +113,18 @@ struct TreeShape {
 //   r . M(a, all - {b}) . cl_b  +  r . M(b, all - {a}) . cl_a,
 // and the pair columns PC(a -> b) = M(a, all - {b}) . cl_b depend only on
 // (a, b, lambda_a, lambda_b), not on the prefix: computed once per point,
-// they turn the last level of steps (n! per lane) into closures.  Compiled
-// in for n >= 5, where the tree's amplitude work dominates the step, and for
-// the FP64 chain at n = 4 (+37 % on GB300); the FP32 table at n = 4 would
-// cost the warp-specialised kernel a resident block per SM, and at n = 3 the
-// table costs more than the level it saves.  -DHEGET_TWO_ENDED=0 turns it off.
+// they turn the last level of steps (n! per lane) into closures.  The walk
+// then never uses the step matrices of the sets of n - 1 photons; the pair
+// columns form theirs directly, and the round tables leave them out, which
+// costs about what the pair columns take.  Compiled in for n >= 4 (at n = 3
+// the extra table phase costs more than the level it saves).
+// -DHEGET_TWO_ENDED=0 turns it off.
 #ifndef HEGET_TWO_ENDED
 #define HEGET_TWO_ENDED 1
 #endif
 template <class R, int N>
 __host__ __device__ constexpr bool tree_two_ended() {
-    return HEGET_TWO_ENDED && (N >= 5 || (N == 4 && sizeof(R) == sizeof(double)));
+    return HEGET_TWO_ENDED && N >= 4;
 }
 
 // Ordered pair (a, b), a != b, as an index in [0, n(n-1)).
@@ -140,8 +141,11 @@ struct RoundTables {
     using S = TreeShape<N, BLOCK, HB, G>;
     static constexpr int P = S::P;
     static constexpr int K = num_pairs(N);
+    // step matrices held: with the two-ended finish, those of sets of at
+    // most n - 2 photons (the pair index lists them first)
+    static constexpr int KW = tree_two_ended<R, N>() ? K - N * (N - 1) : K;
     static constexpr int NS = 1 << N;
-    static constexpr size_t m_elems = (size_t)K * P * 2;
+    static constexpr size_t m_elems = (size_t)KW * P * 2;
     static constexpr size_t c_elems = (size_t)N * P * 2;
     static constexpr size_t x_elems = G > 1 ? (size_t)BLOCK * S::H * 2 : 0;
     static constexpr size_t p_elems = tree_two_ended<R, N>() ? (size_t)N * (N - 1) * P * 4 : 0;
@@ -289,7 +293,7 @@ template <class R, int N, int BLOCK, int BAR = 0, int HB = 0, int G = 1>
 __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G>& tb, const PointRec<R, N>* recs,
                                             int cnt, int ward = -1) {
     using RT = RoundTables<R, N, BLOCK, HB, G>;
-    constexpr int P = RT::P, K = RT::K, NS = RT::NS;
+    constexpr int P = RT::P, K = RT::KW, NS = RT::NS;
     const int tid = threadIdx.x;
     setup_photons_and_sets<R, N, BLOCK, P>(tb.PH, tb.SD, recs, cnt);
     group_sync<BAR, BLOCK>();
@@ -321,21 +325,22 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
     if constexpr (tree_two_ended<R, N>()) {
         // (c) pair columns PC(a -> b) = M(a, all - {b}) . cl_b
         constexpr unsigned FULL = (1u << N) - 1;
-        for (int it = tid; it < N * (N - 1) * P * 4; it += BLOCK) {
-            const int lams = it & 3, q = it >> 2;
+        for (int it = tid; it < N * (N - 1) * P * 2; it += BLOCK) {
+            const int la = it & 1, q = it >> 1;
             const int p = q % P, k = q / P;
             if (p >= cnt) continue;
             const int a = k / (N - 1), t = k - a * (N - 1), b = t + (t >= a);
-            const int la = lams >> 1, lb = lams & 1;
-            const int idx = c_tables.child[child_offset(N) + (FULL & ~((1u << a) | (1u << b))) * N + a];
-            const size_t o = ((size_t)idx * P + p) * 2 + la;
-            const Row<R> m0 = ld_row(tb.M0 + o), m1 = ld_row(tb.M1 + o);
-            const Row<R> c = ld_row(tb.CL + ((size_t)b * P + p) * 2 + lb);
-            Row<R> pc{R(0), R(0), R(0), R(0)};
-            // (M c)_0 = m0 . c, (M c)_1 = m1 . c, as a column (a, b)
-            close_row(m0, c, pc.ar, pc.ai);
-            close_row(m1, c, pc.br, pc.bi);
-            st_row(tb.PC + (size_t)it, pc);
+            // M(a, all - {b}), not held in the step tables, once for both lambda_b
+            const StepMat<R> sm = step_matrix<R>(tb.PH[p * N + a], tb.SD[p * NS + (FULL & ~(1u << b))], la, a == ward);
+#pragma unroll
+            for (int lb = 0; lb < 2; ++lb) {
+                const Row<R> c = ld_row(tb.CL + ((size_t)b * P + p) * 2 + lb);
+                Row<R> pc{R(0), R(0), R(0), R(0)};
+                // (M c)_0 = m0 . c, (M c)_1 = m1 . c, as a column (a, b)
+                close_row(sm.m0, c, pc.ar, pc.ai);
+                close_row(sm.m1, c, pc.br, pc.bi);
+                st_row(tb.PC + ((size_t)k * P + p) * 4 + la * 2 + lb, pc);
+            }
         }
         group_sync<BAR, BLOCK>();
     }

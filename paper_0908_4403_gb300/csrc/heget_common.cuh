@@ -21,7 +21,9 @@ constexpr int kMinN = 2;
 // prefix with photon set S depends on (j, T = S u {j}) only through the step
 // matrix M(j, T) = eps*_j.sigma  (q_T.sigmabar)/q_T^2 with q_T = sum_{i in T}
 // k_i - p2.  Steps exist for 1 <= |T| <= n-1; each (T, j in T) pair gets a
-// compact index, ordered by T then j:
+// compact index, ordered by |T|, then T, then j (so the n(n-1) pairs with
+// |T| = n-1 come last, and a table that needs only the smaller sets stops
+// before them):
 //   pair[idx]        = T | (j << 8)
 //   child[S * n + j] = idx of (S | 1<<j, j)   for j not in S, |S| <= n-2.
 // ---------------------------------------------------------------------------
@@ -50,13 +52,18 @@ __host__ __device__ constexpr TreeTables make_tree_tables() {
         int po = pair_offset(n), co = child_offset(n);
         for (int i = 0; i < (1 << n) * n; ++i) t.child[co + i] = 0xFFFF;
         int idx = 0;
-        for (int T = 1; T < (1 << n) - 1; ++T)
-            for (int j = 0; j < n; ++j)
-                if (T >> j & 1) {
-                    t.pair[po + idx] = (uint16_t)(T | (j << 8));
-                    t.child[co + (T & ~(1 << j)) * n + j] = (uint16_t)idx;
-                    ++idx;
-                }
+        for (int size = 1; size < n; ++size)
+            for (int T = 1; T < (1 << n) - 1; ++T) {
+                int pop = 0;
+                for (int b = 0; b < n; ++b) pop += (T >> b) & 1;
+                if (pop != size) continue;
+                for (int j = 0; j < n; ++j)
+                    if (T >> j & 1) {
+                        t.pair[po + idx] = (uint16_t)(T | (j << 8));
+                        t.child[co + (T & ~(1 << j)) * n + j] = (uint16_t)idx;
+                        ++idx;
+                    }
+            }
     }
     return t;
 }
