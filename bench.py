@@ -86,12 +86,11 @@ def subset_flops_per_point(n: int) -> int:
 def tree_flops_per_point(n: int, fp64: bool = False) -> int:
     """Flops of the ordering tree per point: 2^n helicity lanes, each doing
     sum_{l=2}^{n-1} n!/(n-l)! chain steps (28 flops: r . M, 2x2 complex) and n!
-    closures (16 flops).  From n = 5 (n = 4 in FP64) the walk stops two
-    photons short and closes against per-point pair columns: the steps of
-    level n - 1 go, and n(n-1) 4 pair columns (two 2-vector products, 32
-    flops) are formed."""
+    closures (16 flops).  From n = 4 the walk stops two photons short and
+    closes against per-point pair columns: the steps of level n - 1 go, and
+    n(n-1) 4 pair columns (two 2-vector products, 32 flops) are formed."""
     f = math.factorial(n)
-    two_ended = n >= 5 or (fp64 and n == 4)
+    two_ended = n >= 4
     last = n - 1 if two_ended else n
     steps = sum(f // math.factorial(n - l) for l in range(2, last))
     pairs = n * (n - 1) * 4 * 32 if two_ended else 0
