@@ -104,3 +104,23 @@ def test_helicity_sampling_argument_checks(heget_lib, gpu):
     assert H.heget_get_helicity_sampling(gpu) == 0
     assert H.load().heget_get_helicity_sampling(None) == -1
     assert H.load().heget_set_helicity_sampling(None, 1) == H.HEGET_EINVAL
+
+
+def test_sampling_through_the_batch(heget_lib, sampling):
+    """The mixed-n batch samples the same helicities: each request's sums
+    equal those of a direct launch over the same points (FP64, to rounding;
+    the two paths tile the points differently)."""
+    import torch
+    H = heget_lib
+    S = H.sampler_toy_pdf()
+    reqs = [dict(n=n, precision=64, seed=SEED + 90 + n, i0=5, N=N, sampler=S,
+                 result_dev=torch.zeros(80, dtype=torch.uint8, device="cuda"))
+            for n, N in [(2, 3000), (4, 1500), (6, 80)]]
+    H.heget_xsec_batch(sampling, reqs)
+    torch.cuda.synchronize()
+    for r in reqs:
+        got = H.result_from_tensor(r["result_dev"])
+        _, ref = _weights(H, sampling, r["n"], r["seed"], r["i0"], r["N"], H.HEGET_FP64)
+        assert got.n_pass == ref.n_pass
+        assert got.sum_w == pytest.approx(ref.sum_w, rel=1e-12)
+        assert got.sum_w2 == pytest.approx(ref.sum_w2, rel=1e-12)

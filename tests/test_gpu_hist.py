@@ -54,7 +54,7 @@ def _samplers(H, O, kind):
     return H.sampler_toy_pdf(), O.toy_pdf()
 
 
-@pytest.mark.parametrize("n,kind,N", CASES)
+@pytest.mark.parametrize("n,kind,N", CASES + [(8, "uniform", 700)])
 def test_counts_bit_exact(oracle, heget_lib, gpu, n, kind, N):
     """Unit weights: every event's entries counted, each in the oracle's bin."""
     import torch
