@@ -18,7 +18,9 @@
 // extended by every remaining photon (depth-first, registers hold the stack),
 // so the tree does sum_{l=1}^{n-1} n!/(n-l)! steps and n! closures per
 // helicity instead of n! (n-1) steps.  The step matrices M(j, T) depend on
-// (j, T, lambda_j) only and are precomputed per point in shared memory.
+// (j, T, lambda_j) only and are precomputed per point in shared memory.  From
+// n = 4 the walk also shares the suffix of the last two photons (the
+// two-ended finish below), which removes the level of n! steps.
 //
 // Lanes: one lane per photon-helicity configuration h in [0, 2^n) with
 // s1 = +; every lane of a point walks the same tree (uniform control flow),

@@ -655,9 +655,10 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
 }
 
 // Record of a point that passed the cuts, from its photon momenta (GeV) and
-// irs = 1/sqrt(s-hat) (the fields of event_to_rec for ok = mask = 1).  The
+// irs = 1/sqrt(s-hat): momenta / sqrt(s-hat), denominators, normalisations,
+// the factors to |M|^2 and to the event weight, valid = mask = 1.  The
 // momenta are divided by sqrt(s-hat) in place, and the denominators formed
-// from the scaled values.
+// from the scaled values.  (The caller sets idx and hsel.)
 template <class R, int N>
 __device__ __forceinline__ void pass_to_rec(const MomView& v, double irs, const Physics& ph, PointRec<R, N>& rec) {
     const double is = irs * irs;
