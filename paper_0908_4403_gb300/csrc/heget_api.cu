@@ -252,7 +252,7 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
         L->grid = (int)(tiles < wave ? (tiles < 1 ? 1 : tiles) : wave);
         return 0;
     }
-    L->block = kBlockThreads;
+    L->block = xsec && precision == HEGET_FP32 && alg != kAlgSubset && n == 6 ? 128 : kBlockThreads;   // xsec_block()
     L->tile = tile > 0 ? tile : default_tile(n, xsec);
     const bool sub = alg == kAlgSubset;
     const int e = precision == HEGET_FP32

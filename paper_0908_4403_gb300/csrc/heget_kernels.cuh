@@ -381,17 +381,25 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
 }
 
 // Resident blocks per SM a tile kernel is compiled for (its register
-// budget).  The FP32 tree at n = 6, 7 runs fastest at three blocks of 256
-// threads (80 registers; its shared memory, about 71 KB, allows three),
-// trading a few spills for occupancy, and so does n = 2 (at most 68 KB);
-// elsewhere two (up to 128 registers).
-template <class R, int N, bool ESC, int ALG>
+// budget).  The FP32 tree at n = 6, 7 runs fastest with 768 threads per SM
+// (80 registers; its shared memory allows it), trading a few spills for
+// occupancy, and so does n = 2 (three blocks, at most 68 KB); elsewhere two
+// blocks (up to 128 registers).
+template <class R, int N, int BLOCK, bool ESC, int ALG>
 __host__ __device__ constexpr int tile_min_blocks() {
-    return (sizeof(R) == sizeof(float) && ALG == kAlgTree && !ESC && (N == 6 || N == 7)) || N == 2 ? 3 : 2;
+    return (sizeof(R) == sizeof(float) && ALG == kAlgTree && !ESC && (N == 6 || N == 7)) ? 768 / BLOCK : N == 2 ? 3 : 2;
+}
+// Threads of a fused tile kernel's block: 128 for the FP32 tree at n = 6,
+// whose rounds are bound by their block barriers (half the warps per barrier
+// and, with tables for half the points, twice the blocks per SM: +11 % on
+// GB300), 256 elsewhere.
+template <class R, int N, int ALG>
+__host__ __device__ constexpr int xsec_block() {
+    return sizeof(R) == sizeof(float) && ALG == kAlgTree && N == 6 ? 128 : 256;
 }
 
 template <class R, int N, int BLOCK, bool ESC, int ALG>
-__global__ void __launch_bounds__(BLOCK, tile_min_blocks<R, N, ESC, ALG>())
+__global__ void __launch_bounds__(BLOCK, tile_min_blocks<R, N, BLOCK, ESC, ALG>())
 xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, int tile,
             Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
     extern __shared__ __align__(16) unsigned char smem[];

@@ -49,27 +49,29 @@ static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const Samp
     } else {
         if (L.ws) return (int)cudaErrorInvalidValue;
     }
-    auto k = xsec_kernel<R, N, kBlock, false, ALG>;
-    size_t smem = xsec_smem_bytes<R, N, kBlock, ALG>(L.tile);
+    constexpr int XB = xsec_block<R, N, ALG>();
+    auto k = xsec_kernel<R, N, XB, false, ALG>;
+    size_t smem = xsec_smem_bytes<R, N, XB, ALG>(L.tile);
     if constexpr (sizeof(R) == sizeof(float))
         if (esc.idx) {
-            k = xsec_kernel<R, N, kBlock, true, ALG>;
-            smem = xsec_smem_bytes<R, N, kBlock, table_alg<ALG, true>()>(L.tile);
+            k = xsec_kernel<R, N, XB, true, ALG>;
+            smem = xsec_smem_bytes<R, N, XB, table_alg<ALG, true>()>(L.tile);
         }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    k<<<L.grid, kBlock, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out, esc);
+    k<<<L.grid, XB, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out, esc);
     return (int)cudaGetLastError();
 }
 
 template <class R, int N, int ALG>
 static int occupancy_n(int tile, int* blocks_per_sm, size_t* smem_out) {
-    const size_t smem = xsec_smem_bytes<R, N, kBlock, ALG>(tile);
+    constexpr int XB = xsec_block<R, N, ALG>();
+    const size_t smem = xsec_smem_bytes<R, N, XB, ALG>(tile);
     *smem_out = smem;
-    auto k = xsec_kernel<R, N, kBlock, false, ALG>;
+    auto k = xsec_kernel<R, N, XB, false, ALG>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, XB, smem);
 }
 
 template <int N, int ALG>
