@@ -100,3 +100,17 @@ def test_server_calls_reject_null_arguments_without_gpu(heget_lib):
     assert lib.heget_poll(None, 1, ctypes.byref(r)) == heget_lib.HEGET_EINVAL
     assert lib.heget_wait(None, 1, 0.01, ctypes.byref(r)) == heget_lib.HEGET_EINVAL
     assert lib.heget_server_stop(None) == heget_lib.HEGET_EINVAL
+
+
+def test_distribution_and_sampling_calls_reject_null_context_without_gpu(heget_lib):
+    """heget_hist and the helicity-sampling switch check their arguments on
+    the host (no GPU needed for the refusals)."""
+    H = heget_lib
+    lib = H.load()
+    spec = (H.heget_hist_spec * 1)(H.heget_hist_spec(H.HEGET_OBS_PT_MAX, 10, 0.0, 100.0))
+    S = H.sampler_toy_pdf()
+    assert lib.heget_hist(None, 4, 1, 0, 10, ctypes.byref(S), None, spec, 1, None, None) == H.HEGET_EINVAL
+    assert b"context" in lib.heget_last_error()
+    assert lib.heget_set_helicity_sampling(None, 1) == H.HEGET_EINVAL
+    assert lib.heget_get_helicity_sampling(None) == -1
+    assert H.hist_bins([(H.HEGET_OBS_PT, 10, 0.0, 1.0), (H.HEGET_OBS_DR, 4, 0.0, 4.0)]) == 2 * (12 + 6)
