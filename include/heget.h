@@ -293,7 +293,9 @@ int heget_xsec_finalize(heget_ctx* ctx, heget_xsec_result* result_dev,
 /* Ordering-sum algorithm of a context (amp2, xsec, batch, graphs, server).
  *  HEGET_ALG_TREE (default): the paper's method -- every ordering of the
  *    photons along the fermion line (Sec. 2.1 eqs. (6)-(8), the permutation
- *    program of Appendix A.2), each shared ordered prefix computed once.
+ *    program of Appendix A.2), each shared ordered prefix computed once, and
+ *    for n >= 4 each pair of last photons closed against per-point currents
+ *    from the u end (sub-current reuse from both ends).
  *  HEGET_ALG_SUBSET: the same sum regrouped by the SET of photons attached so
  *    far (a step's propagator depends on the set, not the order), so that the
  *    current of each set and helicity assignment is computed once:
