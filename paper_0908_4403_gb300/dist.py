@@ -3,14 +3,17 @@
 Point i of a run depends only on (seed, i), so ranks take contiguous,
 disjoint point ranges and need no communication while they compute.  The
 only exchange is the combination of the per-rank Monte Carlo sums into the
-job's cross section (the summation step of the paper's program, Sec. 3.1,
-spread over processes).  It gathers eight numbers per rank and combines them
-in rank order with error-free transformations, so every rank gets the same
-bits whatever the process timing.
+job's cross section, and of the per-rank histograms into the job's
+distributions (the summation step of the paper's program, Sec. 3.1, spread
+over processes).  Each gathers the ranks' sums and combines them in rank
+order with error-free transformations, so every rank gets the same bits
+whatever the process timing.
 """
 from __future__ import annotations
 
 import math
+
+import numpy as np
 
 from . import heget as H
 
@@ -84,3 +87,36 @@ def allreduce_result(res: H.heget_xsec_result, sampler_kind: int, group=None) ->
         r.n_pass, r.n_total, r.n_tries, r.n_escalated = (int(x) for x in c.tolist())
         parts.append(r)
     return combine(parts, sampler_kind)
+
+
+def combine_hists(parts) -> np.ndarray:
+    """Histograms of disjoint point shards (heget_hist outputs: for every bin
+    of every spec, sum w and sum w^2), in the given order: each entry
+    combined with TwoSum across the shards and rounded once."""
+    arrs = [np.asarray(p, dtype=np.float64).ravel() for p in parts]
+    if not arrs:
+        raise ValueError("no histograms to combine")
+    hi = np.zeros_like(arrs[0])
+    lo = np.zeros_like(arrs[0])
+    for a in arrs:
+        if a.shape != hi.shape:
+            raise ValueError("histograms of different layouts")
+        s = hi + a
+        bb = s - hi
+        lo += (hi - (s - bb)) + (a - bb)
+        hi = s
+    return hi + lo
+
+
+def allreduce_hist(hist, group=None) -> np.ndarray:
+    """The job's histograms on every rank: all-gather of each rank's
+    heget_hist output over `group`, combined in rank order."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    backend = dist.get_backend(group)
+    device = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+    mine = torch.as_tensor(np.asarray(hist, dtype=np.float64).ravel(), device=device)
+    parts = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    return combine_hists([p.cpu().numpy() for p in parts])

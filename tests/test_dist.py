@@ -1,6 +1,7 @@
 """Host logic of the multi-process path on CPU: point shards cover the run
-exactly once, and the gloo all-gather combination of per-rank sums gives
-every rank the same bits as one process over all points."""
+exactly once, and the gloo all-gather combination of per-rank sums (and of
+per-rank histograms) gives every rank the same bits, equal to one process
+over all points up to the rounding of the combination."""
 import math
 import os
 import socket
@@ -71,8 +72,32 @@ def _rank_main(rank, world, port, n, N, out_dir):
         tot = D.allreduce_result(mine, H.HEGET_SAMPLER_TOY_PDF)
         np.save(os.path.join(out_dir, f"r{rank}.npy"),
                 np.array([tot.sigma_fb, tot.err_fb, tot.sum_w, tot.sum_w2, tot.n_total, tot.n_tries, tot.n_pass]))
+        i0, cnt = D.shard(N, world, rank)
+        ps = O.phase_space(n, SEED, i0, cnt, O.toy_pdf(), O.cuts())
+        flat = np.concatenate([h.ravel() for h in O.hist(n, ps["momenta"], ps["y"], w, HSPECS)])
+        np.save(os.path.join(out_dir, f"h{rank}.npy"), D.allreduce_hist(flat))
     finally:
         dist.destroy_process_group()
+
+
+HSPECS = [(0, 20, 20.0, 420.0), (3, 16, 0.0, 8.0)]
+
+
+def _shard_hist(oracle, n, N, world, rank):
+    i0, cnt = D.shard(N, world, rank)
+    w, _ = _shard_weights(oracle, n, N, world, rank)
+    ps = oracle.phase_space(n, SEED, i0, cnt, oracle.toy_pdf(), oracle.cuts())
+    return np.concatenate([h.ravel() for h in oracle.hist(n, ps["momenta"], ps["y"], w, HSPECS)])
+
+
+def test_combined_shard_histograms_equal_one_run(oracle):
+    n, N = 3, 1501
+    whole = _shard_hist(oracle, n, N, 1, 0)
+    for world in (2, 3):
+        got = D.combine_hists([_shard_hist(oracle, n, N, world, r) for r in range(world)])
+        np.testing.assert_allclose(got, whole, rtol=1e-15, atol=0)
+    with pytest.raises(ValueError):
+        D.combine_hists([np.zeros(4), np.zeros(6)])
 
 
 def _free_port():
@@ -93,3 +118,8 @@ def test_gloo_allreduce_gives_every_rank_the_single_process_result(oracle, tmp_p
              for r in range(world)]
     ref = D.combine(parts, H.HEGET_SAMPLER_TOY_PDF)
     assert got[0][0] == ref.sigma_fb and got[0][2] == ref.sum_w and int(got[0][4]) == N
+    hs = [np.load(tmp_path / f"h{r}.npy") for r in range(world)]
+    for h in hs[1:]:
+        assert np.array_equal(h.view(np.uint64), hs[0].view(np.uint64))   # same bits on every rank
+    ref_h = D.combine_hists([_shard_hist(oracle, n, N, world, r) for r in range(world)])
+    assert np.array_equal(hs[0], ref_h)
