@@ -3,7 +3,7 @@
 logarithm in heget_ps.cuh (Tang, ACM TOMS 16 (1990) 378).  For j = 0..256 and
 F_j = 1 + j/256 it stores ln F_j as a double-double (hi + lo, computed with
 40-digit decimal arithmetic) and 1/F_j rounded to double.  ln 2 itself is
-stored the same way.  Run from anywhere: python gen_logtab.py"""
+stored the same way.  Run from anywhere: python gen_logtab.py [output path]"""
 import os
 from decimal import Decimal, getcontext
 
@@ -17,7 +17,7 @@ def dd(v: Decimal):
     return hi, lo
 
 
-def main():
+def main(out=None):
     lines = [
         "// heget_logtab.h -- generated by gen_logtab.py; do not edit.",
         f"// ln(1 + j/{TABLE}) = hi + lo (double-double) and 1/(1 + j/{TABLE}), j = 0..{TABLE}.",
@@ -37,10 +37,11 @@ def main():
     hi, lo = dd(Decimal(2).ln())
     lines += ["", f"constexpr double kLn2Hi = {hi.hex()};", f"constexpr double kLn2Lo = {lo.hex()};", "",
               "}  // namespace heget", ""]
-    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "heget_logtab.h")
+    out = out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "heget_logtab.h")
     with open(out, "w") as f:
         f.write("\n".join(lines))
 
 
 if __name__ == "__main__":
-    main()
+    import sys
+    main(sys.argv[1] if len(sys.argv) > 1 else None)

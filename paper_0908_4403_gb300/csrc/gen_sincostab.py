@@ -49,7 +49,7 @@ def rounded(v: Decimal) -> float:
     return 0.0 if abs(v) < Decimal(10) ** -40 else float(v)   # exact zeros at the quarter turns
 
 
-def main():
+def main(out=None):
     lines = [
         "// heget_sincostab.h -- generated by gen_sincostab.py; do not edit.",
         f"// (cos, sin) of 2 pi j/{TABLE}, j = 0..{TABLE - 1}, each correctly rounded.",
@@ -64,10 +64,11 @@ def main():
         c, s = cos_sin(2 * PI * j / TABLE)
         lines.append(f"    {{{rounded(c).hex()}, {rounded(s).hex()}}},")
     lines += ["};", "", "}  // namespace heget", ""]
-    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "heget_sincostab.h")
+    out = out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "heget_sincostab.h")
     with open(out, "w") as f:
         f.write("\n".join(lines))
 
 
 if __name__ == "__main__":
-    main()
+    import sys
+    main(sys.argv[1] if len(sys.argv) > 1 else None)

@@ -45,3 +45,12 @@ def test_log_table_is_correctly_rounded():
     lo = float.fromhex(re.search(r"kLn2Lo = " + HEX, text).group(1))
     ln2 = mpmath.log(2)
     assert hi == float(ln2) and lo == float(ln2 - mpmath.mpf(hi))
+
+
+@pytest.mark.parametrize("gen,header", [("gen_logtab.py", "heget_logtab.h"), ("gen_sincostab.py", "heget_sincostab.h")])
+def test_committed_tables_match_their_generators(tmp_path, gen, header):
+    import subprocess
+    import sys
+    out = tmp_path / header
+    subprocess.run([sys.executable, os.path.join(CSRC, gen), str(out)], check=True)
+    assert out.read_bytes() == open(os.path.join(CSRC, header), "rb").read()
