@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -112,16 +113,23 @@ class ClockSampler:
 
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: HEGET_CLOCKS_CSV if set (to keep them), else a temporary file
+        self.path = os.environ.get("HEGET_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                         f"heget_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
                                           "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+        except OSError:   # no nvidia-smi: no clock record
             self.proc = None
+            if getattr(self, "fh", None):
+                self.fh.close()
+                if not os.environ.get("HEGET_CLOCKS_CSV"):
+                    os.remove(self.path)
 
     def stop(self):
         if self.proc is None:
@@ -134,7 +142,11 @@ class ClockSampler:
         self.fh.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        if not os.environ.get("HEGET_CLOCKS_CSV"):
+            os.remove(self.path)
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
