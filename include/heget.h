@@ -232,8 +232,8 @@ typedef struct {
 int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, int count,
                      void* stream);
 
-/* Kinematic distributions (Sec. 5, Fig. 2: the maximum transverse momentum
- * and the Delta R of the final-state photons).  Observables, in GeV for
+/* Kinematic distributions (Sec. 5, Fig. 2: the largest photon transverse
+ * momentum and the photons' Delta R separations).  Observables, in GeV for
  * momenta, with pT = sqrt(px^2 + py^2), the lab pseudorapidity
  * eta = asinh(pz / pT) + y (y the boost rapidity of the toy-PDF sampler, 0
  * otherwise, as for the cuts of Sec. 2.2), phi = atan2(py, px) and

@@ -21,8 +21,8 @@
  *     colour / spin / identical-particle factors of the partonic cross section;
  *   - Sec. 2.1, eq. (4): flat massless n-body phase space, generated with RAMBO
  *     (Kleiss, Stirling, Ellis, Comput. Phys. Commun. 40 (1986) 359), the
- *     generator the paper leaves unnamed (Sec. 3, "given a set of random
- *     numbers, it generates a phase space point");
+ *     generator the paper leaves unnamed (Sec. 3 only says that the kernel
+ *     turns random numbers into a phase-space point and its weight);
  *   - Sec. 2.2, eqs. (9)-(10): the photon cuts.
  *
  * External states follow the textbook helicity construction in the chiral
@@ -643,8 +643,8 @@ void oracle_event_weights(int n, uint64_t seed, int64_t i0, int64_t N,
 
 /*
  * Weighted histograms of kinematic observables of the generated events
- * (Sec. 5, Fig. 2: the maximum transverse momentum and the Delta R between
- * final-state photons).  Observables, with pT = sqrt(px^2 + py^2),
+ * (Sec. 5, Fig. 2: the largest photon transverse momentum and the photons'
+ * Delta R separations).  Observables, with pT = sqrt(px^2 + py^2),
  * eta = asinh(pz / pT) + y (lab frame, as for the cuts of Sec. 2.2),
  * phi = atan2(py, px) and Delta phi folded into [0, pi]:
  *   0 the largest pT of the event's photons   (1 entry per event)
