@@ -436,8 +436,9 @@ int heget_submit(heget_server* s, const heget_request* q, uint64_t* ticket);
  * released), HEGET_EBUSY if not yet, HEGET_ENOTFOUND for an unknown or
  * already released ticket.  Never blocks. */
 int heget_poll(heget_server* s, uint64_t ticket, heget_result* out);
-/* As heget_poll, but waits up to timeout_s seconds; HEGET_ETIMEOUT if the
- * request is still running then (the ticket stays valid). */
+/* As heget_poll, but waits up to timeout_s seconds (>= 0, else
+ * HEGET_EINVAL; capped at 1e7 s); HEGET_ETIMEOUT if the request is still
+ * running then (the ticket stays valid). */
 int heget_wait(heget_server* s, uint64_t ticket, double timeout_s,
                heget_result* out);
 /* Cancels requests not yet admitted (they finish with HEGET_EBUSY), lets

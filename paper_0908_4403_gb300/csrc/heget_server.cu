@@ -343,7 +343,10 @@ void heget_server::run() {
             if (L.busy) {
                 const cudaError_t q = cudaEventQuery(L.done);
                 if (q == cudaSuccess) complete(L, HEGET_OK);
-                else if (q != cudaErrorNotReady) complete(L, HEGET_ECUDA);
+                else if (q != cudaErrorNotReady) {
+                    cudaStreamSynchronize(stream);   // nothing of this server runs on after the error
+                    fail_all(L);
+                }
             }
         }
         {
@@ -466,10 +469,14 @@ int heget_poll(heget_server* s, uint64_t ticket, heget_result* out) {
 
 int heget_wait(heget_server* s, uint64_t ticket, double timeout_s, heget_result* out) {
     if (!s || !out) return fail(HEGET_EINVAL, "NULL argument");
+    if (!(timeout_s >= 0)) return fail(HEGET_EINVAL, "timeout_s must be >= 0");
+    timeout_s = std::min(timeout_s, 1e7);   // keeps the deadline inside the clock's range
     std::unique_lock<std::mutex> lock(s->mu);
     auto st = s->state.find(ticket);
     if (st == s->state.end()) return fail(HEGET_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
-    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                              std::chrono::duration<double>(timeout_s));
     const bool fin = s->cv_done.wait_until(lock, deadline, [&] {
         auto f = s->state.find(ticket);
         return f == s->state.end() || f->second == 2;

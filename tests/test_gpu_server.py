@@ -119,6 +119,10 @@ def test_server_wait_timeout_poll_and_errors(heget_lib, gpu):
     srv = H.heget_server_start(gpu)
     try:
         t = H.heget_submit(srv, 8, SEED + 500, 6_000, S, H.HEGET_FP32)   # ~0.1 s of work
+        for bad in (-1.0, float("nan")):
+            with pytest.raises(H.HegetError) as e:
+                H.heget_wait(srv, t, bad)
+            assert e.value.status == H.HEGET_EINVAL
         with pytest.raises(H.HegetError) as e:
             H.heget_wait(srv, t, 1e-4)
         assert e.value.status == H.HEGET_ETIMEOUT
@@ -141,5 +145,7 @@ def test_server_wait_timeout_poll_and_errors(heget_lib, gpu):
         while g2 is None and time.monotonic() < t_end:
             g2 = H.heget_poll(srv, t2)
         assert g2 is not None and g2.status == H.HEGET_OK
+        t3 = H.heget_submit(srv, 2, SEED + 502, 100, S)
+        assert H.heget_wait(srv, t3, 1e300).status == H.HEGET_OK   # an unbounded wait is capped, not overflowed
     finally:
         H.heget_server_stop(srv)
