@@ -23,6 +23,9 @@
  *    bit1 = s2, bit(2+i) = lambda_{i+1} (1 -> +1, 0 -> -1).  A helicity
  *    mask is an array of 2^(n+2)/32 uint32 words (1 word for n <= 3), bit h
  *    of word h/32; NULL selects all 2^(n+2) combinations.
+ *  - Generated points are numbered: point i of stream `seed` depends only on
+ *    (seed, i).  A call over points i0 .. i0+N-1 needs i0 >= 0 and
+ *    i0 + N <= 2^63 - 1, else HEGET_EINVAL.
  *  - Every call returns an int status (HEGET_OK = 0).  On failure,
  *    heget_last_error() returns a message for the calling thread.  No call
  *    aborts, prints, or allocates device memory except heget_create and the

@@ -1,5 +1,6 @@
 // heget_api.cu -- the C ABI of include/heget.h: context, argument checks,
 // launch shapes, the phase-space kernel and the fixed-order reductions.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -357,6 +358,21 @@ int check_precision(int p) {
     if (p != HEGET_FP32 && p != HEGET_FP64) return fail(HEGET_EINVAL, "precision must be 32 or 64, got %d", p);
     return HEGET_OK;
 }
+
+int check_range(long long i0, long long N) {
+    if (i0 < 0) return fail(HEGET_EINVAL, "i0 = %lld < 0", i0);
+    if (N > 0 && i0 > LLONG_MAX - N) return fail(HEGET_EINVAL, "point indices i0 + N overflow int64");
+    return HEGET_OK;
+}
+
+int check_params(const heget_params* p) {
+    if (!(p->alpha > 0) || !std::isfinite(p->alpha) || !std::isfinite(p->q_charge) || p->q_charge == 0)
+        return fail(HEGET_EINVAL, "alpha must be finite and > 0, q_charge finite and nonzero");
+    if (!(p->pt_min >= 0) || !std::isfinite(p->pt_min) || !(p->eta_max > 0) || !std::isfinite(p->eta_max) ||
+        std::isnan(p->dr_min))
+        return fail(HEGET_EINVAL, "cuts need finite pt_min >= 0 and eta_max > 0, and dr_min not NaN");
+    return HEGET_OK;
+}
 }  // namespace heget
 
 namespace {
@@ -524,9 +540,8 @@ int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind) {
 
 int heget_set_params(heget_ctx* ctx, const heget_params* p) {
     if (!ctx || !p) return fail(HEGET_EINVAL, "NULL argument");
-    if (!(p->alpha > 0) || !std::isfinite(p->alpha) || !std::isfinite(p->q_charge) || p->q_charge == 0)
-        return fail(HEGET_EINVAL, "alpha must be > 0 and q_charge nonzero");
-    if (!(p->pt_min >= 0) || !(p->eta_max > 0)) return fail(HEGET_EINVAL, "cuts need pt_min >= 0, eta_max > 0");
+    int r = check_params(p);
+    if (r) return r;
     ctx->params = *p;
     return HEGET_OK;
 }
@@ -543,7 +558,7 @@ int heget_phase_space_ex(heget_ctx* ctx, uint64_t seed, int64_t i0, int64_t N, i
     int r = check_common(ctx, n, N);
     if (r) return r;
     if ((r = check_sampler(smp))) return r;
-    if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
+    if ((r = check_range(i0, N))) return r;
     if (N == 0) return HEGET_OK;
     DeviceGuard g(ctx->device);
     const SamplerArgs S = sampler_args(smp);
@@ -688,7 +703,7 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
     if (r) return r;
     if ((r = check_precision(precision))) return r;
     if ((r = check_sampler(smp))) return r;
-    if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
+    if ((r = check_range(i0, N))) return r;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     AmpLaunch L;
@@ -817,8 +832,9 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
         int r = check_common(ctx, q.n, q.N);
         if (!r) r = check_precision(q.precision);
         if (!r) r = check_sampler(&q.sampler);
+        if (!r) r = check_range(q.i0, q.N);
         if (r) return fail(r, "request %d: %s", i, heget_last_error());
-        if (q.i0 < 0 || !q.result_dev) return fail(HEGET_EINVAL, "request %d: i0 < 0 or result_dev NULL", i);
+        if (!q.result_dev) return fail(HEGET_EINVAL, "request %d: result_dev is NULL", i);
     }
     if (count == 0) return HEGET_OK;
     DeviceGuard g(ctx->device);

@@ -236,7 +236,7 @@ int heget_hist(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N, cons
     int r = check_common(ctx, n, N);
     if (r) return r;
     if ((r = check_sampler(smp))) return r;
-    if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
+    if ((r = check_range(i0, N))) return r;
     if (!specs || nspec < 1 || nspec > HEGET_HIST_MAX_SPECS)
         return fail(HEGET_EINVAL, "need 1 <= nspec <= %d histogram specs", HEGET_HIST_MAX_SPECS);
     HistArgs H{};

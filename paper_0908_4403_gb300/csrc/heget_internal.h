@@ -82,6 +82,11 @@ int check_sampler(const heget_sampler* s);
 SamplerArgs sampler_args(const heget_sampler* s);
 int check_common(const heget_ctx* ctx, int n, long long N);
 int check_precision(int p);
+// i0 >= 0 and the last point index i0 + N - 1 representable as int64.
+int check_range(long long i0, long long N);
+// Finite alpha > 0, finite nonzero charge, finite pt_min >= 0 and eta_max > 0,
+// dr_min not NaN.
+int check_params(const heget_params* p);
 // Grows a workspace buffer to at least `need` bytes (device, or pinned host).
 int grow(void** p, size_t* cap, size_t need, bool pinned);
 }  // namespace heget

@@ -28,6 +28,7 @@ struct heget_graph {
     cudaGraphExec_t exec = nullptr;
     GraphKernel k[2];   // event kernel, escalation kernel
     int nk = 0;
+    long long N = 0;    // points per replay
 };
 
 namespace {
@@ -65,6 +66,7 @@ int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp,
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
     heget_graph* g = new heget_graph();
     g->ctx = ctx;
+    g->N = N;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         cudaStreamDestroy(st);
@@ -99,7 +101,8 @@ int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp,
 
 int heget_graph_launch(heget_graph* g, uint64_t seed, int64_t i0, void* stream) {
     if (!g) return fail(HEGET_EINVAL, "graph is NULL");
-    if (i0 < 0) return fail(HEGET_EINVAL, "i0 < 0");
+    int r = check_range(i0, g->N);
+    if (r) return r;
     DeviceGuard dg(g->ctx->device);
     long long i0v = i0;
     cudaError_t e = cudaSuccess;

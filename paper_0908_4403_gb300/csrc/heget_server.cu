@@ -425,6 +425,7 @@ int heget_submit(heget_server* s, const heget_request* q, uint64_t* ticket) {
     int r = check_common(s->ctx, q->n, q->N);
     if (!r) r = check_precision(q->precision);
     if (!r) r = check_sampler(&q->sampler);
+    if (!r) r = check_range(q->i0, q->N);
     if (r) return r;
     if (q->N < 1) return fail(HEGET_EINVAL, "a request needs N >= 1");
     Req* rq = new Req();

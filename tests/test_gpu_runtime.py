@@ -146,3 +146,46 @@ def test_failed_call_leaves_no_stale_cuda_error(heget_lib, gpu):
         assert float(x) == 1000.0
     finally:
         H.heget_set_tile(gpu, 8, 64, 1, 0)
+
+
+def test_point_ranges_and_params_are_checked_on_the_host(heget_lib, gpu):
+    """Point indices i0 .. i0+N-1 must fit in int64, and the physics
+    parameters must be finite: every entry point refuses the call before it
+    launches anything, and the context keeps its parameters."""
+    H = heget_lib
+    S = H.sampler_toy_pdf()
+    top = 2 ** 63 - 10
+
+    def refused(call, what="overflow"):
+        with pytest.raises(H.HegetError) as e:
+            call()
+        assert e.value.status == H.HEGET_EINVAL and what in str(e.value)
+
+    refused(lambda: H.heget_phase_space_ex(gpu, 1, top, 100, 4, S))
+    refused(lambda: H.heget_xsec_launch(gpu, 4, 1, top, 100, S, H.HEGET_FP32))
+    refused(lambda: H.heget_hist(gpu, 4, 1, top, 100, S, None, [(0, 10, 0.0, 100.0)], None))
+    refused(lambda: H.heget_xsec_batch(gpu, [dict(n=4, precision=32, seed=1, i0=top, N=100, sampler=S,
+                                                  result_dev=_buf())]))
+    refused(lambda: H.heget_phase_space_ex(gpu, 1, -1, 100, 4, S), "< 0")
+    res = _buf()
+    g = H.heget_graph_xsec(gpu, 4, 1000, S, H.HEGET_FP32, res)
+    try:
+        refused(lambda: H.heget_graph_launch(g, 1, top))
+        H.heget_graph_launch(g, 1, top - 10_000)        # indices near the top of the range still run
+        assert _res(H, res).n_total == 1000
+    finally:
+        H.heget_graph_destroy(g)
+    srv = H.heget_server_start(gpu)
+    try:
+        refused(lambda: H.heget_submit(srv, 4, 1, 100, S, i0=top))
+    finally:
+        H.heget_server_stop(srv)
+
+    before = H.heget_get_params(gpu)
+    for bad in (dict(dr_min=float("nan")), dict(eta_max=float("inf")), dict(pt_min=float("inf")),
+                dict(alpha=float("inf")), dict(q_charge=0.0)):
+        with pytest.raises(H.HegetError) as e:
+            H.heget_set_params(gpu, **bad)
+        assert e.value.status == H.HEGET_EINVAL
+    after = H.heget_get_params(gpu)
+    assert [getattr(after, f) for f, _ in after._fields_] == [getattr(before, f) for f, _ in before._fields_]
