@@ -105,7 +105,12 @@ typedef struct {
 /* Context: binds a CUDA device, holds the physics parameters (defaults:
  * alpha = 1/137.035999, q_charge = 2/3, pt_min = 20, eta_max = 2.5,
  * dr_min = 0.4) and a small workspace.  heget_create allocates the
- * workspace on `device`; returns HEGET_ECUDA if the device is unusable. */
+ * workspace on `device`; returns HEGET_ECUDA if the device is unusable.
+ * The workspace (block partials, escalation lists, result staging) is
+ * shared by every call on the context: issue them from one host thread at a
+ * time and keep them from overlapping on the GPU (one stream per context, or
+ * one context per stream).  The request server is the thread-safe way to
+ * share a device between submitters. */
 int heget_create(int device, heget_ctx** out);
 void heget_destroy(heget_ctx* ctx);
 int heget_set_params(heget_ctx* ctx, const heget_params* p);   /* p: host */
