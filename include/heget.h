@@ -235,8 +235,9 @@ typedef struct {
  * their n and N, form one work list that a single kernel walks, and each
  * request's tile partials are combined in tile order, so a request's result
  * does not depend on what else is in the batch.  reqs: host array of `count`
- * requests.  Grows the context workspace on demand, and synchronizes
- * `stream` before returning. */
+ * requests.  At most 2^22 tiles per precision and call (HEGET_EINVAL
+ * beyond: split the batch).  Grows the context workspace on demand, and
+ * synchronizes `stream` before returning. */
 int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, int count,
                      void* stream);
 

@@ -376,6 +376,10 @@ int check_params(const heget_params* p) {
 }  // namespace heget
 
 namespace {
+// Point tiles of one precision in one heget_xsec_batch call (a 96 MiB work
+// list; 16.7 M points at n = 8, 537 M at n <= 4).
+constexpr long long kMaxBatchTiles = 1ll << 22;
+
 template <class R>
 size_t batch_tile_smem(int n, int tile) {
     switch (n) {
@@ -835,6 +839,18 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
         if (!r) r = check_range(q.i0, q.N);
         if (r) return fail(r, "request %d: %s", i, heget_last_error());
         if (!q.result_dev) return fail(HEGET_EINVAL, "request %d: result_dev is NULL", i);
+    }
+    {   // the work list is staged on the host: bound its length before building it
+        long long tiles[2] = {0, 0};
+        for (int i = 0; i < count; ++i) {
+            const heget_xsec_request& q = reqs[i];
+            const int tile_o = ctx->tiles[1][q.precision == HEGET_FP64][q.n];
+            const long long tile = tile_o > 0 ? tile_o : default_tile(q.n, true);
+            tiles[q.precision == HEGET_FP64] += (q.N + tile - 1) / tile;
+            if (tiles[0] > kMaxBatchTiles || tiles[1] > kMaxBatchTiles)
+                return fail(HEGET_EINVAL, "batch needs more than %lld point tiles per precision: split it",
+                            (long long)kMaxBatchTiles);
+        }
     }
     if (count == 0) return HEGET_OK;
     DeviceGuard g(ctx->device);

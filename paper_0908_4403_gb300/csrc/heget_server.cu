@@ -428,11 +428,15 @@ int heget_submit(heget_server* s, const heget_request* q, uint64_t* ticket) {
     if (!r) r = check_range(q->i0, q->N);
     if (r) return r;
     if (q->N < 1) return fail(HEGET_EINVAL, "a request needs N >= 1");
+    const int t = s->ctx->tiles[1][q->precision == HEGET_FP64][q->n];
+    const int tile = t > 0 ? t : default_tile(q->n, true);
+    const long long ntiles = (q->N + tile - 1) / tile;
+    if (ntiles > (long long)(s->arena.size / sizeof(Partial)))
+        return fail(HEGET_ENOMEM, "request of %lld tiles cannot fit the arena of %zu bytes", ntiles, s->arena.size);
     Req* rq = new Req();
     rq->q = *q;
-    const int t = s->ctx->tiles[1][q->precision == HEGET_FP64][q->n];
-    rq->tile = t > 0 ? t : default_tile(q->n, true);
-    rq->ntiles = (int)((q->N + rq->tile - 1) / rq->tile);
+    rq->tile = tile;
+    rq->ntiles = (int)ntiles;
     rq->next_tile = 0;
     rq->t_submit = now_s();
     {

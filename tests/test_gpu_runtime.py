@@ -167,6 +167,8 @@ def test_point_ranges_and_params_are_checked_on_the_host(heget_lib, gpu):
     refused(lambda: H.heget_xsec_batch(gpu, [dict(n=4, precision=32, seed=1, i0=top, N=100, sampler=S,
                                                   result_dev=_buf())]))
     refused(lambda: H.heget_phase_space_ex(gpu, 1, -1, 100, 4, S), "< 0")
+    refused(lambda: H.heget_xsec_batch(gpu, [dict(n=8, precision=32, seed=1, N=2 ** 40, sampler=S,
+                                                  result_dev=_buf())]), "split")
     res = _buf()
     g = H.heget_graph_xsec(gpu, 4, 1000, S, H.HEGET_FP32, res)
     try:
@@ -178,6 +180,9 @@ def test_point_ranges_and_params_are_checked_on_the_host(heget_lib, gpu):
     srv = H.heget_server_start(gpu)
     try:
         refused(lambda: H.heget_submit(srv, 4, 1, 100, S, i0=top))
+        with pytest.raises(H.HegetError) as e:
+            H.heget_submit(srv, 8, 1, 2 ** 40, S)           # more tile partials than the arena holds
+        assert e.value.status == H.HEGET_ENOMEM
     finally:
         H.heget_server_stop(srv)
 
