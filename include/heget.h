@@ -260,7 +260,7 @@ int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, int count,
 typedef struct {
     int32_t observable; /* HEGET_OBS_* */
     int32_t nbins;      /* >= 1 */
-    double lo, hi;      /* finite, lo < hi */
+    double lo, hi;      /* finite, lo < hi, nbins / (hi - lo) finite */
 } heget_hist_spec;
 
 #define HEGET_HIST_MAX_SPECS 8

@@ -248,8 +248,9 @@ int heget_hist(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N, cons
             return fail(HEGET_EINVAL, "spec %d: unknown observable %d", s, q.observable);
         if (q.nbins < 1 || q.nbins > HEGET_HIST_MAX_BINS - 2)
             return fail(HEGET_EINVAL, "spec %d: nbins = %d", s, q.nbins);
-        if (!std::isfinite(q.lo) || !std::isfinite(q.hi) || !(q.lo < q.hi) || !std::isfinite(q.hi - q.lo))
-            return fail(HEGET_EINVAL, "spec %d: need finite lo < hi", s);
+        if (!std::isfinite(q.lo) || !std::isfinite(q.hi) || !(q.lo < q.hi) || !std::isfinite(q.hi - q.lo) ||
+            !std::isfinite((double)q.nbins / (q.hi - q.lo)))
+            return fail(HEGET_EINVAL, "spec %d: need finite lo < hi and a finite bins-per-unit scale", s);
         H.spec[s].kind = q.observable;
         H.spec[s].nbins = q.nbins;
         H.spec[s].off = total;

@@ -121,7 +121,7 @@ def test_hist_argument_checks(heget_lib, gpu):
     w = torch.ones(10, dtype=torch.float64, device="cuda")
     out = torch.full((64,), 7.0, dtype=torch.float64, device="cuda")
     for bad in ([(9, 4, 0.0, 1.0)], [(PT, 0, 0.0, 1.0)], [(PT, 4, 1.0, 1.0)], [(PT, 4, 0.0, float("inf"))],
-                [(PT, 1023, 0.0, 1.0)], [(PT, 4, 0.0, 1.0)] * 9, []):
+                [(PT, 1023, 0.0, 1.0)], [(PT, 4, 0.0, 1.0)] * 9, [], [(PT, 4, 0.0, 1e-310)]):
         with pytest.raises(H.HegetError):
             H.heget_hist(gpu, 4, 1, 0, 10, S, w, bad, out)
     with pytest.raises(H.HegetError):
