@@ -140,12 +140,19 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
             lines = fh.readlines()
         if not os.environ.get("HEGET_CLOCKS_CSV"):
             os.remove(self.path)
+        return self.summarise(lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, the largest max clock and the throttle reasons
+        seen Active, from nvidia-smi CSV lines in FIELDS order (None if no
+        line parses)."""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
