@@ -315,6 +315,19 @@ def test_toy_pdf_floor_acceptance(oracle):
     assert abs(est - p_acc) < 5 * sigma
 
 
+def test_fixed_and_uniform_samplers(oracle):
+    """The fixed sampler gives sqrt(s-hat) itself; the uniform one is uniform
+    on [lo, hi] (KS test against the library's uniform law); both have y = 0
+    and one attempt per point."""
+    ps = oracle.phase_space(3, 15, 0, 50, oracle.fixed(500.0), None)
+    assert np.all(ps["sqrt_s"] == 500.0) and np.all(ps["y"] == 0) and np.all(ps["tries"] == 1)
+    ps = oracle.phase_space(3, 16, 0, 4000, oracle.uniform(200.0, 2000.0), None)
+    rs = ps["sqrt_s"]
+    assert np.all((rs > 200.0) & (rs < 2000.0))
+    assert stats.kstest(rs, stats.uniform(loc=200.0, scale=1800.0).cdf).pvalue > 1e-4
+    assert np.all(ps["y"] == 0) and np.all(ps["tries"] == 1)
+
+
 # --------------------------------------------------------------------------
 # cuts and cross section
 # --------------------------------------------------------------------------
@@ -358,6 +371,35 @@ def test_n2_cut_acceptance_and_cross_section(oracle):
     assert exact == pytest.approx(137.71, abs=0.01)
     assert abs(sig - exact) < 5 * err
     assert err / sig < 0.01
+
+
+def test_identical_photon_factor_by_soft_emission(oracle):
+    """The 1/n! of eq. (2) beyond n = 2, from soft-photon factorisation.
+    Events of u ubar -> 3 gamma at sqrt(s) = 500 GeV with exactly one photon
+    of energy in [a, b] << sqrt(s) and every photon at |cos theta| < c0 carry,
+    to O(b / sqrt(s)),
+        sigma_3 = 3 (f(3) / f(2)) sigma_2(c0) I,
+    with f(n) the identical-photon factor, 3 the choices of the soft photon,
+    sigma_2(c0) = pi alpha^2 Q^4 (4 atanh c0 - 2 c0) / (3 s) the analytic n = 2
+    cross section at |cos theta| < c0, and I the eikonal integral over the
+    soft photon: d^3k / ((2 pi)^3 2E) e^2 Q^2 2 p1.p2 / (p1.k p2.k) gives
+    I = 4 alpha Q^2 ln(b / a) atanh(c0) / pi.  With f(n) = 1/n! the prefactor
+    is 1 (1/n would give 2)."""
+    rs, a, b, c0, N = 500.0, 2.0, 10.0, 0.8, 4_000_000
+    ps = oracle.phase_space(3, 0x0908440300000303, 0, N, oracle.fixed(rs), None)
+    k = ps["momenta"][:, 2:, :]
+    E, cos = k[:, :, 0], k[:, :, 3] / k[:, :, 0]
+    sel = (((E > a) & (E < b)).sum(axis=1) == 1) & np.all(np.abs(cos) < c0, axis=1)
+    idx = np.nonzero(sel)[0]
+    a2 = oracle.amp2(3, ps["momenta"][idx])
+    w = np.array([oracle.event_weight(3, rs**2, a2[j], ps["weight"][i]) for j, i in enumerate(idx)])
+    sigma3 = w.sum() / N
+    err = math.sqrt(((w**2).sum() / N - sigma3**2) / N)
+    alpha = 1 / 137.035999
+    sigma2 = math.pi * alpha**2 * Q**4 * (4 * math.atanh(c0) - 2 * c0) / (3 * rs**2) * 0.3893793721e12
+    eikonal = 4 * alpha * Q**2 * math.log(b / a) * math.atanh(c0) / math.pi
+    assert err / sigma3 < 0.02
+    assert abs(sigma3 / (sigma2 * eikonal) - 1) < 0.08
 
 
 def test_propagators_spacelike(oracle):
