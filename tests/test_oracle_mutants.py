@@ -70,6 +70,11 @@ MUTANTS = [
     # samplers and cuts
     ("toy PDF: proposal x = u", "double x = u * u;", "double x = u;"),
     ("toy PDF: acceptance (1-x)^2", "if (v < pow(1 - x, b)) return x;", "if (v < pow(1 - x, b - 1)) return x;"),
+    ("toy PDF: floor test reversed", "if (rs > S->floor) {", "if (rs < S->floor) {"),
+    ("toy PDF: y = ln(x1/x2)", "*y = 0.5 * log(x1 / x2);", "*y = log(x1 / x2);"),
+    ("toy PDF: attempts not counted", "            return t;\n", "            return 1;\n"),
+    ("incoming ubar along +z", "p[7] = -rs / 2;", "p[7] = rs / 2;"),
+    ("metric route: sign of the time component", "sign *= (mu == 0) ? -1.0 : 1.0;", "sign *= (mu == 0) ? 1.0 : -1.0;"),
     ("uniform sampler: range from lo to hi - lo", "*sqrt_s = S->lo + (S->hi - S->lo) * u;", "*sqrt_s = (S->hi - S->lo) * u;"),
     ("cuts: boost subtracted", "eta[i] = asinh(p[3] / pt) + y;", "eta[i] = asinh(p[3] / pt) - y;"),
     ("cuts: Delta phi not folded", "if (dphi > M_PI) dphi = 2 * M_PI - dphi;\n                double deta",
