@@ -194,3 +194,37 @@ def test_point_ranges_and_params_are_checked_on_the_host(heget_lib, gpu):
         assert e.value.status == H.HEGET_EINVAL
     after = H.heget_get_params(gpu)
     assert [getattr(after, f) for f, _ in after._fields_] == [getattr(before, f) for f, _ in before._fields_]
+
+
+@pytest.mark.parametrize("n,N,prec", [(4, 70_001, 32), (6, 3_001, 32), (3, 9_999, 64)])
+def test_launch_and_finalize_pair_equals_the_async_call(heget_lib, gpu, n, N, prec):
+    """heget_xsec_launch + heget_xsec_finalize (the bench's step) give the
+    same result as heget_xsec_async; finalising again rereads the same
+    partials; a NULL result buffer is refused."""
+    import torch
+    H = heget_lib
+    S = H.sampler_toy_pdf()
+    ref = _async(H, gpu, n, SEED + 700 + n, N, S, prec, i0=123)
+    H.heget_xsec_launch(gpu, n, SEED + 700 + n, 123, N, S, prec)
+    r1, r2 = _buf(), _buf()
+    H.heget_xsec_finalize(gpu, r1)
+    H.heget_xsec_finalize(gpu, r2)
+    a, b = _res(H, r1), _res(H, r2)
+    assert _same(a, ref) and _same(b, ref) and a.n_total == N
+    with pytest.raises(H.HegetError) as e:
+        H.heget_xsec_finalize(gpu, None)
+    assert e.value.status == H.HEGET_EINVAL
+    torch.cuda.synchronize()
+
+
+def test_fma_peak_probe(heget_lib, gpu):
+    """The FFMA/DFMA throughput probe reports rates of the right size for a
+    GB300 (FP32 tens of TFLOP/s, FP64 about 1/64 of it) and refuses bad
+    arguments."""
+    H = heget_lib
+    f32 = H.heget_measure_fma_peak(gpu, H.HEGET_FP32)
+    f64 = H.heget_measure_fma_peak(gpu, H.HEGET_FP64)
+    assert 20 < f32 < 200 and 0.2 < f64 < 5 and 20 < f32 / f64 < 200
+    with pytest.raises(H.HegetError) as e:
+        H.heget_measure_fma_peak(gpu, 16)
+    assert e.value.status == H.HEGET_EINVAL
