@@ -1,8 +1,10 @@
 """Thin ctypes binding of the C ABI in include/heget.h.
 
 Argument marshalling only: every step of the hot path runs in libheget.so.
-Device arrays are passed as raw pointers (``tensor.data_ptr()``); streams as
-``torch.cuda.Stream.cuda_stream`` integers (0 = legacy default stream).
+Device arrays are CUDA tensors, checked on the host (CUDA, contiguous, element
+size, length) and passed as ``tensor.data_ptr()``, or raw integer addresses,
+passed unchecked; streams are ``torch.cuda.Stream`` objects or their
+``cuda_stream`` integers (0 = legacy default stream).
 Loading fails loudly when the library is missing: there is no CPU fallback.
 """
 from __future__ import annotations
@@ -171,6 +173,39 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _dev(x, what, count, itemsize, floating=None):
+    """Device address of tensor `x`, which must be a contiguous CUDA tensor
+    of at least `count` elements of `itemsize` bytes (floating point or not,
+    when `floating` says so).  A wrong argument raises HEGET_EINVAL here, on
+    the host, instead of reaching a kernel.  None and raw integer addresses
+    pass through unchecked (the library checks NULL)."""
+    if x is None or isinstance(x, int):
+        return x
+    if not getattr(x, "is_cuda", False):
+        bad = "must be a CUDA tensor"
+    elif not x.is_contiguous():
+        bad = "must be contiguous"
+    elif x.element_size() != itemsize or (floating is not None and x.dtype.is_floating_point != floating):
+        kind = "" if floating is None else (" floating-point" if floating else " integer")
+        bad = f"needs {itemsize}-byte{kind} elements, got {x.dtype}"
+    elif x.numel() < count:
+        bad = f"holds {x.numel()} elements, needs {count}"
+    else:
+        return x.data_ptr()
+    raise HegetError(HEGET_EINVAL, f"{what} {bad}")
+
+
+def _f64s(x, what, count):
+    return _dev(x, what, count, 8, True)
+
+
+def _result(x, what="result_dev"):
+    """A device buffer of at least sizeof(heget_xsec_result) bytes, any dtype."""
+    if x is None or isinstance(x, int):
+        return x
+    return _dev(x, what, -(-C.sizeof(heget_xsec_result) // x.element_size()), x.element_size())
+
+
 def _stream(s):
     if s is None:
         return None
@@ -209,33 +244,40 @@ def heget_version() -> str:
 
 
 def heget_phase_space(ctx, seed, N, n, sqrt_s, momenta, weights=None, stream=None):
-    _check(load().heget_phase_space(ctx, seed, N, n, sqrt_s, _ptr(momenta), _ptr(weights), _stream(stream)))
+    _check(load().heget_phase_space(ctx, seed, N, n, sqrt_s, _f64s(momenta, "momenta", N * (n + 2) * 4),
+                                    _f64s(weights, "weights", N), _stream(stream)))
 
 
 def heget_phase_space_ex(ctx, seed, i0, N, n, sampler, momenta=None, weights=None, sqrt_s=None, y=None,
                          mask=None, tries=None, stream=None):
-    _check(load().heget_phase_space_ex(ctx, seed, i0, N, n, C.byref(sampler), _ptr(momenta), _ptr(weights),
-                                       _ptr(sqrt_s), _ptr(y), _ptr(mask), _ptr(tries), _stream(stream)))
+    _check(load().heget_phase_space_ex(ctx, seed, i0, N, n, C.byref(sampler),
+                                       _f64s(momenta, "momenta", N * (n + 2) * 4), _f64s(weights, "weights", N),
+                                       _f64s(sqrt_s, "sqrt_s", N), _f64s(y, "y", N), _dev(mask, "mask", N, 1),
+                                       _dev(tries, "tries", N, 4, False), _stream(stream)))
 
 
 def heget_amp2(ctx, n, N, momenta, amp2, hel_mask=None, precision=HEGET_FP64, stream=None):
-    _check(load().heget_amp2(ctx, n, N, _ptr(momenta), _ptr(hel_mask), precision, _ptr(amp2), _stream(stream)))
+    _check(load().heget_amp2(ctx, n, N, _f64s(momenta, "momenta", N * (n + 2) * 4),
+                             _dev(hel_mask, "hel_mask", max(1, (1 << max(n + 2, 0)) // 32), 4, False), precision,
+                             _f64s(amp2, "amp2", N), _stream(stream)))
 
 
 def heget_ward(ctx, n, N, momenta, photon, ratio, precision=HEGET_FP64, stream=None):
-    _check(load().heget_ward(ctx, n, N, _ptr(momenta), photon, precision, _ptr(ratio), _stream(stream)))
+    _check(load().heget_ward(ctx, n, N, _f64s(momenta, "momenta", N * (n + 2) * 4), photon, precision,
+                             _f64s(ratio, "ratio", N), _stream(stream)))
 
 
 def heget_log_table(x, y, N, stream=None):
-    _check(load().heget_log_table(_ptr(x), _ptr(y), N, _stream(stream)))
+    _check(load().heget_log_table(_f64s(x, "x", N), _f64s(y, "y", N), N, _stream(stream)))
 
 
 def heget_sincos_2pi(words, cs, N, stream=None):
-    _check(load().heget_sincos_2pi(_ptr(words), _ptr(cs), N, _stream(stream)))
+    _check(load().heget_sincos_2pi(_dev(words, "words", 2 * N, 4, False), _f64s(cs, "cs", 2 * N), N,
+                                   _stream(stream)))
 
 
 def heget_f32_round(x, y, N, stream=None):
-    _check(load().heget_f32_round(_ptr(x), _ptr(y), N, _stream(stream)))
+    _check(load().heget_f32_round(_f64s(x, "x", N), _dev(y, "y", N, 4, True), N, _stream(stream)))
 
 
 def heget_check(ctx, stream=None):
@@ -243,8 +285,8 @@ def heget_check(ctx, stream=None):
 
 
 def heget_xsec_async(ctx, n, seed, i0, N, sampler, precision, result_dev, w_out=None, stream=None):
-    _check(load().heget_xsec_async(ctx, n, seed, i0, N, C.byref(sampler), precision, _ptr(result_dev),
-                                   _ptr(w_out), _stream(stream)))
+    _check(load().heget_xsec_async(ctx, n, seed, i0, N, C.byref(sampler), precision, _result(result_dev),
+                                   _f64s(w_out, "w_out", N), _stream(stream)))
 
 
 def heget_xsec(ctx, n, N, seed, sampler, precision=HEGET_FP32, stream=None) -> heget_xsec_result:
@@ -254,12 +296,12 @@ def heget_xsec(ctx, n, N, seed, sampler, precision=HEGET_FP32, stream=None) -> h
 
 
 def heget_xsec_launch(ctx, n, seed, i0, N, sampler, precision, w_out=None, stream=None):
-    _check(load().heget_xsec_launch(ctx, n, seed, i0, N, C.byref(sampler), precision, _ptr(w_out),
+    _check(load().heget_xsec_launch(ctx, n, seed, i0, N, C.byref(sampler), precision, _f64s(w_out, "w_out", N),
                                     _stream(stream)))
 
 
 def heget_xsec_finalize(ctx, result_dev, stream=None):
-    _check(load().heget_xsec_finalize(ctx, _ptr(result_dev), _stream(stream)))
+    _check(load().heget_xsec_finalize(ctx, _result(result_dev), _stream(stream)))
 
 
 def heget_measure_fma_peak(ctx, precision=HEGET_FP32) -> float:
@@ -285,8 +327,8 @@ def heget_hist(ctx, n, seed, i0, N, sampler, w, specs, out, stream=None):
     """specs: list of (observable, nbins, lo, hi); out: device doubles of
     length hist_bins(specs), per spec (nbins + 2) rows of (sum w, sum w^2)."""
     arr = (heget_hist_spec * len(specs))(*[heget_hist_spec(*sp) for sp in specs])
-    _check(load().heget_hist(ctx, n, seed, i0, N, C.byref(sampler), _ptr(w), arr, len(specs), _ptr(out),
-                             _stream(stream)))
+    _check(load().heget_hist(ctx, n, seed, i0, N, C.byref(sampler), _f64s(w, "w", N), arr, len(specs),
+                             _f64s(out, "out", hist_bins(specs)), _stream(stream)))
 
 
 def heget_xsec_batch(ctx, requests, stream=None):
@@ -295,8 +337,8 @@ def heget_xsec_batch(ctx, requests, stream=None):
     for a, r in zip(arr, requests):
         a.n, a.precision, a.seed, a.i0, a.N = r["n"], r["precision"], r["seed"], r.get("i0", 0), r["N"]
         a.sampler = r["sampler"]
-        a.result_dev = _ptr(r["result_dev"])
-        a.w_out = _ptr(r.get("w_out"))
+        a.result_dev = _result(r["result_dev"])
+        a.w_out = _f64s(r.get("w_out"), "w_out", r["N"])
     _check(load().heget_xsec_batch(ctx, arr, len(requests), _stream(stream)))
 
 
@@ -317,7 +359,7 @@ def heget_autotune_load(ctx, path):
 
 def heget_graph_xsec(ctx, n, N, sampler, precision, result_dev):
     g = P()
-    _check(load().heget_graph_xsec(ctx, n, N, C.byref(sampler), precision, _ptr(result_dev), C.byref(g)))
+    _check(load().heget_graph_xsec(ctx, n, N, C.byref(sampler), precision, _result(result_dev), C.byref(g)))
     return g
 
 
@@ -369,7 +411,7 @@ def heget_xsec_noalloc(device, n, seed, i0, N, sampler, precision, result_dev, p
 
 
 def heget_sum(ctx, x, N, out_dev, stream=None):
-    _check(load().heget_sum(ctx, _ptr(x), N, _ptr(out_dev), _stream(stream)))
+    _check(load().heget_sum(ctx, _f64s(x, "x", N), N, _f64s(out_dev, "out_dev", 2), _stream(stream)))
 
 
 def heget_server_start(ctx, max_inflight=0, max_launch_work=0.0, hbm_reserve_frac=0.0, arena_bytes=0):
