@@ -84,6 +84,20 @@ def subset_flops_per_point(n: int) -> int:
     return 32 * steps + 16 * n * (1 << n)
 
 
+def helas4_flops_per_point(n: int) -> int:
+    """For comparison only: the same per-helicity prefix tree in the paper's
+    4-component form, for each of the 2^(n+1) helicities with s2 = -s1 (the
+    others vanish exactly).  A step applies the vertex eps-slash and the
+    propagator q-slash to a 4-spinor -- in the chiral basis each is two 2x2
+    complex products, 8 complex multiplies and 4 adds = 56 flops -- then the
+    couplings and 1/q^2 (8 flops each): 128 flops.  A closure vbar eps-slash
+    psi is 56 + a 4-term complex dot product (30) + the coupling (2) = 88.
+    Steps per helicity: sum_{l=1}^{n-1} n!/(n-l)!; closures: n!."""
+    f = math.factorial(n)
+    steps = sum(f // math.factorial(n - l) for l in range(1, n))
+    return (1 << (n + 1)) * (128 * steps + 88 * f)
+
+
 def tree_flops_per_point(n: int, fp64: bool = False) -> int:
     """Flops of the ordering tree per point: 2^n helicity lanes, each doing
     sum_{l=2}^{n-1} n!/(n-l)! chain steps (28 flops: r . M, 2x2 complex) and n!
@@ -444,6 +458,7 @@ def matrix_section(H, ctx, stream, peak32, peak64, flush):
                                                        / (ms64 * 1e-3) / (FP64_PEAK * 1e12),
                     "subset_fp32_points_per_s": N / (ms32s * 1e-3), "subset_fp64_points_per_s": N / (ms64s * 1e-3),
                     "subset_flops_per_point": subset_flops_per_point(n),
+                    "tree_flops_per_point": tf, "helas4_flops_per_point": helas4_flops_per_point(n),
                     "subset_fp32_frac_of_fp32_peak": subset_flops_per_point(n) * r32[0].n_pass / (ms32s * 1e-3)
                                                      / (FP32_PEAK * 1e12),
                     "oracle": base})

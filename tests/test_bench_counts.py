@@ -44,3 +44,14 @@ def test_subset_flops_by_enumeration(bench, n):
         for S in itertools.combinations(range(n), k):
             steps += len(S) * (1 << k)   # each photon of S attached last, every helicity of S
     assert bench.subset_flops_per_point(n) == 32 * steps + 16 * n * (1 << n)
+
+
+@pytest.mark.parametrize("n", range(2, 9))
+def test_helas4_flops_by_enumeration(bench, n):
+    """The 4-component comparison count: every ordered prefix of 1..n-1
+    photons is a step, every ordering a closure, for 2^(n+1) helicities."""
+    prefixes = set()
+    for perm in itertools.permutations(range(n)):
+        for l in range(1, n):
+            prefixes.add(perm[:l])
+    assert bench.helas4_flops_per_point(n) == (1 << (n + 1)) * (128 * len(prefixes) + 88 * math.factorial(n))
