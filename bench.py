@@ -214,6 +214,14 @@ def cpu_baseline(n, seconds=12.0, sampler=None, cut=None, seed=SEED, N_cap=None)
     rec = {"value": N / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
            "sample": f"points 0..{N - 1} of the n={n} workload (seed {seed:#x}), weights incl. |M|^2 "
                      f"of cut-passing points, {threads} OpenMP threads, {dt:.1f} s"}
+    # one core as well, on the first points of the same sample (about 2 s of work)
+    n1 = min(N, int(N / dt / threads * 2.0))
+    if n1 >= 4:
+        t1 = time.perf_counter()
+        O.event_weights(n, seed, 0, n1, S, Cc, threads=1)
+        d1 = time.perf_counter() - t1
+        rec["single_thread"] = {"value": n1 / d1, "unit": "points/s", "cores": 1,
+                                "sample": f"points 0..{n1 - 1}, 1 thread, {d1:.1f} s"}
     return rec, w
 
 
