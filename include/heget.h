@@ -380,7 +380,12 @@ int heget_autotune_load(heget_ctx* ctx, const char* path);
  * once; heget_graph_launch replays it for a new (seed, i0) by updating the
  * captured event kernel's arguments.  result_dev receives each replay's
  * result.  A graph uses its context's workspace: replays of graphs of one
- * context must be ordered on one stream. */
+ * context must be ordered on one stream.  heget_graph_xsec: EINVAL for a
+ * NULL out or result_dev, N < 1, or a bad n, precision or sampler (the
+ * escalation lists are grown before capture, since a capture cannot
+ * allocate); ECUDA if capture or instantiation fails.  heget_graph_launch:
+ * EINVAL for a NULL graph or i0 outside the point-range rule; ECUDA if the
+ * update or the launch fails.  heget_graph_destroy(NULL) does nothing. */
 typedef struct heget_graph heget_graph;
 int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp,
                      int precision, heget_xsec_result* result_dev,
