@@ -228,6 +228,39 @@ def test_xsec_n2_analytic(heget_lib, gpu):
     assert abs(r.n_pass / 65536 - c0) < 5 * math.sqrt(c0 * (1 - c0) / 65536)
 
 
+@pytest.mark.parametrize("n", [3, 5])
+def test_other_quark_charges_couplings_and_cuts(oracle, heget_lib, gpu, n):
+    """Context parameters reach every step: d dbar -> n gamma (Q = -1/3, the
+    other subprocesses of Sec. 2.1 differ from u ubar only in the charge), a
+    different alpha and different cuts, against the oracle with the same
+    parameters: |M|^2 in FP64, and the fused path's cut masks (bit for bit)
+    and weights."""
+    torch = torch_mod()
+    H = heget_lib
+    alpha, Q, cut = 1 / 128.0, -1 / 3, (30.0, 2.0, 0.6)
+    seed, N = SEED + 80 + n, {3: 1500, 5: 200}[n]
+    H.heget_set_params(gpu, alpha=alpha, q_charge=Q, pt_min=cut[0], eta_max=cut[1], dr_min=cut[2])
+    try:
+        mom = oracle_points(oracle, n, N, seed)
+        ref = oracle.amp2(n, mom, alpha=alpha, Q=Q)
+        m = dev(mom)
+        out = torch.empty(N, dtype=torch.float64, device="cuda")
+        H.heget_amp2(gpu, n, N, m, out, precision=H.HEGET_FP64)
+        torch.cuda.synchronize()
+        assert np.all(rel(out.cpu().numpy(), ref) <= fp64_tolerance(mom))
+        wo, mask, tries = oracle.event_weights(n, seed, 0, N, oracle.toy_pdf(), oracle.cuts(*cut), alpha=alpha, Q=Q)
+        r64, w64 = gpu_xsec(H, gpu, n, N, seed, H.sampler_toy_pdf(), H.HEGET_FP64, want_w=True)
+        r32, w32 = gpu_xsec(H, gpu, n, N, seed, H.sampler_toy_pdf(), H.HEGET_FP32, want_w=True)
+    finally:
+        H.heget_set_params(gpu)
+    np.testing.assert_array_equal(w64 != 0, mask != 0)
+    np.testing.assert_array_equal(w32 != 0, mask != 0)
+    assert 0 < mask.sum() < N and r64.n_pass == r32.n_pass == int(mask.sum())
+    nz = wo != 0
+    assert np.max(rel(w64[nz], wo[nz])) < 1e-11
+    assert np.max(rel(w32[nz], wo[nz])) < 1e-3
+
+
 @pytest.mark.parametrize("n,N", [(2, 4099), (3, 2051), (4, 1030), (5, 130)])
 def test_xsec_event_weights_match_oracle(oracle, heget_lib, gpu, n, N):
     H = heget_lib
