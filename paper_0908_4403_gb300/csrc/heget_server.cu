@@ -22,6 +22,7 @@
 #include <thread>
 #include <vector>
 
+#include "heget_arena.h"
 #include "heget_kernels.cuh"
 #include "heget_internal.h"
 
@@ -78,45 +79,6 @@ size_t xsec_smem_dispatch(int n, int tile) {
     }
 }
 
-// First-fit allocator over the device arena (offsets in bytes, 256-aligned).
-struct Arena {
-    size_t size = 0;
-    std::map<size_t, size_t> free_;      // offset -> length
-    void init(size_t n) {
-        size = n;
-        free_.clear();
-        free_[0] = n;
-    }
-    bool alloc(size_t n, size_t* off) {
-        n = (n + 255) & ~(size_t)255;
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second >= n) {
-                *off = it->first;
-                const size_t rest = it->second - n, at = it->first + n;
-                free_.erase(it);
-                if (rest) free_[at] = rest;
-                return true;
-            }
-        return false;
-    }
-    void release(size_t off, size_t n) {
-        n = (n + 255) & ~(size_t)255;
-        auto it = free_.emplace(off, n).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-};
-
 }  // namespace
 
 struct heget_server {
@@ -124,7 +86,7 @@ struct heget_server {
     heget_server_cfg cfg{};
     cudaStream_t stream = nullptr;
     unsigned char* arena_dev = nullptr;
-    Arena arena;
+    heget::Arena arena;
     heget_xsec_result* results_host = nullptr;   // pinned, one slot per admitted request
     std::vector<int> free_slots;
     Launch launches[2];
