@@ -339,13 +339,15 @@ int heget_get_helicity_sampling(const heget_ctx* ctx);
  * at most about u32 sqrt(sum_h w_h B_h^2 / sum_h w_h |A_h|^2), u32 = 2^-24.
  * Points whose bound exceeds tau are recomputed in FP64 by a second kernel
  * on the same stream (with the subset recursion, whatever the context's
- * algorithm: the same |M|^2 up to rounding, far cheaper at large n): heget_amp2 overwrites their |M|^2, the cross section
- * replaces their FP32 weights by the FP64 ones (in w_out too) and counts
- * them in n_escalated.  tau = 0 (the default) turns it off; 1e-4 is the
+ * algorithm: the same |M|^2 up to rounding, far cheaper at large n):
+ * heget_amp2 overwrites their |M|^2, the cross section replaces their FP32
+ * weights by the FP64 ones (in w_out too) and counts them in n_escalated.  tau = 0 (the default) turns it off; 1e-4 is the
  * threshold of the FP32 accuracy target (the bound is conservative: at
  * n = 8 it flags a few per cent of points whose actual FP32 error is far
  * below tau, and their FP64 recomputation is the cost).  Batches,
- * the server and heget_xsec_noalloc do not escalate (their n_escalated is 0).
+ * the server and heget_xsec_noalloc do not escalate (their n_escalated is 0),
+ * nor does a heget_amp2 call of more than 2^31 - 1 points (its row list is
+ * indexed in int32).
  * heget_amp2_escalated synchronizes `stream` and returns the number of rows
  * the last FP32 heget_amp2 on ctx recomputed. */
 int heget_set_escalation(heget_ctx* ctx, double tau);
