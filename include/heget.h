@@ -341,13 +341,13 @@ int heget_get_helicity_sampling(const heget_ctx* ctx);
  * on the same stream (with the subset recursion, whatever the context's
  * algorithm: the same |M|^2 up to rounding, far cheaper at large n):
  * heget_amp2 overwrites their |M|^2, the cross section replaces their FP32
- * weights by the FP64 ones (in w_out too) and counts them in n_escalated.  tau = 0 (the default) turns it off; 1e-4 is the
- * threshold of the FP32 accuracy target (the bound is conservative: at
- * n = 8 it flags a few per cent of points whose actual FP32 error is far
- * below tau, and their FP64 recomputation is the cost).  Batches,
- * the server and heget_xsec_noalloc do not escalate (their n_escalated is 0),
- * nor does a heget_amp2 call of more than 2^31 - 1 points (its row list is
- * indexed in int32).
+ * weights by the FP64 ones (in w_out too) and counts them in n_escalated.
+ * tau = 0 (the default) turns it off; 1e-4 is the threshold of the FP32
+ * accuracy target (the bound is conservative: at n = 8 it flags a few per
+ * cent of points whose actual FP32 error is far below tau, and their FP64
+ * recomputation is the cost).  Batches, the server and heget_xsec_noalloc do
+ * not escalate (their n_escalated is 0), nor does a heget_amp2 call of more
+ * than 2^31 - 1 points (its row list is indexed in int32).
  * heget_amp2_escalated synchronizes `stream` and returns the number of rows
  * the last FP32 heget_amp2 on ctx recomputed. */
 int heget_set_escalation(heget_ctx* ctx, double tau);
@@ -403,8 +403,9 @@ void heget_graph_destroy(heget_graph* g);
  * device.  Submitted requests wait in arrival order until fewer than
  * max_inflight are admitted and the device arena (arena_bytes, default
  * min(256 MiB, free HBM x (1 - hbm_reserve_frac))) has room for their tile
- * partials (64 bytes per tile of heget_xsec's tile size, plus the result).  Each launch of the mixed-n batch kernel takes tiles round-robin
- * from every admitted request until about max_launch_work FP32-flop
+ * partials (64 bytes per tile of heget_xsec's tile size, plus the result).
+ * Each launch of the mixed-n batch kernel takes tiles round-robin from every
+ * admitted request until about max_launch_work FP32-flop
  * equivalents are filled, so requests arriving while others run share the
  * next launch with them; up to two launches are in flight.  A request's
  * result is bitwise the heget_xsec_batch result of the same request, whatever
