@@ -35,8 +35,10 @@ POINTS = 1 << 20
 SEED = 0x0908440300000002
 METRIC = "u ubar -> n gamma |M|^2 phase-space points/s (n=4 workload; FP32 chain, FP64 phase space + accumulation)"
 WORKLOAD = ("u ubar -> 4 gamma, 1,048,576 points/step/GPU, toy-PDF sqrt(s-hat) = 14 TeV sqrt(x1 x2) > 100 GeV "
-            "with x ~ x^-1/2 (1-x)^3, cuts pT>20 GeV |eta|<2.5 dR>0.4, all 64 helicities, 24 orderings on the "
-            "prefix tree, FP32 chain + FP64 RAMBO/cuts/denominators + double-double sigma accumulation")
+            "with x ~ x^-1/2 (1-x)^3, cuts pT>20 GeV |eta|<2.5 dR>0.4, all 64 helicities")
+PATH = ("24 orderings on the prefix tree with the two-ended finish, FP32 chain + FP64 RAMBO/cuts/denominators "
+        "+ double-double sigma accumulation")
+PATH_ORACLE = "FP64 CPU oracle: each of the 24 orderings from scratch with 4x4 Dirac matrices, compensated sums"
 
 
 # Peaks derived from unit counts and the maximum SM clock (GB300: 152 SMs at
@@ -246,7 +248,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (Philox counter RNG from a seed)",
             "config": {"workload": WORKLOAD.replace("1,048,576", f"{per_step} (bounded CPU sample)"),
-                       "n": N_PHOTONS, "points_per_step": per_step},
+                       "n": N_PHOTONS, "points_per_step": per_step, "path": PATH_ORACLE},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": threads, "kind": "oracle",
                              "sample": f"{per_step} points per step of the n={N_PHOTONS} workload"},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -614,7 +616,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 chain + f64 phase space/accumulation",
             "data": "synthetic (on-device Philox4x32-10 counter RNG from a seed; toy PDF)",
             "config": {"workload": WORKLOAD if (n, N) == (N_PHOTONS, POINTS) else f"n={n}, {N} points/step, toy PDF",
-                       "n": n, "points_per_step": N * ws, "precision": "fp32",
+                       "n": n, "points_per_step": N * ws, "precision": "fp32", "path": PATH,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "compaction": "value counts every generated point; |M|^2 is evaluated for the points that "
                                      "pass the cuts (the others have weight 0), see pass_fraction",
