@@ -228,6 +228,46 @@ def test_xsec_n2_analytic(heget_lib, gpu):
     assert abs(r.n_pass / 65536 - c0) < 5 * math.sqrt(c0 * (1 - c0) / 65536)
 
 
+def _collinear_event(theta, rs=500.0):
+    """u ubar -> 3 gamma at sqrt(s) = rs with photon 1 (100 GeV) at angle
+    theta to the incoming u and photons 2, 3 sharing the rest back to back
+    in their own rest frame."""
+    e = rs / 2
+    k1 = 100.0 * np.array([1.0, math.sin(theta), 0.0, math.cos(theta)])
+    P = np.array([rs, 0.0, 0.0, 0.0]) - k1
+    m = math.sqrt(P[0] ** 2 - P[1:] @ P[1:])
+    beta = P[1:] / P[0]
+    g = 1 / math.sqrt(1 - beta @ beta)
+
+    def boost(p):
+        bp = beta @ p[1:]
+        return np.concatenate([[g * (p[0] + bp)], p[1:] + ((g - 1) * bp / (beta @ beta) + g * p[0]) * beta])
+
+    q = m / 2
+    return np.array([[e, 0, 0, e], [e, 0, 0, -e], k1,
+                     boost(np.array([q, 0, q, 0])), boost(np.array([q, 0, -q, 0]))])
+
+
+def test_nearly_collinear_photons(oracle, heget_lib, gpu):
+    """The method's collinear limit: a photon at 1e-2 .. 1e-4 rad from the
+    beam, where |M|^2 grows as 1/theta^2 and the propagator condition as
+    well.  FP64 within the rounding tolerance of the input; FP32 finite."""
+    torch = torch_mod()
+    H = heget_lib
+    mom = np.stack([_collinear_event(t) for t in (1e-2, 3e-3, 1e-3, 3e-4, 1e-4)])
+    ref = oracle.amp2(3, mom)
+    assert np.all(np.diff(ref) > 0)   # closer to the beam, larger |M|^2
+    m = dev(mom)
+    for prec in (H.HEGET_FP64, H.HEGET_FP32):
+        out = torch.empty(mom.shape[0], dtype=torch.float64, device="cuda")
+        H.heget_amp2(gpu, 3, mom.shape[0], m, out, precision=prec)
+        H.heget_check(gpu)
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        if prec == H.HEGET_FP64:
+            assert np.all(rel(got, ref) <= fp64_tolerance(mom))
+
+
 @pytest.mark.parametrize("n", [3, 5])
 def test_other_quark_charges_couplings_and_cuts(oracle, heget_lib, gpu, n):
     """Context parameters reach every step: d dbar -> n gamma (Q = -1/3, the
