@@ -228,12 +228,12 @@ def test_xsec_n2_analytic(heget_lib, gpu):
     assert abs(r.n_pass / 65536 - c0) < 5 * math.sqrt(c0 * (1 - c0) / 65536)
 
 
-def _collinear_event(theta, rs=500.0):
-    """u ubar -> 3 gamma at sqrt(s) = rs with photon 1 (100 GeV) at angle
+def _edge_event(theta, e1=100.0, rs=500.0):
+    """u ubar -> 3 gamma at sqrt(s) = rs with photon 1 (energy e1) at angle
     theta to the incoming u and photons 2, 3 sharing the rest back to back
     in their own rest frame."""
     e = rs / 2
-    k1 = 100.0 * np.array([1.0, math.sin(theta), 0.0, math.cos(theta)])
+    k1 = e1 * np.array([1.0, math.sin(theta), 0.0, math.cos(theta)])
     P = np.array([rs, 0.0, 0.0, 0.0]) - k1
     m = math.sqrt(P[0] ** 2 - P[1:] @ P[1:])
     beta = P[1:] / P[0]
@@ -248,15 +248,20 @@ def _collinear_event(theta, rs=500.0):
                      boost(np.array([q, 0, q, 0])), boost(np.array([q, 0, -q, 0]))])
 
 
-def test_nearly_collinear_photons(oracle, heget_lib, gpu):
-    """The method's collinear limit: a photon at 1e-2 .. 1e-4 rad from the
-    beam, where |M|^2 grows as 1/theta^2 and the propagator condition as
-    well.  FP64 within the rounding tolerance of the input; FP32 finite."""
+@pytest.mark.parametrize("kind", ["collinear", "soft"])
+def test_nearly_collinear_and_soft_photons(oracle, heget_lib, gpu, kind):
+    """The method's singular limits: a photon at 1e-2 .. 1e-4 rad from the
+    beam (|M|^2 grows as 1/theta^2), or of 1 .. 1e-3 GeV at 1 rad (as 1/E^2),
+    where the propagator condition grows as well.  FP64 within the rounding
+    tolerance of the input; FP32 finite."""
     torch = torch_mod()
     H = heget_lib
-    mom = np.stack([_collinear_event(t) for t in (1e-2, 3e-3, 1e-3, 3e-4, 1e-4)])
+    if kind == "collinear":
+        mom = np.stack([_edge_event(t) for t in (1e-2, 3e-3, 1e-3, 3e-4, 1e-4)])
+    else:
+        mom = np.stack([_edge_event(1.0, e1) for e1 in (1.0, 1e-1, 1e-2, 1e-3)])
     ref = oracle.amp2(3, mom)
-    assert np.all(np.diff(ref) > 0)   # closer to the beam, larger |M|^2
+    assert np.all(np.diff(ref) > 0)   # closer to the limit, larger |M|^2
     m = dev(mom)
     for prec in (H.HEGET_FP64, H.HEGET_FP32):
         out = torch.empty(mom.shape[0], dtype=torch.float64, device="cuda")
