@@ -109,6 +109,9 @@ def _f64(a):
 
 
 def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block (Salmon et al., SC'11): the counter-based
+    generator that stands in for the random numbers the paper's host program
+    draws and copies to the GPU (Sec. 3)."""
     lib = _load()
     c = np.asarray(ctr, dtype=np.uint32).copy()
     k = np.asarray(key, dtype=np.uint32).copy()
@@ -118,6 +121,9 @@ def philox4x32_10(ctr, key):
 
 
 def uniform_draw(seed: int, point: int, stream: int, draw: int) -> float:
+    """Uniform number `draw` of `stream` for phase-space point `point`:
+    Philox counter (point lo, point hi, draw/2, stream), key = seed, words
+    2(d&1), 2(d&1)+1 -> (m + 1/2) 2^-52 with the top 52 bits m."""
     return _load().oracle_uniform(seed, point, stream, draw)
 
 
@@ -131,7 +137,9 @@ def _mask_words(n, mask):
 
 
 def amp2(n: int, mom, hel_mask=None, alpha=ALPHA, Q=Q_U, threads: int | None = None):
-    """sum_{h in mask} |M_h|^2 for each point; mom shape (N, n+2, 4)."""
+    """sum_{h in mask} |M_h|^2 for each point (Sec. 2.1 eqs. (6)-(8), summed
+    over helicities as in eq. (2), couplings included, no colour, spin
+    average or 1/n!); mom shape (N, n+2, 4)."""
     lib = _load()
     m = _f64(mom).reshape(-1, n + 2, 4)
     out = np.zeros(m.shape[0])
@@ -142,7 +150,9 @@ def amp2(n: int, mom, hel_mask=None, alpha=ALPHA, Q=Q_U, threads: int | None = N
 
 
 def amp_hel(n: int, mom, h: int, ward: int = -1, alpha=ALPHA, Q=Q_U):
-    """Complex helicity amplitude M_h and sum over orderings of |A_pi|."""
+    """Complex helicity amplitude M_h (Sec. 2.1 eq. (6): the sum over the n!
+    orderings) and the sum over orderings of |A_pi|; ward >= 0 replaces that
+    photon's polarisation by k/k^0."""
     lib = _load()
     m = _f64(mom).reshape(n + 2, 4)
     re, im, sa = C.c_double(), C.c_double(), C.c_double()
@@ -151,15 +161,22 @@ def amp_hel(n: int, mom, h: int, ward: int = -1, alpha=ALPHA, Q=Q_U):
 
 
 def amp2_metric(n: int, mom, alpha=ALPHA, Q=Q_U) -> float:
+    """sum_h |M_h|^2 by a second route: each photon's polarisation sum
+    replaced by -g_mu,nu (valid for the gauge-invariant sum over orderings),
+    so no polarisation vectors enter."""
     lib = _load()
     return lib.oracle_amp2_metric(n, _ptr(_f64(mom).reshape(n + 2, 4)), alpha, Q)
 
 
 def phase_space_volume(n: int, s: float) -> float:
+    """Volume of flat massless n-body phase space in the normalisation of
+    Sec. 2.1 eq. (4)."""
     return _load().oracle_phase_space_volume(n, s)
 
 
 def rambo(n: int, sqrt_s: float, r):
+    """RAMBO (Kleiss, Stirling, Ellis 1986) for n massless momenta at sqrt_s
+    from 4n uniforms r: (momenta (n, 4), the constant weight of eq. (4))."""
     lib = _load()
     rr = _f64(r).reshape(4 * n)
     out = np.zeros((n, 4))
@@ -168,7 +185,9 @@ def rambo(n: int, sqrt_s: float, r):
 
 
 def phase_space(n: int, seed: int, i0: int, N: int, sampler: Sampler, cut: Cuts | None = None):
-    """Regenerate points i0..i0+N-1: dict of momenta (N, n+2, 4), weight, sqrt_s, y, mask, tries."""
+    """Regenerate points i0..i0+N-1 (the per-event phase-space step of
+    Sec. 3: sqrt(s-hat) sampler, RAMBO, the cuts of Sec. 2.2): dict of momenta
+    (N, n+2, 4), weight, sqrt_s, y, mask, tries."""
     lib = _load()
     mom = np.zeros((N, n + 2, 4))
     w, rs, y = np.zeros(N), np.zeros(N), np.zeros(N)
@@ -186,12 +205,14 @@ def pass_cuts(n: int, k, y: float, cut: Cuts) -> bool:
 
 
 def event_weight(n: int, s: float, amp2_value: float, phi_n: float, mask: int = 1) -> float:
+    """dsigma-hat weight of one event in fb (Sec. 2.1 eq. (2))."""
     return _load().oracle_event_weight(n, s, amp2_value, phi_n, mask)
 
 
 def event_weights(n: int, seed: int, i0: int, N: int, sampler: Sampler, cut: Cuts | None,
                   alpha=ALPHA, Q=Q_U, threads: int | None = None):
-    """Per-event dsigma-hat weights (fb) for points i0..i0+N-1, plus mask and tries."""
+    """Per-event dsigma-hat weights (fb, Sec. 2.1 eq. (2)) for points
+    i0..i0+N-1, plus mask and tries."""
     lib = _load()
     w = np.zeros(N)
     mask = np.zeros(N, dtype=np.uint8)
@@ -210,9 +231,10 @@ class HistSpec(C.Structure):
 
 
 def hist(n: int, mom, y, w, specs):
-    """Weighted histograms of events (momenta (N, n+2, 4), boost rapidities
-    y (N,), weights w (N,)): a list with one (nbins + 2, 2) array per spec
-    (rows: underflow, the bins, overflow; columns: sum w, sum w^2)."""
+    """Weighted histograms of the Sec. 5 / Fig. 2 observables of events
+    (momenta (N, n+2, 4), boost rapidities y (N,), weights w (N,)): a list
+    with one (nbins + 2, 2) array per spec (rows: underflow, the bins,
+    overflow; columns: sum w, sum w^2)."""
     lib = _load()
     mm = _f64(mom).reshape(-1)
     yy, ww = _f64(y), _f64(w)
@@ -229,7 +251,8 @@ def hist(n: int, mom, y, w, specs):
 
 
 def xsec_from_weights(w, tries=None, sampler_kind: int = 0):
-    """sigma and its standard error from per-event weights (N-1 in the variance).
+    """sigma and its standard error from per-event weights (the summation
+    step of Sec. 3.1; N-1 in the variance).
 
     Toy-PDF sampling (kind 2) multiplies by 2 P_acc (the q <-> qbar assignment
     of Sec. 2.1 eq. (1) and the sqrt(s-hat) floor acceptance from draw counts).
