@@ -112,18 +112,27 @@ typedef struct {
  * one context per stream).  The request server is the thread-safe way to
  * share a device between submitters. */
 int heget_create(int device, heget_ctx** out);
+/* Frees the context and its workspace (waits for the batch staging copy);
+ * NULL does nothing.  Work still queued on a stream must not use it. */
 void heget_destroy(heget_ctx* ctx);
-int heget_set_params(heget_ctx* ctx, const heget_params* p);   /* p: host */
+/* Physics parameters of later calls (p: host struct, copied).  EINVAL for a
+ * NULL argument, alpha not finite and > 0, q_charge not finite and nonzero,
+ * pt_min not finite and >= 0, eta_max not finite and > 0, or dr_min NaN. */
+int heget_set_params(heget_ctx* ctx, const heget_params* p);
 int heget_get_params(const heget_ctx* ctx, heget_params* p);   /* p: host */
+/* The message of the calling thread's last failed call (never NULL; owned by
+ * the library, valid until that thread's next call). */
 const char* heget_last_error(void);
+/* Library name, version and target architecture (static string). */
 const char* heget_version(void);
 
 /* Phase space (Sec. 2.1 eq. (4); Sec. 3: random numbers -> phase-space point
  * and Jacobian): for point i in [0, N), draw sqrt(s-hat) with a fixed value,
  * generate n massless photons with RAMBO (Kleiss, Stirling, Ellis 1986) in
  * the partonic CM frame with p1 = (rs/2)(1,0,0,1), p2 = (rs/2)(1,0,0,-1).
- * Random numbers: Philox4x32-10 keyed by `seed`, counter (i, draw, stream),
- * so point i depends only on (seed, i).
+ * Random numbers: Philox4x32-10 keyed by `seed`, counter (i lo, i hi,
+ * draw / 2, stream), two draws per block, so point i depends only on
+ * (seed, i).
  *   momenta: [N][n+2][4] FP64 (may be NULL); weights: [N] FP64 flat
  *   phase-space weight Phi_n(s-hat) in GeV^(2n-4) (may be NULL).
  * EINVAL: n not in [2, 8], N < 0, sqrt_s <= 0. */
@@ -134,7 +143,8 @@ int heget_phase_space(heget_ctx* ctx, uint64_t seed, int64_t N, int n,
 /* General form: points i0 .. i0+N-1, sampler `smp` (host struct), the cut
  * mask of Sec. 2.2 evaluated with eta_lab = eta_cm + y.  Any output may be
  * NULL.  sqrt_s_out, y_out: [N] FP64; mask_out: [N] uint8 (1 = passes);
- * tries_out: [N] int32 outer sampler attempts. */
+ * tries_out: [N] int32 outer sampler attempts.  EINVAL as for
+ * heget_phase_space, and for a bad sampler or point range. */
 int heget_phase_space_ex(heget_ctx* ctx, uint64_t seed, int64_t i0, int64_t N,
                          int n, const heget_sampler* smp, double* momenta,
                          double* weights, double* sqrt_s_out, double* y_out,
