@@ -302,7 +302,8 @@ int heget_hist(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t N,
  * heget_xsec_finalize enqueues the fixed-order combination of the partials of
  * the most recent heget_xsec_launch on this context into result_dev.  The
  * pair is equivalent to heget_xsec_async and exists so that callers can time
- * or graph-capture the halves separately. */
+ * or graph-capture the halves separately.  Errors as for heget_xsec_async;
+ * heget_xsec_finalize also refuses a NULL result_dev. */
 int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0,
                       int64_t N, const heget_sampler* smp, int precision,
                       double* w_out, void* stream);
@@ -381,7 +382,9 @@ int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind);
  * it (*best_tile, 0 = default) with its time (*best_ms).  Allocates and frees
  * temporary probe buffers; synchronizes.  heget_autotune_save /
  * heget_autotune_load store and restore the context's tuned tiles in a text
- * file keyed by GPU name (other GPUs' lines are kept). */
+ * file keyed by GPU name (other GPUs' lines are kept).  EINVAL for bad n,
+ * precision, kind, probe_points < 1 or a path that cannot be opened; ECUDA
+ * if no candidate ran (the context keeps its previous tile). */
 int heget_autotune(heget_ctx* ctx, int n, int precision, int kind,
                    int64_t probe_points, int* best_tile, double* best_ms);
 int heget_autotune_save(const heget_ctx* ctx, const char* path);
@@ -476,7 +479,9 @@ int heget_server_stop(heget_server* s);
 /* Device FMA throughput: runs independent FMA chains (8 per thread) in
  * every thread of a grid that fills the GPU and reports the achieved rate in
  * TFLOP/s (2 flops per FMA) in *tflops.  precision: HEGET_FP32 or HEGET_FP64.
- * The measured denominator of the FMA-pipe roofline.  Synchronizes. */
+ * The measured denominator of the FMA-pipe roofline.  Uses the legacy
+ * default stream and a temporary device buffer; synchronizes.  EINVAL for a
+ * NULL argument or a bad precision; ECUDA if a launch fails. */
 int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
 
 /* heget_xsec_async for callers that cannot allocate device memory.  The
@@ -513,7 +518,10 @@ int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, int64_t N,
 
 /* Compensated sums of x[0..N-1] (the accumulator of heget_xsec, exposed):
  * out_dev[0] = sum x, out_dev[1] = sum x^2, each rounded once from a
- * double-double accumulation in a fixed order.  out_dev: 2 doubles. */
+ * double-double accumulation in a fixed order (the same bits for any
+ * launch shape).  x: [N] device doubles; out_dev: 2 device doubles.  Uses
+ * the context workspace.  EINVAL for a NULL context or out_dev, N < 0, or
+ * x NULL with N > 0. */
 int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev,
               void* stream);
 
