@@ -518,8 +518,8 @@ int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, int64_t N,
 
 /* Compensated sums of x[0..N-1] (the accumulator of heget_xsec, exposed):
  * out_dev[0] = sum x, out_dev[1] = sum x^2, each rounded once from a
- * double-double accumulation in a fixed order (the same bits for any
- * launch shape).  x: [N] device doubles; out_dev: 2 device doubles.  Uses
+ * double-double accumulation in a fixed order (the same bits for the same
+ * x on a given GPU model).  x: [N] device doubles; out_dev: 2 device doubles.  Uses
  * the context workspace.  EINVAL for a NULL context or out_dev, N < 0, or
  * x NULL with N > 0. */
 int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev,
