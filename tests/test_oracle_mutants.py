@@ -1,6 +1,7 @@
 """The pins must catch plausible mistakes in the oracle.
 
-Each mutant below is a copy of ``oracle/heget_oracle.c`` with one small edit
+Each mutant below is a copy of ``oracle/heget_oracle.c`` (or of the Python
+wrappers in ``oracle/__init__.py``) with one small edit
 of the kind a careful reader could still make while restating the paper --
 a dropped term, a wrong sign, a transposed index, a missing conjugation, a
 wrong normalisation.  Every copy is built in a scratch directory and the
@@ -97,11 +98,34 @@ MUTANTS = [
 ]
 
 
-def _sandbox(base, name, src):
-    """A scratch tree with the pin tests and an oracle package built from `src`."""
-    d = os.path.join(base, name.replace(" ", "_").replace("/", "_").replace(":", "").replace("^", ""))
+# The same for the Python wrappers (``oracle/__init__.py``): the arithmetic
+# they hold (the toy-PDF cross-section scale of the summation step) and the
+# order of the arguments they marshal.
+PY_MUTANTS = [
+    ("toy-PDF sigma without the q <-> qbar factor 2", "scale = 2.0 * N / float(np.sum(tries))",
+     "scale = N / float(np.sum(tries))"),
+    ("toy-PDF acceptance inverted", "scale = 2.0 * N / float(np.sum(tries))",
+     "scale = 2.0 * float(np.sum(tries)) / N"),
+    ("toy-PDF scale applied to the wrong sampler", "if sampler_kind == 2:", "if sampler_kind == 1:"),
+    ("event weights: alpha and Q swapped", "alpha, Q, th, _ptr(w), _ptr(mask), _ptr(tries))",
+     "Q, alpha, th, _ptr(w), _ptr(mask), _ptr(tries))"),
+    ("amp2: alpha and Q swapped", "_ptr(mw), alpha, Q, th, _ptr(out))", "_ptr(mw), Q, alpha, th, _ptr(out))"),
+    ("phase space: sqrt(s-hat) and y outputs swapped", "_ptr(mom), _ptr(w), _ptr(rs), _ptr(y), _ptr(mask)",
+     "_ptr(mom), _ptr(w), _ptr(y), _ptr(rs), _ptr(mask)"),
+]
+
+
+def _sandbox(base, name, src, py_src=None):
+    """A scratch tree with the pin tests and an oracle package built from `src`
+    (and `py_src` as its wrappers, else the repository's)."""
+    d = os.path.join(base, name.replace(" ", "_").replace("/", "_").replace(":", "").replace("^", "")
+                     .replace("<->", "to").replace("(", "").replace(")", ""))
     os.makedirs(os.path.join(d, "oracle"))
-    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), os.path.join(d, "oracle"))
+    if py_src is None:
+        shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), os.path.join(d, "oracle"))
+    else:
+        with open(os.path.join(d, "oracle", "__init__.py"), "w") as f:
+            f.write(py_src)
     with open(os.path.join(d, "oracle", "heget_oracle.c"), "w") as f:
         f.write(src)
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
@@ -122,16 +146,20 @@ def _run(d):
 
 def test_pins_catch_every_mutant(tmp_path):
     src = open(os.path.join(ROOT, "oracle", "heget_oracle.c")).read()
+    py = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
     for name, find, repl in MUTANTS:
         assert src.count(find) == 1, f"mutant {name!r}: its text must occur exactly once"
-    cases = [("unmodified", src)] + [(name, src.replace(find, repl)) for name, find, repl in MUTANTS]
-    dirs = [_sandbox(str(tmp_path), name, s) for name, s in cases]
+    for name, find, repl in PY_MUTANTS:
+        assert py.count(find) == 1, f"mutant {name!r}: its text must occur exactly once"
+    cases = ([("unmodified", src, None)] + [(name, src.replace(find, repl), None) for name, find, repl in MUTANTS]
+             + [(name, src, py.replace(find, repl)) for name, find, repl in PY_MUTANTS])
+    dirs = [_sandbox(str(tmp_path), name, s, p) for name, s, p in cases]
     with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         results = list(ex.map(_run, dirs))
     rc0, out0 = results[0]
     assert rc0 == 0, f"the unmodified oracle fails its pins in the harness:\n{out0}"
     survived, broken = [], []
-    for (name, _), (rc, out) in zip(cases[1:], results[1:]):
+    for (name, _, _), (rc, out) in zip(cases[1:], results[1:]):
         if rc == 0:
             survived.append(name)
         elif rc != 1:   # 1 = tests failed; anything else is a harness or build problem

@@ -16,6 +16,7 @@ from helpers import (boost_matrix, helicity_index, mask_words, mdot,
 
 E2_DEFAULT = 4 * math.pi / 137.035999
 Q = 2.0 / 3.0
+GEV2_TO_FB = 0.3893793721e12   # (hbar c)^2 in GeV^2 fb
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -371,6 +372,65 @@ def test_n2_cut_acceptance_and_cross_section(oracle):
     assert exact == pytest.approx(137.71, abs=0.01)
     assert abs(sig - exact) < 5 * err
     assert err / sig < 0.01
+
+
+def _toy_pdf_sigma_n2(pt_min=20.0, eta_max=2.5, e_beam=7000.0, floor=100.0, alpha=1 / 137.035999):
+    """u ubar -> 2 gamma cross section under the toy PDF by quadrature.
+
+    x1, x2 each follow Beta(1/2, 4), sqrt(s-hat) = 2 e_beam sqrt(x1 x2) must
+    exceed `floor`, either beam may carry the quark (a factor 2, Sec. 2.1
+    eq. (1)), and the photons must pass the cuts of Sec. 2.2 in the lab
+    frame, boosted by y = ln(x1/x2)/2 from the partonic one.  At n = 2 the
+    partonic cross section is known in closed form: the photons are back to
+    back at cos(theta*) = +-c, so pT = (sqrt(s-hat)/2) sqrt(1 - c^2), the lab
+    pseudorapidities are +-atanh(c) + y, Delta R >= pi passes any cut below
+    pi, and
+        d sigma-hat / d c = pi alpha^2 Q^4 (1 + c^2) / (3 s-hat (1 - c^2)),
+    whose integral over |c| < c_max is pi alpha^2 Q^4 (4 atanh c_max - 2 c_max)
+    / (3 s-hat), with c_max = min(tanh(eta_max - |y|), sqrt(1 - 4 pT_min^2 /
+    s-hat)).  With u_i = sqrt(x_i) the Beta density becomes 2 (1 - u^2)^3 / B
+    (B = B(1/2, 4) = 32/35), and with tau = u1 u2, rho = ln(u1/u2) = y
+    (du1 du2 = dtau drho / 2) the integral runs over floor / (2 e_beam) <
+    tau < 1, |rho| < -ln tau."""
+    B = 32.0 / 35.0
+    E = 2 * e_beam
+
+    def partonic_over_shat(shat, rho):   # sigma-hat s-hat / (pi alpha^2 Q^4 / 3)
+        if abs(rho) >= eta_max:
+            return 0.0
+        c = min(math.tanh(eta_max - abs(rho)), math.sqrt(1 - 4 * pt_min**2 / shat))
+        return 4 * math.atanh(c) - 2 * c
+
+    def inner(s):   # tau = e^s
+        tau = math.exp(s)
+        shat = (tau * E) ** 2
+        rmax = min(-s, eta_max)
+        kink = eta_max - math.atanh(math.sqrt(1 - 4 * pt_min**2 / shat))
+
+        def g(rho):
+            u1s, u2s = tau * math.exp(rho), tau * math.exp(-rho)
+            return (1 - u1s) ** 3 * (1 - u2s) ** 3 * partonic_over_shat(shat, rho)
+
+        v, _ = integrate.quad(g, 0.0, rmax, points=[kink] if 0 < kink < rmax else None, limit=200,
+                              epsabs=0, epsrel=1e-11)
+        return 2 * v * tau / shat   # both signs of rho; dtau = tau ds
+
+    I, _ = integrate.quad(inner, math.log(floor / E), 0.0, limit=400, epsabs=0, epsrel=1e-10)
+    return 2 * (2 / B) ** 2 * 0.5 * I * math.pi * alpha**2 * Q**4 / 3 * GEV2_TO_FB
+
+
+def test_toy_pdf_cross_section_scale(oracle):
+    """The toy-PDF cross section sigma = 2 P_acc <w> (Sec. 2.1 eq. (1)-(2):
+    the q <-> qbar factor 2, the acceptance of the sqrt(s-hat) floor from the
+    draw counts, and the weights of eq. (2) with the cuts of Sec. 2.2) against
+    the same integral done by quadrature at n = 2, where the partonic cross
+    section is known in closed form."""
+    exact = _toy_pdf_sigma_n2()
+    assert exact == pytest.approx(193.766, rel=1e-5)
+    w, mask, tries = oracle.event_weights(2, 0x0908440300000321, 0, 400_000, oracle.toy_pdf(), oracle.cuts())
+    sig, err = oracle.xsec_from_weights(w, tries, 2)
+    assert err / sig < 0.01
+    assert abs(sig - exact) < 5 * err
 
 
 def test_identical_photon_factor_by_soft_emission(oracle):
