@@ -22,12 +22,12 @@
 // n = 4 the walk also shares the suffix of the last two photons (the
 // two-ended finish below), which removes the level of n! steps.
 //
-// Lanes: one lane per photon-helicity configuration h in [0, 2^n) with
-// s1 = +; every lane of a point walks the same tree (uniform control flow),
-// reading the same table entries up to the lambda_j bit (broadcast loads).
-// The s1 = - configurations follow from parity, |M_{-h}|^2 = |M_h|^2
-// (checked against the oracle), folded into a per-lane weight
-// w_h = [mask(+,-,h)] + [mask(-,+,~h)].
+// Lanes: each lane carries one to four photon-helicity configurations h in
+// [0, 2^n) with s1 = + (TreeShape); the lanes of a warp walk the same
+// subtrees (uniform control flow), reading the same table entries up to the
+// lambda_j bit (broadcast loads).  The s1 = - configurations follow from
+// parity, |M_{-h}|^2 = |M_h|^2 (checked against the oracle), folded into a
+// per-configuration weight w_h = [mask(+,-,h)] + [mask(-,+,~h)].
 #pragma once
 
 #include "heget_ps.cuh"
@@ -87,27 +87,38 @@ template <class R> __device__ __forceinline__ R rsq(R x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 
+template <class R> __device__ __forceinline__ R fmad(R a, R b, R c);
+template <> __device__ __forceinline__ float fmad<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fmad<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Lane layout of the tree (a compile-time shape):
 //   * each lane carries H = 2^HB photon-helicity configurations ("rows"), which
 //     differ in the helicities of the top HB photons NB..N-1 (NB = N - HB); one
 //     lane's rows share every table load and all index arithmetic, so the
 //     per-step overhead is spread over H row updates;
-//   * a point's 2^NB lanes form a group; G groups per point split the n(n-1)
-//     depth-2 prefixes between them (a group must fill whole warps, so that a
-//     warp walks one subtree and its table reads stay broadcasts) and add their
-//     partial amplitudes before squaring;
-//   * P = BLOCK / (2^NB G) points share one round of tables.
-// (HB, G) = (0, 1) is one helicity configuration per lane, one group.
+//   * the 2^NB lanes of one point are contiguous ("point lanes"); a group holds
+//     the point lanes of all P points of a round, and G groups split the
+//     ordered prefixes of depth D0 between them (prefix k goes to group k % G)
+//     and add their partial amplitudes before squaring.  A group fills whole
+//     warps, so that every warp walks one sequence of subtrees with
+//     warp-uniform control flow and its table reads are broadcasts per point;
+//   * thread t: group g = t / (P 2^NB), point slot (t / 2^NB) % P, helicity
+//     bits hl = t % 2^NB.
+// The walk below depth D0 keeps one row set per level in registers; D0 = 3 at
+// n = 8 with four rows per lane (the top of the stack is recomputed per
+// prefix instead of held, two extra steps per 85), else 2.
 template <int N, int BLOCK, int HB, int G>
 struct TreeShape {
     static constexpr int H = 1 << HB;
     static constexpr int NB = N - HB;
-    static constexpr int NSL = 1 << NB;      // lanes of a group
-    static constexpr int LPP = NSL * G;      // lanes of a point
-    static constexpr int P = BLOCK / LPP;    // points per round
-    static_assert(HB >= 0 && HB <= 2 && HB < N, "1, 2 or 4 rows per lane");
-    static_assert(P >= 1 && BLOCK % LPP == 0, "a round holds whole points");
-    static_assert(G == 1 || (NSL >= 32 && N >= 3), "subtree groups fill whole warps");
+    static constexpr int NSL = 1 << NB;      // lanes of one point
+    static constexpr int GL = BLOCK / G;     // lanes of a group
+    static constexpr int P = GL / NSL;       // points per round
+    static constexpr int D0 = (N == 8 && HB >= 2) ? 3 : N >= 3 ? 2 : 1;
+    static constexpr int NPRE = D0 == 3 ? N * (N - 1) * (N - 2) : D0 == 2 ? N * (N - 1) : N;
+    static_assert(HB >= 0 && HB <= 2 && (HB == 0 || NB >= 2), "1, 2 or 4 rows per lane");
+    static_assert(BLOCK % G == 0 && GL % NSL == 0 && P >= 1, "a round holds whole points");
+    static_assert(G == 1 || GL % 32 == 0, "subtree groups fill whole warps");
 };
 
 // Two-ended finish of the tree (sub-current reuse from the u side): with two
@@ -135,9 +146,10 @@ __host__ __device__ __forceinline__ int pair_slot(int a, int b) {
     return a * (N - 1) + b - (b > a);
 }
 
-// Shared-memory tables of one round.
-// Entry layout [index][point][lambda] so that the lanes of a warp, which read
-// one index for one or a few points and both lambdas, hit distinct banks.
+// Shared-memory tables of one round.  Every lane of a point reads one index
+// for its point and one or two lambdas, so entries are laid out
+// [index][point][lambda] (plus the two rows of a step matrix next to each
+// other): the lanes of a warp hit a few consecutive 16-byte rows.
 template <class R, int N, int BLOCK, int HB = 0, int G = 1>
 struct RoundTables {
     using S = TreeShape<N, BLOCK, HB, G>;
@@ -147,28 +159,26 @@ struct RoundTables {
     // most n - 2 photons (the pair index lists them first)
     static constexpr int KW = tree_two_ended<R, N>() ? K - N * (N - 1) : K;
     static constexpr int NS = 1 << N;
-    static constexpr size_t m_elems = (size_t)KW * P * 2;
-    static constexpr size_t c_elems = (size_t)N * P * 2;
+    static constexpr size_t m_elems = (size_t)KW * P * 4;   // [idx][p][lambda][row 0, row 1]
+    static constexpr size_t c_elems = (size_t)N * P * 2;    // [j][p][lambda]
     static constexpr size_t x_elems = G > 1 ? (size_t)BLOCK * S::H * 2 : 0;
     static constexpr size_t p_elems = tree_two_ended<R, N>() ? (size_t)N * (N - 1) * P * 4 : 0;
-    static constexpr size_t bytes = (2 * m_elems + 2 * c_elems + p_elems) * sizeof(Row<R>)   // M0, M1, CL, R1, PC
-                                  + (size_t)P * N * sizeof(Row<R>)                 // photon data
-                                  + (size_t)P * NS * sizeof(Row<R>)                // set data
-                                  + x_elems * sizeof(R)                            // group exchange
-                                  + (size_t)(BLOCK / 32) * sizeof(R) + 16;         // reduction
-    Row<R>* M0;
-    Row<R>* M1;
-    Row<R>* CL;
-    Row<R>* R1;
+    static constexpr size_t bytes = (m_elems + 2 * c_elems + p_elems) * sizeof(Row<R>)   // MT, CL, R1, PC
+                                  + (size_t)P * N * sizeof(Row<R>)                      // photon data
+                                  + (size_t)P * NS * sizeof(Row<R>)                     // set data
+                                  + x_elems * sizeof(R)                                 // group exchange
+                                  + (size_t)(BLOCK / 32) * sizeof(R) + 16;              // reduction
+    Row<R>* MT;   // step matrices M(j, T)^lambda
+    Row<R>* CL;   // closures (eps*_j . sigma) u_R
+    Row<R>* R1;   // first rows vbar(p2) . M(j, {j})
+    Row<R>* PC;   // [pair_slot(a, b)][P][lambda_a 2 + lambda_b]: pair columns (two-ended finish)
     Row<R>* PH;   // [P][N]: (sin th, cos th, cos ph, sin ph)
     Row<R>* SD;   // [P][2^N]: (A, D, Bre, Bim) = ((q0+q3), (q0-q3), q1, q2) / q^2
-    Row<R>* PC;   // [pair_slot(a, b)][P][lambda_a 2 + lambda_b]: pair columns (two-ended finish)
     R* XCH;       // [BLOCK][H][2]: partial amplitudes of the subtree groups
     R* RED;       // [BLOCK/32]
     __device__ __forceinline__ explicit RoundTables(unsigned char* base) {
-        M0 = reinterpret_cast<Row<R>*>(base);
-        M1 = M0 + m_elems;
-        CL = M1 + m_elems;
+        MT = reinterpret_cast<Row<R>*>(base);
+        CL = MT + m_elems;
         R1 = CL + c_elems;
         PC = R1 + c_elems;
         PH = PC + p_elems;
@@ -279,14 +289,21 @@ __device__ __forceinline__ StepMat<R> step_matrix(const Row<R>& ph, const Row<R>
     return o;
 }
 
-// acc[b] += r[b] . c, c = (ca, cb) a column 2-spinor
+// acc += r . c, c = (ca, cb) a column 2-spinor: a chain of fused
+// multiply-adds into the accumulator (8 per closure)
 template <class R>
 __device__ __forceinline__ void close_row(const Row<R>& r, const Row<R>& c, R& are, R& aim) {
-    are += r.ar * c.ar - r.ai * c.ai + r.br * c.br - r.bi * c.bi;
-    aim += r.ar * c.ai + r.ai * c.ar + r.br * c.bi + r.bi * c.br;
+    are = fmad<R>(r.ar, c.ar, are);
+    are = fmad<R>(-r.ai, c.ai, are);
+    are = fmad<R>(r.br, c.br, are);
+    are = fmad<R>(-r.bi, c.bi, are);
+    aim = fmad<R>(r.ar, c.ai, aim);
+    aim = fmad<R>(r.ai, c.ar, aim);
+    aim = fmad<R>(r.br, c.bi, aim);
+    aim = fmad<R>(r.bi, c.br, aim);
 }
 
-// Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Two phases
+// Fill the round tables for points recs[0 .. cnt-1] (cnt <= P).  Phases
 // separated by barriers; all threads of the block must call it.  Everything
 // here runs in R: the FP64 content (invariants) is already in the records.
 // ward >= 0 replaces the polarisation of that photon by k/k^0 in every step,
@@ -309,17 +326,15 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
         const uint16_t pr = c_tables.pair[pair_offset(N) + idx];
         const int T = pr & 0xFF, j = pr >> 8;
         const StepMat<R> sm = step_matrix<R>(tb.PH[p * N + j], tb.SD[p * NS + T], lam_bit, j == ward);
-        const Row<R>& m0 = sm.m0;
         const Row<R>& m1 = sm.m1;
-        const R e00 = sm.e00, e10r = sm.e10r, e10i = sm.e10i;
-        const size_t o = ((size_t)idx * P + p) * 2 + lam_bit;
-        st_row(tb.M0 + o, m0);
-        st_row(tb.M1 + o, m1);
+        const size_t o = (((size_t)idx * P + p) * 2 + lam_bit) * 2;
+        st_row(tb.MT + o, sm.m0);
+        st_row(tb.MT + o + 1, m1);
         if (T == (1 << j)) {
             const size_t oc = ((size_t)j * P + p) * 2 + lam_bit;
             const R n1 = recs[p].n1;
             const R n2 = recs[p].n2;
-            st_row(tb.CL + oc, Row<R>{n1 * e00, R(0), n1 * e10r, n1 * e10i});
+            st_row(tb.CL + oc, Row<R>{n1 * sm.e00, R(0), n1 * sm.e10r, n1 * sm.e10i});
             st_row(tb.R1 + oc, Row<R>{n2 * m1.ar, n2 * m1.ai, n2 * m1.br, n2 * m1.bi});
         }
     }
@@ -348,18 +363,24 @@ __device__ __forceinline__ void setup_round(const RoundTables<R, N, BLOCK, HB, G
     }
 }
 
-// Per-lane view of the round tables.
+// Per-lane view of the round tables: pointers already offset to the lane's
+// point slot; per table index the step matrices advance by 4P rows, the
+// closures and first rows by 2P per photon, the pair columns by 4P per pair.
 template <class R, int N, int BLOCK, int HB = 0, int G = 1>
 struct LaneTables {
-    using S = TreeShape<N, BLOCK, HB, G>;
-    const Row<R>* M0;
-    const Row<R>* M1;
-    const Row<R>* CL;
-    const Row<R>* R1;
-    int pp;       // 2 * point slot
+    const Row<R>* mt;
+    const Row<R>* cl;
+    const Row<R>* r1;
+    const Row<R>* pc;
     unsigned hl;  // helicity bits of photons 0 .. NB-1 (lambda = bit set -> +1)
-    const Row<R>* PC;   // pair columns (two-ended finish), else NULL
 };
+
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ LaneTables<R, N, BLOCK, HB, G> lane_tables(const RoundTables<R, N, BLOCK, HB, G>& tb,
+                                                                      int slot, int hl) {
+    return LaneTables<R, N, BLOCK, HB, G>{tb.MT + 4 * slot, tb.CL + 2 * slot, tb.R1 + 2 * slot, tb.PC + 4 * slot,
+                                          (unsigned)hl};
+}
 
 // Rows r[b] . M, photon j below NB: every row of the lane has the same lambda.
 template <class R, int H>
@@ -382,13 +403,12 @@ __device__ __forceinline__ void attach(const LaneTables<R, N, BLOCK, HB, G>& L, 
                                        const Row<R> (&r)[1 << HB], Row<R> (&o)[1 << HB]) {
     using S = TreeShape<N, BLOCK, HB, G>;
     constexpr int H = S::H, NB = S::NB, P = S::P;
-    const int base = idx * P * 2 + L.pp;
+    const Row<R>* e = L.mt + idx * (4 * P);
     if (HB == 0 || j < NB) {
-        const int e = base + ((L.hl >> j) & 1);
-        step_same<R, H>(o, r, ld_row(L.M0 + e), ld_row(L.M1 + e));
+        e += ((L.hl >> j) & 1) * 2;
+        step_same<R, H>(o, r, ld_row(e), ld_row(e + 1));
     } else {
-        const Row<R> a0 = ld_row(L.M0 + base), a1 = ld_row(L.M1 + base);
-        const Row<R> b0 = ld_row(L.M0 + base + 1), b1 = ld_row(L.M1 + base + 1);
+        const Row<R> a0 = ld_row(e), a1 = ld_row(e + 1), b0 = ld_row(e + 2), b1 = ld_row(e + 3);
         if constexpr (HB == 1) {
             step_split<R, H, 0>(o, r, a0, a1, b0, b1);
         } else if constexpr (HB == 2) {
@@ -404,13 +424,13 @@ __device__ __forceinline__ void close_rows(const LaneTables<R, N, BLOCK, HB, G>&
                                            R (&are)[1 << HB], R (&aim)[1 << HB]) {
     using S = TreeShape<N, BLOCK, HB, G>;
     constexpr int H = S::H, NB = S::NB, P = S::P;
-    const int base = j * P * 2 + L.pp;
+    const Row<R>* c = L.cl + j * (2 * P);
     if (HB == 0 || j < NB) {
-        const Row<R> c = ld_row(L.CL + base + ((L.hl >> j) & 1));
+        const Row<R> c0 = ld_row(c + ((L.hl >> j) & 1));
 #pragma unroll
-        for (int b = 0; b < H; ++b) close_row(r[b], c, are[b], aim[b]);
+        for (int b = 0; b < H; ++b) close_row(r[b], c0, are[b], aim[b]);
     } else {
-        const Row<R> c0 = ld_row(L.CL + base), c1 = ld_row(L.CL + base + 1);
+        const Row<R> c0 = ld_row(c), c1 = ld_row(c + 1);
         if (HB == 1 || j == NB) {
 #pragma unroll
             for (int b = 0; b < H; ++b) close_row(r[b], (b & 1) ? c1 : c0, are[b], aim[b]);
@@ -421,21 +441,62 @@ __device__ __forceinline__ void close_rows(const LaneTables<R, N, BLOCK, HB, G>&
     }
 }
 
+// Pair closures of the rows when photon b (a < b) is the top photon NB + KB
+// and a is below NB: row takes lambda_b = bit KB of its index.
+template <class R, int H, int KB>
+__device__ __forceinline__ void close_pair_split(const Row<R> (&r)[H], const Row<R>& ab0, const Row<R>& ab1,
+                                                 const Row<R>& ba0, const Row<R>& ba1, R (&are)[H], R (&aim)[H]) {
+#pragma unroll
+    for (int row = 0; row < H; ++row) {
+        const bool lb = (row >> KB) & 1;
+        close_row(r[row], lb ? ab1 : ab0, are[row], aim[row]);
+        close_row(r[row], lb ? ba1 : ba0, are[row], aim[row]);
+    }
+}
+
 // The two orderings left below a node of depth n - 2 by the pair columns:
-// acc += r . PC(a -> b) + r . PC(b -> a), each row with its own lambdas.
+// acc += r . PC(a -> b) + r . PC(b -> a), a < b, each row with its own
+// lambdas.  Which of a, b are top photons is warp-uniform; each case loads
+// only the entries its rows use.
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void close_pair(const LaneTables<R, N, BLOCK, HB, G>& L, int a, int b,
                                            const Row<R> (&r)[1 << HB], R (&are)[1 << HB], R (&aim)[1 << HB]) {
     using S = TreeShape<N, BLOCK, HB, G>;
     constexpr int H = S::H, NB = S::NB, P = S::P;
-    const Row<R>* ab = L.PC + ((size_t)pair_slot<N>(a, b) * P) * 4 + 2 * L.pp;
-    const Row<R>* ba = L.PC + ((size_t)pair_slot<N>(b, a) * P) * 4 + 2 * L.pp;
+    const Row<R>* ab = L.pc + pair_slot<N>(a, b) * (4 * P);
+    const Row<R>* ba = L.pc + pair_slot<N>(b, a) * (4 * P);
+    if (HB == 0 || b < NB) {
+        const int la = (L.hl >> a) & 1, lb = (L.hl >> b) & 1;
+        const Row<R> c1 = ld_row(ab + la * 2 + lb), c2 = ld_row(ba + lb * 2 + la);
 #pragma unroll
-    for (int row = 0; row < H; ++row) {
-        const int la = a < NB ? (int)((L.hl >> a) & 1) : (row >> (a - NB)) & 1;
-        const int lb = b < NB ? (int)((L.hl >> b) & 1) : (row >> (b - NB)) & 1;
-        close_row(r[row], ld_row(ab + la * 2 + lb), are[row], aim[row]);
-        close_row(r[row], ld_row(ba + lb * 2 + la), are[row], aim[row]);
+        for (int row = 0; row < H; ++row) {
+            close_row(r[row], c1, are[row], aim[row]);
+            close_row(r[row], c2, are[row], aim[row]);
+        }
+    } else if (a < NB) {
+        const int la = (L.hl >> a) & 1;
+        const Row<R> ab0 = ld_row(ab + la * 2), ab1 = ld_row(ab + la * 2 + 1);
+        const Row<R> ba0 = ld_row(ba + la), ba1 = ld_row(ba + 2 + la);
+        if constexpr (HB == 1) {
+            close_pair_split<R, H, 0>(r, ab0, ab1, ba0, ba1, are, aim);
+        } else if constexpr (HB == 2) {
+            if (b == NB) close_pair_split<R, H, 0>(r, ab0, ab1, ba0, ba1, are, aim);
+            else close_pair_split<R, H, 1>(r, ab0, ab1, ba0, ba1, are, aim);
+        }
+    } else if constexpr (HB == 2) {
+        // a = NB, b = NB + 1: lambda_a = row bit 0, lambda_b = row bit 1
+        Row<R> cab[4], cba[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            cab[e] = ld_row(ab + e);
+            cba[e] = ld_row(ba + e);
+        }
+#pragma unroll
+        for (int row = 0; row < H; ++row) {
+            const int la = row & 1, lb = row >> 1;
+            close_row(r[row], cab[la * 2 + lb], are[row], aim[row]);
+            close_row(r[row], cba[lb * 2 + la], are[row], aim[row]);
+        }
     }
 }
 
@@ -444,13 +505,13 @@ template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void first_rows(const LaneTables<R, N, BLOCK, HB, G>& L, int j, Row<R> (&r)[1 << HB]) {
     using S = TreeShape<N, BLOCK, HB, G>;
     constexpr int H = S::H, NB = S::NB, P = S::P;
-    const int base = j * P * 2 + L.pp;
+    const Row<R>* e = L.r1 + j * (2 * P);
     if (HB == 0 || j < NB) {
-        const Row<R> a = ld_row(L.R1 + base + ((L.hl >> j) & 1));
+        const Row<R> a = ld_row(e + ((L.hl >> j) & 1));
 #pragma unroll
         for (int b = 0; b < H; ++b) r[b] = a;
     } else {
-        const Row<R> a0 = ld_row(L.R1 + base), a1 = ld_row(L.R1 + base + 1);
+        const Row<R> a0 = ld_row(e), a1 = ld_row(e + 1);
         if (HB == 1 || j == NB) {
 #pragma unroll
             for (int b = 0; b < H; ++b) r[b] = (b & 1) ? a1 : a0;
@@ -461,35 +522,94 @@ __device__ __forceinline__ void first_rows(const LaneTables<R, N, BLOCK, HB, G>&
     }
 }
 
-// Levels at the bottom of the tree written out without loops: 0, 1 (the
-// last two photons as two chains) or 2 (also the loop over the last three),
-// per precision and photon count.  FP32 values from a GB300 sweep (n = 5
-// +26 %, n = 7 +19 %, n = 8 +23 % over none; n = 4, 6 best without); they
-// can be overridden with -DHEGET_F32_UNROLL_<n>=..
-#ifndef HEGET_F32_UNROLL_4
-#define HEGET_F32_UNROLL_4 0
-#endif
-#ifndef HEGET_F32_UNROLL_5
-#define HEGET_F32_UNROLL_5 2
-#endif
-#ifndef HEGET_F32_UNROLL_6
-#define HEGET_F32_UNROLL_6 0
-#endif
-#ifndef HEGET_F32_UNROLL_7
-#define HEGET_F32_UNROLL_7 1
-#endif
-#ifndef HEGET_F32_UNROLL_8
-#define HEGET_F32_UNROLL_8 1
-#endif
-template <class R, int N>
-__host__ __device__ constexpr int tree_unroll() {
-    if (sizeof(R) != sizeof(float)) return 0;
-    return N == 4 ? HEGET_F32_UNROLL_4 : N == 5 ? HEGET_F32_UNROLL_5 : N == 6 ? HEGET_F32_UNROLL_6
-         : N == 7 ? HEGET_F32_UNROLL_7 : N == 8 ? HEGET_F32_UNROLL_8 : 0;
+__device__ __forceinline__ int tree_child(int n, unsigned T, int j) {
+    return c_tables.child[child_offset(n) + T * n + j];
+}
+
+// The bottom three levels of the walk, written out from the per-set index
+// entry (Bottom3): below a node with rows r and three photons a < b < c
+// left, attach each of them and close the two orderings of the other two by
+// the pair columns.  KA, KB, KC: -1 for a photon below NB (its lambda is the
+// lane's bit), else the row bit that carries its lambda; fixed per case, so
+// every load and row selection is resolved at compile time.
+template <class R, int N, int BLOCK, int HB, int G, int K>
+__device__ __forceinline__ void bottom_step(const LaneTables<R, N, BLOCK, HB, G>& L, int st, int lam,
+                                            const Row<R> (&r)[1 << HB], Row<R> (&o)[1 << HB]) {
+    constexpr int P = TreeShape<N, BLOCK, HB, G>::P, H = 1 << HB;
+    const Row<R>* e = L.mt + st * (4 * P);
+    if constexpr (K < 0) {
+        e += lam * 2;
+        step_same<R, H>(o, r, ld_row(e), ld_row(e + 1));
+    } else {
+        step_split<R, H, K>(o, r, ld_row(e), ld_row(e + 1), ld_row(e + 2), ld_row(e + 3));
+    }
+}
+
+template <class R, int N, int BLOCK, int HB, int G, int K1, int K2>
+__device__ __forceinline__ void bottom_pair(const LaneTables<R, N, BLOCK, HB, G>& L, int s12, int s21, int l1, int l2,
+                                            const Row<R> (&r)[1 << HB], R (&are)[1 << HB], R (&aim)[1 << HB]) {
+    constexpr int P = TreeShape<N, BLOCK, HB, G>::P, H = 1 << HB;
+    // PC(y -> z)[ly][lz] and PC(z -> y)[lz][ly]
+    const Row<R>* ab = L.pc + s12 * (4 * P);
+    const Row<R>* ba = L.pc + s21 * (4 * P);
+    Row<R> c1[4], c2[4];   // entries by row-dependent lambdas (index 2 ly' + lz')
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int vy = v >> 1, vz = v & 1;
+        if ((K1 < 0 && vy) || (K2 < 0 && vz)) continue;   // only the entries the rows use
+        const int ly = K1 < 0 ? l1 : vy, lz = K2 < 0 ? l2 : vz;
+        c1[v] = ld_row(ab + ly * 2 + lz);
+        c2[v] = ld_row(ba + lz * 2 + ly);
+    }
+#pragma unroll
+    for (int row = 0; row < H; ++row) {
+        const int vy = K1 < 0 ? 0 : (row >> (K1 < 0 ? 0 : K1)) & 1;
+        const int vz = K2 < 0 ? 0 : (row >> (K2 < 0 ? 0 : K2)) & 1;
+        close_row(r[row], c1[vy * 2 + vz], are[row], aim[row]);
+        close_row(r[row], c2[vy * 2 + vz], are[row], aim[row]);
+    }
+}
+
+template <class R, int N, int BLOCK, int HB, int G, int KA, int KB, int KC>
+__device__ __forceinline__ void bottom3_case(const LaneTables<R, N, BLOCK, HB, G>& L, const Bottom3& e, int a, int b,
+                                             int c, const Row<R> (&r)[1 << HB], R (&are)[1 << HB],
+                                             R (&aim)[1 << HB]) {
+    constexpr int H = 1 << HB;
+    const int la = KA < 0 ? (int)((L.hl >> a) & 1) : 0;
+    const int lb = KB < 0 ? (int)((L.hl >> b) & 1) : 0;
+    const int lc = KC < 0 ? (int)((L.hl >> c) & 1) : 0;
+    Row<R> r2[H];
+    bottom_step<R, N, BLOCK, HB, G, KA>(L, e.st[0], la, r, r2);
+    bottom_pair<R, N, BLOCK, HB, G, KB, KC>(L, e.pc[0], e.pc[1], lb, lc, r2, are, aim);
+    bottom_step<R, N, BLOCK, HB, G, KB>(L, e.st[1], lb, r, r2);
+    bottom_pair<R, N, BLOCK, HB, G, KA, KC>(L, e.pc[2], e.pc[3], la, lc, r2, are, aim);
+    bottom_step<R, N, BLOCK, HB, G, KC>(L, e.st[2], lc, r, r2);
+    bottom_pair<R, N, BLOCK, HB, G, KA, KB>(L, e.pc[4], e.pc[5], la, lb, r2, are, aim);
+}
+
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ void bottom3(const LaneTables<R, N, BLOCK, HB, G>& L, const Row<R> (&r)[1 << HB],
+                                        unsigned T, R (&are)[1 << HB], R (&aim)[1 << HB]) {
+    constexpr int NB = N - HB;
+    constexpr unsigned FULL = (1u << N) - 1;
+    const unsigned rem = FULL & ~T, rem2 = rem & (rem - 1);
+    const int a = __ffs(rem) - 1, b = __ffs(rem2) - 1, c = __ffs(rem2 & (rem2 - 1)) - 1;
+    const Bottom3& e = c_bottom.e[bottom_offset(N) + T];
+    // the top photons are the highest: c is one before b is, a never is
+    if (HB == 0 || c < NB) {
+        bottom3_case<R, N, BLOCK, HB, G, -1, -1, -1>(L, e, a, b, c, r, are, aim);
+    } else if constexpr (HB == 1) {
+        bottom3_case<R, N, BLOCK, HB, G, -1, -1, 0>(L, e, a, b, c, r, are, aim);
+    } else if constexpr (HB == 2) {
+        if (b >= NB) bottom3_case<R, N, BLOCK, HB, G, -1, 0, 1>(L, e, a, b, c, r, are, aim);
+        else if (c == NB) bottom3_case<R, N, BLOCK, HB, G, -1, -1, 0>(L, e, a, b, c, r, are, aim);
+        else bottom3_case<R, N, BLOCK, HB, G, -1, -1, 1>(L, e, a, b, c, r, are, aim);
+    }
 }
 
 // Depth-first walk of the ordering tree below a node at depth D (D photons
-// attached, set T, current rows r), adding the closures to acc.
+// attached, set T, current rows r), adding the closures to acc.  The last
+// three levels are written out (bottom3); above them the loop stays rolled.
 template <class R, int N, int D, int BLOCK, int HB, int G>
 __device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK, HB, G>& L, const Row<R> (&r)[1 << HB],
                                         unsigned T, R (&are)[1 << HB], R (&aim)[1 << HB]) {
@@ -499,82 +619,76 @@ __device__ __forceinline__ void descend(const LaneTables<R, N, BLOCK, HB, G>& L,
     } else if constexpr (D == N - 2 && tree_two_ended<R, N>()) {
         const unsigned rem = FULL & ~T;
         close_pair<R, N, BLOCK, HB, G>(L, __ffs(rem) - 1, __ffs(rem & (rem - 1)) - 1, r, are, aim);
-    } else if constexpr (D == N - 2 && tree_unroll<R, N>() >= 1) {
-        // two photons a < b left: the orderings (a, b) and (b, a) as two
-        // independent chains, accumulated in the loop's order
-        const unsigned rem = FULL & ~T;
-        const int a = __ffs(rem) - 1, b = __ffs(rem & (rem - 1)) - 1;
-        Row<R> ra[1 << HB], rb[1 << HB];
-        attach<R, N, BLOCK, HB, G>(L, a, c_tables.child[child_offset(N) + T * N + a], r, ra);
-        attach<R, N, BLOCK, HB, G>(L, b, c_tables.child[child_offset(N) + T * N + b], r, rb);
-        close_rows<R, N, BLOCK, HB, G>(L, b, ra, are, aim);
-        close_rows<R, N, BLOCK, HB, G>(L, a, rb, are, aim);
-    } else if constexpr (D == N - 3 && tree_unroll<R, N>() >= 2) {
-        // three photons left: the loop over them unrolled
-        unsigned rem = FULL & ~T;
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            const int j = __ffs(rem) - 1;
-            rem &= rem - 1;
-            Row<R> r2[1 << HB];
-            attach<R, N, BLOCK, HB, G>(L, j, c_tables.child[child_offset(N) + T * N + j], r, r2);
-            descend<R, N, D + 1, BLOCK, HB, G>(L, r2, T | (1u << j), are, aim);
-        }
+    } else if constexpr (D == N - 3 && tree_two_ended<R, N>() && N >= 5) {
+        bottom3<R, N, BLOCK, HB, G>(L, r, T, are, aim);
     } else {
         unsigned rem = FULL & ~T;
 #pragma unroll 1
         while (rem) {
             const int j = __ffs(rem) - 1;
             rem &= rem - 1;
-            const int idx = c_tables.child[child_offset(N) + T * N + j];
             Row<R> r2[1 << HB];
-            attach<R, N, BLOCK, HB, G>(L, j, idx, r, r2);
+            attach<R, N, BLOCK, HB, G>(L, j, tree_child(N, T, j), r, r2);
             descend<R, N, D + 1, BLOCK, HB, G>(L, r2, T | (1u << j), are, aim);
         }
     }
 }
 
-// Subtrees below the depth-2 prefixes k = GI, GI + G, ... of the n(n-1)
-// prefixes (j1, j2) in lexicographic order.  GI is a template argument so
-// that every loop bound and table index below stays warp-uniform.
-template <class R, int N, int BLOCK, int HB, int G, int GI>
-__device__ __forceinline__ void tree_group(const LaneTables<R, N, BLOCK, HB, G>& L, R (&are)[1 << HB],
-                                           R (&aim)[1 << HB]) {
-    constexpr int H = 1 << HB;
-#pragma unroll 1
-    for (int k = GI; k < N * (N - 1); k += G) {
-        const int j1 = k / (N - 1), t = k - j1 * (N - 1), j2 = t + (t >= j1);
-        Row<R> r1[H], r2[H];
-        first_rows<R, N, BLOCK, HB, G>(L, j1, r1);
-        attach<R, N, BLOCK, HB, G>(L, j2, c_tables.child[child_offset(N) + (1u << j1) * N + j2], r1, r2);
-        descend<R, N, 2, BLOCK, HB, G>(L, r2, (1u << j1) | (1u << j2), are, aim);
+// Ordered prefix k (lexicographic) of depth D = 2 or 3: photons j1, j2 (, j3).
+template <int N, int D>
+__host__ __device__ __forceinline__ void tree_prefix(int k, int& j1, int& j2, int& j3) {
+    if constexpr (D == 2) {
+        j1 = k / (N - 1);
+        const int t = k - j1 * (N - 1);
+        j2 = t + (t >= j1);
+        j3 = -1;
+    } else {
+        constexpr int W2 = (N - 1) * (N - 2);
+        j1 = k / W2;
+        const int t = k - j1 * W2;
+        const int t2 = t / (N - 2), t3 = t - t2 * (N - 2);
+        j2 = t2 + (t2 >= j1);
+        // j3: the t3-th photon (in order) other than j1 and j2
+        const int lo = j1 < j2 ? j1 : j2, hi = j1 < j2 ? j2 : j1;
+        j3 = t3 + (t3 >= lo);
+        j3 += j3 >= hi;
     }
 }
 
-// The orderings of group g for one lane: with one group all n! orderings,
-// otherwise the group's share of the depth-2 subtrees (a group is a whole
-// number of warps, so the switch below never diverges inside a warp).  Sums,
-// per row, the helicity amplitude (up to normalisation) for s1 = +.
+// The orderings of group g for one lane: the subtrees below the ordered
+// prefixes k = g, g + G, ... of depth D0 (lexicographic), each prefix's rows
+// formed from the first rows by D0 - 1 steps.  Sums, per row, the helicity
+// amplitude (up to normalisation) for s1 = +.  g is the same for every lane of
+// a warp, so every loop bound and table index below is warp-uniform.
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void tree_amplitude(const LaneTables<R, N, BLOCK, HB, G>& L, int g, R (&are)[1 << HB],
                                                R (&aim)[1 << HB]) {
-    constexpr int H = 1 << HB;
+    using S = TreeShape<N, BLOCK, HB, G>;
+    constexpr int H = S::H;
 #pragma unroll
     for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
-    if constexpr (G == 1) {
 #pragma unroll 1
-        for (int j = 0; j < N; ++j) {
+    for (int k = g; k < S::NPRE; k += G) {
+        if constexpr (S::D0 == 1) {
             Row<R> r1[H];
-            first_rows<R, N, BLOCK, HB, G>(L, j, r1);
-            descend<R, N, 1, BLOCK, HB, G>(L, r1, 1u << j, are, aim);
-        }
-    } else {
-        static_assert(G == 2 || G == 4, "2 or 4 subtree groups");
-        switch (g) {
-            case 0: tree_group<R, N, BLOCK, HB, G, 0>(L, are, aim); break;
-            case 1: tree_group<R, N, BLOCK, HB, G, 1>(L, are, aim); break;
-            case 2: if constexpr (G > 2) tree_group<R, N, BLOCK, HB, G, 2>(L, are, aim); break;
-            default: if constexpr (G > 3) tree_group<R, N, BLOCK, HB, G, 3>(L, are, aim); break;
+            first_rows<R, N, BLOCK, HB, G>(L, k, r1);
+            descend<R, N, 1, BLOCK, HB, G>(L, r1, 1u << k, are, aim);
+        } else if constexpr (S::D0 == 2) {
+            int j1, j2, j3;
+            tree_prefix<N, 2>(k, j1, j2, j3);
+            Row<R> r1[H], r2[H];
+            first_rows<R, N, BLOCK, HB, G>(L, j1, r1);
+            attach<R, N, BLOCK, HB, G>(L, j2, tree_child(N, 1u << j1, j2), r1, r2);
+            descend<R, N, 2, BLOCK, HB, G>(L, r2, (1u << j1) | (1u << j2), are, aim);
+        } else {
+            int j1, j2, j3;
+            tree_prefix<N, 3>(k, j1, j2, j3);
+            Row<R> r1[H], r2[H], r3[H];
+            first_rows<R, N, BLOCK, HB, G>(L, j1, r1);
+            const unsigned T2 = (1u << j1) | (1u << j2);
+            attach<R, N, BLOCK, HB, G>(L, j2, tree_child(N, 1u << j1, j2), r1, r2);
+            attach<R, N, BLOCK, HB, G>(L, j3, tree_child(N, T2, j3), r2, r3);
+            descend<R, N, 3, BLOCK, HB, G>(L, r3, T2 | (1u << j3), are, aim);
         }
     }
 }
@@ -600,18 +714,20 @@ __device__ __forceinline__ float sel_weight(int hsel, unsigned lam, float w) {
     return hsel == -1 ? w : (int)lam == hsel ? (float)(1 << (N + 2)) : 0.0f;
 }
 
-// Lane coordinates in a round: point slot, subtree group, group-local lane.
+
+// Lane coordinates in a round: subtree group, point slot, helicity bits.
 template <int N, int BLOCK, int HB, int G>
 struct LaneId {
     using S = TreeShape<N, BLOCK, HB, G>;
-    int slot, g, hl;
+    int g, slot, hl;
     __device__ __forceinline__ explicit LaneId(int tid)
-        : slot(tid / S::LPP), g((tid % S::LPP) / S::NSL), hl(tid % S::NSL) {}
+        : g(tid / S::GL), slot((tid % S::GL) / S::NSL), hl(tid % S::NSL) {}
 };
 
 // The complete amplitudes of the lane's rows: with several subtree groups,
 // every group leaves its partial sums in shared memory and group 0 adds them
-// (the other groups' amplitudes become 0).  All threads must call it.
+// in group order (the other groups' amplitudes become 0).  All threads must
+// call it.
 template <class R, int N, int BLOCK, int BAR, int HB, int G>
 __device__ __forceinline__ void combine_groups(const RoundTables<R, N, BLOCK, HB, G>& tb, const LaneId<N, BLOCK, HB, G>& id,
                                                R (&are)[1 << HB], R (&aim)[1 << HB]) {
@@ -626,9 +742,9 @@ __device__ __forceinline__ void combine_groups(const RoundTables<R, N, BLOCK, HB
         }
         group_sync<BAR, BLOCK>();
         if (id.g == 0) {
-#pragma unroll
+#pragma unroll 1
             for (int gg = 1; gg < G; ++gg) {
-                const R* y = tb.XCH + (size_t)(threadIdx.x + gg * S::NSL) * H * 2;
+                const R* y = tb.XCH + (size_t)(threadIdx.x + gg * S::GL) * H * 2;
 #pragma unroll
                 for (int b = 0; b < H; ++b) {
                     are[b] += y[2 * b];
@@ -642,23 +758,24 @@ __device__ __forceinline__ void combine_groups(const RoundTables<R, N, BLOCK, HB
     }
 }
 
-// Sum (MAX = false) or maximum (MAX = true) of v over the lanes of each point;
-// the result is valid in the point's first lane.  All threads must call it.
+// Sum (MAX = false) or maximum (MAX = true) of v over the point lanes of
+// group 0 (the other groups hold zeros); the result is valid in the point's
+// first lane of group 0.  All threads must call it.
 template <class R, int N, int BLOCK, int BAR, int HB, int G, bool MAX>
 __device__ __forceinline__ R point_reduce(const RoundTables<R, N, BLOCK, HB, G>& tb, R v) {
     using S = TreeShape<N, BLOCK, HB, G>;
-    constexpr int W = S::LPP < 32 ? S::LPP : 32;
+    constexpr int W = S::NSL < 32 ? S::NSL : 32;
 #pragma unroll
     for (int off = 1; off < W; off <<= 1) {
         const R o = __shfl_xor_sync(0xffffffffu, v, off);
         v = MAX ? fmax(v, o) : v + o;
     }
-    if constexpr (S::LPP > 32) {
+    if constexpr (S::NSL > 32) {
         const int tid = threadIdx.x;
         if ((tid & 31) == 0) tb.RED[tid >> 5] = v;
         group_sync<BAR, BLOCK>();
-        if (tid % S::LPP == 0)
-            for (int w = 1; w < S::LPP / 32; ++w) {
+        if (tid < S::GL && tid % S::NSL == 0)
+            for (int w = 1; w < S::NSL / 32; ++w) {
                 const R o = tb.RED[(tid >> 5) + w];
                 v = MAX ? fmax(v, o) : v + o;
             }
@@ -679,7 +796,7 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, Poin
     constexpr int P = S::P, H = S::H;
     const RT tb(table_smem);
     const LaneId<N, BLOCK, HB, G> id(threadIdx.x);
-    const LaneTables<R, N, BLOCK, HB, G> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl, tb.PC};
+    const LaneTables<R, N, BLOCK, HB, G> L = lane_tables(tb, id.slot, id.hl);
     float wh[H];
 #pragma unroll
     for (int b = 0; b < H; ++b) wh[b] = lane_weight<N>(mask, (unsigned)id.hl | ((unsigned)b << S::NB));
@@ -709,7 +826,7 @@ __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, Poin
             }
         }
         v = point_reduce<R, N, BLOCK, BAR, HB, G, false>(tb, v);
-        if (threadIdx.x % S::LPP == 0 && id.slot < rc) recs[base + id.slot].ssum = v;
+        if (id.g == 0 && id.hl == 0 && id.slot < rc) recs[base + id.slot].ssum = v;
         group_sync<BAR, BLOCK>();
     }
 }
@@ -726,7 +843,7 @@ __device__ __forceinline__ void ward_rounds(unsigned char* table_smem, PointRec<
     constexpr int P = RT::P;
     const RT tb(table_smem);
     const LaneId<N, BLOCK, 0, 1> id(threadIdx.x);
-    const LaneTables<R, N, BLOCK> L{tb.M0, tb.M1, tb.CL, tb.R1, 2 * id.slot, (unsigned)id.hl, tb.PC};
+    const LaneTables<R, N, BLOCK> L = lane_tables(tb, id.slot, id.hl);
     for (int base = 0; base < cnt; base += P) {
         const int rc = min(P, cnt - base);
         R best[2];
@@ -738,7 +855,7 @@ __device__ __forceinline__ void ward_rounds(unsigned char* table_smem, PointRec<
             best[pass] = point_reduce<R, N, BLOCK, 0, 0, 1, true>(tb, are[0] * are[0] + aim[0] * aim[0]);
             __syncthreads();
         }
-        if (threadIdx.x % (1 << N) == 0 && id.slot < rc) {
+        if (id.hl == 0 && id.slot < rc) {
             const R a = best[0], w = best[1];
             recs[base + id.slot].ssum = a > R(0) ? sqrt(w / a) : (w > R(0) ? R(INFINITY) : R(0));
         }

@@ -71,6 +71,54 @@ __host__ __device__ constexpr TreeTables make_tree_tables() {
 // one copy per translation unit, built at compile time
 static __constant__ const TreeTables c_tables = make_tree_tables();
 
+// The last three levels of the walk below a node whose set T leaves three
+// photons a < b < c: the step indices of attaching a, b and c to T, and the
+// ordered pair slots a (n - 1) + b - [b > a] of the pairs left after each
+// attach, (b, c), (c, b), (a, c), (c, a), (a, b), (b, a).  Indexed by T for
+// n = 5..8 (entries of other sets unused); 32 bytes, so that a warp reads an
+// entry in two 16-byte constant loads.
+struct alignas(16) Bottom3 {
+    uint16_t st[3];
+    uint16_t pc[6];
+    uint16_t pad[7];
+};
+__host__ __device__ constexpr int bottom_offset(int n) {
+    int o = 0;
+    for (int m = 5; m < n; ++m) o += 1 << m;
+    return o;
+}
+constexpr int kBottomTotal = bottom_offset(kMaxN + 1);
+
+struct BottomTables {
+    Bottom3 e[kBottomTotal];
+};
+
+__host__ __device__ constexpr BottomTables make_bottom_tables() {
+    BottomTables b{};
+    const TreeTables t = make_tree_tables();
+    for (int n = 5; n <= kMaxN; ++n) {
+        const int co = child_offset(n);
+        for (int T = 0; T < (1 << n); ++T) {
+            int pop = 0;
+            for (int i = 0; i < n; ++i) pop += (T >> i) & 1;
+            if (pop != n - 3) continue;
+            int r[3] = {0, 0, 0}, k = 0;
+            for (int i = 0; i < n; ++i)
+                if (!((T >> i) & 1)) r[k++] = i;
+            Bottom3& e = b.e[bottom_offset(n) + T];
+            for (int x = 0; x < 3; ++x) e.st[x] = t.child[co + T * n + r[x]];
+            const int pairs[3][2] = {{r[1], r[2]}, {r[0], r[2]}, {r[0], r[1]}};
+            for (int x = 0; x < 3; ++x) {
+                const int y = pairs[x][0], z = pairs[x][1];
+                e.pc[2 * x] = (uint16_t)(y * (n - 1) + z - (z > y));
+                e.pc[2 * x + 1] = (uint16_t)(z * (n - 1) + y - (y > z));
+            }
+        }
+    }
+    return b;
+}
+static __constant__ const BottomTables c_bottom = make_bottom_tables();
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the
 // published round function: two 32x32->64 multiplies per round, Weyl key

@@ -13,47 +13,30 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 
 constexpr int kBatchThreads = 256;   // threads of the mixed-n batch kernel
 
-// Tree shape per precision and photon count: 2^HB helicity configurations
-// per lane and G subtree groups per point (see TreeShape).  FP64 keeps one
-// configuration per lane: its DFMA pipe, not instruction issue, is the limit.
-// The FP32 defaults are the fastest of a sweep on GB300 (n = 6, 7: two rows
-// per lane and two subtree groups, +10-18 % over one configuration per lane;
-// n = 5: one configuration per lane, since 16-lane groups share warps).
-// The FP32 shapes can be overridden at build time
-// (-DHEGET_F32_HB_<n>=.. -DHEGET_F32_G_<n>=..).
-#ifndef HEGET_F32_HB_5
-#define HEGET_F32_HB_5 0
-#endif
-#ifndef HEGET_F32_G_5
-#define HEGET_F32_G_5 1
-#endif
-#ifndef HEGET_F32_HB_6
-#define HEGET_F32_HB_6 1
-#endif
-#ifndef HEGET_F32_G_6
-#define HEGET_F32_G_6 2
-#endif
-#ifndef HEGET_F32_HB_7
-#define HEGET_F32_HB_7 1
-#endif
-#ifndef HEGET_F32_G_7
-#define HEGET_F32_G_7 2
-#endif
-#ifndef HEGET_F32_HB_8
-#define HEGET_F32_HB_8 1
-#endif
-#ifndef HEGET_F32_G_8
-#define HEGET_F32_G_8 2
-#endif
+// Tree shape per precision, photon count and threads of the rounds: 2^HB
+// helicity configurations per lane and G subtree groups (see TreeShape).
+// FP64 keeps one configuration per lane: its DFMA pipe, not instruction
+// issue, is the limit.  FP32 from n = 5 carries four configurations per lane,
+// which spreads each step's table loads and index work over four row updates,
+// and as many groups as make a group one warp-aligned set of point lanes
+// (8, 16, 32, 64 lanes per point at n = 5, 6, 7, 8) with the prefixes shared
+// out evenly where the block allows it (n(n-1) = 20, 30, 42 depth-2 prefixes
+// at n = 5, 6, 7; 336 depth-3 prefixes at n = 8).
 template <int HB_, int G_>
 struct ShapeOf {
     static constexpr int HB = HB_, G = G_;
 };
-template <class R, int N> struct DefaultShape : ShapeOf<0, 1> {};
-template <> struct DefaultShape<float, 5> : ShapeOf<HEGET_F32_HB_5, HEGET_F32_G_5> {};
-template <> struct DefaultShape<float, 6> : ShapeOf<HEGET_F32_HB_6, HEGET_F32_G_6> {};
-template <> struct DefaultShape<float, 7> : ShapeOf<HEGET_F32_HB_7, HEGET_F32_G_7> {};
-template <> struct DefaultShape<float, 8> : ShapeOf<HEGET_F32_HB_8, HEGET_F32_G_8> {};
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr int tree_hb() {
+    return sizeof(R) == sizeof(float) && N >= 5 ? 2 : 0;
+}
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr int tree_groups() {
+    // lanes of one point: 2^(N - 2); a group needs whole warps
+    return tree_hb<R, N, BLOCK>() == 0 ? 1 : N == 6 ? BLOCK / 32 : (N == 7 && BLOCK % 224 == 0) ? BLOCK / 32 : BLOCK / 64;
+}
+template <class R, int N, int BLOCK>
+struct DefaultShape : ShapeOf<tree_hb<R, N, BLOCK>(), tree_groups<R, N, BLOCK>()> {};
 
 // Shared-memory table layouts: the tree's (kAlgTree), the subset
 // recursion's without (kAlgSubset) or with (kTabSubsetKappa) the arrays of
@@ -61,12 +44,18 @@ template <> struct DefaultShape<float, 8> : ShapeOf<HEGET_F32_HB_8, HEGET_F32_G_
 constexpr int kTabSubsetKappa = 2;
 
 // Round-table bytes of layout TAB: the tree's default shape (at least those
-// of one configuration per lane, which the gauge check uses), the subset
+// of one configuration per lane, which the gauge check uses, where the block
+// holds whole points of that shape), the subset
 // recursion's, or the larger of the two.
+template <class R, int N, int BLOCK>
+__host__ __device__ constexpr size_t ward_table_bytes() {
+    if constexpr (BLOCK % (1 << N) == 0) return RoundTables<R, N, BLOCK>::bytes;
+    else return 0;
+}
 template <class R, int N, int BLOCK, int TAB = kAlgAny>
 __host__ __device__ constexpr size_t table_bytes() {
-    using SH = DefaultShape<R, N>;
-    constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = RoundTables<R, N, BLOCK>::bytes;
+    using SH = DefaultShape<R, N, BLOCK>;
+    constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = ward_table_bytes<R, N, BLOCK>();
     constexpr size_t c = SubsetTables<R, N, BLOCK>::bytes_core, ck = SubsetTables<R, N, BLOCK>::bytes;
     constexpr size_t ab = a > b ? a : b;
     return align16(TAB == kAlgTree ? ab : TAB == kAlgSubset ? c : TAB == kTabSubsetKappa ? ck : (ab > ck ? ab : ck));
@@ -91,7 +80,7 @@ __device__ __forceinline__ void amp_rounds(unsigned char* smem, PointRec<R, N>* 
     if constexpr (ALG == kAlgSubset) {
         amplitude_rounds_subset<R, N, BLOCK, BAR>(smem, recs, cnt, mask, kappa);
     } else if constexpr (ALG == kAlgTree) {
-        using SH = DefaultShape<R, N>;
+        using SH = DefaultShape<R, N, BLOCK>;
         amplitude_rounds<R, N, BLOCK, BAR, SH::HB, SH::G>(smem, recs, cnt, mask);
         if (kappa) kappa_rounds<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
     } else if (alg == kAlgSubset) {
@@ -166,7 +155,7 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
 #pragma unroll
         for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
     rec.hsel = -1;
-    fill_denominators<R, N, true>(v, E2, is, false, rec);
+    if constexpr (N <= 5) fill_denominators<R, N, true>(v, E2, is, false, rec);   // n >= 6: denominators_parallel
     rec.e2 = R(E2 * irs);
     rec.n1 = R(sqrt(2.0 * E1 * irs));
     rec.n2 = R(sqrt(2.0 * E2 * irs));
@@ -178,6 +167,37 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
     rec.mask = 1;
     rec.tries = 1;
     if (!ok) atomicOr(flag, 1);
+}
+
+// Denominators of the records recs[0 .. cnt-1] at n >= 6: one (record, set)
+// item per thread of the calling threads (local id lid of nthr), so that the
+// FP64 pipe runs whole warps.  view(c, E2, is) gives record c's photon
+// momenta, the energy of p2 and the scale 1/s-hat (SCALE: momenta in GeV).
+// Nothing at n <= 5 (the records hold their denominators already).
+template <class R, int N, bool SCALE, class View>
+__device__ __forceinline__ void denominators_parallel(PointRec<R, N>* recs, int cnt, int lid, int nthr,
+                                                      const View& view) {
+    if constexpr (N >= 6) {
+        constexpr int NSET = (1 << N) - 2;
+        for (int it = lid; it < cnt * NSET; it += nthr) {
+            const int c = it / NSET;
+            const unsigned T = 1u + (unsigned)(it - c * NSET);
+            double E2, is;
+            const MomView v = view(c, E2, is);
+            recs[c].t[T] = set_denominator<R, N, SCALE>(v, E2, is, T);
+        }
+    }
+}
+
+// Staged input row c (stride srow) as a view for denominators_parallel: the
+// photons, the energy of p2 and 1/s-hat as input_to_rec forms them (a row it
+// refuses is never evaluated).
+__device__ __forceinline__ MomView row_view(double* stage, int srow, int c, double& E2, double& is) {
+    double* row = stage + (size_t)c * srow;
+    E2 = row[4];
+    const double s = 2.0 * (row[0] * row[4] - row[3] * row[7]);
+    is = s > 0 ? 1.0 / s : 1.0;
+    return MomView{row + 8, 1, 4};
 }
 
 template <class R, int N, int BLOCK, bool ESC, int ALG>
@@ -201,6 +221,11 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
         }
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
+        if constexpr (N >= 6) {
+            denominators_parallel<R, N, true>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
+                return row_view(stage, SROW, c, E2, is);
+            });
+        }
         __syncthreads();
         amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, cnt, mask, ph.alg, esc);
         const float thr = esc ? esc_threshold(ph.esc_tau) : 0.0f;
@@ -233,6 +258,11 @@ ward_kernel(const double* __restrict__ mom, long long npts, int ward, double* __
         }
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
+        if constexpr (N >= 6) {
+            denominators_parallel<R, N, true>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
+                return row_view(stage, SROW, c, E2, is);
+            });
+        }
         __syncthreads();
         ward_rounds<R, N, BLOCK>(smem, recs, cnt, ward);
         for (int t = threadIdx.x; t < cnt; t += BLOCK)
@@ -342,6 +372,14 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         PointRec<R, N>& rec = recs[c];
         pass_to_rec<R, N>(MomView{stage + rec.idx, tile, kMomSlots}, rec.fac, ph, rec);
     }
+    if constexpr (N >= 6) {
+        __syncthreads();   // the staged momenta are scaled in place by pass_to_rec
+        denominators_parallel<R, N, false>(recs, npass, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
+            E2 = 0.5;
+            is = 1.0;
+            return MomView{stage + recs[c].idx, tile, kMomSlots};
+        });
+    }
     __syncthreads();
     amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, npass, nullptr, ph.alg, kEsc);
     // one thread per record: weight and double-double accumulation; records
@@ -381,21 +419,20 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
 }
 
 // Resident blocks per SM a tile kernel is compiled for (its register
-// budget).  The FP32 tree at n = 6, 7 runs fastest with 768 threads per SM
-// (80 registers; its shared memory allows it), trading a few spills for
-// occupancy, and so does n = 2 (three blocks, at most 68 KB); elsewhere two
-// blocks (up to 128 registers).
+// budget; a sub-partition holds at most 16384 registers of its warps): for
+// the FP32 tree three 160-thread blocks at n = 6 and two blocks above (four
+// warps per sub-partition, 128 registers); n = 2 three blocks (at most
+// 68 KB); elsewhere two blocks (up to 128 registers).
 template <class R, int N, int BLOCK, bool ESC, int ALG>
 __host__ __device__ constexpr int tile_min_blocks() {
-    return (sizeof(R) == sizeof(float) && ALG == kAlgTree && !ESC && (N == 6 || N == 7)) ? 768 / BLOCK : N == 2 ? 3 : 2;
+    return (sizeof(R) == sizeof(float) && ALG == kAlgTree && !ESC && N == 6) ? 3 : N == 2 ? 3 : 2;
 }
-// Threads of a fused tile kernel's block: 128 for the FP32 tree at n = 6,
-// whose rounds are bound by their block barriers (half the warps per barrier
-// and, with tables for half the points, twice the blocks per SM: +11 % on
-// GB300), 256 elsewhere.
+// Threads of a fused tile kernel's block: for the FP32 tree, as many warps as
+// share out the depth-2 prefixes evenly with one subtree group per warp
+// (30 / 5 at n = 6, 42 / 7 at n = 7), 256 elsewhere.
 template <class R, int N, int ALG>
 __host__ __device__ constexpr int xsec_block() {
-    return sizeof(R) == sizeof(float) && ALG == kAlgTree && N == 6 ? 128 : 256;
+    return sizeof(R) == sizeof(float) && ALG == kAlgTree ? (N == 6 ? 160 : N == 7 ? 224 : 256) : 256;
 }
 
 template <class R, int N, int BLOCK, bool ESC, int ALG>
@@ -444,6 +481,14 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
             recs[t].idx = t;
             recs[t].hsel = point_hsel<N>(ph, seed, (uint64_t)esc.idx[base + c0 + t]);
         }
+        if constexpr (N >= 6) {
+            __syncthreads();
+            denominators_parallel<double, N, false>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
+                E2 = 0.5;
+                is = 1.0;
+                return MomView{stage + c, tile, kMomSlots};
+            });
+        }
         __syncthreads();
         amp_rounds<double, N, BLOCK, 0, kAlgSubset>(smem, recs, cnt, nullptr, kAlgSubset);
         for (int t = threadIdx.x; t < cnt; t += BLOCK) {
@@ -482,6 +527,11 @@ amp2_list_kernel(const double* __restrict__ mom, const int* __restrict__ list, c
         }
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<double, N>(stage + t * SROW, ph, recs[t], flag);
+        if constexpr (N >= 6) {
+            denominators_parallel<double, N, true>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
+                return row_view(stage, SROW, c, E2, is);
+            });
+        }
         __syncthreads();
         amp_rounds<double, N, BLOCK, 0, kAlgSubset>(smem, recs, cnt, mask, kAlgSubset);
         for (int t = threadIdx.x; t < cnt; t += BLOCK) out[list[t0 + t]] = (double)recs[t].ssum * recs[t].fac;
@@ -704,6 +754,14 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
             if (g < tot)
                 pass_to_rec<R, N>(MomView{stage + rs_ring[g].idx, kWsStage, kMomSlots}, rs_ring[g].fac, ph,
                                   rs_ring[g]);
+            if constexpr (N >= 6) {
+                named_sync(kBarProducers, kWsStage);   // scaled momenta in place
+                denominators_parallel<R, N, false>(rs_ring, tot, g, kWsStage, [&](int c, double& E2, double& is) {
+                    E2 = 0.5;
+                    is = 1.0;
+                    return MomView{stage + rs_ring[c].idx, kWsStage, kMomSlots};
+                });
+            }
             // every producer has read the staged momenta it needed before any
             // of them generates the next stage into its column
             named_sync(kBarProducers, kWsStage);

@@ -601,13 +601,13 @@ __device__ __forceinline__ double phase_space_weight(double s) {
 // built up over the sets in increasing order in registers: with h the
 // highest photon of T and U = T - {h},
 //   t_T = t_U + e_h(U),  e_h(U) = d_h + sum_{j in U} s_jh = e_h(U - {l}) + s_lh
-// (l the lowest photon of U): two additions per set.  For larger n (where
-// the tree dwarfs this) t_T = (sum_{i in T} k_i - p2)^2 by components, set
-// by set.
+// (l the lowest photon of U): two additions per set.  Larger n: see
+// set_denominator.
 template <class R, int N, bool SCALE>
 __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, double is, bool massless,
                                                   PointRec<R, N>& rec) {
-    if constexpr (N <= 5) {
+    static_assert(N <= 5, "n >= 6 forms its denominators set by set (set_denominator)");
+    {
         double d[N], sij[N * (N - 1) / 2 > 0 ? N * (N - 1) / 2 : 1];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
@@ -636,22 +636,26 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
                 if (h < N - 1) t[T] = tt;
             }
         }
-    } else {
-#pragma unroll 1
-        for (int T = 1; T < (1 << N) - 1; ++T) {
-            double q0 = -E2, q1 = 0.0, q2 = 0.0, q3 = E2;
-#pragma unroll 1
-            for (int i = 0; i < N; ++i)
-                if (T >> i & 1) {
-                    q0 += p(i, 0);
-                    q1 += p(i, 1);
-                    q2 += p(i, 2);
-                    q3 += p(i, 3);
-                }
-            const double tt = q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3;
-            rec.t[T] = rec_value<R>(SCALE ? tt * is : tt);
-        }
     }
+}
+
+// One denominator for n >= 6 (where the tree dwarfs this, and one thread per
+// set keeps every lane of the FP64 pipe busy): t_T = (sum_{i in T} k_i - p2)^2
+// by components, times `is` if SCALE.  Callers run it over (record, set)
+// pairs after the records are built (denominators_parallel).
+template <class R, int N, bool SCALE>
+__device__ __forceinline__ R set_denominator(const MomView& p, double E2, double is, unsigned T) {
+    double q0 = -E2, q1 = 0.0, q2 = 0.0, q3 = E2;
+#pragma unroll 1
+    for (int i = 0; i < N; ++i)
+        if (T >> i & 1) {
+            q0 += p(i, 0);
+            q1 += p(i, 1);
+            q2 += p(i, 2);
+            q3 += p(i, 3);
+        }
+    const double tt = q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3;
+    return rec_value<R>(SCALE ? tt * is : tt);
 }
 
 // Record of a point that passed the cuts, from its photon momenta (GeV) and
@@ -670,7 +674,7 @@ __device__ __forceinline__ void pass_to_rec(const MomView& v, double irs, const 
             v(a, m) = k;
             rec.k[a][m] = rec_value<R>(k);
         }
-    fill_denominators<R, N, false>(v, 0.5, 1.0, true, rec);
+    if constexpr (N <= 5) fill_denominators<R, N, false>(v, 0.5, 1.0, true, rec);   // n >= 6: denominators_parallel
     rec.e2 = R(0.5);
     rec.n1 = R(1);
     rec.n2 = R(1);

@@ -84,7 +84,7 @@ def momentum_violation(mom):
     return np.maximum(2.22e-16, d)
 
 
-def fp64_tolerance(mom, floor=2e-12):
+def fp64_tolerance(mom, floor=1e-12):
     """Per-point relative tolerance of an FP64 |M|^2 against the oracle:
     a floor for rounding-order differences over the ordering and helicity
     sums, plus 16 n times the momentum-conservation violation of the input

@@ -60,6 +60,41 @@ static void check_pair_columns() {
     }
 }
 
+// prefix decoding of the walk: every ordered prefix of depth 2 and 3 exactly
+// once, in lexicographic order, with distinct photons
+template <int N>
+static void check_prefixes() {
+    int last = -1;
+    for (int k = 0; k < N * (N - 1); ++k) {
+        int a, b, c;
+        tree_prefix<N, 2>(k, a, b, c);
+        const int key = a * N + b;
+        CHECK(a >= 0 && a < N && b >= 0 && b < N && a != b && key > last, "n=%d depth-2 prefix %d = (%d, %d)", N, k, a, b);
+        last = key;
+    }
+    last = -1;
+    for (int k = 0; k < N * (N - 1) * (N - 2); ++k) {
+        int a, b, c;
+        tree_prefix<N, 3>(k, a, b, c);
+        const int key = (a * N + b) * N + c;
+        CHECK(a >= 0 && b >= 0 && c >= 0 && a < N && b < N && c < N && a != b && a != c && b != c && key > last,
+              "n=%d depth-3 prefix %d = (%d, %d, %d)", N, k, a, b, c);
+        last = key;
+    }
+}
+
+// lane layout of a shape: every (group, point slot, helicity bits) once per
+// block, groups warp-aligned, prefixes shared out evenly where the block's
+// default allows it
+template <class R, int N, int BLOCK>
+static void check_shape(bool even) {
+    using SH = DefaultShape<R, N, BLOCK>;
+    using S = TreeShape<N, BLOCK, SH::HB, SH::G>;
+    CHECK(SH::G * S::P * S::NSL == BLOCK, "n=%d block %d: lanes do not tile the block", N, BLOCK);
+    CHECK(SH::G == 1 || S::GL % 32 == 0, "n=%d block %d: group of %d lanes", N, BLOCK, S::GL);
+    if (even) CHECK(S::NPRE % SH::G == 0, "n=%d block %d: %d prefixes over %d groups", N, BLOCK, S::NPRE, SH::G);
+}
+
 static size_t resident_blocks(size_t smem_per_block) {
     const size_t per_sm = 228 * 1024, reserved = 1024;
     return per_sm / (smem_per_block + reserved);
@@ -67,11 +102,24 @@ static size_t resident_blocks(size_t smem_per_block) {
 
 int main() {
     check_tree_tables();
+    check_prefixes<4>();
+    check_prefixes<5>();
+    check_prefixes<6>();
+    check_prefixes<7>();
+    check_prefixes<8>();
+    check_shape<float, 5, 256>(true);
+    check_shape<float, 6, 160>(true);
+    check_shape<float, 6, 256>(false);
+    check_shape<float, 7, 224>(true);
+    check_shape<float, 7, 256>(false);
+    check_shape<float, 8, 256>(true);
     check_pair_columns<float, 4, 0, 1, 256>();
-    check_pair_columns<float, 5, 0, 1, 256>();
-    check_pair_columns<float, 6, 1, 2, 128>();
-    check_pair_columns<float, 7, 1, 2, 256>();
-    check_pair_columns<float, 8, 1, 2, 256>();
+    check_pair_columns<float, 5, 2, 4, 256>();
+    check_pair_columns<float, 6, 2, 5, 160>();
+    check_pair_columns<float, 6, 2, 8, 256>();
+    check_pair_columns<float, 7, 2, 7, 224>();
+    check_pair_columns<float, 7, 2, 4, 256>();
+    check_pair_columns<float, 8, 2, 4, 256>();
     check_pair_columns<double, 4, 0, 1, 256>();
     check_pair_columns<double, 8, 0, 1, 256>();
     // occupancy the tuned launch shapes rely on
@@ -84,10 +132,12 @@ int main() {
     CHECK(resident_blocks(ws4e) >= 2, "warp-specialised n=4 tree with escalation: %zu bytes", ws4e);
     const size_t ws5 = ws_smem_bytes<float, 5, kAlgTree>() + 2 * ws_stage(5) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws5) >= 2, "warp-specialised n=5 tree: %zu bytes", ws5);
-    const size_t t6 = xsec_smem_bytes<float, 6, 128, kAlgTree>(32);
-    CHECK(resident_blocks(t6) >= 5, "tile n=6 tree (128 threads): %zu bytes, fewer than 5 blocks per SM", t6);
-    const size_t t7 = xsec_smem_bytes<float, 7, 256, kAlgTree>(8);
-    CHECK(resident_blocks(t7) >= 3, "tile n=7 tree: %zu bytes, fewer than 3 blocks per SM", t7);
+    const size_t t6 = xsec_smem_bytes<float, 6, 160, kAlgTree>(32);
+    CHECK(resident_blocks(t6) >= 3, "tile n=6 tree (160 threads): %zu bytes, fewer than 3 blocks per SM", t6);
+    const size_t t7 = xsec_smem_bytes<float, 7, 224, kAlgTree>(8);
+    CHECK(resident_blocks(t7) >= 2, "tile n=7 tree (224 threads): %zu bytes, fewer than 2 blocks per SM", t7);
+    const size_t t8 = xsec_smem_bytes<float, 8, 256, kAlgTree>(4);
+    CHECK(resident_blocks(t8) >= 2, "tile n=8 tree: %zu bytes, fewer than 2 blocks per SM", t8);
     CHECK(sizeof(SampleDraw) == 16, "SampleDraw is %zu bytes", sizeof(SampleDraw));
     std::printf("layout checks: %d failures\n", failures);
     return failures ? 1 : 0;

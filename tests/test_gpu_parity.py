@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances: FP64 chain within helpers.fp64_tolerance per point (a 2e-12
+Tolerances: FP64 chain within helpers.fp64_tolerance per point (a 1e-12
 floor for rounding-order differences over up to n! 2^(n+2) terms, plus input
 rounding amplified by the smallest propagator denominator); FP32 chain median
 <= 1e-4 and max <= 1e-3 relative; phase-space momenta within 1e-12 sqrt(s)
