@@ -486,11 +486,9 @@ int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
 
 /* heget_xsec_async for callers that cannot allocate device memory.  The
  * paper has no counterpart: this is a service of this library.  Such callers
- * include code that runs while a stream is being captured into a CUDA graph
- * (an allocation cannot be captured), applications whose device memory is
- * owned by a framework arena or a custom allocator that a library must not
- * bypass, and latency-critical paths that cannot afford the implicit
- * synchronisation of cudaMalloc.
+ * include applications whose device memory is owned by a framework arena or
+ * a custom allocator that a library must not bypass, and latency-critical
+ * paths that cannot afford the implicit synchronisation of cudaMalloc.
  *
  * No context is needed and nothing is allocated: no cudaMalloc, no cudaFree,
  * no allocating library routine.  The per-block partial sums that
@@ -507,10 +505,15 @@ int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
  * blocks and has no limit; otherwise N may be at most 4096 x the xsec tile
  * (for example 131,072 points at n = 6 and 16,384 at n = 8 in FP32).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any
+ * stream capture.  The address belongs to the device's primary context:
+ * after cudaDeviceReset a process must not call this again on that device.
  * Every call shares the one array per device and leaves its contents
  * behind; nothing in it needs clearing, but calls that overlap on the GPU
- * (concurrent streams) race on it and must not be issued. */
+ * (concurrent streams) race on it and must not be issued.
+ * EINVAL, as heget_xsec_async: bad n, N < 0, i0 < 0 or i0 + N beyond int64,
+ * bad precision or sampler, NULL result_dev, params that heget_set_params
+ * refuses, a device that is not present, or N beyond the limit above. */
 int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, int64_t N,
                        const heget_sampler* smp, const heget_params* params,
                        int precision, heget_xsec_result* result_dev,

@@ -253,7 +253,9 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
         L->grid = (int)(tiles < wave ? (tiles < 1 ? 1 : tiles) : wave);
         return 0;
     }
-    L->block = xsec && precision == HEGET_FP32 && alg != kAlgSubset && n == 6 ? 128 : kBlockThreads;   // xsec_block()
+    // xsec_block(): the FP32 tree's tile kernel at n = 6, 7 runs 160 / 224 threads
+    L->block = xsec && precision == HEGET_FP32 && alg != kAlgSubset && (n == 6 || n == 7) ? (n == 6 ? 160 : 224)
+                                                                                        : kBlockThreads;
     L->tile = tile > 0 ? tile : default_tile(n, xsec);
     const bool sub = alg == kAlgSubset;
     const int e = precision == HEGET_FP32
@@ -938,8 +940,10 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
 // code cannot hand the array's name to a kernel (in host code it names a
 // host-side stand-in), so the first call on each device looks up the device
 // address with cudaGetSymbolAddress while that device is current and caches
-// it.  Each call's blocks overwrite exactly the entries its own finalize
-// reads, so nothing has to be cleared between calls.
+// it.  The address belongs to the device's primary context: after a
+// cudaDeviceReset the process must not call this again on that device.  Each
+// call's blocks overwrite exactly the entries its own finalize reads, so
+// nothing has to be cleared between calls.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kNoAllocMaxBlocks = 4096;   // 4096 partials x 64 B = 256 KiB per device
@@ -968,13 +972,14 @@ extern "C" int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, 
                                   const heget_sampler* smp, const heget_params* params, int precision,
                                   heget_xsec_result* result_dev, void* stream) {
     if (n < kMinN || n > kMaxN) return fail(HEGET_EINVAL, "n = %d outside [2, 8]", n);
-    if (N < 0 || i0 < 0) return fail(HEGET_EINVAL, "N and i0 must be >= 0");
-    int r = check_precision(precision);
+    if (N < 0) return fail(HEGET_EINVAL, "N = %lld < 0", (long long)N);
+    int r = check_range(i0, N);
     if (r) return r;
+    if ((r = check_precision(precision))) return r;
     if ((r = check_sampler(smp))) return r;
     if (!result_dev) return fail(HEGET_EINVAL, "result_dev is NULL");
-    heget_params p = params ? *params : heget_params{1.0 / 137.035999, 2.0 / 3.0, 20.0, 2.5, 0.4};
-    if (!(p.alpha > 0) || !(p.eta_max > 0) || !(p.pt_min >= 0)) return fail(HEGET_EINVAL, "bad params");
+    const heget_params p = params ? *params : heget_params{1.0 / 137.035999, 2.0 / 3.0, 20.0, 2.5, 0.4};
+    if ((r = check_params(&p))) return r;   // the same refusals as heget_set_params
     int count = 0;
     cudaError_t e = cudaGetDeviceCount(&count);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
