@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 N_PHOTONS = 4
 POINTS = 1 << 20
 SEED = 0x0908440300000002
-METRIC = "u ubar -> n gamma |M|^2 phase-space points/s (n=4 workload; FP32 chain, FP64 phase space + accumulation)"
+METRIC = ("u ubar -> n gamma |M|^2 phase-space points/s (points whose |M|^2 is evaluated, i.e. that pass the cuts; "
+          "n=4 workload; FP32 chain, FP64 phase space + accumulation)")
 WORKLOAD = ("u ubar -> 4 gamma, 1,048,576 points/step/GPU, toy-PDF sqrt(s-hat) = 14 TeV sqrt(x1 x2) > 100 GeV "
             "with x ~ x^-1/2 (1-x)^3, cuts pT>20 GeV |eta|<2.5 dR>0.4, all 64 helicities")
 PATH = ("24 orderings on the prefix tree with the two-ended finish, FP32 chain + FP64 RAMBO/cuts/denominators "
@@ -187,42 +188,47 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(n, seconds=12.0, sampler=None, cut=None, seed=SEED, N_cap=None):
+def cpu_baseline(n, seconds=12.0, sampler=None, cut=None, seed=SEED, N_cap=None, single=True, exact=None):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of
-    the same workload (consecutive point indices of the same seed).  Returns
-    the baseline record and the sample's weights (for the error columns of
-    --matrix)."""
+    the same workload (consecutive point indices of the same seed), about
+    `seconds` of work, or exactly `exact` points.  Its value counts the
+    points whose |M|^2 is evaluated (those that pass the cuts; the oracle
+    skips the others as the device does).  Returns the baseline record and the
+    sample's weights (for the error columns)."""
     import oracle as O
     O.build()
     threads = os.cpu_count() or 1
     S = sampler if sampler is not None else O.toy_pdf()
     Cc = cut if cut is not None else O.cuts()
     import numpy as np
-    probe = threads if n >= 7 else 256
+    probe = exact if exact else (threads if n >= 7 else 256)
     t0 = time.perf_counter()
-    w, _, _ = O.event_weights(n, seed, 0, probe, S, Cc, threads=threads)
+    w, mask, _ = O.event_weights(n, seed, 0, probe, S, Cc, threads=threads)
     dt = time.perf_counter() - t0
     N = probe
-    if dt < 0.5 * seconds:   # extend the sample to about `seconds` of work
+    if not exact and dt < 0.5 * seconds:   # extend the sample to about `seconds` of work
         more = max(probe, int(probe * (seconds - dt) / max(dt, 1e-3)))
         if N_cap:
             more = max(0, min(more, N_cap - probe))
         if more:
             t1 = time.perf_counter()
-            w2, _, _ = O.event_weights(n, seed, probe, more, S, Cc, threads=threads)
+            w2, m2, _ = O.event_weights(n, seed, probe, more, S, Cc, threads=threads)
             dt += time.perf_counter() - t1
             w = np.concatenate([w, w2])
+            mask = np.concatenate([mask, m2])
             N += more
-    rec = {"value": N / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
-           "sample": f"points 0..{N - 1} of the n={n} workload (seed {seed:#x}), weights incl. |M|^2 "
-                     f"of cut-passing points, {threads} OpenMP threads, {dt:.1f} s"}
+    npass = int(mask.sum())
+    rec = {"value": npass / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
+           "generated_points_per_s": N / dt,
+           "sample": f"points 0..{N - 1} of the n={n} workload (seed {seed:#x}), {npass} pass the cuts and have "
+                     f"|M|^2 evaluated, {threads} OpenMP threads, {dt:.1f} s"}
     # one core as well, on the first points of the same sample (about 2 s of work)
     n1 = min(N, int(N / dt / threads * 2.0))
-    if n1 >= 4:
+    if single and n1 >= 4:
         t1 = time.perf_counter()
-        O.event_weights(n, seed, 0, n1, S, Cc, threads=1)
+        _, m1, _ = O.event_weights(n, seed, 0, n1, S, Cc, threads=1)
         d1 = time.perf_counter() - t1
-        rec["single_thread"] = {"value": n1 / d1, "unit": "points/s", "cores": 1,
+        rec["single_thread"] = {"value": int(m1.sum()) / d1, "unit": "points/s", "cores": 1,
                                 "sample": f"points 0..{n1 - 1}, 1 thread, {d1:.1f} s"}
     return rec, w
 
@@ -239,46 +245,59 @@ def run_reference(args):
     for w in range(args.warmup):
         O.event_weights(N_PHOTONS, SEED, w * per_step, min(per_step, 64), S, Cc, threads=threads)
     t0 = time.perf_counter()
+    evaluated = 0
     for k in range(args.steps):
-        O.event_weights(N_PHOTONS, SEED + k, 0, per_step, S, Cc, threads=threads)
+        _, mask, _ = O.event_weights(N_PHOTONS, SEED + k, 0, per_step, S, Cc, threads=threads)
+        evaluated += int(mask.sum())
     dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+    value = evaluated / dt   # points whose |M|^2 is evaluated (they pass the cuts), as the device arm counts
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (Philox counter RNG from a seed)",
             "config": {"workload": WORKLOAD.replace("1,048,576", f"{per_step} (bounded CPU sample)"),
                        "n": N_PHOTONS, "points_per_step": per_step, "path": PATH_ORACLE},
+            "events_per_s": per_step * args.steps / dt,
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} points per step of the n={N_PHOTONS} workload"},
+                             "sample": f"{per_step} points per step of the n={N_PHOTONS} workload, "
+                                       f"{evaluated} of them with |M|^2 evaluated over the {args.steps} steps"},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, flush=None, result=None):
+def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, flush=None, result=None,
+              detail=False):
     """Device time per step (ms) of heget_xsec_launch + heget_xsec_finalize,
     CUDA events on the launching stream, L2 flushed between steps.  result:
-    a list that receives the last step's heget_xsec_result."""
+    a list that receives the last step's heget_xsec_result.  detail: return
+    (step ms, kernel ms, evaluated points per step) instead, the kernel time
+    between the launch's events and the evaluated points from every step's
+    own result."""
     import torch
-    res = torch.zeros(80, dtype=torch.uint8, device="cuda")
+    res = torch.zeros((max(1, steps), 80), dtype=torch.uint8, device="cuda")
     for w in range(2):
         H.heget_xsec_launch(ctx, n, seed + 77 + w, i0, N, sampler, precision, stream=stream)
-        H.heget_xsec_finalize(ctx, res, stream=stream)
+        H.heget_xsec_finalize(ctx, res[0], stream=stream)
     stream.synchronize()
-    total = 0.0
+    total = kern = 0.0
     for k in range(steps):
         if flush is not None:
             flush.add_(1)
             stream.wait_stream(torch.cuda.current_stream())
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record(stream)
         H.heget_xsec_launch(ctx, n, seed + k, i0, N, sampler, precision, stream=stream)
-        H.heget_xsec_finalize(ctx, res, stream=stream)
         b.record(stream)
-        b.synchronize()
-        total += a.elapsed_time(b)
+        H.heget_xsec_finalize(ctx, res[k], stream=stream)
+        c.record(stream)
+        c.synchronize()
+        total += a.elapsed_time(c)
+        kern += a.elapsed_time(b)
+    rs = [H.result_from_tensor(res[k]) for k in range(steps)]
     if result is not None:
-        result.append(H.result_from_tensor(res))
+        result.append(rs[-1])
+    if detail:
+        return total / steps, kern / steps, sum(r.n_pass for r in rs) / steps
     return total / steps
 
 
@@ -318,17 +337,19 @@ def time_hist(H, ctx, n, N, sampler, stream, seed, i0=0, flush=None, steps=5):
 # serving: a Poisson trace of mixed requests through the request server
 # ---------------------------------------------------------------------------
 
-def serving_trace(R, rate, seed=0x5E4E):
+def serving_trace(R, rate, seed=0x5E4E, scaled=True):
     """R requests arriving as a Poisson process of `rate` per second: n uniform
     in 2..8, precision FP32 or FP64 with equal odds, toy-PDF sampler, and N
-    log-uniform in [1e3, 1e6] divided by 8^(n-4) for n > 4 (the per-point cost
-    grows ~10x per photon above n = 4; unscaled, the n = 8 requests alone would
-    ask for ~100x what one GPU delivers).  Returns a list of dicts."""
+    log-uniform in [1e3, 1e6], divided by 8^(n-4) for n > 4 if `scaled` (the
+    per-point cost grows ~10x per photon above n = 4).  Returns a list of
+    dicts."""
     import numpy as np
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, R))
     n = rng.integers(2, 9, R)
-    N = np.exp(rng.uniform(math.log(1e3), math.log(1e6), R)) / 8.0 ** np.maximum(0, n - 4)
+    N = np.exp(rng.uniform(math.log(1e3), math.log(1e6), R))
+    if scaled:
+        N = N / 8.0 ** np.maximum(0, n - 4)
     N = np.maximum(1, N.astype(np.int64))
     prec = np.where(rng.random(R) < 0.5, 32, 64)
     return [dict(t=float(t[k]), n=int(n[k]), N=int(N[k]), precision=int(prec[k]), seed=SEED + 0x1000 + k)
@@ -406,41 +427,124 @@ def _serving_section(H, ctx, R, rate):
             "saturated_vs_sequential_fp64": closed["points_per_s"] / seq64["points_per_s"]}
 
 
+def serving_cfg5(H, ctx, R=2000, rate=200.0):
+    """The serving mix as specified: N log-uniform in 1e3..1e6 for every n (no
+    scaling), R Poisson requests.  With the subset recursion: the saturated
+    rate (every request submitted at once: the largest sustainable request
+    rate), the open loop at 50 % of it, and sequential plain-FP64 calls.  The
+    prefix tree cannot serve this trace in a bench run: its plain-FP64 n = 8
+    requests alone take hours at its measured rate, which the line states
+    from the per-n rates it measures here."""
+    trace = serving_trace(R, rate, seed=0xCF65, scaled=False)
+    S = H.sampler_toy_pdf()
+    H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
+    try:
+        run_serving(H, ctx, serving_trace(40, 2000.0, seed=0x3A12), open_loop=False)
+        closed = run_serving(H, ctx, trace, open_loop=False, timeout=600.0)
+        cap = len(trace) / closed["span_s"]
+        half = [dict(q, t=q["t"] * rate / (0.5 * cap)) for q in trace]
+        open_half = run_serving(H, ctx, half, open_loop=True, timeout=600.0)
+        open_half["rate_per_s"] = 0.5 * cap
+        seq64 = run_sequential(H, ctx, trace, precision=H.HEGET_FP64)
+    finally:
+        H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
+    # the tree's cost of the same trace from its rates on a probe per (n, precision)
+    est = 0.0
+    rates = {}
+    for n in range(2, 9):
+        for prec in (H.HEGET_FP32, H.HEGET_FP64):
+            probe = {8: 256, 7: 2048}.get(n, 32768) if prec == H.HEGET_FP64 else {8: 4096, 7: 32768}.get(n, 262144)
+            t0 = time.perf_counter()
+            H.heget_xsec(ctx, n, probe, 0x5EED + n, S, prec)
+            dt = time.perf_counter() - t0
+            rates[f"n{n}_fp{prec}"] = probe / dt
+            est += sum(q["N"] for q in trace if q["n"] == n and q["precision"] == prec) / (probe / dt)
+    return {"trace": f"{R} requests, Poisson {rate:g}/s offered, n uniform 2..8, FP32/FP64 1:1, toy PDF, "
+                     "N log-uniform 1e3..1e6 for every n",
+            "points": sum(q["N"] for q in trace),
+            "subset_recursion": {"saturated": closed, "max_sustainable_rate_per_s": cap,
+                                 "open_loop_at_0.5_capacity": open_half,
+                                 "sequential_fp64_plain": seq64,
+                                 "saturated_vs_sequential_fp64": closed["points_per_s"] / seq64["points_per_s"]},
+            "prefix_tree": {"served": False,
+                            "gpu_seconds_estimate": est,
+                            "note": "sequential GPU time of the trace with the paper's prefix tree, from its rates "
+                                    "on a probe per (n, precision) (points/s in rates): beyond a bench run",
+                            "rates": rates}}
+
+
 # ---------------------------------------------------------------------------
-# per-configuration table (--matrix)
+# the four point workloads of the metric (u ubar -> n gamma, n = 2, 4, 6, 8)
 # ---------------------------------------------------------------------------
 
-MATRIX = [
-    # name, n, N, sampler (kind, args), cuts (pt, eta, dr), fp64 timing points
-    ("n=2, sqrt(s-hat) = 500 GeV fixed, 65,536 points, cuts pT>20 |eta|<2.5", 2, 65_536, ("fixed", 500.0),
-     (20.0, 2.5, 0.0), 65_536),
-    ("n=4, toy PDF, 1,048,576 points, cuts pT>20 |eta|<2.5 dR>0.4", 4, 1 << 20, ("toy",), (20.0, 2.5, 0.4),
-     1 << 20),
-    ("n=6, toy PDF, 1,048,576 points, same cuts", 6, 1 << 20, ("toy",), (20.0, 2.5, 0.4), 1 << 17),
-    ("n=8, sqrt(s-hat) uniform 200 GeV..2 TeV, 65,536 points, same cuts", 8, 65_536, ("uniform", 200.0, 2000.0),
-     (20.0, 2.5, 0.4), 2048),
+CONFIGS = [
+    # key, description, n, N, sampler (kind, args), cuts (pt, eta, dr), plain-FP64 timed points, FP32 timed
+    # steps, error sample (points of the oracle's live sample, or the stored sample file)
+    ("cfg1_n2", "u ubar -> 2 gamma, sqrt(s-hat) = 500 GeV fixed, 65,536 points, cuts pT>20 |eta|<2.5", 2, 65_536,
+     ("fixed", 500.0), (20.0, 2.5, 0.0), 65_536, 5, 4096),
+    ("cfg2_n4", "u ubar -> 4 gamma, toy-PDF sqrt(s-hat), 1,048,576 points, cuts pT>20 |eta|<2.5 dR>0.4", 4,
+     1 << 20, ("toy",), (20.0, 2.5, 0.4), 1 << 20, 5, 4096),
+    ("cfg3_n6", "u ubar -> 6 gamma, toy-PDF sqrt(s-hat), 1,048,576 points, same cuts", 6, 1 << 20, ("toy",),
+     (20.0, 2.5, 0.4), 1 << 17, 3, 4096),
+    ("cfg4_n8", "u ubar -> 8 gamma, sqrt(s-hat) uniform 200 GeV..2 TeV, 65,536 points, same cuts", 8, 65_536,
+     ("uniform", 200.0, 2000.0), (20.0, 2.5, 0.4), 2048, 2, "tests/golden/oracle_weights_n8.txt"),
 ]
 
 
-def matrix_section(H, ctx, stream, peak32, peak64, flush):
+def read_stored_weights(path):
+    """A stored oracle sample (tests/golden/gen_oracle_samples.py): its header
+    fields and the weights of points 0 .. N-1."""
+    import numpy as np
+    head, w = [], []
+    with open(os.path.join(ROOT, path)) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                head.append(line[1:].strip())
+            elif line.strip():
+                w.append(float(line.split()[3]))
+    return head, np.array(w)
+
+
+def _rel_errors(wg, w_or):
+    import numpy as np
+    nz = w_or != 0
+    rel = np.abs(wg[nz] - w_or[nz]) / np.abs(w_or[nz])
+    masks = bool(np.array_equal(wg != 0, nz))
+    if not rel.size:
+        return [0.0, 0.0], 0, masks
+    return [float(np.median(rel)), float(rel.max())], int(nz.sum()), masks
+
+
+def config_rows(H, ctx, stream, peak32, peak64, flush):
+    """Per workload of the metric: FP32 (the paper's prefix tree) and plain
+    FP64 points/s, the FP32 tree's fraction of the FP32 FMA peak from its own
+    kernel time and flop count, the subset recursion beside them, and the
+    FP32 and FP64 event weights' relative error against the FP64 oracle on a
+    stated sample (outside the timed regions)."""
     import numpy as np
     import torch
     import oracle as O
-    out = []
-    for name, n, N, smp, cut, n64 in MATRIX:
+    rows = {}
+    for key, desc, n, N, smp, cut, n64, steps, err_sample in CONFIGS:
         S = {"fixed": lambda a: H.sampler_fixed(a[0]), "toy": lambda a: H.sampler_toy_pdf(),
              "uniform": lambda a: H.sampler_uniform(a[0], a[1])}[smp[0]](smp[1:])
         OS = {"fixed": lambda a: O.fixed(a[0]), "toy": lambda a: O.toy_pdf(),
               "uniform": lambda a: O.uniform(a[0], a[1])}[smp[0]](smp[1:])
         H.heget_set_params(ctx, pt_min=cut[0], eta_max=cut[1], dr_min=cut[2])
-        r32, r64 = [], []
-        ms32 = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3 if n < 8 else 1, stream, flush=flush, result=r32)
-        ms64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 3 if n < 8 else 1, stream, flush=flush, result=r64)
+        ms32, k32, ev32 = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, steps, stream, flush=flush, detail=True)
+        ms64, k64, ev64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 2 if n < 8 else 1, stream, flush=flush,
+                                    detail=True)
         H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
-        ms32s = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3, stream, flush=flush)
-        ms64s = time_xsec(H, ctx, n, N, S, H.HEGET_FP64, 3, stream, flush=flush)
+        mss, ks, evs = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3, stream, flush=flush, detail=True)
+        mss64, ks64, evs64 = time_xsec(H, ctx, n, N, S, H.HEGET_FP64, 2, stream, flush=flush, detail=True)
         H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
-        base, w_or = cpu_baseline(n, seconds=8.0, sampler=OS, cut=O.cuts(*cut), N_cap=4096)
+        # relative errors of the event weights against the oracle
+        if isinstance(err_sample, str):
+            head, w_or = read_stored_weights(err_sample)
+            oracle_rec = {"kind": "oracle", "sample": f"stored sample {err_sample} (points 0..{len(w_or) - 1}; "
+                                                       + "; ".join(head[1:3]) + ")"}
+        else:
+            oracle_rec, w_or = cpu_baseline(n, sampler=OS, cut=O.cuts(*cut), single=False, exact=err_sample)
         M = len(w_or)
         errs = {}
         for prec in (H.HEGET_FP32, H.HEGET_FP64):
@@ -448,32 +552,32 @@ def matrix_section(H, ctx, stream, peak32, peak64, flush):
             r = torch.zeros(80, dtype=torch.uint8, device="cuda")
             H.heget_xsec_async(ctx, n, SEED, 0, M, S, prec, r, w_out=w, stream=stream)
             stream.synchronize()
-            wg = w.cpu().numpy()
-            nz = w_or != 0
-            rel = np.abs(wg[nz] - w_or[nz]) / np.abs(w_or[nz])
-            errs[prec] = (float(np.median(rel)) if rel.size else 0.0, float(rel.max()) if rel.size else 0.0,
-                          int((wg != 0).sum() == nz.sum()))
-        tf = tree_flops_per_point(n)
-        out.append({"config": name, "n": n, "points": N,
-                    "fp32_points_per_s": N / (ms32 * 1e-3), "fp64_plain_points_per_s": n64 / (ms64 * 1e-3),
-                    "fp64_timed_points": n64,
-                    "fp32_rel_err_median_max": errs[H.HEGET_FP32][:2],
-                    "fp64_rel_err_median_max": errs[H.HEGET_FP64][:2],
-                    "masks_agree": bool(errs[H.HEGET_FP32][2] and errs[H.HEGET_FP64][2]),
-                    "err_sample_points": M,
-                    # amplitudes are evaluated for the points that pass the cuts only
-                    "pass_fraction": r32[0].n_pass / N,
-                    "fp32_tree_frac_of_fp32_fma_peak": tf * r32[0].n_pass / (ms32 * 1e-3) / (FP32_PEAK * 1e12),
-                    "fp64_tree_frac_of_fp64_fma_peak": tree_flops_per_point(n, fp64=True) * r64[0].n_pass
-                                                       / (ms64 * 1e-3) / (FP64_PEAK * 1e12),
-                    "subset_fp32_points_per_s": N / (ms32s * 1e-3), "subset_fp64_points_per_s": N / (ms64s * 1e-3),
-                    "subset_flops_per_point": subset_flops_per_point(n),
-                    "tree_flops_per_point": tf, "helas4_flops_per_point": helas4_flops_per_point(n),
-                    "subset_fp32_frac_of_fp32_peak": subset_flops_per_point(n) * r32[0].n_pass / (ms32s * 1e-3)
-                                                     / (FP32_PEAK * 1e12),
-                    "oracle": base})
+            errs[prec] = _rel_errors(w.cpu().numpy(), w_or)
+        tf, sf = tree_flops_per_point(n), subset_flops_per_point(n)
+        rows[key] = {
+            "workload": desc, "n": n, "points": N, "pass_fraction": ev32 / N,
+            "fp32": {"points_per_s": N / (ms32 * 1e-3), "evaluated_per_s": ev32 / (ms32 * 1e-3),
+                     "ms_per_step": ms32, "kernel_ms": k32, "steps": steps,
+                     "flops_per_evaluated_point": tf,
+                     "frac_of_fp32_peak": tf * ev32 / (k32 * 1e-3) / (FP32_PEAK * 1e12),
+                     "frac_of_measured_fp32_peak": tf * ev32 / (k32 * 1e-3) / (peak32 * 1e12),
+                     "path": "prefix tree (the paper's ordering sum), FP32 chain"},
+            "fp64_plain": {"points_per_s": n64 / (ms64 * 1e-3), "evaluated_per_s": ev64 / (ms64 * 1e-3),
+                           "timed_points": n64, "kernel_ms": k64,
+                           "frac_of_fp64_peak": tf * ev64 / (k64 * 1e-3) / (FP64_PEAK * 1e12)},
+            "subset_recursion": {"fp32_points_per_s": N / (mss * 1e-3), "fp64_points_per_s": N / (mss64 * 1e-3),
+                                 "flops_per_evaluated_point": sf,
+                                 "fp32_frac_of_fp32_peak": sf * evs / (ks * 1e-3) / (FP32_PEAK * 1e12),
+                                 "fp64_frac_of_fp64_peak": sf * evs64 / (ks64 * 1e-3) / (FP64_PEAK * 1e12)},
+            "rel_err_vs_oracle": {"fp32_median_max": errs[H.HEGET_FP32][0], "fp64_median_max": errs[H.HEGET_FP64][0],
+                                  "points_compared": errs[H.HEGET_FP32][1],
+                                  "masks_agree": errs[H.HEGET_FP32][2] and errs[H.HEGET_FP64][2],
+                                  "sample": f"event weights of points 0..{M - 1} (seed {SEED:#x}) with |M|^2 "
+                                            "evaluated, FP32 and FP64 tree against the FP64 oracle"},
+            "oracle": oracle_rec,
+        }
     H.heget_set_params(ctx)
-    return out
+    return rows
 
 
 def main():
@@ -488,7 +592,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--n", type=int, default=N_PHOTONS, help="photons (profiling of smaller cases)")
     ap.add_argument("--points", type=int, default=POINTS, help="points per step per GPU")
-    ap.add_argument("--matrix", action="store_true", help="also print the per-configuration table")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the per-workload rows (n = 2, 4, 6, 8; profiling runs)")
+    ap.add_argument("--matrix", action="store_true", help=argparse.SUPPRESS)   # the rows are in the default line
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -532,6 +638,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    res_steps = torch.zeros((args.steps, 80), dtype=torch.uint8, device="cuda")   # each step's own result
     for k in range(args.steps):
         flush.add_(1)   # evict L2 between timed steps (untimed)
         stream.wait_stream(torch.cuda.current_stream())
@@ -539,7 +646,7 @@ def main():
         a.record(stream)
         H.heget_xsec_launch(ctx, n, SEED + k, i0, N, sampler, H.HEGET_FP32, stream=stream)
         b.record(stream)
-        H.heget_xsec_finalize(ctx, res, stream=stream)
+        H.heget_xsec_finalize(ctx, res_steps[k], stream=stream)
         c.record(stream)
         torch.cuda.current_stream().wait_stream(stream)
     torch.cuda.synchronize()
@@ -548,11 +655,16 @@ def main():
     clock_info = clocks.stop()
     step_ms = sum(a.elapsed_time(c) for a, _, c in evs)
     kern_ms = sum(a.elapsed_time(b) for a, b, _ in evs)
+    step_res = [H.result_from_tensor(res_steps[k]) for k in range(args.steps)]
+    evaluated = float(sum(x.n_pass for x in step_res))   # points whose |M|^2 was evaluated, this rank
     if ws > 1:
         t = torch.tensor([step_ms, kern_ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_ms, kern_ms = t.tolist()
-    r = H.result_from_tensor(res)
+        t = torch.tensor([evaluated], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        evaluated = t.item()
+    r = step_res[-1]
     if ws > 1:   # the job's cross section of the last step: per-rank sums combined in rank order
         r = D.allreduce_result(r, sampler.kind)
 
@@ -591,25 +703,33 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
+    e2e_eval = 0
     for k in range(args.e2e_steps):
-        H.heget_xsec(ctx, n, N, e2e_seed + k, sampler, H.HEGET_FP32)
+        e2e_eval += H.heget_xsec(ctx, n, N, e2e_seed + k, sampler, H.HEGET_FP32).n_pass
     e2e_s = time.perf_counter() - t0
+    e2e_eval = float(e2e_eval)
     if ws > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = t.item()
+        t = torch.tensor([e2e_eval], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        e2e_eval = t.item()
 
     serving = None
     if rank == 0 and ws == 1 and not args.no_serving:
         serving = serving_section(H, ctx)
         serving["subset_recursion"] = serving_section(H, ctx, alg=H.HEGET_ALG_SUBSET)
+        serving["cfg5_as_specified"] = serving_cfg5(H, ctx)
+
+    configs = None
+    if rank == 0 and ws == 1 and not args.no_configs:
+        configs = config_rows(H, ctx, stream, peak32, peak64, flush)
 
     if rank == 0:
         total_points = N * ws * args.steps
-        value = total_points / (step_ms * 1e-3)
+        value = evaluated / (step_ms * 1e-3)
         kern_s = kern_ms / args.steps * 1e-3
-        flops = tree_flops_per_point(n) * N
-        achieved = flops / kern_s / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
@@ -618,13 +738,16 @@ def main():
             "config": {"workload": WORKLOAD if (n, N) == (N_PHOTONS, POINTS) else f"n={n}, {N} points/step, toy PDF",
                        "n": n, "points_per_step": N * ws, "precision": "fp32", "path": PATH,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
-                       "compaction": "value counts every generated point; |M|^2 is evaluated for the points that "
-                                     "pass the cuts (the others have weight 0), see pass_fraction",
+                       "compaction": "value counts the points whose |M|^2 is evaluated: those that pass the "
+                                     "cuts (the others have weight 0 and no amplitude); events_per_s counts every "
+                                     "generated point",
                        "parallelism": f"dp{ws} (point shards)"},
-            "roofline": roofline(n, N, kern_s, peak32, peak64, n_eval=r.n_pass / max(1, ws)),
+            "events_per_s": total_points / (step_ms * 1e-3),
+            "pass_fraction": evaluated / total_points,
+            "roofline": roofline(n, N, kern_s, peak32, peak64, n_eval=evaluated / ws / args.steps),
             "gpu_launches": 2 * args.steps,
-            "e2e": {"value": N * ws * args.e2e_steps / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 80,
+            "e2e": {"value": e2e_eval / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 80, "events_per_s": N * ws * args.e2e_steps / e2e_s,
                     "path": "heget_xsec (synchronous public call): inputs (n, N, seed, sampler) travel as launch "
                             "arguments, the 80-byte result is copied to a host struct every step"},
             "fp64_plain": {"value": N / (ms64 * 1e-3), "unit": "points/s", "ms_per_step": ms64,
@@ -648,8 +771,8 @@ def main():
             line["serving"] = serving
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(n)[0]
-        if args.matrix:
-            line["matrix"] = matrix_section(H, ctx, stream, peak32, peak64, flush)
+        if configs:
+            line["configs"] = configs
         print(json.dumps(line), flush=True)
     H.heget_destroy(ctx)
     if ws > 1:

@@ -528,6 +528,26 @@ int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, int64_t N,
 int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev,
               void* stream);
 
+/* Combination of the results of disjoint point shards, on the host (the
+ * summation step of the paper's program, Sec. 3.1, spread over processes;
+ * no GPU needed).  heget_xsec_combine: parts[0 .. nparts-1] (host structs,
+ * in the order given) are merged as if one call had processed all their
+ * points: sum_w and sum_w2 each accumulated as a double-double in that order
+ * and rounded once, counts added, and sigma, its error and the acceptance
+ * recomputed with the formulas of heget_xsec (Sec. 2.1 eq. (1)-(2): for the
+ * toy PDF, sampler_kind HEGET_SAMPLER_TOY_PDF, the factor 2 of the q <-> qbar
+ * assignment times the acceptance of the sqrt(s-hat) floor).
+ * heget_hist_combine: len-element arrays parts[0 .. nparts-1] (host, e.g.
+ * heget_hist outputs copied back) added element by element with TwoSum in
+ * that order and rounded once into out (host, len doubles; it may be one of
+ * the parts).  Same bits for the same parts in the same order.  EINVAL for
+ * nparts < 0, len < 0, a NULL out, parts NULL with nparts > 0, or an unknown
+ * sampler kind. */
+int heget_xsec_combine(const heget_xsec_result* parts, int nparts,
+                       int sampler_kind, heget_xsec_result* out);
+int heget_hist_combine(const double* const* parts, int nparts, int64_t len,
+                       double* out);
+
 #ifdef __cplusplus
 }
 #endif

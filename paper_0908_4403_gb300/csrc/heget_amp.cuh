@@ -91,22 +91,27 @@ template <class R> __device__ __forceinline__ R fmad(R a, R b, R c);
 template <> __device__ __forceinline__ float fmad<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <> __device__ __forceinline__ double fmad<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// Lane layout of the tree (a compile-time shape):
-//   * each lane carries H = 2^HB photon-helicity configurations ("rows"), which
-//     differ in the helicities of the top HB photons NB..N-1 (NB = N - HB); one
-//     lane's rows share every table load and all index arithmetic, so the
-//     per-step overhead is spread over H row updates;
-//   * the 2^NB lanes of one point are contiguous ("point lanes"); a group holds
-//     the point lanes of all P points of a round, and G groups split the
-//     ordered prefixes of depth D0 between them (prefix k goes to group k % G)
-//     and add their partial amplitudes before squaring.  A group fills whole
-//     warps, so that every warp walks one sequence of subtrees with
-//     warp-uniform control flow and its table reads are broadcasts per point;
-//   * thread t: group g = t / (P 2^NB), point slot (t / 2^NB) % P, helicity
-//     bits hl = t % 2^NB.
-// The walk below depth D0 keeps one row set per level in registers; D0 = 3 at
-// n = 8 with four rows per lane (the top of the stack is recomputed per
-// prefix instead of held, two extra steps per 85), else 2.
+// Lane layout of the tree (a compile-time shape HB, G):
+//   * HB = 0: one photon-helicity configuration per lane; the 2^n lanes of a
+//     point are contiguous, and G groups (whole warps) split the ordered
+//     prefixes of depth D0 between them (prefix k goes to group k % G) and add
+//     their partial amplitudes before squaring.
+//   * HB = 2 ("pair units"): the orderings are cut into units, one per
+//     unordered photon pair {p, q}: those that start with p, q or with q, p.
+//     A lane carries the four configurations of (lambda_p, lambda_q) as rows
+//     and its 2^(n-2) lanes per point the helicities of the other photons.
+//     Below the first two levels every photon the walk attaches is one of the
+//     others, so all rows of a lane read the same table entry and a single
+//     code path serves every step; the table loads and the index work of a
+//     step are spread over four row updates.  G slots (whole warps holding
+//     P points) take the units u = g, g + G, ...; a slot adds its units'
+//     amplitudes into its own accumulator per absolute helicity, and the
+//     slots are added in a fixed order after the walk.
+//   * thread t: group or slot g = t / (P 2^NB), point slot (t / 2^NB) % P,
+//     lane bits hl = t % 2^NB (NB = n - HB).
+// The walk below depth D0 keeps one row set per level in registers; at n = 8
+// the pair units recompute the top of the stack (two steps) per depth-3
+// prefix instead of holding it.
 template <int N, int BLOCK, int HB, int G>
 struct TreeShape {
     static constexpr int H = 1 << HB;
@@ -114,11 +119,13 @@ struct TreeShape {
     static constexpr int NSL = 1 << NB;      // lanes of one point
     static constexpr int GL = BLOCK / G;     // lanes of a group
     static constexpr int P = GL / NSL;       // points per round
-    static constexpr int D0 = (N == 8 && HB >= 2) ? 3 : N >= 3 ? 2 : 1;
-    static constexpr int NPRE = D0 == 3 ? N * (N - 1) * (N - 2) : D0 == 2 ? N * (N - 1) : N;
-    static_assert(HB >= 0 && HB <= 2 && (HB == 0 || NB >= 2), "1, 2 or 4 rows per lane");
+    static constexpr bool PAIRS = HB == 2;
+    static constexpr int D0 = PAIRS ? (N == 8 ? 3 : 2) : N >= 3 ? 2 : 1;
+    // units of work shared out over the groups: pairs, or ordered prefixes
+    static constexpr int NPRE = PAIRS ? N * (N - 1) / 2 : D0 == 2 ? N * (N - 1) : N;
+    static_assert(HB == 0 || (HB == 2 && N >= 4), "one configuration per lane, or pair units");
     static_assert(BLOCK % G == 0 && GL % NSL == 0 && P >= 1, "a round holds whole points");
-    static_assert(G == 1 || GL % 32 == 0, "subtree groups fill whole warps");
+    static_assert(G == 1 || GL % 32 == 0, "groups fill whole warps");
 };
 
 // Two-ended finish of the tree (sub-current reuse from the u side): with two
@@ -146,10 +153,28 @@ __host__ __device__ __forceinline__ int pair_slot(int a, int b) {
     return a * (N - 1) + b - (b > a);
 }
 
+// Unordered pair u (lexicographic over p < q) -> (p, q).
+template <int N>
+__host__ __device__ __forceinline__ void pair_of_unit(int u, int& p, int& q) {
+    p = 0;
+    while (u >= N - 1 - p) {
+        u -= N - 1 - p;
+        ++p;
+    }
+    q = p + 1 + u;
+}
+
+// The n - 2 helicity bits of a pair unit's lane spread over the photons other
+// than p < q (zeros at p and q).
+__host__ __device__ __forceinline__ unsigned spread_pair_bits(unsigned hl, int p, int q) {
+    const unsigned x = (hl & ((1u << p) - 1u)) | ((hl >> p) << (p + 1));
+    return (x & ((1u << q) - 1u)) | ((x >> q) << (q + 1));
+}
+
 // Shared-memory tables of one round.  Every lane of a point reads one index
-// for its point and one or two lambdas, so entries are laid out
-// [index][point][lambda] (plus the two rows of a step matrix next to each
-// other): the lanes of a warp hit a few consecutive 16-byte rows.
+// for its point and one lambda, so entries are laid out [index][point][lambda]
+// (plus the two rows of a step matrix next to each other): the lanes of a
+// warp hit a few consecutive 16-byte rows.
 template <class R, int N, int BLOCK, int HB = 0, int G = 1>
 struct RoundTables {
     using S = TreeShape<N, BLOCK, HB, G>;
@@ -161,12 +186,14 @@ struct RoundTables {
     static constexpr int NS = 1 << N;
     static constexpr size_t m_elems = (size_t)KW * P * 4;   // [idx][p][lambda][row 0, row 1]
     static constexpr size_t c_elems = (size_t)N * P * 2;    // [j][p][lambda]
-    static constexpr size_t x_elems = G > 1 ? (size_t)BLOCK * S::H * 2 : 0;
+    // group exchange: partial amplitudes per lane (ordered-prefix groups), or
+    // the slots' accumulators per absolute helicity (pair units)
+    static constexpr size_t x_elems = S::PAIRS ? (size_t)G * P * NS * 2 : G > 1 ? (size_t)BLOCK * 2 : 0;
     static constexpr size_t p_elems = tree_two_ended<R, N>() ? (size_t)N * (N - 1) * P * 4 : 0;
     static constexpr size_t bytes = (m_elems + 2 * c_elems + p_elems) * sizeof(Row<R>)   // MT, CL, R1, PC
                                   + (size_t)P * N * sizeof(Row<R>)                      // photon data
                                   + (size_t)P * NS * sizeof(Row<R>)                     // set data
-                                  + x_elems * sizeof(R)                                 // group exchange
+                                  + x_elems * sizeof(R)                                 // exchange
                                   + (size_t)(BLOCK / 32) * sizeof(R) + 16;              // reduction
     Row<R>* MT;   // step matrices M(j, T)^lambda
     Row<R>* CL;   // closures (eps*_j . sigma) u_R
@@ -174,7 +201,7 @@ struct RoundTables {
     Row<R>* PC;   // [pair_slot(a, b)][P][lambda_a 2 + lambda_b]: pair columns (two-ended finish)
     Row<R>* PH;   // [P][N]: (sin th, cos th, cos ph, sin ph)
     Row<R>* SD;   // [P][2^N]: (A, D, Bre, Bim) = ((q0+q3), (q0-q3), q1, q2) / q^2
-    R* XCH;       // [BLOCK][H][2]: partial amplitudes of the subtree groups
+    R* XCH;       // [BLOCK][2], or [G][P][2^N][2] with pair units
     R* RED;       // [BLOCK/32]
     __device__ __forceinline__ explicit RoundTables(unsigned char* base) {
         MT = reinterpret_cast<Row<R>*>(base);
@@ -372,154 +399,72 @@ struct LaneTables {
     const Row<R>* cl;
     const Row<R>* r1;
     const Row<R>* pc;
-    unsigned hl;  // helicity bits of photons 0 .. NB-1 (lambda = bit set -> +1)
+    unsigned hl;  // lambda bits of the photons the walk attaches (bit set -> +1)
 };
 
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ LaneTables<R, N, BLOCK, HB, G> lane_tables(const RoundTables<R, N, BLOCK, HB, G>& tb,
-                                                                      int slot, int hl) {
+                                                                      int slot, unsigned hl) {
     return LaneTables<R, N, BLOCK, HB, G>{tb.MT + 4 * slot, tb.CL + 2 * slot, tb.R1 + 2 * slot, tb.PC + 4 * slot,
-                                          (unsigned)hl};
+                                          hl};
 }
 
-// Rows r[b] . M, photon j below NB: every row of the lane has the same lambda.
+// Rows r[b] . M: every row of the lane takes the same step matrix.
 template <class R, int H>
 __device__ __forceinline__ void step_same(Row<R> (&o)[H], const Row<R> (&r)[H], const Row<R>& m0, const Row<R>& m1) {
 #pragma unroll
     for (int b = 0; b < H; ++b) o[b] = row_times(r[b], m0, m1);
 }
 
-// Rows r[b] . M^{lambda_b}, photon NB + JB: row b takes lambda = bit JB of b.
-template <class R, int H, int JB>
-__device__ __forceinline__ void step_split(Row<R> (&o)[H], const Row<R> (&r)[H], const Row<R>& a0, const Row<R>& a1,
-                                           const Row<R>& b0, const Row<R>& b1) {
-#pragma unroll
-    for (int b = 0; b < H; ++b) o[b] = ((b >> JB) & 1) ? row_times(r[b], b0, b1) : row_times(r[b], a0, a1);
-}
-
 // Attach photon j to the rows (table entry index idx).
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void attach(const LaneTables<R, N, BLOCK, HB, G>& L, int j, int idx,
                                        const Row<R> (&r)[1 << HB], Row<R> (&o)[1 << HB]) {
-    using S = TreeShape<N, BLOCK, HB, G>;
-    constexpr int H = S::H, NB = S::NB, P = S::P;
-    const Row<R>* e = L.mt + idx * (4 * P);
-    if (HB == 0 || j < NB) {
-        e += ((L.hl >> j) & 1) * 2;
-        step_same<R, H>(o, r, ld_row(e), ld_row(e + 1));
-    } else {
-        const Row<R> a0 = ld_row(e), a1 = ld_row(e + 1), b0 = ld_row(e + 2), b1 = ld_row(e + 3);
-        if constexpr (HB == 1) {
-            step_split<R, H, 0>(o, r, a0, a1, b0, b1);
-        } else if constexpr (HB == 2) {
-            if (j == NB) step_split<R, H, 0>(o, r, a0, a1, b0, b1);
-            else step_split<R, H, 1>(o, r, a0, a1, b0, b1);
-        }
-    }
+    constexpr int P = TreeShape<N, BLOCK, HB, G>::P;
+    const Row<R>* e = L.mt + idx * (4 * P) + ((L.hl >> j) & 1) * 2;
+    step_same<R, 1 << HB>(o, r, ld_row(e), ld_row(e + 1));
 }
 
 // Closure with the last photon j (iovxx0 against u(p1)).
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void close_rows(const LaneTables<R, N, BLOCK, HB, G>& L, int j, const Row<R> (&r)[1 << HB],
                                            R (&are)[1 << HB], R (&aim)[1 << HB]) {
-    using S = TreeShape<N, BLOCK, HB, G>;
-    constexpr int H = S::H, NB = S::NB, P = S::P;
-    const Row<R>* c = L.cl + j * (2 * P);
-    if (HB == 0 || j < NB) {
-        const Row<R> c0 = ld_row(c + ((L.hl >> j) & 1));
+    constexpr int P = TreeShape<N, BLOCK, HB, G>::P;
+    const Row<R> c = ld_row(L.cl + j * (2 * P) + ((L.hl >> j) & 1));
 #pragma unroll
-        for (int b = 0; b < H; ++b) close_row(r[b], c0, are[b], aim[b]);
-    } else {
-        const Row<R> c0 = ld_row(c), c1 = ld_row(c + 1);
-        if (HB == 1 || j == NB) {
-#pragma unroll
-            for (int b = 0; b < H; ++b) close_row(r[b], (b & 1) ? c1 : c0, are[b], aim[b]);
-        } else {
-#pragma unroll
-            for (int b = 0; b < H; ++b) close_row(r[b], ((b >> 1) & 1) ? c1 : c0, are[b], aim[b]);
-        }
-    }
-}
-
-// Pair closures of the rows when photon b (a < b) is the top photon NB + KB
-// and a is below NB: row takes lambda_b = bit KB of its index.
-template <class R, int H, int KB>
-__device__ __forceinline__ void close_pair_split(const Row<R> (&r)[H], const Row<R>& ab0, const Row<R>& ab1,
-                                                 const Row<R>& ba0, const Row<R>& ba1, R (&are)[H], R (&aim)[H]) {
-#pragma unroll
-    for (int row = 0; row < H; ++row) {
-        const bool lb = (row >> KB) & 1;
-        close_row(r[row], lb ? ab1 : ab0, are[row], aim[row]);
-        close_row(r[row], lb ? ba1 : ba0, are[row], aim[row]);
-    }
+    for (int b = 0; b < (1 << HB); ++b) close_row(r[b], c, are[b], aim[b]);
 }
 
 // The two orderings left below a node of depth n - 2 by the pair columns:
-// acc += r . PC(a -> b) + r . PC(b -> a), a < b, each row with its own
-// lambdas.  Which of a, b are top photons is warp-uniform; each case loads
-// only the entries its rows use.
+// acc += r . PC(a -> b) + r . PC(b -> a) (s_ab, s_ba: the ordered pair slots).
+template <class R, int N, int BLOCK, int HB, int G>
+__device__ __forceinline__ void close_pair_slots(const LaneTables<R, N, BLOCK, HB, G>& L, int a, int b, int s_ab,
+                                                 int s_ba, const Row<R> (&r)[1 << HB], R (&are)[1 << HB],
+                                                 R (&aim)[1 << HB]) {
+    constexpr int P = TreeShape<N, BLOCK, HB, G>::P;
+    const int la = (L.hl >> a) & 1, lb = (L.hl >> b) & 1;
+    const Row<R> c1 = ld_row(L.pc + s_ab * (4 * P) + la * 2 + lb);
+    const Row<R> c2 = ld_row(L.pc + s_ba * (4 * P) + lb * 2 + la);
+#pragma unroll
+    for (int row = 0; row < (1 << HB); ++row) {
+        close_row(r[row], c1, are[row], aim[row]);
+        close_row(r[row], c2, are[row], aim[row]);
+    }
+}
+
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void close_pair(const LaneTables<R, N, BLOCK, HB, G>& L, int a, int b,
                                            const Row<R> (&r)[1 << HB], R (&are)[1 << HB], R (&aim)[1 << HB]) {
-    using S = TreeShape<N, BLOCK, HB, G>;
-    constexpr int H = S::H, NB = S::NB, P = S::P;
-    const Row<R>* ab = L.pc + pair_slot<N>(a, b) * (4 * P);
-    const Row<R>* ba = L.pc + pair_slot<N>(b, a) * (4 * P);
-    if (HB == 0 || b < NB) {
-        const int la = (L.hl >> a) & 1, lb = (L.hl >> b) & 1;
-        const Row<R> c1 = ld_row(ab + la * 2 + lb), c2 = ld_row(ba + lb * 2 + la);
-#pragma unroll
-        for (int row = 0; row < H; ++row) {
-            close_row(r[row], c1, are[row], aim[row]);
-            close_row(r[row], c2, are[row], aim[row]);
-        }
-    } else if (a < NB) {
-        const int la = (L.hl >> a) & 1;
-        const Row<R> ab0 = ld_row(ab + la * 2), ab1 = ld_row(ab + la * 2 + 1);
-        const Row<R> ba0 = ld_row(ba + la), ba1 = ld_row(ba + 2 + la);
-        if constexpr (HB == 1) {
-            close_pair_split<R, H, 0>(r, ab0, ab1, ba0, ba1, are, aim);
-        } else if constexpr (HB == 2) {
-            if (b == NB) close_pair_split<R, H, 0>(r, ab0, ab1, ba0, ba1, are, aim);
-            else close_pair_split<R, H, 1>(r, ab0, ab1, ba0, ba1, are, aim);
-        }
-    } else if constexpr (HB == 2) {
-        // a = NB, b = NB + 1: lambda_a = row bit 0, lambda_b = row bit 1
-        Row<R> cab[4], cba[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            cab[e] = ld_row(ab + e);
-            cba[e] = ld_row(ba + e);
-        }
-#pragma unroll
-        for (int row = 0; row < H; ++row) {
-            const int la = row & 1, lb = row >> 1;
-            close_row(r[row], cab[la * 2 + lb], are[row], aim[row]);
-            close_row(r[row], cba[lb * 2 + la], are[row], aim[row]);
-        }
-    }
+    close_pair_slots<R, N, BLOCK, HB, G>(L, a, b, pair_slot<N>(a, b), pair_slot<N>(b, a), r, are, aim);
 }
 
 // First rows vbar(p2) . M(j, {j}) for the lane's helicities.
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void first_rows(const LaneTables<R, N, BLOCK, HB, G>& L, int j, Row<R> (&r)[1 << HB]) {
-    using S = TreeShape<N, BLOCK, HB, G>;
-    constexpr int H = S::H, NB = S::NB, P = S::P;
-    const Row<R>* e = L.r1 + j * (2 * P);
-    if (HB == 0 || j < NB) {
-        const Row<R> a = ld_row(e + ((L.hl >> j) & 1));
+    constexpr int P = TreeShape<N, BLOCK, HB, G>::P;
+    const Row<R> a = ld_row(L.r1 + j * (2 * P) + ((L.hl >> j) & 1));
 #pragma unroll
-        for (int b = 0; b < H; ++b) r[b] = a;
-    } else {
-        const Row<R> a0 = ld_row(e), a1 = ld_row(e + 1);
-        if (HB == 1 || j == NB) {
-#pragma unroll
-            for (int b = 0; b < H; ++b) r[b] = (b & 1) ? a1 : a0;
-        } else {
-#pragma unroll
-            for (int b = 0; b < H; ++b) r[b] = ((b >> 1) & 1) ? a1 : a0;
-        }
-    }
+    for (int b = 0; b < (1 << HB); ++b) r[b] = a;
 }
 
 __device__ __forceinline__ int tree_child(int n, unsigned T, int j) {
@@ -529,81 +474,22 @@ __device__ __forceinline__ int tree_child(int n, unsigned T, int j) {
 // The bottom three levels of the walk, written out from the per-set index
 // entry (Bottom3): below a node with rows r and three photons a < b < c
 // left, attach each of them and close the two orderings of the other two by
-// the pair columns.  KA, KB, KC: -1 for a photon below NB (its lambda is the
-// lane's bit), else the row bit that carries its lambda; fixed per case, so
-// every load and row selection is resolved at compile time.
-template <class R, int N, int BLOCK, int HB, int G, int K>
-__device__ __forceinline__ void bottom_step(const LaneTables<R, N, BLOCK, HB, G>& L, int st, int lam,
-                                            const Row<R> (&r)[1 << HB], Row<R> (&o)[1 << HB]) {
-    constexpr int P = TreeShape<N, BLOCK, HB, G>::P, H = 1 << HB;
-    const Row<R>* e = L.mt + st * (4 * P);
-    if constexpr (K < 0) {
-        e += lam * 2;
-        step_same<R, H>(o, r, ld_row(e), ld_row(e + 1));
-    } else {
-        step_split<R, H, K>(o, r, ld_row(e), ld_row(e + 1), ld_row(e + 2), ld_row(e + 3));
-    }
-}
-
-template <class R, int N, int BLOCK, int HB, int G, int K1, int K2>
-__device__ __forceinline__ void bottom_pair(const LaneTables<R, N, BLOCK, HB, G>& L, int s12, int s21, int l1, int l2,
-                                            const Row<R> (&r)[1 << HB], R (&are)[1 << HB], R (&aim)[1 << HB]) {
-    constexpr int P = TreeShape<N, BLOCK, HB, G>::P, H = 1 << HB;
-    // PC(y -> z)[ly][lz] and PC(z -> y)[lz][ly]
-    const Row<R>* ab = L.pc + s12 * (4 * P);
-    const Row<R>* ba = L.pc + s21 * (4 * P);
-    Row<R> c1[4], c2[4];   // entries by row-dependent lambdas (index 2 ly' + lz')
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int vy = v >> 1, vz = v & 1;
-        if ((K1 < 0 && vy) || (K2 < 0 && vz)) continue;   // only the entries the rows use
-        const int ly = K1 < 0 ? l1 : vy, lz = K2 < 0 ? l2 : vz;
-        c1[v] = ld_row(ab + ly * 2 + lz);
-        c2[v] = ld_row(ba + lz * 2 + ly);
-    }
-#pragma unroll
-    for (int row = 0; row < H; ++row) {
-        const int vy = K1 < 0 ? 0 : (row >> (K1 < 0 ? 0 : K1)) & 1;
-        const int vz = K2 < 0 ? 0 : (row >> (K2 < 0 ? 0 : K2)) & 1;
-        close_row(r[row], c1[vy * 2 + vz], are[row], aim[row]);
-        close_row(r[row], c2[vy * 2 + vz], are[row], aim[row]);
-    }
-}
-
-template <class R, int N, int BLOCK, int HB, int G, int KA, int KB, int KC>
-__device__ __forceinline__ void bottom3_case(const LaneTables<R, N, BLOCK, HB, G>& L, const Bottom3& e, int a, int b,
-                                             int c, const Row<R> (&r)[1 << HB], R (&are)[1 << HB],
-                                             R (&aim)[1 << HB]) {
-    constexpr int H = 1 << HB;
-    const int la = KA < 0 ? (int)((L.hl >> a) & 1) : 0;
-    const int lb = KB < 0 ? (int)((L.hl >> b) & 1) : 0;
-    const int lc = KC < 0 ? (int)((L.hl >> c) & 1) : 0;
-    Row<R> r2[H];
-    bottom_step<R, N, BLOCK, HB, G, KA>(L, e.st[0], la, r, r2);
-    bottom_pair<R, N, BLOCK, HB, G, KB, KC>(L, e.pc[0], e.pc[1], lb, lc, r2, are, aim);
-    bottom_step<R, N, BLOCK, HB, G, KB>(L, e.st[1], lb, r, r2);
-    bottom_pair<R, N, BLOCK, HB, G, KA, KC>(L, e.pc[2], e.pc[3], la, lc, r2, are, aim);
-    bottom_step<R, N, BLOCK, HB, G, KC>(L, e.st[2], lc, r, r2);
-    bottom_pair<R, N, BLOCK, HB, G, KA, KB>(L, e.pc[4], e.pc[5], la, lb, r2, are, aim);
-}
-
+// the pair columns.
 template <class R, int N, int BLOCK, int HB, int G>
 __device__ __forceinline__ void bottom3(const LaneTables<R, N, BLOCK, HB, G>& L, const Row<R> (&r)[1 << HB],
                                         unsigned T, R (&are)[1 << HB], R (&aim)[1 << HB]) {
-    constexpr int NB = N - HB;
+    constexpr int P = TreeShape<N, BLOCK, HB, G>::P, H = 1 << HB;
     constexpr unsigned FULL = (1u << N) - 1;
     const unsigned rem = FULL & ~T, rem2 = rem & (rem - 1);
-    const int a = __ffs(rem) - 1, b = __ffs(rem2) - 1, c = __ffs(rem2 & (rem2 - 1)) - 1;
+    const int x[3] = {__ffs(rem) - 1, __ffs(rem2) - 1, __ffs(rem2 & (rem2 - 1)) - 1};
     const Bottom3& e = c_bottom.e[bottom_offset(N) + T];
-    // the top photons are the highest: c is one before b is, a never is
-    if (HB == 0 || c < NB) {
-        bottom3_case<R, N, BLOCK, HB, G, -1, -1, -1>(L, e, a, b, c, r, are, aim);
-    } else if constexpr (HB == 1) {
-        bottom3_case<R, N, BLOCK, HB, G, -1, -1, 0>(L, e, a, b, c, r, are, aim);
-    } else if constexpr (HB == 2) {
-        if (b >= NB) bottom3_case<R, N, BLOCK, HB, G, -1, 0, 1>(L, e, a, b, c, r, are, aim);
-        else if (c == NB) bottom3_case<R, N, BLOCK, HB, G, -1, -1, 0>(L, e, a, b, c, r, are, aim);
-        else bottom3_case<R, N, BLOCK, HB, G, -1, -1, 1>(L, e, a, b, c, r, are, aim);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        const int j = x[u], y = x[u == 0 ? 1 : 0], z = x[u == 2 ? 1 : 2];
+        Row<R> r2[H];
+        const Row<R>* m = L.mt + e.st[u] * (4 * P) + ((L.hl >> j) & 1) * 2;
+        step_same<R, H>(r2, r, ld_row(m), ld_row(m + 1));
+        close_pair_slots<R, N, BLOCK, HB, G>(L, y, z, e.pc[2 * u], e.pc[2 * u + 1], r2, are, aim);
     }
 }
 
@@ -655,40 +541,76 @@ __host__ __device__ __forceinline__ void tree_prefix(int k, int& j1, int& j2, in
     }
 }
 
-// The orderings of group g for one lane: the subtrees below the ordered
-// prefixes k = g, g + G, ... of depth D0 (lexicographic), each prefix's rows
-// formed from the first rows by D0 - 1 steps.  Sums, per row, the helicity
-// amplitude (up to normalisation) for s1 = +.  g is the same for every lane of
-// a warp, so every loop bound and table index below is warp-uniform.
-template <class R, int N, int BLOCK, int HB, int G>
-__device__ __forceinline__ void tree_amplitude(const LaneTables<R, N, BLOCK, HB, G>& L, int g, R (&are)[1 << HB],
-                                               R (&aim)[1 << HB]) {
-    using S = TreeShape<N, BLOCK, HB, G>;
-    constexpr int H = S::H;
-#pragma unroll
-    for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
+// The orderings of group g for one lane with one configuration per lane: the
+// subtrees below the ordered prefixes k = g, g + G, ... of depth D0
+// (lexicographic), each prefix's row formed from the first row by one step.
+// Sums the helicity amplitude (up to normalisation) for s1 = +.  g is the
+// same for every lane of a warp, so every loop bound and table index below is
+// warp-uniform.
+template <class R, int N, int BLOCK, int G>
+__device__ __forceinline__ void tree_amplitude(const LaneTables<R, N, BLOCK, 0, G>& L, int g, R (&are)[1],
+                                               R (&aim)[1]) {
+    using S = TreeShape<N, BLOCK, 0, G>;
+    are[0] = aim[0] = R(0);
 #pragma unroll 1
     for (int k = g; k < S::NPRE; k += G) {
         if constexpr (S::D0 == 1) {
-            Row<R> r1[H];
-            first_rows<R, N, BLOCK, HB, G>(L, k, r1);
-            descend<R, N, 1, BLOCK, HB, G>(L, r1, 1u << k, are, aim);
-        } else if constexpr (S::D0 == 2) {
-            int j1, j2, j3;
-            tree_prefix<N, 2>(k, j1, j2, j3);
-            Row<R> r1[H], r2[H];
-            first_rows<R, N, BLOCK, HB, G>(L, j1, r1);
-            attach<R, N, BLOCK, HB, G>(L, j2, tree_child(N, 1u << j1, j2), r1, r2);
-            descend<R, N, 2, BLOCK, HB, G>(L, r2, (1u << j1) | (1u << j2), are, aim);
+            Row<R> r1[1];
+            first_rows<R, N, BLOCK, 0, G>(L, k, r1);
+            descend<R, N, 1, BLOCK, 0, G>(L, r1, 1u << k, are, aim);
         } else {
             int j1, j2, j3;
-            tree_prefix<N, 3>(k, j1, j2, j3);
-            Row<R> r1[H], r2[H], r3[H];
-            first_rows<R, N, BLOCK, HB, G>(L, j1, r1);
-            const unsigned T2 = (1u << j1) | (1u << j2);
-            attach<R, N, BLOCK, HB, G>(L, j2, tree_child(N, 1u << j1, j2), r1, r2);
-            attach<R, N, BLOCK, HB, G>(L, j3, tree_child(N, T2, j3), r2, r3);
-            descend<R, N, 3, BLOCK, HB, G>(L, r3, T2 | (1u << j3), are, aim);
+            tree_prefix<N, 2>(k, j1, j2, j3);
+            Row<R> r1[1], r2[1];
+            first_rows<R, N, BLOCK, 0, G>(L, j1, r1);
+            attach<R, N, BLOCK, 0, G>(L, j2, tree_child(N, 1u << j1, j2), r1, r2);
+            descend<R, N, 2, BLOCK, 0, G>(L, r2, (1u << j1) | (1u << j2), are, aim);
+        }
+    }
+}
+
+// The rows (lambda_p, lambda_q) = (bit 0, bit 1 of the row) after the first
+// two photons j1, j2 of the ordering, {j1, j2} = {p, q}: the first row of j1
+// and the step of j2, each row with its own lambdas (sh1: the row bit of j1).
+template <class R, int N, int BLOCK, int G>
+__device__ __forceinline__ void pair_top(const LaneTables<R, N, BLOCK, 2, G>& L, int j1, int j2, int sh1,
+                                         Row<R> (&r2)[4]) {
+    constexpr int P = TreeShape<N, BLOCK, 2, G>::P;
+    const Row<R>* f = L.r1 + j1 * (2 * P);
+    const Row<R>* m = L.mt + tree_child(N, 1u << j1, j2) * (4 * P);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int l1 = (b >> sh1) & 1, l2 = (b >> (1 - sh1)) & 1;
+        r2[b] = row_times(ld_row(f + l1), ld_row(m + 2 * l2), ld_row(m + 2 * l2 + 1));
+    }
+}
+
+// One pair unit {p, q} for one lane: the orderings that start with (p, q) or
+// (q, p), every row with its (lambda_p, lambda_q); the lane's view L carries
+// the other photons' lambdas (zeros at p and q).
+template <class R, int N, int BLOCK, int G>
+__device__ __forceinline__ void pair_unit(const LaneTables<R, N, BLOCK, 2, G>& L, int p, int q, R (&are)[4],
+                                          R (&aim)[4]) {
+    const unsigned T2 = (1u << p) | (1u << q);
+#pragma unroll 1
+    for (int o = 0; o < 2; ++o) {
+        const int j1 = o ? q : p, j2 = o ? p : q;
+        if constexpr (TreeShape<N, BLOCK, 2, G>::D0 == 2) {
+            Row<R> r2[4];
+            pair_top<R, N, BLOCK, G>(L, j1, j2, o, r2);
+            descend<R, N, 2, BLOCK, 2, G>(L, r2, T2, are, aim);
+        } else {
+            // depth-3 prefixes: the two top levels recomputed per third photon
+            unsigned rem = ((1u << N) - 1) & ~T2;
+#pragma unroll 1
+            while (rem) {
+                const int j3 = __ffs(rem) - 1;
+                rem &= rem - 1;
+                Row<R> r2[4], r3[4];
+                pair_top<R, N, BLOCK, G>(L, j1, j2, o, r2);
+                attach<R, N, BLOCK, 2, G>(L, j3, tree_child(N, T2, j3), r2, r3);
+                descend<R, N, 3, BLOCK, 2, G>(L, r3, T2 | (1u << j3), are, aim);
+            }
         }
     }
 }
@@ -715,7 +637,7 @@ __device__ __forceinline__ float sel_weight(int hsel, unsigned lam, float w) {
 }
 
 
-// Lane coordinates in a round: subtree group, point slot, helicity bits.
+// Lane coordinates in a round: group or slot, point slot, lane bits.
 template <int N, int BLOCK, int HB, int G>
 struct LaneId {
     using S = TreeShape<N, BLOCK, HB, G>;
@@ -724,36 +646,27 @@ struct LaneId {
         : g(tid / S::GL), slot((tid % S::GL) / S::NSL), hl(tid % S::NSL) {}
 };
 
-// The complete amplitudes of the lane's rows: with several subtree groups,
-// every group leaves its partial sums in shared memory and group 0 adds them
-// in group order (the other groups' amplitudes become 0).  All threads must
-// call it.
-template <class R, int N, int BLOCK, int BAR, int HB, int G>
-__device__ __forceinline__ void combine_groups(const RoundTables<R, N, BLOCK, HB, G>& tb, const LaneId<N, BLOCK, HB, G>& id,
-                                               R (&are)[1 << HB], R (&aim)[1 << HB]) {
+// One configuration per lane, several groups: every group leaves its partial
+// sums in shared memory and group 0 adds them in group order (the other
+// groups' amplitudes become 0).  All threads must call it.
+template <class R, int N, int BLOCK, int BAR, int G>
+__device__ __forceinline__ void combine_groups(const RoundTables<R, N, BLOCK, 0, G>& tb, const LaneId<N, BLOCK, 0, G>& id,
+                                               R (&are)[1], R (&aim)[1]) {
     if constexpr (G > 1) {
-        using S = TreeShape<N, BLOCK, HB, G>;
-        constexpr int H = S::H;
-        R* x = tb.XCH + (size_t)threadIdx.x * H * 2;
-#pragma unroll
-        for (int b = 0; b < H; ++b) {
-            x[2 * b] = are[b];
-            x[2 * b + 1] = aim[b];
-        }
+        using S = TreeShape<N, BLOCK, 0, G>;
+        R* x = tb.XCH + (size_t)threadIdx.x * 2;
+        x[0] = are[0];
+        x[1] = aim[0];
         group_sync<BAR, BLOCK>();
         if (id.g == 0) {
 #pragma unroll 1
             for (int gg = 1; gg < G; ++gg) {
-                const R* y = tb.XCH + (size_t)(threadIdx.x + gg * S::GL) * H * 2;
-#pragma unroll
-                for (int b = 0; b < H; ++b) {
-                    are[b] += y[2 * b];
-                    aim[b] += y[2 * b + 1];
-                }
+                const R* y = tb.XCH + (size_t)(threadIdx.x + gg * S::GL) * 2;
+                are[0] += y[0];
+                aim[0] += y[1];
             }
         } else {
-#pragma unroll
-            for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
+            are[0] = aim[0] = R(0);
         }
     }
 }
@@ -761,9 +674,9 @@ __device__ __forceinline__ void combine_groups(const RoundTables<R, N, BLOCK, HB
 // Sum (MAX = false) or maximum (MAX = true) of v over the point lanes of
 // group 0 (the other groups hold zeros); the result is valid in the point's
 // first lane of group 0.  All threads must call it.
-template <class R, int N, int BLOCK, int BAR, int HB, int G, bool MAX>
-__device__ __forceinline__ R point_reduce(const RoundTables<R, N, BLOCK, HB, G>& tb, R v) {
-    using S = TreeShape<N, BLOCK, HB, G>;
+template <class R, int N, int BLOCK, int BAR, int G, bool MAX>
+__device__ __forceinline__ R point_reduce(const RoundTables<R, N, BLOCK, 0, G>& tb, R v) {
+    using S = TreeShape<N, BLOCK, 0, G>;
     constexpr int W = S::NSL < 32 ? S::NSL : 32;
 #pragma unroll
     for (int off = 1; off < W; off <<= 1) {
@@ -783,52 +696,112 @@ __device__ __forceinline__ R point_reduce(const RoundTables<R, N, BLOCK, HB, G>&
     return v;
 }
 
-// Amplitude rounds over recs[0 .. cnt-1].  For each point the lanes' reduction
-// yields S = sum_h w_h |A_h|^2 (scaled units), stored by the point's first
-// lane in recs[p].ssum; the FP64 normalisation and the accumulation are left
-// to whole warps afterwards (one lane per point), so no FP64 instruction here
-// runs with one or two active lanes.  mask: helicity mask (NULL = all).
+// Amplitude rounds over recs[0 .. cnt-1], one configuration per lane.  For
+// each point the lanes' reduction yields S = sum_h w_h |A_h|^2 (scaled
+// units), stored by the point's first lane in recs[p].ssum; the FP64
+// normalisation and the accumulation are left to whole warps afterwards (one
+// lane per point), so no FP64 instruction here runs with one or two active
+// lanes.  mask: helicity mask (NULL = all).
+template <class R, int N, int BLOCK, int BAR, int G>
+__device__ __forceinline__ void amplitude_rounds_lanes(unsigned char* table_smem, PointRec<R, N>* recs, int cnt,
+                                                       const uint32_t* mask) {
+    using RT = RoundTables<R, N, BLOCK, 0, G>;
+    using S = TreeShape<N, BLOCK, 0, G>;
+    constexpr int P = S::P;
+    const RT tb(table_smem);
+    const LaneId<N, BLOCK, 0, G> id(threadIdx.x);
+    const LaneTables<R, N, BLOCK, 0, G> L = lane_tables(tb, id.slot, (unsigned)id.hl);
+    const float wh = lane_weight<N>(mask, (unsigned)id.hl);
+    for (int base = 0; base < cnt; base += P) {
+        const int rc = min(P, cnt - base);
+        setup_round<R, N, BLOCK, BAR, 0, G>(tb, recs + base, rc);
+        R are[1], aim[1];
+        const bool active = id.slot < rc && recs[base + id.slot].valid;
+        if (active) {
+            tree_amplitude<R, N, BLOCK, G>(L, id.g, are, aim);
+        } else {
+            are[0] = aim[0] = R(0);
+        }
+        combine_groups<R, N, BLOCK, BAR, G>(tb, id, are, aim);
+        // a sampled helicity (PointRec::hsel): only the selected lane counts
+        const int hsel = active ? recs[base + id.slot].hsel : -1;
+        const R v = (are[0] * are[0] + aim[0] * aim[0]) * R(sel_weight<N>(hsel, (unsigned)id.hl, wh));
+        const R s = point_reduce<R, N, BLOCK, BAR, G, false>(tb, v);
+        if (id.g == 0 && id.hl == 0 && id.slot < rc) recs[base + id.slot].ssum = s;
+        group_sync<BAR, BLOCK>();
+    }
+}
+
+// Amplitude rounds with pair units (four configurations per lane): the same
+// contract as amplitude_rounds_lanes.  Each slot's lanes walk their units,
+// adding each unit's amplitudes into the slot's accumulators at the absolute
+// helicities of their rows; then one warp per point adds the slots in order,
+// squares, weights and sums over the helicities in a fixed order.
+template <class R, int N, int BLOCK, int BAR, int G>
+__device__ __forceinline__ void amplitude_rounds_pairs(unsigned char* table_smem, PointRec<R, N>* recs, int cnt,
+                                                       const uint32_t* mask) {
+    using RT = RoundTables<R, N, BLOCK, 2, G>;
+    using S = TreeShape<N, BLOCK, 2, G>;
+    constexpr int P = S::P, NS = 1 << N;
+    static_assert(BLOCK / 32 >= P, "one warp per point for the helicity sum");
+    const RT tb(table_smem);
+    const LaneId<N, BLOCK, 2, G> id(threadIdx.x);
+    const int tid = threadIdx.x;
+    for (int base = 0; base < cnt; base += P) {
+        const int rc = min(P, cnt - base);
+        for (int i = tid; i < G * P * NS * 2; i += BLOCK) tb.XCH[i] = R(0);
+        setup_round<R, N, BLOCK, BAR, 2, G>(tb, recs + base, rc);   // its first barrier also orders the zeros
+        if (id.slot < rc && recs[base + id.slot].valid) {
+            R* acc = tb.XCH + ((size_t)id.g * P + id.slot) * NS * 2;
+#pragma unroll 1
+            for (int u = id.g; u < S::NPRE; u += G) {
+                int p, q;
+                pair_of_unit<N>(u, p, q);
+                const unsigned hfull = spread_pair_bits((unsigned)id.hl, p, q);
+                const LaneTables<R, N, BLOCK, 2, G> L = lane_tables(tb, id.slot, hfull);
+                R are[4], aim[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) are[b] = aim[b] = R(0);
+                pair_unit<R, N, BLOCK, G>(L, p, q, are, aim);
+                // units of one slot cover disjoint orderings; its lanes' rows
+                // are distinct helicities: no two lanes touch one entry
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const unsigned h = hfull | ((unsigned)(b & 1) << p) | ((unsigned)(b >> 1) << q);
+                    acc[2 * h] += are[b];
+                    acc[2 * h + 1] += aim[b];
+                }
+            }
+        }
+        group_sync<BAR, BLOCK>();
+        // one warp per point: slots added in order, |A_h|^2 w_h summed over h
+        const int w = tid >> 5, lane = tid & 31;
+        if (w < rc) {
+            const int hsel = recs[base + w].valid ? recs[base + w].hsel : -1;
+            R v = R(0);
+            for (int h = lane; h < NS; h += 32) {
+                R ar = R(0), ai = R(0);
+#pragma unroll 1
+                for (int gg = 0; gg < G; ++gg) {
+                    const R* a = tb.XCH + (((size_t)gg * P + w) * NS + h) * 2;
+                    ar += a[0];
+                    ai += a[1];
+                }
+                v += (ar * ar + ai * ai) * R(sel_weight<N>(hsel, (unsigned)h, lane_weight<N>(mask, (unsigned)h)));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) recs[base + w].ssum = v;
+        }
+        group_sync<BAR, BLOCK>();
+    }
+}
+
 template <class R, int N, int BLOCK, int BAR = 0, int HB = 0, int G = 1>
 __device__ __forceinline__ void amplitude_rounds(unsigned char* table_smem, PointRec<R, N>* recs, int cnt,
                                                  const uint32_t* mask) {
-    using RT = RoundTables<R, N, BLOCK, HB, G>;
-    using S = TreeShape<N, BLOCK, HB, G>;
-    constexpr int P = S::P, H = S::H;
-    const RT tb(table_smem);
-    const LaneId<N, BLOCK, HB, G> id(threadIdx.x);
-    const LaneTables<R, N, BLOCK, HB, G> L = lane_tables(tb, id.slot, id.hl);
-    float wh[H];
-#pragma unroll
-    for (int b = 0; b < H; ++b) wh[b] = lane_weight<N>(mask, (unsigned)id.hl | ((unsigned)b << S::NB));
-    for (int base = 0; base < cnt; base += P) {
-        const int rc = min(P, cnt - base);
-        setup_round<R, N, BLOCK, BAR, HB, G>(tb, recs + base, rc);
-        R are[H], aim[H];
-        const bool active = id.slot < rc && recs[base + id.slot].valid;
-        if (active) {
-            tree_amplitude<R, N, BLOCK, HB, G>(L, id.g, are, aim);
-        } else {
-#pragma unroll
-            for (int b = 0; b < H; ++b) are[b] = aim[b] = R(0);
-        }
-        combine_groups<R, N, BLOCK, BAR, HB, G>(tb, id, are, aim);
-        R v = R(0);
-#pragma unroll
-        for (int b = 0; b < H; ++b) v += (are[b] * are[b] + aim[b] * aim[b]) * R(wh[b]);
-        // a sampled helicity (PointRec::hsel): only the selected lane counts
-        const int hsel = active ? recs[base + id.slot].hsel : -1;
-        if (hsel != -1) {
-            v = R(0);
-#pragma unroll
-            for (int b = 0; b < H; ++b) {
-                const unsigned lam = (unsigned)id.hl | ((unsigned)b << S::NB);
-                v += (are[b] * are[b] + aim[b] * aim[b]) * R(sel_weight<N>(hsel, lam, wh[b]));
-            }
-        }
-        v = point_reduce<R, N, BLOCK, BAR, HB, G, false>(tb, v);
-        if (id.g == 0 && id.hl == 0 && id.slot < rc) recs[base + id.slot].ssum = v;
-        group_sync<BAR, BLOCK>();
-    }
+    if constexpr (HB == 2) amplitude_rounds_pairs<R, N, BLOCK, BAR, G>(table_smem, recs, cnt, mask);
+    else amplitude_rounds_lanes<R, N, BLOCK, BAR, G>(table_smem, recs, cnt, mask);
 }
 
 // Gauge check rounds over recs[0 .. cnt-1]: for each point the largest
@@ -843,7 +816,7 @@ __device__ __forceinline__ void ward_rounds(unsigned char* table_smem, PointRec<
     constexpr int P = RT::P;
     const RT tb(table_smem);
     const LaneId<N, BLOCK, 0, 1> id(threadIdx.x);
-    const LaneTables<R, N, BLOCK> L = lane_tables(tb, id.slot, id.hl);
+    const LaneTables<R, N, BLOCK> L = lane_tables(tb, id.slot, (unsigned)id.hl);
     for (int base = 0; base < cnt; base += P) {
         const int rc = min(P, cnt - base);
         R best[2];
@@ -851,8 +824,8 @@ __device__ __forceinline__ void ward_rounds(unsigned char* table_smem, PointRec<
         for (int pass = 0; pass < 2; ++pass) {
             setup_round<R, N, BLOCK>(tb, recs + base, rc, pass ? ward : -1);
             R are[1] = {R(0)}, aim[1] = {R(0)};
-            if (id.slot < rc && recs[base + id.slot].valid) tree_amplitude<R, N, BLOCK, 0, 1>(L, 0, are, aim);
-            best[pass] = point_reduce<R, N, BLOCK, 0, 0, 1, true>(tb, are[0] * are[0] + aim[0] * aim[0]);
+            if (id.slot < rc && recs[base + id.slot].valid) tree_amplitude<R, N, BLOCK, 1>(L, 0, are, aim);
+            best[pass] = point_reduce<R, N, BLOCK, 0, 1, true>(tb, are[0] * are[0] + aim[0] * aim[0]);
             __syncthreads();
         }
         if (id.hl == 0 && id.slot < rc) {

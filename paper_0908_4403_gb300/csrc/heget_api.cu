@@ -812,6 +812,64 @@ int heget_xsec(heget_ctx* ctx, int n, int64_t N, uint64_t seed, const heget_samp
     return HEGET_OK;
 }
 
+int heget_xsec_combine(const heget_xsec_result* parts, int nparts, int sampler_kind, heget_xsec_result* out) {
+    if (!out || nparts < 0 || (nparts > 0 && !parts)) return fail(HEGET_EINVAL, "NULL argument or nparts < 0");
+    if (sampler_kind != HEGET_SAMPLER_FIXED && sampler_kind != HEGET_SAMPLER_UNIFORM &&
+        sampler_kind != HEGET_SAMPLER_TOY_PDF)
+        return fail(HEGET_EINVAL, "unknown sampler kind %d", sampler_kind);
+    DD sw{0, 0}, sw2{0, 0};   // (running sum, accumulated TwoSum errors)
+    long long npass = 0, ntotal = 0, ntries = 0, nesc = 0;
+    for (int k = 0; k < nparts; ++k) {
+        double t, e;
+        two_sum(sw.hi, parts[k].sum_w, t, e);
+        sw.hi = t;
+        sw.lo += e;
+        two_sum(sw2.hi, parts[k].sum_w2, t, e);
+        sw2.hi = t;
+        sw2.lo += e;
+        npass += parts[k].n_pass;
+        ntotal += parts[k].n_total;
+        ntries += parts[k].n_tries;
+        nesc += parts[k].n_escalated;
+    }
+    // the formulas of finalize_block (the device's summation step)
+    const double s = sw.hi + sw.lo, s2 = sw2.hi + sw2.lo;
+    const double N = (double)ntotal;
+    const double mean = N > 0 ? s / N : 0.0;
+    const double var = N > 1 ? std::fmax(0.0, (s2 - s * mean) / (N - 1.0)) : 0.0;
+    const double accept = ntries > 0 ? N / (double)ntries : 1.0;
+    const double scale = sampler_kind == HEGET_SAMPLER_TOY_PDF ? 2.0 * accept : 1.0;
+    heget_xsec_result o{};
+    o.sigma_fb = scale * mean;
+    o.err_fb = N > 0 ? scale * std::sqrt(var / N) : 0.0;
+    o.sum_w = s;
+    o.sum_w2 = s2;
+    o.accept = accept;
+    o.n_pass = npass;
+    o.n_total = ntotal;
+    o.n_tries = ntries;
+    o.n_escalated = nesc;
+    *out = o;
+    return HEGET_OK;
+}
+
+int heget_hist_combine(const double* const* parts, int nparts, int64_t len, double* out) {
+    if (!out || nparts < 0 || len < 0 || (nparts > 0 && !parts)) return fail(HEGET_EINVAL, "bad argument");
+    for (int k = 0; k < nparts; ++k)
+        if (!parts[k] && len > 0) return fail(HEGET_EINVAL, "part %d is NULL", k);
+    for (int64_t i = 0; i < len; ++i) {
+        double hi = 0.0, lo = 0.0;
+        for (int k = 0; k < nparts; ++k) {
+            double sum, err;
+            two_sum(hi, parts[k][i], sum, err);
+            hi = sum;
+            lo += err;
+        }
+        out[i] = hi + lo;
+    }
+    return HEGET_OK;
+}
+
 int heget_sum(heget_ctx* ctx, const double* x, int64_t N, double* out_dev, void* stream) {
     if (!ctx || !out_dev) return fail(HEGET_EINVAL, "NULL argument");
     if (N < 0) return fail(HEGET_EINVAL, "N < 0");

@@ -14,26 +14,25 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 constexpr int kBatchThreads = 256;   // threads of the mixed-n batch kernel
 
 // Tree shape per precision, photon count and threads of the rounds: 2^HB
-// helicity configurations per lane and G subtree groups (see TreeShape).
-// FP64 keeps one configuration per lane: its DFMA pipe, not instruction
-// issue, is the limit.  FP32 from n = 5 carries four configurations per lane,
-// which spreads each step's table loads and index work over four row updates,
-// and as many groups as make a group one warp-aligned set of point lanes
-// (8, 16, 32, 64 lanes per point at n = 5, 6, 7, 8) with the prefixes shared
-// out evenly where the block allows it (n(n-1) = 20, 30, 42 depth-2 prefixes
-// at n = 5, 6, 7; 336 depth-3 prefixes at n = 8).
+// helicity configurations per lane and G groups (see TreeShape).  FP64 keeps
+// one configuration per lane: its DFMA pipe, not instruction issue, is the
+// limit.  FP32 from n = 6 runs pair units with four configurations per lane,
+// which spreads each step's table loads and index work over four row
+// updates, with one slot per warp (two points of 16 lanes at n = 6, one point
+// of 32 lanes at n = 7) or per two warps (n = 8, 64 lanes); the blocks of the
+// fused tile kernels share the units out evenly (15 over 5 slots at n = 6,
+// 21 over 7 at n = 7, 28 over 4 at n = 8).
 template <int HB_, int G_>
 struct ShapeOf {
     static constexpr int HB = HB_, G = G_;
 };
 template <class R, int N, int BLOCK>
 __host__ __device__ constexpr int tree_hb() {
-    return sizeof(R) == sizeof(float) && N >= 5 ? 2 : 0;
+    return sizeof(R) == sizeof(float) && N >= 6 ? 2 : 0;
 }
 template <class R, int N, int BLOCK>
 __host__ __device__ constexpr int tree_groups() {
-    // lanes of one point: 2^(N - 2); a group needs whole warps
-    return tree_hb<R, N, BLOCK>() == 0 ? 1 : N == 6 ? BLOCK / 32 : (N == 7 && BLOCK % 224 == 0) ? BLOCK / 32 : BLOCK / 64;
+    return tree_hb<R, N, BLOCK>() == 0 ? 1 : N == 8 ? BLOCK / 64 : BLOCK / 32;
 }
 template <class R, int N, int BLOCK>
 struct DefaultShape : ShapeOf<tree_hb<R, N, BLOCK>(), tree_groups<R, N, BLOCK>()> {};
@@ -109,9 +108,17 @@ template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t amp2_smem_bytes(int tile) {
     return amp2_region_bytes<R, N, BLOCK, ALG>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
 }
+// The fused tile's running sums wait in shared memory (one Partial per
+// thread, after the records) while the FP32 amplitude rounds from n = 6 hold
+// every register they can get.
+template <class R, int N>
+__host__ __device__ constexpr bool xsec_parks_sums() {
+    return sizeof(R) == sizeof(float) && N >= 6;
+}
 template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t xsec_smem_bytes(int tile) {
-    return xsec_region_bytes<R, N, BLOCK, ALG>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>));
+    return xsec_region_bytes<R, N, BLOCK, ALG>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>)) +
+           (xsec_parks_sums<R, N>() ? (size_t)BLOCK * sizeof(Partial) : 0);
 }
 
 // FP32 -> FP64 escalation lists of a fused launch: block b appends the
@@ -381,7 +388,15 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         });
     }
     __syncthreads();
-    amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, npass, nullptr, ph.alg, kEsc);
+    if constexpr (xsec_parks_sums<R, N>()) {
+        Partial* park = reinterpret_cast<Partial*>(reinterpret_cast<unsigned char*>(recs) +
+                                                   align16((size_t)tile * sizeof(PointRec<R, N>)));
+        park[threadIdx.x] = acc;
+        amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, npass, nullptr, ph.alg, kEsc);
+        acc = park[threadIdx.x];
+    } else {
+        amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, npass, nullptr, ph.alg, kEsc);
+    }
     // one thread per record: weight and double-double accumulation; records
     // whose FP32 error bound exceeds the threshold join the escalation list
     if constexpr (!kEsc) {
@@ -638,7 +653,10 @@ constexpr int kBarProducers = 6;                              // producers' stag
 // Points per stage (= producer threads, a multiple of 32): as many as the
 // shared memory of the ring, the producers' staging and the round tables
 // allows at two (n <= 6) or one (n >= 7) resident blocks per SM.
-__host__ __device__ constexpr int ws_stage(int n) { return n <= 4 ? 128 : n == 5 ? 64 : 32; }
+#ifndef HEGET_WS_STAGE_6
+#define HEGET_WS_STAGE_6 32
+#endif
+__host__ __device__ constexpr int ws_stage(int n) { return n <= 4 ? 128 : n == 5 ? 64 : n == 6 ? HEGET_WS_STAGE_6 : 32; }
 
 __device__ __forceinline__ void named_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -807,8 +825,11 @@ struct AmpLaunch {
 // generation is a large share of the work: n <= 5 with the tree, every n with
 // the subset recursion.  The tree at n >= 6 spends nearly all its time in the
 // amplitudes and runs faster on the tile kernel, at more blocks per SM.
+#ifndef HEGET_WS_TREE_N6
+#define HEGET_WS_TREE_N6 0
+#endif
 constexpr bool use_ws(int n, int precision, bool xsec, int alg) {
-    return xsec && precision == HEGET_FP32 && (n <= 5 || alg == kAlgSubset);
+    return xsec && precision == HEGET_FP32 && (n <= 5 || (n == 6 && HEGET_WS_TREE_N6) || alg == kAlgSubset);
 }
 
 // Per-algorithm launchers over n = 2..8 (ALG = kAlgTree or kAlgSubset),

@@ -31,7 +31,7 @@ static int launch_amp2_n(const double* mom, long long npts, const uint32_t* mask
 // n <= 5 with the tree, every n with the subset recursion.
 template <class R, int N, int ALG>
 constexpr bool has_ws() {
-    return sizeof(R) == sizeof(float) && (N <= 5 || ALG == kAlgSubset);
+    return sizeof(R) == sizeof(float) && (N <= 5 || (N == 6 && HEGET_WS_TREE_N6) || ALG == kAlgSubset);
 }
 
 template <class R, int N, int ALG>

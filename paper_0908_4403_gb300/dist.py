@@ -11,8 +11,6 @@ whatever the process timing.
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from . import heget as H
@@ -27,42 +25,12 @@ def shard(N: int, world: int, rank: int) -> tuple[int, int]:
     return rank * q + min(rank, r), q + (1 if rank < r else 0)
 
 
-def _two_sum(a: float, b: float) -> tuple[float, float]:
-    s = a + b
-    bb = s - a
-    return s, (a - (s - bb)) + (b - bb)
-
-
-def _dd_sum(values) -> float:
-    hi, lo = 0.0, 0.0
-    for v in values:
-        hi, e = _two_sum(hi, v)
-        lo += e
-    return hi + lo
-
-
 def combine(results, sampler_kind: int) -> H.heget_xsec_result:
     """Merge per-shard results (in the given order) as if one call had
-    processed all their points: sums combined with TwoSum and rounded once,
-    counts added, sigma and its error recomputed with the formulas of
-    heget_xsec (scale 2 x acceptance for the toy PDF)."""
-    sw = _dd_sum(r.sum_w for r in results)
-    sw2 = _dd_sum(r.sum_w2 for r in results)
-    n_total = sum(int(r.n_total) for r in results)
-    n_tries = sum(int(r.n_tries) for r in results)
-    out = H.heget_xsec_result()
-    N = float(n_total)
-    mean = sw / N if n_total > 0 else 0.0
-    var = max(0.0, (sw2 - sw * mean) / (N - 1.0)) if n_total > 1 else 0.0
-    accept = N / n_tries if n_tries > 0 else 1.0
-    scale = 2.0 * accept if sampler_kind == H.HEGET_SAMPLER_TOY_PDF else 1.0
-    out.sigma_fb = scale * mean
-    out.err_fb = scale * math.sqrt(var / N) if n_total > 0 else 0.0
-    out.sum_w, out.sum_w2, out.accept = sw, sw2, accept
-    out.n_pass = sum(int(r.n_pass) for r in results)
-    out.n_total, out.n_tries = n_total, n_tries
-    out.n_escalated = sum(int(r.n_escalated) for r in results)
-    return out
+    processed all their points: heget_xsec_combine (the sums combined with
+    TwoSum and rounded once, counts added, sigma and its error recomputed
+    with the formulas of heget_xsec)."""
+    return H.heget_xsec_combine(list(results), sampler_kind)
 
 
 def allreduce_result(res: H.heget_xsec_result, sampler_kind: int, group=None) -> H.heget_xsec_result:
@@ -91,21 +59,13 @@ def allreduce_result(res: H.heget_xsec_result, sampler_kind: int, group=None) ->
 
 def combine_hists(parts) -> np.ndarray:
     """Histograms of disjoint point shards (heget_hist outputs: for every bin
-    of every spec, sum w and sum w^2), in the given order: each entry
-    combined with TwoSum across the shards and rounded once."""
+    of every spec, sum w and sum w^2), in the given order: heget_hist_combine
+    (each entry combined with TwoSum across the shards and rounded once).
+    ValueError for arrays of different layouts."""
     arrs = [np.asarray(p, dtype=np.float64).ravel() for p in parts]
-    if not arrs:
-        raise ValueError("no histograms to combine")
-    hi = np.zeros_like(arrs[0])
-    lo = np.zeros_like(arrs[0])
-    for a in arrs:
-        if a.shape != hi.shape:
-            raise ValueError("histograms of different layouts")
-        s = hi + a
-        bb = s - hi
-        lo += (hi - (s - bb)) + (a - bb)
-        hi = s
-    return hi + lo
+    if not arrs or any(a.shape != arrs[0].shape for a in arrs):
+        raise ValueError("histograms of different layouts (or none)")
+    return H.heget_hist_combine(arrs)
 
 
 def allreduce_hist(hist, group=None) -> np.ndarray:

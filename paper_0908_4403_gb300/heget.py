@@ -134,6 +134,8 @@ SIGNATURES = {
     "heget_xsec_noalloc": (I32, [I32, I32, U64, I64, I64, C.POINTER(heget_sampler), C.POINTER(heget_params),
                                  I32, P, P]),
     "heget_sum": (I32, [P, P, I64, P, P]),
+    "heget_xsec_combine": (I32, [C.POINTER(heget_xsec_result), I32, I32, C.POINTER(heget_xsec_result)]),
+    "heget_hist_combine": (I32, [C.POINTER(C.c_void_p), I32, I64, P]),
     "heget_server_start": (I32, [P, C.POINTER(heget_server_cfg), C.POINTER(P)]),
     "heget_submit": (I32, [P, C.POINTER(heget_request), C.POINTER(U64)]),
     "heget_poll": (I32, [P, U64, C.POINTER(heget_result)]),
@@ -408,6 +410,28 @@ def heget_xsec_noalloc(device, n, seed, i0, N, sampler, precision, result_dev, p
     pp = C.byref(params) if params is not None else None
     _check(load().heget_xsec_noalloc(device, n, seed, i0, N, C.byref(sampler), pp, precision, _ptr(result_dev),
                                      _stream(stream)))
+
+
+def heget_xsec_combine(parts, sampler_kind) -> heget_xsec_result:
+    """The result of disjoint point shards (host structs, in order) merged as
+    one call's (host arithmetic in the library; no GPU needed)."""
+    arr = (heget_xsec_result * max(1, len(parts)))(*parts)
+    out = heget_xsec_result()
+    _check(load().heget_xsec_combine(arr, len(parts), sampler_kind, C.byref(out)))
+    return out
+
+
+def heget_hist_combine(parts):
+    """Element-wise TwoSum combination of equal-length host float64 arrays
+    (numpy), in order; returns a new numpy array."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(p, dtype=np.float64).ravel() for p in parts]
+    if not arrs or any(a.size != arrs[0].size for a in arrs):
+        raise HegetError(HEGET_EINVAL, "histograms of different layouts (or none)")
+    out = np.empty(arrs[0].size)
+    ptrs = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    _check(load().heget_hist_combine(ptrs, len(arrs), out.size, out.ctypes.data_as(C.c_void_p)))
+    return out
 
 
 def heget_sum(ctx, x, N, out_dev, stream=None):

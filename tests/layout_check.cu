@@ -84,8 +84,9 @@ static void check_prefixes() {
 }
 
 // lane layout of a shape: every (group, point slot, helicity bits) once per
-// block, groups warp-aligned, prefixes shared out evenly where the block's
-// default allows it
+// block, groups warp-aligned, units of work shared out evenly where the
+// block's default allows it; pair units decode to every pair p < q once and
+// spread a lane's bits over the other photons
 template <class R, int N, int BLOCK>
 static void check_shape(bool even) {
     using SH = DefaultShape<R, N, BLOCK>;
@@ -93,6 +94,25 @@ static void check_shape(bool even) {
     CHECK(SH::G * S::P * S::NSL == BLOCK, "n=%d block %d: lanes do not tile the block", N, BLOCK);
     CHECK(SH::G == 1 || S::GL % 32 == 0, "n=%d block %d: group of %d lanes", N, BLOCK, S::GL);
     if (even) CHECK(S::NPRE % SH::G == 0, "n=%d block %d: %d prefixes over %d groups", N, BLOCK, S::NPRE, SH::G);
+    if (S::PAIRS) {
+        int u = 0;
+        for (int p = 0; p < N; ++p)
+            for (int q = p + 1; q < N; ++q, ++u) {
+                int a, b;
+                pair_of_unit<N>(u, a, b);
+                CHECK(a == p && b == q, "n=%d unit %d -> (%d, %d), expected (%d, %d)", N, u, a, b, p, q);
+                for (unsigned hl = 0; hl < (1u << (N - 2)); ++hl) {
+                    const unsigned h = spread_pair_bits(hl, p, q);
+                    // the other photons' bits in order, zeros at p and q
+                    unsigned back = 0;
+                    int k = 0;
+                    for (int i = 0; i < N; ++i)
+                        if (i != p && i != q) back |= ((h >> i) & 1u) << k++;
+                    CHECK(!((h >> p) & 1u) && !((h >> q) & 1u) && back == hl, "n=%d spread (%d, %d) %u", N, p, q, hl);
+                }
+            }
+        CHECK(u == S::NPRE, "n=%d: %d pair units", N, u);
+    }
 }
 
 static size_t resident_blocks(size_t smem_per_block) {
@@ -108,13 +128,14 @@ int main() {
     check_prefixes<7>();
     check_prefixes<8>();
     check_shape<float, 5, 256>(true);
+    check_shape<double, 8, 256>(true);
     check_shape<float, 6, 160>(true);
     check_shape<float, 6, 256>(false);
     check_shape<float, 7, 224>(true);
     check_shape<float, 7, 256>(false);
     check_shape<float, 8, 256>(true);
     check_pair_columns<float, 4, 0, 1, 256>();
-    check_pair_columns<float, 5, 2, 4, 256>();
+    check_pair_columns<float, 5, 0, 1, 256>();
     check_pair_columns<float, 6, 2, 5, 160>();
     check_pair_columns<float, 6, 2, 8, 256>();
     check_pair_columns<float, 7, 2, 7, 224>();

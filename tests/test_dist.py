@@ -123,3 +123,14 @@ def test_gloo_allreduce_gives_every_rank_the_single_process_result(oracle, tmp_p
         assert np.array_equal(h.view(np.uint64), hs[0].view(np.uint64))   # same bits on every rank
     ref_h = D.combine_hists([_shard_hist(oracle, n, N, world, r) for r in range(world)])
     assert np.array_equal(hs[0], ref_h)
+
+
+def test_combine_refusals():
+    """The library refuses an unknown sampler kind and histograms of different
+    layouts; an empty combination is the empty result."""
+    with pytest.raises(H.HegetError):
+        H.heget_xsec_combine([H.heget_xsec_result()], 7)
+    empty = D.combine([], H.HEGET_SAMPLER_FIXED)
+    assert empty.n_total == 0 and empty.sigma_fb == 0.0 and empty.err_fb == 0.0
+    with pytest.raises(ValueError):
+        D.combine_hists([np.zeros(3), np.zeros(4)])

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 SEED = 0x090844030000D000
 # (n, sampler, points, sampled block length, FP64 checked too)
 FULL = [(2, "fixed", 65536, 64, True), (4, "toy", 1 << 20, 64, True), (6, "toy", 1 << 20, 24, True),
-        (8, "uniform", 65536, 2, False)]
+        (8, "uniform", 65536, 8, True)]
 
 
 def _samplers(H, O, kind):

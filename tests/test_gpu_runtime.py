@@ -53,9 +53,10 @@ def test_batch_alone_equals_in_mix_and_matches_single_runs(heget_lib, gpu):
         assert got.n_total == ref.n_total == r["N"]
         assert got.n_pass == ref.n_pass and got.n_tries == ref.n_tries
         if r["N"]:
-            # FP64: the same arithmetic in another tile order; FP32 at n <= 4: heget_xsec_async runs the
-            # warp-specialised kernel, whose FP32 rounding differs per point (~1e-7) from the tile kernel
-            rel = 1e-12 if r["precision"] == 64 else 1e-7
+            # FP64: the same arithmetic in another tile order; FP32: heget_xsec_async runs the
+            # warp-specialised kernel (n <= 5) or a tile kernel of another block size (n = 6, 7), whose
+            # sums over orderings run in another order: per-point FP32 rounding differences (~1e-6)
+            rel = 1e-12 if r["precision"] == 64 else 1e-5
             assert got.sum_w == pytest.approx(ref.sum_w, rel=rel, abs=0)
             assert got.sigma_fb == pytest.approx(ref.sigma_fb, rel=rel, abs=0)
 
