@@ -499,11 +499,13 @@ int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
  * heget_xsec_async; params (host, may be NULL for the defaults) replaces the
  * context's parameters; `device` selects the GPU.
  *
- * Limit: a call needs one partial per block of its launch; if that exceeds
- * 4096 the call fails with HEGET_EINVAL and a message giving the largest N
- * for this n and precision.  FP32 at n <= 4 launches one resident wave of
- * blocks and has no limit; otherwise N may be at most 4096 x the xsec tile
- * (for example 131,072 points at n = 6 and 16,384 at n = 8 in FP32).
+ * It launches what heget_xsec_async launches by default (prefix tree), so
+ * the results are the same bits.  Limit: a call needs one partial per block
+ * of its launch; if that exceeds 4096 the call fails with HEGET_EINVAL and a
+ * message giving the largest N for this n and precision.  FP32 at n <= 6
+ * launches one resident wave of blocks and has no limit; otherwise N may be
+ * at most 4096 x the default xsec tile (for example 32,768 points at n = 7
+ * and 16,384 at n = 8 in FP32, 524,288 at n <= 4 in FP64).
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) and keeps it; make that first call before any
  * stream capture.  The address belongs to the device's primary context:

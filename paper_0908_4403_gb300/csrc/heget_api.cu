@@ -241,8 +241,8 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
     if (L->ws) {
         // warp-specialised: fixed stage size, one resident wave of blocks that
         // each pipeline many stages
-        L->block = kWsConsumers + ws_stage(n);
-        L->tile = ws_stage(n);
+        L->block = ws_consumers(n, alg) + ws_stage(n, alg);
+        L->tile = ws_stage(n, alg);
         const int e = alg == kAlgSubset ? occupancy_ws_alg<kAlgSubset>(n, &bpsm, &smem)
                                         : occupancy_ws_alg<kAlgTree>(n, &bpsm, &smem);
         if (e) return e;
@@ -1047,9 +1047,10 @@ extern "C" int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, 
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     AmpLaunch L;
-    // warp-specialised only up to n = 4 (one resident wave, any N); above, the
-    // tile kernel with its default tile, whose grid bounds N
-    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true, n <= 4 ? 0 : default_tile(n, true))))
+    // the default launch of heget_xsec_async (the tree): the warp-specialised
+    // kernel in FP32 up to n = 6 (one resident wave, any N), else the tile
+    // kernel with its default tile, whose grid bounds N
+    if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true, 0)))
         return cuda_fail((cudaError_t)r, "occupancy");
     if (N > 0 && L.grid > kNoAllocMaxBlocks)
         return fail(HEGET_EINVAL,

@@ -622,14 +622,15 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 //
 // GB300 runs FP64 at ~1/64 of the FP32 rate and with long latency, so the FP64
 // event generation (RAMBO, cuts, denominators) costs more than the FP32
-// amplitudes at small n (and at every n with the subset recursion) and needs
-// many events in flight while the amplitudes run.  Each block therefore splits into
-// roles that run concurrently:
-//   warps 0..7  (256 threads): consumers -- the amplitude rounds of the tree,
-//               and the sampler draws of the stage two ahead;
-//   warps 8..   (ws_stage(n) threads): producers -- one event per thread per
-//               stage from its draws: the FP64 rest (sqrt(s-hat), RAMBO, cuts,
-//               records).
+// amplitudes at small n (and at every n with the subset recursion), and at
+// n = 6 still about half of them, and needs many events in flight while the
+// amplitudes run.  Each block therefore splits into roles that run
+// concurrently:
+//   consumers (ws_consumers(n, alg) threads, the first warps): the amplitude
+//               rounds, and the sampler draws of the stage two ahead;
+//   producers (ws_stage(n, alg) threads, the last warps): one event per
+//               thread per stage from its draws: the FP64 rest (sqrt(s-hat),
+//               RAMBO, cuts, records).
 // The sampler (the toy PDF's rejection loops) is integer and FP32 work whose
 // iteration counts differ from lane to lane; run on the producers it would
 // idle the FP64 pipe, on the consumers it fills their waits.
@@ -642,21 +643,24 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 // roles split),
 // while the consumers' own rounds synchronise on barrier kBarRounds.  Every
 // thread of both roles runs the same number of stages, so each barrier
-// instance collects exactly 256 + ws_stage(n) arrivals.  A block walks tiles
+// instance collects exactly ws_consumers + ws_stage arrivals.  A block walks tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the grid is sized to the resident
 // blocks so that each block pipelines many stages.
 // ---------------------------------------------------------------------------
-constexpr int kWsConsumers = 256;
 constexpr int kBarRounds = 1, kBarFull = 2, kBarEmpty = 4;   // named barrier ids (2,3 / 4,5)
 constexpr int kBarProducers = 6;                              // producers' stage compaction
 
+// Consumer threads: 256, or 160 for the FP32 tree at n = 6 (five pair-unit
+// slots of two points share out the 15 units evenly, and two blocks of 224
+// threads fit an SM at 144 registers).
+__host__ __device__ constexpr int ws_consumers(int n, int alg) { return n == 6 && alg == 0 ? 160 : 256; }
 // Points per stage (= producer threads, a multiple of 32): as many as the
 // shared memory of the ring, the producers' staging and the round tables
-// allows at two (n <= 6) or one (n >= 7) resident blocks per SM.
-#ifndef HEGET_WS_STAGE_6
-#define HEGET_WS_STAGE_6 32
-#endif
-__host__ __device__ constexpr int ws_stage(int n) { return n <= 4 ? 128 : n == 5 ? 64 : n == 6 ? HEGET_WS_STAGE_6 : 32; }
+// allows at two (n <= 6) or one (n >= 7) resident blocks per SM; 64 for the
+// tree at n = 6, whose FP64 generation then spans two warps.
+__host__ __device__ constexpr int ws_stage(int n, int alg) {
+    return n <= 4 ? 128 : n == 5 ? 64 : n == 6 && alg == 0 ? 64 : 32;
+}
 
 __device__ __forceinline__ void named_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -665,34 +669,38 @@ __device__ __forceinline__ void named_arrive(int id, int count) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <class R, int N, int ALG>
+// Shared-memory layout of the warp-specialised kernel of algorithm ALG with
+// table layout TAB: round tables, the double-buffered ring of records, the
+// producers' staging.
+template <class R, int N, int ALG, int TAB>
 __host__ __device__ constexpr size_t ws_recs_offset() {
-    return table_bytes<R, N, kWsConsumers, ALG>();
+    return table_bytes<R, N, ws_consumers(N, ALG), TAB>();
 }
-template <class R, int N, int ALG>
+template <class R, int N, int ALG, int TAB>
 __host__ __device__ constexpr size_t ws_stage_offset() {
-    return ws_recs_offset<R, N, ALG>() + 2 * align16((size_t)ws_stage(N) * sizeof(PointRec<R, N>));
+    return ws_recs_offset<R, N, ALG, TAB>() + 2 * align16((size_t)ws_stage(N, ALG) * sizeof(PointRec<R, N>));
 }
-template <class R, int N, int ALG>
+template <class R, int N, int ALG, int TAB = ALG>
 __host__ __device__ constexpr size_t ws_smem_bytes() {
-    return ws_stage_offset<R, N, ALG>() + align16((size_t)ws_stage(N) * N * kMomSlots * sizeof(double));
+    return ws_stage_offset<R, N, ALG, TAB>() + align16((size_t)ws_stage(N, ALG) * N * kMomSlots * sizeof(double));
 }
-template <class R, int N, int ALG>
+template <class R, int N, int ALG, int TAB>
 __host__ __device__ constexpr int ws_min_blocks() {
-    return ws_smem_bytes<R, N, ALG>() <= 113 * 1024 ? 2 : 1;
+    return ws_smem_bytes<R, N, ALG, TAB>() <= 113 * 1024 ? 2 : 1;
 }
 
 template <class R, int N, bool ESC, int ALG>
-__global__ void __launch_bounds__(kWsConsumers + ws_stage(N), ws_min_blocks<R, N, table_alg<ALG, ESC>()>())
+__global__ void __launch_bounds__(ws_consumers(N, ALG) + ws_stage(N, ALG), ws_min_blocks<R, N, ALG, table_alg<ALG, ESC>()>())
 xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph,
                Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
-    constexpr int kWsStage = ws_stage(N);
+    constexpr int kWsConsumers = ws_consumers(N, ALG);
+    constexpr int kWsStage = ws_stage(N, ALG);
     constexpr int kWsThreads = kWsConsumers + kWsStage;
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int TAB = table_alg<ALG, ESC>();
-    PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N, TAB>());
+    PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N, ALG, TAB>());
     constexpr size_t ring_stride = align16((size_t)kWsStage * sizeof(PointRec<R, N>)) / sizeof(PointRec<R, N>);
-    double* stage = reinterpret_cast<double*>(smem + ws_stage_offset<R, N, TAB>());
+    double* stage = reinterpret_cast<double*>(smem + ws_stage_offset<R, N, ALG, TAB>());
     __shared__ int s_cnt[kWsStage / 32];
     __shared__ int stage_n[2];   // records (cut-passing points) of the stage in each ring slot
     __shared__ SampleDraw s_draw[2][kWsStage];   // sampler draws of the stage in each slot
@@ -825,11 +833,8 @@ struct AmpLaunch {
 // generation is a large share of the work: n <= 5 with the tree, every n with
 // the subset recursion.  The tree at n >= 6 spends nearly all its time in the
 // amplitudes and runs faster on the tile kernel, at more blocks per SM.
-#ifndef HEGET_WS_TREE_N6
-#define HEGET_WS_TREE_N6 0
-#endif
 constexpr bool use_ws(int n, int precision, bool xsec, int alg) {
-    return xsec && precision == HEGET_FP32 && (n <= 5 || (n == 6 && HEGET_WS_TREE_N6) || alg == kAlgSubset);
+    return xsec && precision == HEGET_FP32 && (n <= 6 || alg == kAlgSubset);
 }
 
 // Per-algorithm launchers over n = 2..8 (ALG = kAlgTree or kAlgSubset),

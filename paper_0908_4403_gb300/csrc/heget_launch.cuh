@@ -31,7 +31,7 @@ static int launch_amp2_n(const double* mom, long long npts, const uint32_t* mask
 // n <= 5 with the tree, every n with the subset recursion.
 template <class R, int N, int ALG>
 constexpr bool has_ws() {
-    return sizeof(R) == sizeof(float) && (N <= 5 || (N == 6 && HEGET_WS_TREE_N6) || ALG == kAlgSubset);
+    return sizeof(R) == sizeof(float) && (N <= 6 || ALG == kAlgSubset);
 }
 
 template <class R, int N, int ALG>
@@ -40,10 +40,11 @@ static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const Samp
     if constexpr (has_ws<R, N, ALG>()) {
         if (L.ws) {
             auto k = esc.idx ? xsec_ws_kernel<R, N, true, ALG> : xsec_ws_kernel<R, N, false, ALG>;
-            const size_t smem = esc.idx ? ws_smem_bytes<R, N, table_alg<ALG, true>()>() : ws_smem_bytes<R, N, ALG>();
+            const size_t smem = esc.idx ? ws_smem_bytes<R, N, ALG, table_alg<ALG, true>()>() : ws_smem_bytes<R, N, ALG>();
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return (int)e;
-            k<<<L.grid, kWsConsumers + ws_stage(N), smem, st>>>(seed, i0, npts, S, ph, partials, w_out, esc);
+            k<<<L.grid, ws_consumers(N, ALG) + ws_stage(N, ALG), smem, st>>>(seed, i0, npts, S, ph, partials, w_out,
+                                                                             esc);
             return (int)cudaGetLastError();
         }
     } else {
@@ -82,7 +83,7 @@ static int occupancy_ws_n(int* blocks_per_sm, size_t* smem_out) {
         auto k = xsec_ws_kernel<float, N, false, ALG>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
-        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kWsConsumers + ws_stage(N),
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, ws_consumers(N, ALG) + ws_stage(N, ALG),
                                                                  smem);
     } else {
         return (int)cudaErrorInvalidValue;

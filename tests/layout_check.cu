@@ -144,15 +144,18 @@ int main() {
     check_pair_columns<double, 4, 0, 1, 256>();
     check_pair_columns<double, 8, 0, 1, 256>();
     // occupancy the tuned launch shapes rely on
-    const size_t draws4 = 2 * ws_stage(4) * sizeof(SampleDraw) + 256;
+    const size_t draws4 = 2 * ws_stage(4, kAlgTree) * sizeof(SampleDraw) + 256;
     const size_t ws4 = ws_smem_bytes<float, 4, kAlgTree>() + draws4;
     CHECK(resident_blocks(ws4) >= 2, "warp-specialised n=4 tree: %zu bytes, fewer than 2 blocks per SM", ws4);
     const size_t ws4s = ws_smem_bytes<float, 4, kAlgSubset>() + draws4;
     CHECK(resident_blocks(ws4s) >= 2, "warp-specialised n=4 subset: %zu bytes, fewer than 2 blocks per SM", ws4s);
-    const size_t ws4e = ws_smem_bytes<float, 4, table_alg<kAlgTree, true>()>() + draws4;
+    const size_t ws4e = ws_smem_bytes<float, 4, kAlgTree, table_alg<kAlgTree, true>()>() + draws4;
     CHECK(resident_blocks(ws4e) >= 2, "warp-specialised n=4 tree with escalation: %zu bytes", ws4e);
-    const size_t ws5 = ws_smem_bytes<float, 5, kAlgTree>() + 2 * ws_stage(5) * sizeof(SampleDraw) + 256;
+    const size_t ws5 = ws_smem_bytes<float, 5, kAlgTree>() + 2 * ws_stage(5, kAlgTree) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws5) >= 2, "warp-specialised n=5 tree: %zu bytes", ws5);
+    const size_t ws6 = ws_smem_bytes<float, 6, kAlgTree>() + 2 * ws_stage(6, kAlgTree) * sizeof(SampleDraw) + 256;
+    CHECK(resident_blocks(ws6) >= 2, "warp-specialised n=6 tree: %zu bytes", ws6);
+    check_shape<float, 6, ws_consumers(6, kAlgTree)>(true);
     const size_t t6 = xsec_smem_bytes<float, 6, 160, kAlgTree>(32);
     CHECK(resident_blocks(t6) >= 3, "tile n=6 tree (160 threads): %zu bytes, fewer than 3 blocks per SM", t6);
     const size_t t7 = xsec_smem_bytes<float, 7, 224, kAlgTree>(8);

@@ -19,7 +19,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-XSEC_TILE_N6 = 32          # default xsec tile at n = 6 (points per block)
+XSEC_TILE_N7 = 8           # default xsec tile at n = 7 (points per block of the tile kernel)
 NOALLOC_MAX_BLOCKS = 4096  # the static scratch holds this many block partials
 
 
@@ -46,8 +46,8 @@ def _same(a, b):
     assert math.isfinite(a.sigma_fb) and a.sigma_fb > 0
 
 
-@pytest.mark.parametrize("n,N,precision", [(4, 100_003, 32), (3, 20_000, 64),
-                                           (6, NOALLOC_MAX_BLOCKS * XSEC_TILE_N6, 32)])
+@pytest.mark.parametrize("n,N,precision", [(4, 100_003, 32), (3, 20_000, 64), (6, 60_001, 32),
+                                           (7, NOALLOC_MAX_BLOCKS * XSEC_TILE_N7, 32)])
 def test_noalloc_matches_xsec_async_twice(heget_lib, gpu, n, N, precision):
     H = heget_lib
     sampler = H.sampler_toy_pdf()
@@ -67,8 +67,8 @@ def test_noalloc_refuses_oversized_calls(heget_lib, gpu):
     st = lib.heget_xsec_noalloc(0, 8, 1, 0, 1 << 20, ctypes.byref(s), None, 32, res.data_ptr(), None)
     assert st == H.HEGET_EINVAL
     assert b"no-allocation path" in lib.heget_last_error()
-    # one point past the largest accepted size at n = 6
-    st = lib.heget_xsec_noalloc(0, 6, 1, 0, NOALLOC_MAX_BLOCKS * XSEC_TILE_N6 + 1, ctypes.byref(s), None, 32,
+    # one point past the largest accepted size at n = 7
+    st = lib.heget_xsec_noalloc(0, 7, 1, 0, NOALLOC_MAX_BLOCKS * XSEC_TILE_N7 + 1, ctypes.byref(s), None, 32,
                                 res.data_ptr(), None)
     assert st == H.HEGET_EINVAL
 
