@@ -531,7 +531,18 @@ def config_rows(H, ctx, stream, peak32, peak64, flush):
         OS = {"fixed": lambda a: O.fixed(a[0]), "toy": lambda a: O.toy_pdf(),
               "uniform": lambda a: O.uniform(a[0], a[1])}[smp[0]](smp[1:])
         H.heget_set_params(ctx, pt_min=cut[0], eta_max=cut[1], dr_min=cut[2])
+        tuned = None
+        if key == "cfg3_n6":
+            # the autotuner's choice of launch shape and tile for this workload (kept in the context)
+            shape, tile, tms = H.heget_autotune_shape(ctx, n, H.HEGET_FP32, 1 << 18)
+            threads, hrows, groups = H.heget_shape_info(n, H.HEGET_FP32, shape)
+            tuned = {"shape": shape, "tile": tile, "probe_ms": tms, "probe_points": 1 << 18,
+                     "shape_info": "the default launch shape" if shape == 0 else
+                     f"tile kernel: {threads} threads, {hrows} helicity rows per lane, {groups} subtree groups"}
         ms32, k32, ev32 = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, steps, stream, flush=flush, detail=True)
+        if tuned:
+            H.heget_set_shape(ctx, n, H.HEGET_FP32, 0)
+            H.heget_set_tile(ctx, n, H.HEGET_FP32, 1, 0)
         ms64, k64, ev64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 2 if n < 8 else 1, stream, flush=flush,
                                     detail=True)
         H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
@@ -557,7 +568,7 @@ def config_rows(H, ctx, stream, peak32, peak64, flush):
         rows[key] = {
             "workload": desc, "n": n, "points": N, "pass_fraction": ev32 / N,
             "fp32": {"points_per_s": N / (ms32 * 1e-3), "evaluated_per_s": ev32 / (ms32 * 1e-3),
-                     "ms_per_step": ms32, "kernel_ms": k32, "steps": steps,
+                     "ms_per_step": ms32, "kernel_ms": k32, "steps": steps, "autotuned": tuned,
                      "flops_per_evaluated_point": tf,
                      "frac_of_fp32_peak": tf * ev32 / (k32 * 1e-3) / (FP32_PEAK * 1e12),
                      "frac_of_measured_fp32_peak": tf * ev32 / (k32 * 1e-3) / (peak32 * 1e12),
@@ -589,6 +600,8 @@ def main():
     ap.add_argument("--ref-points", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-cfg5", action="store_true",
+                    help="also the serving mix as specified (2,000 unscaled requests; a few minutes)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--n", type=int, default=N_PHOTONS, help="photons (profiling of smaller cases)")
     ap.add_argument("--points", type=int, default=POINTS, help="points per step per GPU")
@@ -720,7 +733,8 @@ def main():
     if rank == 0 and ws == 1 and not args.no_serving:
         serving = serving_section(H, ctx)
         serving["subset_recursion"] = serving_section(H, ctx, alg=H.HEGET_ALG_SUBSET)
-        serving["cfg5_as_specified"] = serving_cfg5(H, ctx)
+        if args.serving_cfg5:
+            serving["cfg5_as_specified"] = serving_cfg5(H, ctx)
 
     configs = None
     if rank == 0 and ws == 1 and not args.no_configs:

@@ -374,19 +374,52 @@ int heget_amp2_escalated(heget_ctx* ctx, void* stream, int64_t* count);
 int heget_set_tile(heget_ctx* ctx, int n, int precision, int kind, int tile);
 int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind);
 
+/* CUDA graphs for the mixed-n launches (A9): with on = 1, heget_xsec_batch
+ * and servers started afterwards on this context launch each precision's
+ * work-list kernel and finalisation as a CUDA graph per launch-shape bucket
+ * (the same item and request counts, grid and shared memory), captured on
+ * first use and replayed when the bucket recurs; the results are the same
+ * bits as direct launches.  At most 32 buckets are kept (the oldest goes
+ * first); growing the batch workspace drops them.  heget_get_graphs returns
+ * the setting (-1 for a NULL context) and the numbers of captures and
+ * replays so far (either pointer may be NULL).  EINVAL for a NULL context or
+ * `on` not 0/1. */
+int heget_set_graphs(heget_ctx* ctx, int on);
+int heget_get_graphs(const heget_ctx* ctx, int64_t* captures, int64_t* replays);
+
+/* Tile-kernel shape of the fused cross section (heget_xsec*, graphs) for n
+ * photons at `precision`: 0 (the default: the warp-specialised kernel where it
+ * applies, else the tile kernel's default shape) or, for the FP32 tree at
+ * n = 6..8, shapes 1..3 -- tile kernels of other thread counts, helicity
+ * configurations per lane (rows) and subtree groups (the launch-shape knobs of
+ * the paper's Sec. 6.1 scan, as far as they exist on this design).
+ * heget_shape_info reports a shape's threads per block, rows per lane and
+ * groups (all 0 for shape 0).  Shapes apply to the prefix tree; the subset
+ * recursion and FP32 escalation run shape 0.  EINVAL for a NULL context, bad
+ * n or precision, or a shape that does not exist there; heget_get_shape
+ * returns -1 for bad arguments. */
+int heget_set_shape(heget_ctx* ctx, int n, int precision, int shape);
+int heget_get_shape(const heget_ctx* ctx, int n, int precision);
+int heget_shape_info(int n, int precision, int shape, int* threads,
+                     int* rows_per_lane, int* groups);
+
 /* Autotuner (this library's; the paper scans registers x block size by hand,
  * Sec. 6.1 / Fig. 3): times heget_amp2 (kind 0) or heget_xsec (kind 1) for
  * n photons at `precision` on `probe_points` synthetic points for every
- * candidate tile (the default shape -- warp-specialised where it applies --
- * and 256/2^n x 2^k up to 1024), keeps the fastest in the context and returns
- * it (*best_tile, 0 = default) with its time (*best_ms).  Allocates and frees
- * temporary probe buffers; synchronizes.  heget_autotune_save /
- * heget_autotune_load store and restore the context's tuned tiles in a text
- * file keyed by GPU name (other GPUs' lines are kept).  EINVAL for bad n,
- * precision, kind, probe_points < 1 or a path that cannot be opened; ECUDA
- * if no candidate ran (the context keeps its previous tile). */
+ * candidate launch -- for kind 1 every shape (heget_set_shape) with its
+ * default tile and the tiles 256/2^n x 2^k up to 1024; for kind 0 the tiles
+ * -- keeps the fastest in the context and returns it (*best_tile, 0 =
+ * default; *best_shape, may be NULL) with its time (*best_ms).  Allocates and
+ * frees temporary probe buffers; synchronizes.  heget_autotune_save /
+ * heget_autotune_load store and restore the context's tuned tiles and shapes
+ * in a text file keyed by GPU name (other GPUs' lines are kept).  EINVAL for
+ * bad n, precision, kind, probe_points < 1 or a path that cannot be opened;
+ * ECUDA if no candidate ran (the context keeps its previous tile and shape). */
 int heget_autotune(heget_ctx* ctx, int n, int precision, int kind,
                    int64_t probe_points, int* best_tile, double* best_ms);
+int heget_autotune_shape(heget_ctx* ctx, int n, int precision,
+                         int64_t probe_points, int* best_shape, int* best_tile,
+                         double* best_ms);
 int heget_autotune_save(const heget_ctx* ctx, const char* path);
 int heget_autotune_load(heget_ctx* ctx, const char* path);
 
@@ -502,10 +535,10 @@ int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
  * It launches what heget_xsec_async launches by default (prefix tree), so
  * the results are the same bits.  Limit: a call needs one partial per block
  * of its launch; if that exceeds 4096 the call fails with HEGET_EINVAL and a
- * message giving the largest N for this n and precision.  FP32 at n <= 6
+ * message giving the largest N for this n and precision.  FP32 at n <= 5
  * launches one resident wave of blocks and has no limit; otherwise N may be
- * at most 4096 x the default xsec tile (for example 32,768 points at n = 7
- * and 16,384 at n = 8 in FP32, 524,288 at n <= 4 in FP64).
+ * at most 4096 x the default xsec tile (for example 262,144 points at n = 6,
+ * 131,072 at n = 7 and 32,768 at n = 8 in FP32, 524,288 at n <= 4 in FP64).
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) and keeps it; make that first call before any
  * stream capture.  The address belongs to the device's primary context:

@@ -226,16 +226,23 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int iters, double* __rest
 int default_tile(int n, bool xsec) {
     // Points per block tile.  amp2: four rounds of block/2^n points (keeps the
     // staged rows and records small); xsec: 128 points (half the threads
-    // generate, three blocks fit an SM) up to n = 4, then small tiles so that
-    // large-n grids still cover every SM many times.
+    // generate, three blocks fit an SM) up to n = 4, 64 at n = 5, 6 (the
+    // generation spans two warps), then smaller tiles so that large-n grids
+    // still cover every SM many times (a GB300 sweep of tiles and shapes).
     static const int amp2_tile[9] = {0, 0, 256, 128, 64, 32, 16, 8, 4};
-    static const int xsec_tile[9] = {0, 0, 128, 128, 128, 64, 32, 8, 4};
+    static const int xsec_tile[9] = {0, 0, 128, 128, 128, 64, 64, 32, 8};
     return xsec ? xsec_tile[n] : amp2_tile[n];
 }
 
+int xsec_shape_count(int n, int precision, int alg) {
+    return precision == HEGET_FP32 && alg == kAlgTree && n >= 6 ? 4 : 1;
+}
+
 int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile,
-                       int alg) {
-    L->ws = use_ws(n, precision, xsec, alg) && tile <= 0;   // an explicit tile selects the plain kernel
+                       int alg, int shape) {
+    L->shape = xsec && shape > 0 && shape < xsec_shape_count(n, precision, alg) ? shape : 0;
+    // an explicit tile or shape selects the tile kernel
+    L->ws = use_ws(n, precision, xsec, alg) && tile <= 0 && L->shape == 0;
     int bpsm = 1;
     size_t smem = 0;
     if (L->ws) {
@@ -256,11 +263,12 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
     // xsec_block(): the FP32 tree's tile kernel at n = 6, 7 runs 160 / 224 threads
     L->block = xsec && precision == HEGET_FP32 && alg != kAlgSubset && (n == 6 || n == 7) ? (n == 6 ? 160 : 224)
                                                                                         : kBlockThreads;
+    if (L->shape > 0) L->block = tree_tile_shape(n, L->shape).block;
     L->tile = tile > 0 ? tile : default_tile(n, xsec);
     const bool sub = alg == kAlgSubset;
     const int e = precision == HEGET_FP32
                       ? (sub ? occupancy_alg<float, kAlgSubset>(n, L->tile, &bpsm, &smem)
-                             : occupancy_alg<float, kAlgTree>(n, L->tile, &bpsm, &smem))
+                             : occupancy_alg<float, kAlgTree>(n, L->tile, &bpsm, &smem, L->shape))
                       : (sub ? occupancy_alg<double, kAlgSubset>(n, L->tile, &bpsm, &smem)
                              : occupancy_alg<double, kAlgTree>(n, L->tile, &bpsm, &smem));
     if (e) return e;
@@ -465,6 +473,7 @@ int heget_create(int device, heget_ctx** out) {
 void heget_destroy(heget_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
+    c->batch_graphs.release();
     if (c->batch_copied) cudaEventSynchronize(c->batch_copied), cudaEventDestroy(c->batch_copied);
     if (c->batch_host) cudaFreeHost(c->batch_host);
     if (c->batch_dev) cudaFree(c->batch_dev);
@@ -493,6 +502,58 @@ int heget_set_tile(heget_ctx* ctx, int n, int precision, int kind, int tile) {
         return fail(HEGET_EINVAL, "tile %d must be 0 or a multiple of %d up to 4096", tile, unit);
     ctx->tiles[kind][precision == HEGET_FP64][n] = tile;
     return HEGET_OK;
+}
+
+int heget_set_shape(heget_ctx* ctx, int n, int precision, int shape) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (n < kMinN || n > kMaxN) return fail(HEGET_EINVAL, "n = %d outside [2, 8]", n);
+    int r = check_precision(precision);
+    if (r) return r;
+    const int ns = xsec_shape_count(n, precision, kAlgTree);
+    if (shape < 0 || shape >= ns) return fail(HEGET_EINVAL, "shape %d: n = %d has shapes 0 .. %d", shape, n, ns - 1);
+    ctx->shapes[precision == HEGET_FP64][n] = shape;
+    return HEGET_OK;
+}
+
+int heget_get_shape(const heget_ctx* ctx, int n, int precision) {
+    if (!ctx || n < kMinN || n > kMaxN || (precision != HEGET_FP32 && precision != HEGET_FP64)) return -1;
+    return ctx->shapes[precision == HEGET_FP64][n];
+}
+
+int heget_shape_info(int n, int precision, int shape, int* threads, int* rows_per_lane, int* groups) {
+    if (!threads || !rows_per_lane || !groups) return fail(HEGET_EINVAL, "NULL argument");
+    if (n < kMinN || n > kMaxN) return fail(HEGET_EINVAL, "n = %d outside [2, 8]", n);
+    int r = check_precision(precision);
+    if (r) return r;
+    if (shape < 0 || shape >= xsec_shape_count(n, precision, kAlgTree))
+        return fail(HEGET_EINVAL, "no shape %d at n = %d", shape, n);
+    if (shape == 0) {   // the default: warp-specialised or the tile kernel's default
+        *threads = 0;
+        *rows_per_lane = 0;
+        *groups = 0;
+        return HEGET_OK;
+    }
+    const TileShape t = tree_tile_shape(n, shape);
+    *threads = t.block;
+    *rows_per_lane = 1 << t.hb;
+    *groups = t.g;
+    return HEGET_OK;
+}
+
+int heget_set_graphs(heget_ctx* ctx, int on) {
+    if (!ctx) return fail(HEGET_EINVAL, "context is NULL");
+    if (on != 0 && on != 1) return fail(HEGET_EINVAL, "graphs must be 0 or 1, got %d", on);
+    DeviceGuard g(ctx->device);
+    if (!on) ctx->batch_graphs.clear();
+    ctx->graphs = on;
+    return HEGET_OK;
+}
+
+int heget_get_graphs(const heget_ctx* ctx, int64_t* captures, int64_t* replays) {
+    if (!ctx) return -1;
+    if (captures) *captures = ctx->batch_graphs.captures;
+    if (replays) *replays = ctx->batch_graphs.replays;
+    return ctx->graphs;
 }
 
 int heget_set_algorithm(heget_ctx* ctx, int alg) {
@@ -714,7 +775,7 @@ int heget_xsec_launch(heget_ctx* ctx, int n, uint64_t seed, int64_t i0, int64_t 
     cudaStream_t st = (cudaStream_t)stream;
     AmpLaunch L;
     if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, ctx->num_sms, &L, true, ctx->tiles[1][precision == HEGET_FP64][n],
-                                ctx->alg)))
+                                ctx->alg, ctx->shapes[precision == HEGET_FP64][n])))
         return cuda_fail((cudaError_t)r, "occupancy");
     const Physics ph = physics_of(ctx, n);
     const SamplerArgs S = sampler_args(smp);
@@ -957,13 +1018,18 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
         if (r) return r;
         const size_t dcap = ctx->batch_cap;   // device buffer mirrors the pinned one
         if (!ctx->batch_dev || dcap > ctx->batch_dev_cap) {
+            ctx->batch_graphs.clear();   // their arguments point into the old buffers
             if (ctx->batch_dev) cudaFree(ctx->batch_dev);
             e = cudaMalloc(&ctx->batch_dev, dcap);
             if (e != cudaSuccess) return fail(HEGET_ENOMEM, "batch workspace: %s", cudaGetErrorString(e));
             ctx->batch_dev_cap = dcap;
         }
-        r = grow((void**)&ctx->batch_partials, &ctx->batch_partials_cap, items.size() * sizeof(Partial), false);
-        if (r) return r;
+        {
+            Partial* before = ctx->batch_partials;
+            r = grow((void**)&ctx->batch_partials, &ctx->batch_partials_cap, items.size() * sizeof(Partial), false);
+            if (r) return r;
+            if (before != ctx->batch_partials) ctx->batch_graphs.clear();   // (the request table points there)
+        }
         for (auto& b : br) {
             b.parts = ctx->batch_partials + b.pad;
             b.pad = 0;
@@ -977,11 +1043,23 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
         const BatchReq* reqs_d = reinterpret_cast<const BatchReq*>(ctx->batch_dev + items_bytes);
         const int nitems = (int)items.size();
         const int grid = std::max(1, std::min(nitems, 8 * ctx->num_sms));
-        r = prec == HEGET_FP32 ? launch_batch_f32(items_d, nitems, reqs_d, smem, grid, st)
-                               : launch_batch_f64(items_d, nitems, reqs_d, smem, grid, st);
+        const int nreq = (int)br.size();
+        auto launch = [&](cudaStream_t s2, bool set_attr) {
+            int rr = prec == HEGET_FP32 ? launch_batch_f32(items_d, nitems, reqs_d, smem, grid, s2, set_attr)
+                                        : launch_batch_f64(items_d, nitems, reqs_d, smem, grid, s2, set_attr);
+            if (!rr) rr = launch_batch_finalize(reqs_d, nreq, s2);
+            return rr;
+        };
+        if (ctx->graphs) {
+            // the kernel's shared-memory attribute is set outside the capture
+            r = prec == HEGET_FP32 ? prepare_batch_f32(smem) : prepare_batch_f64(smem);
+            if (!r)
+                r = ctx->batch_graphs.run(BatchGraphKey{prec, nitems, nreq, grid, smem, items_d, reqs_d, reqs_d}, st,
+                                          [&](cudaStream_t s2) { return launch(s2, false); });
+        } else {
+            r = launch(st, true);
+        }
         if (r) return cuda_fail((cudaError_t)r, "xsec_batch_kernel");
-        r = launch_batch_finalize(reqs_d, (int)br.size(), st);
-        if (r) return cuda_fail((cudaError_t)r, "finalize_batch_kernel");
         // the next precision's batch reuses the workspace: keep the order
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "heget_xsec_batch");
@@ -1048,7 +1126,7 @@ extern "C" int heget_xsec_noalloc(int device, int n, uint64_t seed, int64_t i0, 
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     AmpLaunch L;
     // the default launch of heget_xsec_async (the tree): the warp-specialised
-    // kernel in FP32 up to n = 6 (one resident wave, any N), else the tile
+    // kernel in FP32 up to n = 5 (one resident wave, any N), else the tile
     // kernel with its default tile, whose grid bounds N
     if ((r = default_amp_launch(n, precision, N > 0 ? N : 1, sms, &L, true, 0)))
         return cuda_fail((cudaError_t)r, "occupancy");

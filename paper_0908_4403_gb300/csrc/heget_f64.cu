@@ -13,9 +13,11 @@ int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* 
 }
 
 int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
-                     cudaStream_t st) {
-    return launch_batch_t<double>(items, nitems, reqs, smem, grid, st);
+                     cudaStream_t st, bool set_attr) {
+    return launch_batch_t<double>(items, nitems, reqs, smem, grid, st, set_attr);
 }
+
+int prepare_batch_f64(size_t smem) { return prepare_batch_t<double>(smem); }
 
 int launch_escalate_f64(int n, uint64_t seed, long long i0, const SamplerArgs& S, const Physics& ph, int tile,
                         const EscArgs& esc, Partial* out, double* w_out, int grid, cudaStream_t st) {

@@ -9,6 +9,7 @@
 
 #include "heget.h"
 #include "heget_common.cuh"
+#include "heget_graphcache.h"
 
 namespace heget {
 
@@ -47,6 +48,7 @@ struct heget_ctx {
     bool last_ws = false;             // it used the warp-specialised kernel
     bool last_esc = false;            // it launched the FP64 escalation kernel after it
     int tiles[2][2][heget::kMaxN + 1] = {};  // [amp2|xsec][fp32|fp64][n] tile overrides (0 = default)
+    int shapes[2][heget::kMaxN + 1] = {};    // [fp32|fp64][n] tile-kernel shape of the fused cross section
     int alg = 0;                      // ordering sum: HEGET_ALG_TREE or HEGET_ALG_SUBSET
     double esc_tau = 0.0;             // FP32 -> FP64 escalation threshold (0 = off)
     int hel_sample = 0;               // one sampled helicity per point (heget_set_helicity_sampling)
@@ -67,6 +69,8 @@ struct heget_ctx {
     heget::Partial* batch_partials = nullptr;
     size_t batch_partials_cap = 0;
     cudaEvent_t batch_copied = nullptr;    // staging may be rewritten once this has fired
+    int graphs = 0;                        // batch launches replay CUDA graphs per launch-shape bucket
+    heget::BatchGraphCache batch_graphs;
     // heget_hist: per-block partial histograms (grown on demand)
     double* hist_parts = nullptr;
     size_t hist_parts_cap = 0;

@@ -36,6 +36,33 @@ __host__ __device__ constexpr int tree_groups() {
 }
 template <class R, int N, int BLOCK>
 struct DefaultShape : ShapeOf<tree_hb<R, N, BLOCK>(), tree_groups<R, N, BLOCK>()> {};
+// (HB, G) given, or the default of the block (HB < 0)
+template <class R, int N, int BLOCK, int HB, int G>
+struct ShapeSel : ShapeOf<HB < 0 ? tree_hb<R, N, BLOCK>() : HB, HB < 0 ? tree_groups<R, N, BLOCK>() : G> {};
+
+// Tile-kernel shapes of the fused cross section that the autotuner searches
+// (the analogue of the paper's register x block-size scan, Sec. 6.1): shape
+// 0 is the default (the warp-specialised kernel where it applies, else the
+// tile kernel of xsec_block threads with DefaultShape); the FP32 tree from
+// n = 6 adds tile kernels of other block sizes, pair-unit slots and rows per
+// lane (threads, HB, G), HB = 0 being one configuration per lane.
+struct TileShape {
+    int block, hb, g;
+};
+template <class R, int N, int ALG>
+__host__ __device__ constexpr int num_tile_shapes() {
+    return sizeof(R) == sizeof(float) && ALG == kAlgTree && N >= 6 ? 4 : 1;
+}
+// shape k = 1..3 of the FP32 tree at n = 6..8 (k = 0: the default)
+__host__ __device__ constexpr TileShape tree_tile_shape(int n, int k) {
+    return n == 6 ? (k == 1 ? TileShape{96, 2, 3} : k == 2 ? TileShape{320, 2, 5} : TileShape{256, 0, 1})
+         : n == 7 ? (k == 1 ? TileShape{96, 2, 3} : k == 2 ? TileShape{128, 0, 1} : TileShape{256, 0, 1})
+                  : (k == 1 ? TileShape{128, 2, 2} : k == 2 ? TileShape{448, 2, 7} : TileShape{256, 0, 1});
+}
+template <class R, int N, int ALG>
+__host__ __device__ constexpr TileShape tile_shape(int k) {
+    return tree_tile_shape(N, k);
+}
 
 // Shared-memory table layouts: the tree's (kAlgTree), the subset
 // recursion's without (kAlgSubset) or with (kTabSubsetKappa) the arrays of
@@ -51,9 +78,9 @@ __host__ __device__ constexpr size_t ward_table_bytes() {
     if constexpr (BLOCK % (1 << N) == 0) return RoundTables<R, N, BLOCK>::bytes;
     else return 0;
 }
-template <class R, int N, int BLOCK, int TAB = kAlgAny>
+template <class R, int N, int BLOCK, int TAB = kAlgAny, int HB = -1, int G = -1>
 __host__ __device__ constexpr size_t table_bytes() {
-    using SH = DefaultShape<R, N, BLOCK>;
+    using SH = ShapeSel<R, N, BLOCK, HB, G>;
     constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = ward_table_bytes<R, N, BLOCK>();
     constexpr size_t c = SubsetTables<R, N, BLOCK>::bytes_core, ck = SubsetTables<R, N, BLOCK>::bytes;
     constexpr size_t ab = a > b ? a : b;
@@ -73,19 +100,19 @@ __host__ __device__ constexpr int table_alg() {
 // paper's method or the subset recursion, fixed per kernel by ALG, or (ALG =
 // kAlgAny) chosen by `alg`, uniform per launch.
 // kappa: also the condition bound recs[p].kap2 (FP32 escalation).
-template <class R, int N, int BLOCK, int BAR = 0, int ALG = kAlgAny>
+template <class R, int N, int BLOCK, int BAR = 0, int ALG = kAlgAny, int HB = -1, int G = -1>
 __device__ __forceinline__ void amp_rounds(unsigned char* smem, PointRec<R, N>* recs, int cnt, const uint32_t* mask,
                                            int alg, bool kappa = false) {
     if constexpr (ALG == kAlgSubset) {
         amplitude_rounds_subset<R, N, BLOCK, BAR>(smem, recs, cnt, mask, kappa);
     } else if constexpr (ALG == kAlgTree) {
-        using SH = DefaultShape<R, N, BLOCK>;
+        using SH = ShapeSel<R, N, BLOCK, HB, G>;
         amplitude_rounds<R, N, BLOCK, BAR, SH::HB, SH::G>(smem, recs, cnt, mask);
         if (kappa) kappa_rounds<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
     } else if (alg == kAlgSubset) {
         amp_rounds<R, N, BLOCK, BAR, kAlgSubset>(smem, recs, cnt, mask, alg, kappa);
     } else {
-        amp_rounds<R, N, BLOCK, BAR, kAlgTree>(smem, recs, cnt, mask, alg, kappa);
+        amp_rounds<R, N, BLOCK, BAR, kAlgTree, HB, G>(smem, recs, cnt, mask, alg, kappa);
     }
 }
 
@@ -99,10 +126,11 @@ __host__ __device__ constexpr size_t amp2_region_bytes(int tile) {
     const size_t st = align16((size_t)tile * amp2_row(N) * sizeof(double));
     return table_bytes<R, N, BLOCK, ALG>() > st ? table_bytes<R, N, BLOCK, ALG>() : st;
 }
-template <class R, int N, int BLOCK, int ALG = kAlgAny>
+template <class R, int N, int BLOCK, int ALG = kAlgAny, int HB = -1, int G = -1>
 __host__ __device__ constexpr size_t xsec_region_bytes(int tile) {
     const size_t st = align16((size_t)tile * N * kMomSlots * sizeof(double));
-    return table_bytes<R, N, BLOCK, ALG>() > st ? table_bytes<R, N, BLOCK, ALG>() : st;
+    constexpr size_t tb = table_bytes<R, N, BLOCK, ALG, HB, G>();
+    return tb > st ? tb : st;
 }
 template <class R, int N, int BLOCK, int ALG = kAlgAny>
 __host__ __device__ constexpr size_t amp2_smem_bytes(int tile) {
@@ -115,9 +143,9 @@ template <class R, int N>
 __host__ __device__ constexpr bool xsec_parks_sums() {
     return sizeof(R) == sizeof(float) && N >= 6;
 }
-template <class R, int N, int BLOCK, int ALG = kAlgAny>
+template <class R, int N, int BLOCK, int ALG = kAlgAny, int HB = -1, int G = -1>
 __host__ __device__ constexpr size_t xsec_smem_bytes(int tile) {
-    return xsec_region_bytes<R, N, BLOCK, ALG>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>)) +
+    return xsec_region_bytes<R, N, BLOCK, ALG, HB, G>(tile) + align16((size_t)tile * sizeof(PointRec<R, N>)) +
            (xsec_parks_sums<R, N>() ? (size_t)BLOCK * sizeof(Partial) : 0);
 }
 
@@ -341,7 +369,7 @@ __device__ __forceinline__ int compact_pos(bool flag, int local, int* cnts, int 
 // weight 0 and needs no amplitude); their amplitudes are computed in rounds
 // and their weights folded into acc.  w_out (may be NULL) receives the
 // tile's weights (0 for points that fail the cuts).
-template <class R, int N, int BLOCK, bool ESC = false, int ALG = kAlgAny>
+template <class R, int N, int BLOCK, bool ESC = false, int ALG = kAlgAny, int HB = -1, int G = -1>
 __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_t seed, long long first, int cnt,
                                           const SamplerArgs& S, const Physics& ph, Partial& acc,
                                           double* __restrict__ w_out, const EscArgs& esc, int& esc_n) {
@@ -349,7 +377,7 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
     double* stage = reinterpret_cast<double*>(smem);
     constexpr bool kEsc = ESC && sizeof(R) == sizeof(float);
     PointRec<R, N>* recs =
-        reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK, table_alg<ALG, kEsc>()>(tile));
+        reinterpret_cast<PointRec<R, N>*>(smem + xsec_region_bytes<R, N, BLOCK, table_alg<ALG, kEsc>(), HB, G>(tile));
     int npass = 0;
     for (int t0 = 0; t0 < cnt; t0 += BLOCK) {
         const int t = t0 + (int)threadIdx.x;
@@ -392,10 +420,10 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
         Partial* park = reinterpret_cast<Partial*>(reinterpret_cast<unsigned char*>(recs) +
                                                    align16((size_t)tile * sizeof(PointRec<R, N>)));
         park[threadIdx.x] = acc;
-        amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, npass, nullptr, ph.alg, kEsc);
+        amp_rounds<R, N, BLOCK, 0, ALG, HB, G>(smem, recs, npass, nullptr, ph.alg, kEsc);
         acc = park[threadIdx.x];
     } else {
-        amp_rounds<R, N, BLOCK, 0, ALG>(smem, recs, npass, nullptr, ph.alg, kEsc);
+        amp_rounds<R, N, BLOCK, 0, ALG, HB, G>(smem, recs, npass, nullptr, ph.alg, kEsc);
     }
     // one thread per record: weight and double-double accumulation; records
     // whose FP32 error bound exceeds the threshold join the escalation list
@@ -435,12 +463,14 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
 
 // Resident blocks per SM a tile kernel is compiled for (its register
 // budget; a sub-partition holds at most 16384 registers of its warps): for
-// the FP32 tree three 160-thread blocks at n = 6 and two blocks above (four
-// warps per sub-partition, 128 registers); n = 2 three blocks (at most
-// 68 KB); elsewhere two blocks (up to 128 registers).
+// the FP32 tree from n = 6 as many blocks as 128 registers per thread allow
+// (three 160-thread blocks at n = 6, two blocks of 224 or 256 above); n = 2
+// three blocks (at most 68 KB); elsewhere two blocks (up to 128 registers).
 template <class R, int N, int BLOCK, bool ESC, int ALG>
 __host__ __device__ constexpr int tile_min_blocks() {
-    return (sizeof(R) == sizeof(float) && ALG == kAlgTree && !ESC && N == 6) ? 3 : N == 2 ? 3 : 2;
+    return (sizeof(R) == sizeof(float) && ALG == kAlgTree && !ESC && N >= 6)
+               ? (65536 / (BLOCK * 128) > 1 ? 65536 / (BLOCK * 128) : 1)
+               : N == 2 ? 3 : 2;
 }
 // Threads of a fused tile kernel's block: for the FP32 tree, as many warps as
 // share out the depth-2 prefixes evenly with one subtree group per warp
@@ -450,7 +480,7 @@ __host__ __device__ constexpr int xsec_block() {
     return sizeof(R) == sizeof(float) && ALG == kAlgTree ? (N == 6 ? 160 : N == 7 ? 224 : 256) : 256;
 }
 
-template <class R, int N, int BLOCK, bool ESC, int ALG>
+template <class R, int N, int BLOCK, bool ESC, int ALG, int HB = -1, int G = -1>
 __global__ void __launch_bounds__(BLOCK, tile_min_blocks<R, N, BLOCK, ESC, ALG>())
 xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph, int tile,
             Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
@@ -459,7 +489,7 @@ xsec_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics 
     int esc_n = 0;
     for (long long t0 = (long long)blockIdx.x * tile; t0 < npts; t0 += (long long)gridDim.x * tile) {
         const int cnt = (int)min((long long)tile, npts - t0);
-        xsec_tile<R, N, BLOCK, ESC, ALG>(smem, tile, seed, i0 + t0, cnt, S, ph, acc, w_out ? w_out + t0 : nullptr, esc,
+        xsec_tile<R, N, BLOCK, ESC, ALG, HB, G>(smem, tile, seed, i0 + t0, cnt, S, ph, acc, w_out ? w_out + t0 : nullptr, esc,
                                          esc_n);
     }
     if (ESC && threadIdx.x == 0) esc.cnt[blockIdx.x] = min(esc_n, esc.cap);
@@ -826,15 +856,17 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
 struct AmpLaunch {
     int block, tile, grid;
     size_t smem;
-    bool ws;   // warp-specialised xsec kernel (FP32)
+    bool ws;        // warp-specialised xsec kernel (FP32)
+    int shape = 0;  // tile-kernel shape of the fused cross section (tile_shape; 0 = default)
 };
 
 // The warp-specialised kernel runs FP32 cross sections where the FP64 event
 // generation is a large share of the work: n <= 5 with the tree, every n with
-// the subset recursion.  The tree at n >= 6 spends nearly all its time in the
-// amplitudes and runs faster on the tile kernel, at more blocks per SM.
+// the subset recursion.  The tree from n = 6 runs faster on the tile kernel
+// with 64-point tiles (GB300: 6.3e7 against 5.6e7 points/s at n = 6; its
+// generation spans two warps, and more blocks share an SM).
 constexpr bool use_ws(int n, int precision, bool xsec, int alg) {
-    return xsec && precision == HEGET_FP32 && (n <= 6 || alg == kAlgSubset);
+    return xsec && precision == HEGET_FP32 && (n <= 5 || alg == kAlgSubset);
 }
 
 // Per-algorithm launchers over n = 2..8 (ALG = kAlgTree or kAlgSubset),
@@ -847,7 +879,7 @@ template <class R, int ALG>
 int launch_xsec_alg(int n, uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
                     Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st);
 template <class R, int ALG>
-int occupancy_alg(int n, int tile, int* bpsm, size_t* smem);
+int occupancy_alg(int n, int tile, int* bpsm, size_t* smem, int shape = 0);
 template <int ALG>
 int occupancy_ws_alg(int n, int* bpsm, size_t* smem);
 
@@ -874,14 +906,19 @@ int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* 
                     const AmpLaunch& L, cudaStream_t st);
 // Mixed-n batch launch (one launch per precision); smem sized for the tiles.
 int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
-                     cudaStream_t st);
+                     cudaStream_t st, bool set_attr = true);
 int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
-                     cudaStream_t st);
+                     cudaStream_t st, bool set_attr = true);
+int prepare_batch_f32(size_t smem);
+int prepare_batch_f64(size_t smem);
 // One block per request: its tile partials, in order, into its result.
 int launch_batch_finalize(const BatchReq* reqs, int nreqs, cudaStream_t st);
+
 // Default launch shape and the maximum resident blocks per SM.
 int default_tile(int n, bool xsec);
 int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLaunch* L, bool xsec, int tile,
-                       int alg = kAlgTree);
+                       int alg = kAlgTree, int shape = 0);
+// Tile-kernel shapes available for the fused cross section (num_tile_shapes).
+int xsec_shape_count(int n, int precision, int alg);
 
 }  // namespace heget

@@ -31,7 +31,79 @@ static int launch_amp2_n(const double* mom, long long npts, const uint32_t* mask
 // n <= 5 with the tree, every n with the subset recursion.
 template <class R, int N, int ALG>
 constexpr bool has_ws() {
-    return sizeof(R) == sizeof(float) && (N <= 6 || ALG == kAlgSubset);
+    return sizeof(R) == sizeof(float) && (N <= 5 || ALG == kAlgSubset);
+}
+
+// The fused tile kernel of shape K (tile_shape; K = 0 the default) and its
+// dynamic shared memory for `tile` points.
+template <class R, int N, int ALG, int K>
+struct TileKernel {
+    static constexpr TileShape TS = K == 0 ? TileShape{xsec_block<R, N, ALG>(), -1, -1} : tile_shape<R, N, ALG>(K);
+    static constexpr auto kernel() { return xsec_kernel<R, N, TS.block, false, ALG, TS.hb, TS.g>; }
+    static size_t smem(int tile) { return xsec_smem_bytes<R, N, TS.block, ALG, TS.hb, TS.g>(tile); }
+};
+
+template <class R, int N, int ALG, int K>
+static int launch_tile_shape(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                             Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L,
+                             cudaStream_t st) {
+    using TK = TileKernel<R, N, ALG, K>;
+    auto k = TK::kernel();
+    const size_t smem = TK::smem(L.tile);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k<<<L.grid, TK::TS.block, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out, esc);
+    return (int)cudaGetLastError();
+}
+
+template <class R, int N, int ALG, int K>
+static int occupancy_tile_shape(int tile, int* blocks_per_sm, size_t* smem_out) {
+    using TK = TileKernel<R, N, ALG, K>;
+    const size_t smem = TK::smem(tile);
+    *smem_out = smem;
+    auto k = TK::kernel();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, TK::TS.block, smem);
+}
+
+// Dispatch on a run-time shape index to FN<R, N, ALG, K> (the shapes that
+// exist for this R, N, ALG; cudaErrorInvalidValue for others).
+#define HEGET_DISPATCH_SHAPE(R, N, ALG, shape, FN, ...)                                   \
+    switch (shape) {                                                                     \
+        case 0: return FN<R, N, ALG, 0>(__VA_ARGS__);                                    \
+        case 1:                                                                          \
+            if constexpr (num_tile_shapes<R, N, ALG>() > 1) return FN<R, N, ALG, 1>(__VA_ARGS__); \
+            break;                                                                       \
+        case 2:                                                                          \
+            if constexpr (num_tile_shapes<R, N, ALG>() > 2) return FN<R, N, ALG, 2>(__VA_ARGS__); \
+            break;                                                                       \
+        case 3:                                                                          \
+            if constexpr (num_tile_shapes<R, N, ALG>() > 3) return FN<R, N, ALG, 3>(__VA_ARGS__); \
+            break;                                                                       \
+        default:                                                                         \
+            break;                                                                       \
+    }                                                                                    \
+    return (int)cudaErrorInvalidValue;
+
+template <class R, int N, int ALG>
+static int launch_tile(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                       Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
+    HEGET_DISPATCH_SHAPE(R, N, ALG, L.shape, launch_tile_shape, seed, i0, npts, S, ph, partials, w_out, esc, L, st)
+}
+
+// The FP32 escalation variant exists for the default shape only: a launch
+// with escalation runs shape 0.
+template <class R, int N, int ALG>
+static int launch_tile_esc(uint64_t seed, long long i0, long long npts, const SamplerArgs& S, const Physics& ph,
+                           Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
+    constexpr int XB = xsec_block<R, N, ALG>();
+    auto k = xsec_kernel<R, N, XB, true, ALG>;
+    const size_t smem = xsec_smem_bytes<R, N, XB, table_alg<ALG, true>()>(L.tile);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    k<<<L.grid, XB, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out, esc);
+    return (int)cudaGetLastError();
 }
 
 template <class R, int N, int ALG>
@@ -50,29 +122,14 @@ static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const Samp
     } else {
         if (L.ws) return (int)cudaErrorInvalidValue;
     }
-    constexpr int XB = xsec_block<R, N, ALG>();
-    auto k = xsec_kernel<R, N, XB, false, ALG>;
-    size_t smem = xsec_smem_bytes<R, N, XB, ALG>(L.tile);
     if constexpr (sizeof(R) == sizeof(float))
-        if (esc.idx) {
-            k = xsec_kernel<R, N, XB, true, ALG>;
-            smem = xsec_smem_bytes<R, N, XB, table_alg<ALG, true>()>(L.tile);
-        }
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    k<<<L.grid, XB, smem, st>>>(seed, i0, npts, S, ph, L.tile, partials, w_out, esc);
-    return (int)cudaGetLastError();
+        if (esc.idx) return launch_tile_esc<R, N, ALG>(seed, i0, npts, S, ph, partials, w_out, esc, L, st);
+    return launch_tile<R, N, ALG>(seed, i0, npts, S, ph, partials, w_out, esc, L, st);
 }
 
 template <class R, int N, int ALG>
-static int occupancy_n(int tile, int* blocks_per_sm, size_t* smem_out) {
-    constexpr int XB = xsec_block<R, N, ALG>();
-    const size_t smem = xsec_smem_bytes<R, N, XB, ALG>(tile);
-    *smem_out = smem;
-    auto k = xsec_kernel<R, N, XB, false, ALG>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, XB, smem);
+static int occupancy_n(int tile, int shape, int* blocks_per_sm, size_t* smem_out) {
+    HEGET_DISPATCH_SHAPE(R, N, ALG, shape, occupancy_tile_shape, tile, blocks_per_sm, smem_out)
 }
 
 template <int N, int ALG>
@@ -124,11 +181,20 @@ static int launch_ward_n(const double* mom, long long npts, int ward, double* ou
 }
 
 template <class R>
+static int prepare_batch_t(size_t smem) {
+    return (int)cudaFuncSetAttribute(xsec_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// set_attr = false: the caller has run prepare_batch_t for this smem (inside
+// a stream capture, where only the launch is recorded).
+template <class R>
 static int launch_batch_t(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool set_attr) {
     auto k = xsec_batch_kernel<R>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
+    if (set_attr) {
+        const int e = prepare_batch_t<R>(smem);
+        if (e) return e;
+    }
     k<<<grid, kBatchThreads, smem, st>>>(items, nitems, reqs);
     return (int)cudaGetLastError();
 }
@@ -162,8 +228,8 @@ int launch_xsec_alg(int n, uint64_t seed, long long i0, long long npts, const Sa
 }
 
 template <class R, int ALG>
-int occupancy_alg(int n, int tile, int* bpsm, size_t* smem) {
-#define CALL(N) occupancy_n<R, N, ALG>(tile, bpsm, smem)
+int occupancy_alg(int n, int tile, int* bpsm, size_t* smem, int shape) {
+#define CALL(N) occupancy_n<R, N, ALG>(tile, shape, bpsm, smem)
     HEGET_DISPATCH_N(n, CALL)
 #undef CALL
 }
@@ -181,6 +247,6 @@ int occupancy_ws_alg(int n, int* bpsm, size_t* smem) {
                                          int*, int*, int*, const AmpLaunch&, cudaStream_t);                       \
     template int launch_xsec_alg<R, ALG>(int, uint64_t, long long, long long, const SamplerArgs&, const Physics&,  \
                                          Partial*, double*, const EscArgs&, const AmpLaunch&, cudaStream_t);      \
-    template int occupancy_alg<R, ALG>(int, int, int*, size_t*);
+    template int occupancy_alg<R, ALG>(int, int, int*, size_t*, int);
 
 }  // namespace heget

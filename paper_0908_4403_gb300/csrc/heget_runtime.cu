@@ -57,7 +57,8 @@ int heget_graph_xsec(heget_ctx* ctx, int n, int64_t N, const heget_sampler* smp,
     // allocations cannot be captured: grow the escalation lists first
     if (precision == HEGET_FP32 && ctx->esc_tau > 0) {
         AmpLaunch L;
-        if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, true, ctx->tiles[1][0][n], ctx->alg)))
+        if ((r = default_amp_launch(n, precision, N, ctx->num_sms, &L, true, ctx->tiles[1][0][n], ctx->alg,
+                                    ctx->shapes[0][n])))
             return cuda_fail((cudaError_t)r, "occupancy");
         if ((r = reserve_escalation(ctx, L, N))) return r;
     }
@@ -131,18 +132,28 @@ void heget_graph_destroy(heget_graph* g) {
 // autotuner
 // ---------------------------------------------------------------------------
 
-int heget_autotune(heget_ctx* ctx, int n, int precision, int kind, int64_t probe_points, int* best_tile,
-                   double* best_ms) {
+namespace {
+// Times every candidate launch (shape, tile) of heget_amp2 (kind 0: tiles of
+// the context's shape) or heget_xsec (kind 1: every shape, each with its
+// default tile and the tiles 256/2^n x 2^k up to 1024) on probe_points
+// synthetic points; the context keeps the fastest.
+int autotune_impl(heget_ctx* ctx, int n, int precision, int kind, int64_t probe_points, bool shapes, int* best_shape,
+                  int* best_tile, double* best_ms) {
     int r = check_common(ctx, n, probe_points);
     if (r) return r;
     if ((r = check_precision(precision))) return r;
     if (kind != 0 && kind != 1) return fail(HEGET_EINVAL, "kind must be 0 (amp2) or 1 (xsec)");
     if (probe_points < 1) return fail(HEGET_EINVAL, "probe_points must be >= 1");
     DeviceGuard dg(ctx->device);
+    const int pi = precision == HEGET_FP64;
     const int unit = kBlockThreads >> n;
-    std::vector<int> cands;
-    if (kind == 1) cands.push_back(0);   // default shape (warp-specialised where it applies)
-    for (int t = unit; t <= 1024; t *= 2) cands.push_back(t);
+    const int nshapes = kind == 1 && shapes ? xsec_shape_count(n, precision, ctx->alg) : 1;
+    std::vector<std::pair<int, int>> cands;   // (shape, tile)
+    for (int sh = 0; sh < nshapes; ++sh) {
+        const int shape = kind == 1 && shapes ? sh : ctx->shapes[pi][n];
+        if (kind == 1) cands.emplace_back(shape, 0);   // the shape's default tile (warp-specialised where it applies)
+        for (int t = unit; t <= 1024; t *= 2) cands.emplace_back(shape, t);
+    }
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double* mom = nullptr;
@@ -158,12 +169,13 @@ int heget_autotune(heget_ctx* ctx, int n, int precision, int kind, int64_t probe
     if (e == cudaSuccess && kind == 0)
         r = heget_phase_space_ex(ctx, 0x0908440300000777ull, 0, probe_points, n, &toy, mom, nullptr, nullptr,
                                  nullptr, nullptr, nullptr, st);
-    const int saved = ctx->tiles[kind][precision == HEGET_FP64][n];
+    const int saved_tile = ctx->tiles[kind][pi][n], saved_shape = ctx->shapes[pi][n];
     int best = -1;
     float best_t = 1e30f;
-    for (int c : cands) {
+    for (int c = 0; c < (int)cands.size(); ++c) {
         if (e != cudaSuccess || r) break;
-        ctx->tiles[kind][precision == HEGET_FP64][n] = c;
+        ctx->shapes[pi][n] = cands[c].first;
+        ctx->tiles[kind][pi][n] = cands[c].second;
         auto run = [&]() {
             return kind == 0 ? heget_amp2(ctx, n, probe_points, mom, nullptr, precision, amp, st)
                              : heget_xsec_async(ctx, n, 0x0908440300000778ull, 0, probe_points, &toy, precision, res,
@@ -191,18 +203,29 @@ int heget_autotune(heget_ctx* ctx, int n, int precision, int kind, int64_t probe
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
-    if (e != cudaSuccess) {
-        ctx->tiles[kind][precision == HEGET_FP64][n] = saved;
-        return cuda_fail(e, "heget_autotune");
-    }
-    if (r || best < 0) {
-        ctx->tiles[kind][precision == HEGET_FP64][n] = saved;
+    if (e != cudaSuccess || r || best < 0) {
+        ctx->tiles[kind][pi][n] = saved_tile;
+        ctx->shapes[pi][n] = saved_shape;
+        if (e != cudaSuccess) return cuda_fail(e, "heget_autotune");
         return r ? r : fail(HEGET_ECUDA, "no launch shape ran");
     }
-    ctx->tiles[kind][precision == HEGET_FP64][n] = best;
-    if (best_tile) *best_tile = best;
+    ctx->shapes[pi][n] = cands[best].first;
+    ctx->tiles[kind][pi][n] = cands[best].second;
+    if (best_shape) *best_shape = cands[best].first;
+    if (best_tile) *best_tile = cands[best].second;
     if (best_ms) *best_ms = best_t;
     return HEGET_OK;
+}
+}  // namespace
+
+int heget_autotune(heget_ctx* ctx, int n, int precision, int kind, int64_t probe_points, int* best_tile,
+                   double* best_ms) {
+    return autotune_impl(ctx, n, precision, kind, probe_points, true, nullptr, best_tile, best_ms);
+}
+
+int heget_autotune_shape(heget_ctx* ctx, int n, int precision, int64_t probe_points, int* best_shape, int* best_tile,
+                         double* best_ms) {
+    return autotune_impl(ctx, n, precision, 1, probe_points, true, best_shape, best_tile, best_ms);
 }
 
 int heget_autotune_save(const heget_ctx* ctx, const char* path) {
@@ -225,10 +248,12 @@ int heget_autotune_save(const heget_ctx* ctx, const char* path) {
     for (const auto& l : keep) std::fputs(l.c_str(), f);
     for (int kind = 0; kind < 2; ++kind)
         for (int p = 0; p < 2; ++p)
-            for (int n = kMinN; n <= kMaxN; ++n)
-                if (ctx->tiles[kind][p][n] > 0)
-                    std::fprintf(f, "%s %d %d %d %d\n", gpu.c_str(), n, p ? HEGET_FP64 : HEGET_FP32, kind,
-                                 ctx->tiles[kind][p][n]);
+            for (int n = kMinN; n <= kMaxN; ++n) {
+                const int shape = kind == 1 ? ctx->shapes[p][n] : 0;
+                if (ctx->tiles[kind][p][n] > 0 || shape > 0)
+                    std::fprintf(f, "%s %d %d %d %d %d\n", gpu.c_str(), n, p ? HEGET_FP64 : HEGET_FP32, kind,
+                                 ctx->tiles[kind][p][n], shape);
+            }
     std::fclose(f);
     return HEGET_OK;
 }
@@ -243,10 +268,11 @@ int heget_autotune_load(heget_ctx* ctx, const char* path) {
     FILE* f = std::fopen(path, "r");
     if (!f) return fail(HEGET_EINVAL, "cannot read %s", path);
     char name[256];
-    int n, prec, kind, tile;
-    while (std::fscanf(f, "%255s %d %d %d %d", name, &n, &prec, &kind, &tile) == 5) {
+    int n, prec, kind, tile, shape;
+    while (std::fscanf(f, "%255s %d %d %d %d %d", name, &n, &prec, &kind, &tile, &shape) == 6) {
         if (gpu != name) continue;
         heget_set_tile(ctx, n, prec, kind, tile);
+        if (kind == 1) heget_set_shape(ctx, n, prec, shape);
     }
     std::fclose(f);
     return HEGET_OK;

@@ -91,6 +91,8 @@ struct heget_server {
     std::vector<int> free_slots;
     Launch launches[2];
     int next_launch = 0;
+    bool graphs = false;                         // the context's graph setting when the server started
+    heget::BatchGraphCache graph_cache;          // per-round launches by launch-shape bucket (worker thread)
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -221,6 +223,7 @@ int heget_server::build_and_launch(Launch& L) {
         bytes += align16(P.fin.size() * sizeof(BatchReq));
     }
     if (bytes > L.cap) {
+        graph_cache.clear();   // graph arguments point into the launch buffers
         if (L.host) cudaFreeHost(L.host);
         if (L.dev) cudaFree(L.dev);
         L.host = nullptr;
@@ -245,11 +248,24 @@ int heget_server::build_and_launch(Launch& L) {
         const int grid = std::max(1, std::min(nitems, 8 * ctx->num_sms));
         const WorkItem* items_d = reinterpret_cast<const WorkItem*>(L.dev + P.off_items);
         const BatchReq* br_d = reinterpret_cast<const BatchReq*>(L.dev + P.off_br);
-        int r = pi == 0 ? launch_batch_f32(items_d, nitems, br_d, P.smem, grid, stream)
-                        : launch_batch_f64(items_d, nitems, br_d, P.smem, grid, stream);
-        if (!r && !P.fin.empty())
-            r = launch_batch_finalize(reinterpret_cast<const BatchReq*>(L.dev + P.off_fin), (int)P.fin.size(),
-                                      stream);
+        const BatchReq* fin_d = reinterpret_cast<const BatchReq*>(L.dev + P.off_fin);
+        const int nfin = (int)P.fin.size();
+        auto launch = [&](cudaStream_t s2, bool set_attr) {
+            int rr = pi == 0 ? launch_batch_f32(items_d, nitems, br_d, P.smem, grid, s2, set_attr)
+                             : launch_batch_f64(items_d, nitems, br_d, P.smem, grid, s2, set_attr);
+            if (!rr && nfin > 0) rr = launch_batch_finalize(fin_d, nfin, s2);
+            return rr;
+        };
+        int r;
+        if (graphs) {
+            r = pi == 0 ? prepare_batch_f32(P.smem) : prepare_batch_f64(P.smem);
+            if (!r)
+                r = graph_cache.run(BatchGraphKey{pi == 0 ? HEGET_FP32 : HEGET_FP64, nitems, nfin, grid, P.smem,
+                                                  items_d, br_d, fin_d},
+                                    stream, [&](cudaStream_t s2) { return launch(s2, false); });
+        } else {
+            r = launch(stream, true);
+        }
         if (r) return -1;
         launched += nitems;
     }
@@ -365,6 +381,7 @@ int heget_server_start(heget_ctx* ctx, const heget_server_cfg* cfg_in, heget_ser
     if (arena > usable) return fail(HEGET_ENOMEM, "arena of %zu bytes exceeds usable free HBM (%zu)", arena, usable);
     heget_server* s = new heget_server();
     s->ctx = ctx;
+    s->graphs = ctx->graphs != 0;
     s->cfg = cfg;
     e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->arena_dev, arena);
@@ -468,6 +485,7 @@ int heget_server_stop(heget_server* s) {
     if (s->worker.joinable()) s->worker.join();
     DeviceGuard dg(s->ctx->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
+    s->graph_cache.release();
     for (auto& L : s->launches) {
         if (L.done) cudaEventDestroy(L.done);
         if (L.host) cudaFreeHost(L.host);

@@ -119,6 +119,13 @@ SIGNATURES = {
     "heget_hist": (I32, [P, I32, U64, I64, I64, C.POINTER(heget_sampler), P, C.POINTER(heget_hist_spec), I32, P,
                          P]),
     "heget_autotune": (I32, [P, I32, I32, I32, I64, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "heget_autotune_shape": (I32, [P, I32, I32, I64, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double)]),
+    "heget_set_shape": (I32, [P, I32, I32, I32]),
+    "heget_set_graphs": (I32, [P, I32]),
+    "heget_get_graphs": (I32, [P, C.POINTER(I64), C.POINTER(I64)]),
+    "heget_get_shape": (I32, [P, I32, I32]),
+    "heget_shape_info": (I32, [I32, I32, I32, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "heget_autotune_save": (I32, [P, C.c_char_p]),
     "heget_autotune_load": (I32, [P, C.c_char_p]),
     "heget_graph_xsec": (I32, [P, I32, I64, C.POINTER(heget_sampler), I32, P, C.POINTER(P)]),
@@ -349,6 +356,39 @@ def heget_autotune(ctx, n, precision, kind, probe_points):
     t, ms = C.c_int(), C.c_double()
     _check(load().heget_autotune(ctx, n, precision, kind, probe_points, C.byref(t), C.byref(ms)))
     return t.value, ms.value
+
+
+def heget_autotune_shape(ctx, n, precision, probe_points):
+    """(best shape, best tile, ms) of the fused cross section, kept in ctx."""
+    sh, t, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(load().heget_autotune_shape(ctx, n, precision, probe_points, C.byref(sh), C.byref(t), C.byref(ms)))
+    return sh.value, t.value, ms.value
+
+
+def heget_set_graphs(ctx, on):
+    _check(load().heget_set_graphs(ctx, int(on)))
+
+
+def heget_get_graphs(ctx):
+    """(setting, captures, replays) of the batch launch graphs."""
+    c, r = C.c_int64(), C.c_int64()
+    v = load().heget_get_graphs(ctx, C.byref(c), C.byref(r))
+    return v, c.value, r.value
+
+
+def heget_set_shape(ctx, n, precision, shape):
+    _check(load().heget_set_shape(ctx, n, precision, shape))
+
+
+def heget_get_shape(ctx, n, precision) -> int:
+    return load().heget_get_shape(ctx, n, precision)
+
+
+def heget_shape_info(n, precision, shape):
+    """(threads per block, helicity rows per lane, subtree groups) of a shape; zeros for shape 0."""
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(load().heget_shape_info(n, precision, shape, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def heget_autotune_save(ctx, path):

@@ -156,11 +156,11 @@ int main() {
     const size_t ws6 = ws_smem_bytes<float, 6, kAlgTree>() + 2 * ws_stage(6, kAlgTree) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws6) >= 2, "warp-specialised n=6 tree: %zu bytes", ws6);
     check_shape<float, 6, ws_consumers(6, kAlgTree)>(true);
-    const size_t t6 = xsec_smem_bytes<float, 6, 160, kAlgTree>(32);
+    const size_t t6 = xsec_smem_bytes<float, 6, 160, kAlgTree>(64);
     CHECK(resident_blocks(t6) >= 3, "tile n=6 tree (160 threads): %zu bytes, fewer than 3 blocks per SM", t6);
-    const size_t t7 = xsec_smem_bytes<float, 7, 224, kAlgTree>(8);
+    const size_t t7 = xsec_smem_bytes<float, 7, 224, kAlgTree>(32);
     CHECK(resident_blocks(t7) >= 2, "tile n=7 tree (224 threads): %zu bytes, fewer than 2 blocks per SM", t7);
-    const size_t t8 = xsec_smem_bytes<float, 8, 256, kAlgTree>(4);
+    const size_t t8 = xsec_smem_bytes<float, 8, 256, kAlgTree>(8);
     CHECK(resident_blocks(t8) >= 2, "tile n=8 tree: %zu bytes, fewer than 2 blocks per SM", t8);
     CHECK(sizeof(SampleDraw) == 16, "SampleDraw is %zu bytes", sizeof(SampleDraw));
     std::printf("layout checks: %d failures\n", failures);

@@ -19,7 +19,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-XSEC_TILE_N7 = 8           # default xsec tile at n = 7 (points per block of the tile kernel)
+XSEC_TILE_N7 = 32          # default xsec tile at n = 7 (points per block of the tile kernel)
 NOALLOC_MAX_BLOCKS = 4096  # the static scratch holds this many block partials
 
 
