@@ -156,6 +156,10 @@ int heget_phase_space_ex(heget_ctx* ctx, uint64_t seed, int64_t i0, int64_t N,
  * the couplings (-e Q)^n; without colour, spin-average or 1/n! factors.
  * precision: HEGET_FP32 (spinor algebra in FP32, propagator denominators
  * from FP64 invariants) or HEGET_FP64.  momenta: [N][n+2][4]; amp2: [N].
+ * The points must conserve momentum, p1 + p2 = sum of the photons (every
+ * point of heget_phase_space does, to FP64 rounding): from n = 6 the FP32
+ * path forms the denominator of a photon set with more than n/2 photons
+ * from its complement, (k_T - p2)^2 = (p1 - k_{all - T})^2.
  * Host-side EINVAL: n not in [2, 8], N < 0, NULL arrays, bad precision.
  * Device-side check: a point with a non-finite entry, or p1 / p2 not
  * massless along +z / -z, gets amp2 = NaN and raises the context's input

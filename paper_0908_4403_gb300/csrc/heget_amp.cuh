@@ -215,12 +215,57 @@ struct RoundTables {
     }
 };
 
-// Photon data PH[p][j] = (sin th, cos th, cos ph, sin ph) and set data
-// SD[p][T] = (q0+q3, q0-q3, q1, q2) / t_T, q_T = sum_{i in T} k_i - p2, for
-// the points recs[0 .. cnt-1] (P slots).  Everything runs in R: the FP64
-// content (denominators) is already in the records.
+// Photon direction (sin th, cos th, cos ph, sin ph) of momentum k.
+template <class R>
+__device__ __forceinline__ Row<R> photon_row(const R* k) {
+    const R pt2 = k[1] * k[1] + k[2] * k[2];
+    const R ka2 = pt2 + k[3] * k[3];
+    const R rk = rsq<R>(ka2);
+    Row<R> d;
+    d.ai = k[3] * rk;                        // cos theta
+    if (pt2 > R(1e-24) * ka2) {
+        const R rpt = rsq<R>(pt2);
+        d.ar = pt2 * rpt * rk;               // sin theta
+        d.br = k[1] * rpt;                   // cos phi
+        d.bi = k[2] * rpt;                   // sin phi
+    } else {  // photon along z: the phi -> 0 limit of the polarisation
+        d.ar = R(0);
+        d.br = R(1);
+        d.bi = R(0);
+    }
+    return d;
+}
+
+// Set data (q0+q3, q0-q3, q1, q2) / t_T of set T (0 < T < 2^N - 1), q_T =
+// sum_{i in T} k_i - p2, from a record: t_T as the record holds it (from
+// FP64, rounded once) or as the float-float sum of its invariants.
+template <class R, int N>
+__device__ __forceinline__ Row<R> set_row(const PointRec<R, N>& rc, unsigned T) {
+    R q0 = -rc.e2, q1 = R(0), q2 = R(0), q3 = rc.e2;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (T >> i & 1) {
+            q0 += rc.k[i][0];
+            q1 += rc.k[i][1];
+            q2 += rc.k[i][2];
+            q3 += rc.k[i][3];
+        }
+    R tT;
+    if constexpr (rec_invariants<R, N>()) tT = rec_denominator<N>(rc.inv, T);
+    else tT = rc.t[T];
+    const R it_ = recip<R>(tT);
+    return Row<R>{(q0 + q3) * it_, (q0 - q3) * it_, q1 * it_, q2 * it_};
+}
+
+// Photon data PH[p][j] (photon_row) and set data SD[p][T] (set_row) for the
+// points recs[0 .. cnt-1] (P slots).  Everything runs in R: the records hold
+// t_T from FP64, or the FP64 invariants it is a float-float sum of.  list
+// (optional): the sets by size (build_set_list), the order in which the
+// threads take them, so that the float-float sums of a warp's lanes share
+// their loop counts.
 template <class R, int N, int BLOCK, int P>
-__device__ __forceinline__ void setup_photons_and_sets(Row<R>* PH, Row<R>* SD, const PointRec<R, N>* recs, int cnt) {
+__device__ __forceinline__ void setup_photons_and_sets(Row<R>* PH, Row<R>* SD, const PointRec<R, N>* recs, int cnt,
+                                                       const unsigned char* list = nullptr) {
     constexpr int NS = 1 << N;
     const int tid = threadIdx.x;
     constexpr int n_ph = P * N, n_sd = P * NS;
@@ -228,44 +273,13 @@ __device__ __forceinline__ void setup_photons_and_sets(Row<R>* PH, Row<R>* SD, c
         if (it < n_ph) {
             const int p = it / N, j = it - p * N;
             if (p >= cnt) continue;
-            const R* k = recs[p].k[j];
-            const R pt2 = k[1] * k[1] + k[2] * k[2];
-            const R ka2 = pt2 + k[3] * k[3];
-            const R rk = rsq<R>(ka2);
-            Row<R> d;
-            d.ai = k[3] * rk;                        // cos theta
-            if (pt2 > R(1e-24) * ka2) {
-                const R rpt = rsq<R>(pt2);
-                d.ar = pt2 * rpt * rk;               // sin theta
-                d.br = k[1] * rpt;                   // cos phi
-                d.bi = k[2] * rpt;                   // sin phi
-            } else {  // photon along z: the phi -> 0 limit of the polarisation
-                d.ar = R(0);
-                d.br = R(1);
-                d.bi = R(0);
-            }
-            PH[p * N + j] = d;
+            PH[p * N + j] = photon_row<R>(recs[p].k[j]);
         } else {
             const int r = it - n_ph;
-            const int p = r / NS, T = r - p * NS;
+            const int p = r / NS, e = r - p * NS;
+            const int T = list ? (int)list[e] : e;
             if (p >= cnt || T == 0 || T == NS - 1) continue;
-            const PointRec<R, N>& rc = recs[p];
-            R q0 = -rc.e2, q1 = R(0), q2 = R(0), q3 = rc.e2;
-#pragma unroll
-            for (int i = 0; i < N; ++i)
-                if (T >> i & 1) {
-                    q0 += rc.k[i][0];
-                    q1 += rc.k[i][1];
-                    q2 += rc.k[i][2];
-                    q3 += rc.k[i][3];
-                }
-            const R it_ = recip<R>(rc.t[T]);   // t_T from FP64, rounded once
-            Row<R> d;
-            d.ar = (q0 + q3) * it_;
-            d.ai = (q0 - q3) * it_;
-            d.br = q1 * it_;
-            d.bi = q2 * it_;
-            SD[p * NS + T] = d;
+            SD[p * NS + T] = set_row<R, N>(recs[p], (unsigned)T);
         }
     }
 }

@@ -13,6 +13,7 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 
 constexpr int kBatchThreads = 256;   // threads of the mixed-n batch kernel
 
+
 // Tree shape per precision, photon count and threads of the rounds: 2^HB
 // helicity configurations per lane and G groups (see TreeShape).  FP64 keeps
 // one configuration per lane: its DFMA pipe, not instruction issue, is the
@@ -68,6 +69,7 @@ __host__ __device__ constexpr TileShape tile_shape(int k) {
 // recursion's without (kAlgSubset) or with (kTabSubsetKappa) the arrays of
 // the FP32 condition bound, or room for any of them (kAlgAny).
 constexpr int kTabSubsetKappa = 2;
+constexpr int kTabTreeKappa = 3;   // the tree's tables or the condition bound's
 
 // Round-table bytes of layout TAB: the tree's default shape (at least those
 // of one configuration per lane, which the gauge check uses, where the block
@@ -82,9 +84,10 @@ template <class R, int N, int BLOCK, int TAB = kAlgAny, int HB = -1, int G = -1>
 __host__ __device__ constexpr size_t table_bytes() {
     using SH = ShapeSel<R, N, BLOCK, HB, G>;
     constexpr size_t a = RoundTables<R, N, BLOCK, SH::HB, SH::G>::bytes, b = ward_table_bytes<R, N, BLOCK>();
-    constexpr size_t c = SubsetTables<R, N, BLOCK>::bytes_core, ck = SubsetTables<R, N, BLOCK>::bytes;
-    constexpr size_t ab = a > b ? a : b;
-    return align16(TAB == kAlgTree ? ab : TAB == kAlgSubset ? c : TAB == kTabSubsetKappa ? ck : (ab > ck ? ab : ck));
+    constexpr size_t c = MeetTables<R, N, BLOCK>::bytes, kb = KappaTables<R, N, BLOCK>::bytes;
+    constexpr size_t ab = a > b ? a : b, ck = c > kb ? c : kb;
+    return align16(TAB == kAlgTree ? ab : TAB == kAlgSubset ? c : TAB == kTabSubsetKappa ? ck
+                 : TAB == kTabTreeKappa ? (ab > kb ? ab : kb) : (ab > ck ? ab : ck));
 }
 
 // The table layout of a kernel of algorithm ALG: the condition-bound pass
@@ -93,7 +96,7 @@ __host__ __device__ constexpr size_t table_bytes() {
 // reserves both.
 template <int ALG, bool KAPPA>
 __host__ __device__ constexpr int table_alg() {
-    return !KAPPA ? ALG : ALG == kAlgTree ? kAlgAny : ALG == kAlgSubset ? kTabSubsetKappa : ALG;
+    return !KAPPA ? ALG : ALG == kAlgTree ? kTabTreeKappa : ALG == kAlgSubset ? kTabSubsetKappa : ALG;
 }
 
 // The amplitude rounds of the ordering-sum algorithm: the prefix tree of the
@@ -104,7 +107,8 @@ template <class R, int N, int BLOCK, int BAR = 0, int ALG = kAlgAny, int HB = -1
 __device__ __forceinline__ void amp_rounds(unsigned char* smem, PointRec<R, N>* recs, int cnt, const uint32_t* mask,
                                            int alg, bool kappa = false) {
     if constexpr (ALG == kAlgSubset) {
-        amplitude_rounds_subset<R, N, BLOCK, BAR>(smem, recs, cnt, mask, kappa);
+        amplitude_rounds_meet<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
+        if (kappa) kappa_rounds<R, N, BLOCK, BAR>(smem, recs, cnt, mask);
     } else if constexpr (ALG == kAlgTree) {
         using SH = ShapeSel<R, N, BLOCK, HB, G>;
         amplitude_rounds<R, N, BLOCK, BAR, SH::HB, SH::G>(smem, recs, cnt, mask);
@@ -191,6 +195,7 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
         for (int m = 0; m < 4; ++m) rec.k[a][m] = R(v(a, m) * irs);
     rec.hsel = -1;
     if constexpr (N <= 5) fill_denominators<R, N, true>(v, E2, is, false, rec);   // n >= 6: denominators_parallel
+    rec.e1 = R(E1 * irs);
     rec.e2 = R(E2 * irs);
     rec.n1 = R(sqrt(2.0 * E1 * irs));
     rec.n2 = R(sqrt(2.0 * E2 * irs));
@@ -204,39 +209,59 @@ __device__ __forceinline__ void input_to_rec(const double* __restrict__ row, con
     if (!ok) atomicOr(flag, 1);
 }
 
-// Denominators of the records recs[0 .. cnt-1] at n >= 6: one (record, set)
-// item per thread of the calling threads (local id lid of nthr), so that the
-// FP64 pipe runs whole warps.  view(c, E2, is) gives record c's photon
-// momenta, the energy of p2 and the scale 1/s-hat (SCALE: momenta in GeV).
-// Nothing at n <= 5 (the records hold their denominators already).
-template <class R, int N, bool SCALE, class View>
+// Denominators of the records recs[0 .. cnt-1] at n >= 6 by the calling
+// threads (local id lid of nthr), one item per thread so that the FP64 pipe
+// runs whole warps: FP32 records get their n(n+1)/2 invariants (item =
+// (record, invariant)), FP64 records their 2^n - 2 denominators (item =
+// (record, set)).  view(c, E1, E2, is) gives record c's photon momenta, the
+// energies of p1 and p2 and the scale 1/s-hat (SCALE: momenta in GeV; MASSLESS: photons on
+// shell, k^2 = 0).  Nothing at n <= 5 (the records hold their denominators
+// already).
+template <class R, int N, bool SCALE, bool MASSLESS, class View>
 __device__ __forceinline__ void denominators_parallel(PointRec<R, N>* recs, int cnt, int lid, int nthr,
                                                       const View& view) {
-    if constexpr (N >= 6) {
+    if constexpr (rec_invariants<R, N>()) {
+        constexpr int NI = N * (N + 3) / 2;
+        for (int it = lid; it < cnt * NI; it += nthr) {
+            const int c = it / NI, q = it - c * NI;
+            double E1, E2, is;
+            const MomView v = view(c, E1, E2, is);
+            recs[c].inv[q] = split_ff(rec_invariant<N, SCALE>(v, E1, E2, is, MASSLESS, q));
+        }
+    } else if constexpr (N >= 6) {
         constexpr int NSET = (1 << N) - 2;
         for (int it = lid; it < cnt * NSET; it += nthr) {
             const int c = it / NSET;
             const unsigned T = 1u + (unsigned)(it - c * NSET);
-            double E2, is;
-            const MomView v = view(c, E2, is);
+            double E1, E2, is;
+            const MomView v = view(c, E1, E2, is);
             recs[c].t[T] = set_denominator<R, N, SCALE>(v, E2, is, T);
         }
     }
 }
 
 // Staged input row c (stride srow) as a view for denominators_parallel: the
-// photons, the energy of p2 and 1/s-hat as input_to_rec forms them (a row it
+// photons, the energies of p1 and p2 and 1/s-hat as input_to_rec forms them (a row it
 // refuses is never evaluated).
-__device__ __forceinline__ MomView row_view(double* stage, int srow, int c, double& E2, double& is) {
+__device__ __forceinline__ MomView row_view(double* stage, int srow, int c, double& E1, double& E2, double& is) {
     double* row = stage + (size_t)c * srow;
+    E1 = row[0];
     E2 = row[4];
     const double s = 2.0 * (row[0] * row[4] - row[3] * row[7]);
     is = s > 0 ? 1.0 / s : 1.0;
     return MomView{row + 8, 1, 4};
 }
 
+// Resident blocks per SM an amp2 kernel is compiled for: the FP32 subset
+// recursion from n = 6 keeps three blocks of its 60 KB tables (at most 85
+// registers a thread); elsewhere the compiler's choice.
+template <class R, int N, int ALG>
+__host__ __device__ constexpr int amp2_min_blocks() {
+    return sizeof(R) == sizeof(float) && ALG == kAlgSubset && N >= 6 ? 3 : 1;
+}
+
 template <class R, int N, int BLOCK, bool ESC, int ALG>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, amp2_min_blocks<R, N, ALG>())
 amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __restrict__ mask,
             double* __restrict__ out, int tile, Physics ph, int* __restrict__ flag, int* __restrict__ esc_list,
             int* __restrict__ esc_count) {
@@ -257,8 +282,8 @@ amp2_kernel(const double* __restrict__ mom, long long npts, const uint32_t* __re
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         if constexpr (N >= 6) {
-            denominators_parallel<R, N, true>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
-                return row_view(stage, SROW, c, E2, is);
+            denominators_parallel<R, N, true, false>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E1, double& E2, double& is) {
+                return row_view(stage, SROW, c, E1, E2, is);
             });
         }
         __syncthreads();
@@ -294,8 +319,8 @@ ward_kernel(const double* __restrict__ mom, long long npts, int ward, double* __
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<R, N>(stage + t * SROW, ph, recs[t], flag);
         if constexpr (N >= 6) {
-            denominators_parallel<R, N, true>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
-                return row_view(stage, SROW, c, E2, is);
+            denominators_parallel<R, N, true, false>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E1, double& E2, double& is) {
+                return row_view(stage, SROW, c, E1, E2, is);
             });
         }
         __syncthreads();
@@ -409,8 +434,8 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
     }
     if constexpr (N >= 6) {
         __syncthreads();   // the staged momenta are scaled in place by pass_to_rec
-        denominators_parallel<R, N, false>(recs, npass, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
-            E2 = 0.5;
+        denominators_parallel<R, N, false, true>(recs, npass, threadIdx.x, BLOCK, [&](int c, double& E1, double& E2, double& is) {
+            E1 = E2 = 0.5;
             is = 1.0;
             return MomView{stage + recs[c].idx, tile, kMomSlots};
         });
@@ -528,8 +553,8 @@ xsec_escalate_kernel(uint64_t seed, long long i0, SamplerArgs S, Physics ph, int
         }
         if constexpr (N >= 6) {
             __syncthreads();
-            denominators_parallel<double, N, false>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
-                E2 = 0.5;
+            denominators_parallel<double, N, false, true>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E1, double& E2, double& is) {
+                E1 = E2 = 0.5;
                 is = 1.0;
                 return MomView{stage + c, tile, kMomSlots};
             });
@@ -573,8 +598,8 @@ amp2_list_kernel(const double* __restrict__ mom, const int* __restrict__ list, c
         __syncthreads();
         for (int t = threadIdx.x; t < cnt; t += BLOCK) input_to_rec<double, N>(stage + t * SROW, ph, recs[t], flag);
         if constexpr (N >= 6) {
-            denominators_parallel<double, N, true>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E2, double& is) {
-                return row_view(stage, SROW, c, E2, is);
+            denominators_parallel<double, N, true, false>(recs, cnt, threadIdx.x, BLOCK, [&](int c, double& E1, double& E2, double& is) {
+                return row_view(stage, SROW, c, E1, E2, is);
             });
         }
         __syncthreads();
@@ -812,8 +837,8 @@ xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physi
                                   rs_ring[g]);
             if constexpr (N >= 6) {
                 named_sync(kBarProducers, kWsStage);   // scaled momenta in place
-                denominators_parallel<R, N, false>(rs_ring, tot, g, kWsStage, [&](int c, double& E2, double& is) {
-                    E2 = 0.5;
+                denominators_parallel<R, N, false, true>(rs_ring, tot, g, kWsStage, [&](int c, double& E1, double& E2, double& is) {
+                    E1 = E2 = 0.5;
                     is = 1.0;
                     return MomView{stage + rs_ring[c].idx, kWsStage, kMomSlots};
                 });

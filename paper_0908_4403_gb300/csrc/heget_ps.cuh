@@ -20,15 +20,36 @@ namespace heget {
 // that the FP32 chain works on O(1) numbers; the mass dimension 4 - 2n of
 // |M|^2 is restored by `fac`.  The propagator denominators
 //   t_T = (sum_{i in T} k_i - p2)^2 / s-hat,   T a proper photon subset,
-// are computed in FP64 when the record is built (see fill_denominators) and
-// rounded once to R, so an FP32 chain sees denominators with FP64 accuracy.
+// come from FP64: FP64 records and FP32 records up to n = 5 hold every t_T,
+// computed in FP64 when the record is built (fill_denominators,
+// set_denominator) and rounded once to R.  FP32 records from n = 6 hold the
+// Lorentz invariants instead, t_T being a sum of them over T or, by momentum
+// conservation (k_T - p2 = p1 - k_S, S = all - T), over its complement S,
+//   t_T = sum_{i in T} d_i + sum_{i<j in T} s_ij = sum_{i in S} d'_i + sum_{i<j in S} s_ij,
+//   d_i = k_i^2 - 2 k_i.p2,  d'_i = k_i^2 - 2 k_i.p1,  s_ij = 2 k_i.k_j,
+// each computed in FP64 and kept as an unevaluated sum of two floats
+// (hi + lo, about 48 significant bits); the rounds add up those of the
+// smaller of T and S in float-float arithmetic (rec_denominator), so the
+// FP32 chain again sees t_T with far more than FP32 accuracy, while the FP64
+// pipe forms n(n+3)/2 invariants per point instead of 2^n - 2 sums.
 template <class R, int N>
-struct alignas(16) PointRec {
+__host__ __device__ constexpr bool rec_invariants() {
+    return sizeof(R) == sizeof(float) && N >= 6;
+}
+template <class R, int N, bool INV = rec_invariants<R, N>()>
+struct RecDenominators {
+    R t[1 << N];      // t_T by subset bitmask T (entries 0 and 2^n - 1 unused)
+};
+template <class R, int N>
+struct RecDenominators<R, N, true> {
+    float2 inv[N * (N + 3) / 2];   // (hi, lo): d_i at i, s_ij at N + pair_index(i, j), d'_i after them
+};
+template <class R, int N>
+struct alignas(16) PointRec : RecDenominators<R, N> {
     double fac;       // (4 pi alpha Q^2)^n s-hat^(2-n): scaled sum -> |M|^2
     double wfac;      // scaled sum -> event weight (fb); 0 if masked
-    R t[1 << N];      // t_T by subset bitmask T (entries 0 and 2^n - 1 unused)
     R k[N][4];        // photon momenta / sqrt(s-hat)
-    R e2;             // energy of p2 / sqrt(s-hat)  (p2 = e2 (1, 0, 0, -1))
+    R e1, e2;         // energies of p1, p2 / sqrt(s-hat)  (p1 = e1 (1, 0, 0, 1), p2 = e2 (1, 0, 0, -1))
     R n1, n2;         // sqrt(2 e1), sqrt(2 e2): spinor normalisations
     R ssum;           // result of the tree: sum_h w_h |A_h|^2 in scaled units
     R kap2;           // sum_h w_h B_h^2, B_h >= sum over orderings |A_pi,h| (condition bound)
@@ -601,8 +622,9 @@ __device__ __forceinline__ double phase_space_weight(double s) {
 // built up over the sets in increasing order in registers: with h the
 // highest photon of T and U = T - {h},
 //   t_T = t_U + e_h(U),  e_h(U) = d_h + sum_{j in U} s_jh = e_h(U - {l}) + s_lh
-// (l the lowest photon of U): two additions per set.  Larger n: see
-// set_denominator.
+// (l the lowest photon of U): two additions per set.  Larger n: FP64
+// records use set_denominator, FP32 records keep the invariants
+// (rec_invariant).
 template <class R, int N, bool SCALE>
 __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, double is, bool massless,
                                                   PointRec<R, N>& rec) {
@@ -639,10 +661,10 @@ __device__ __forceinline__ void fill_denominators(const MomView& p, double E2, d
     }
 }
 
-// One denominator for n >= 6 (where the tree dwarfs this, and one thread per
-// set keeps every lane of the FP64 pipe busy): t_T = (sum_{i in T} k_i - p2)^2
-// by components, times `is` if SCALE.  Callers run it over (record, set)
-// pairs after the records are built (denominators_parallel).
+// One denominator of an FP64 record for n >= 6 (one thread per set keeps
+// every lane of the FP64 pipe busy): t_T = (sum_{i in T} k_i - p2)^2 by
+// components, times `is` if SCALE.  Callers run it over (record, set) pairs
+// after the records are built (denominators_parallel).
 template <class R, int N, bool SCALE>
 __device__ __forceinline__ R set_denominator(const MomView& p, double E2, double is, unsigned T) {
     double q0 = -E2, q1 = 0.0, q2 = 0.0, q3 = E2;
@@ -656,6 +678,108 @@ __device__ __forceinline__ R set_denominator(const MomView& p, double E2, double
         }
     const double tt = q0 * q0 - q1 * q1 - q2 * q2 - q3 * q3;
     return rec_value<R>(SCALE ? tt * is : tt);
+}
+
+// Photon sets as bitmasks: C(n, k), and the rank of S among the sets of its
+// size in numeric order (numeric order of bitmasks is colexicographic order,
+// so rank(S) = sum over the set bits b_1 < b_2 < ... of C(b_m, m)).
+__host__ __device__ constexpr int set_binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+// offset of the size-k sets in a list ordered by size, then numerically
+__host__ __device__ constexpr int set_level_offset(int n, int k) {
+    int o = 0;
+    for (int j = 0; j < k; ++j) o += set_binom(n, j);
+    return o;
+}
+template <int N>
+__device__ __forceinline__ int set_rank(unsigned S) {
+    int r = 0, m = 0;
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+        if (S >> b & 1) r += set_binom(b, ++m);
+    return r;
+}
+// list[offset(|S|) + rank(S)] = S for every S < 2^N (and rank[S] = rank(S)
+// if rank != NULL), by threads lid = 0 .. nthr-1.
+template <int N>
+__device__ __forceinline__ void build_set_list(unsigned char* list, unsigned char* rank, int lid, int nthr) {
+    for (int S = lid; S < (1 << N); S += nthr) {
+        const int r = set_rank<N>((unsigned)S);
+        list[set_level_offset(N, __popc(S)) + r] = (unsigned char)S;
+        if (rank) rank[S] = (unsigned char)r;
+    }
+}
+
+// float -> double by integer operations on the bit pattern (exact; f32_rn
+// leaves no subnormals, so only zero needs its own case).
+__device__ __forceinline__ double f64_of_f32(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    const unsigned int hi = e == 0u ? (u & 0x80000000u) : (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(e == 0u ? 0u : u << 29));
+}
+
+// Invariant q of a record from FP64 momenta p, p1 = E1 (1, 0, 0, 1) and
+// p2 = E2 (1, 0, 0, -1): q < N: d_q; N <= q < N + N(N-1)/2: s_ij for
+// q = N + pair_index(i, j); after them d'_i; times `is` if SCALE.
+template <int N, bool SCALE>
+__device__ __forceinline__ double rec_invariant(const MomView& p, double E1, double E2, double is, bool massless,
+                                                int q) {
+    constexpr int NP = N * (N - 1) / 2;
+    double v;
+    if (q < N || q >= N + NP) {
+        const bool one = q >= N + NP;   // d'_i: against p1
+        const int i = one ? q - N - NP : q;
+        const double e = p(i, 0), x = p(i, 1), y = p(i, 2), z = p(i, 3);
+        const double lin = one ? 2.0 * E1 * (e - z) : 2.0 * E2 * (e + z);
+        v = massless ? -lin : (e * e - x * x - y * y - z * z) - lin;
+    } else {
+        int i = 0, r = q - N;
+        while (r >= N - 1 - i) {
+            r -= N - 1 - i;
+            ++i;
+        }
+        const int j = i + 1 + r;
+        v = 2.0 * (p(i, 0) * p(j, 0) - p(i, 1) * p(j, 1) - p(i, 2) * p(j, 2) - p(i, 3) * p(j, 3));
+    }
+    return SCALE ? v * is : v;
+}
+
+// v as hi + lo: hi = v rounded to float, lo = the rest rounded to float
+// (|v - hi - lo| <= 2^-48 |v| roughly).
+__device__ __forceinline__ float2 split_ff(double v) {
+    const float hi = f32_rn(v);
+    return make_float2(hi, f32_rn(v - f64_of_f32(hi)));
+}
+
+// t_T of a record that holds invariants: their float-float sum over the
+// smaller of T and its complement S (the d_i over T, or the d'_i over S,
+// then the s_ij, i < j, by increasing i then j), each term added with an
+// error-free two-sum into (S, E); rounded once to float.
+template <int N>
+__device__ __forceinline__ float rec_denominator(const float2* inv, unsigned T) {
+    constexpr int NP = N * (N - 1) / 2;
+    const bool comp = __popc(T) > N / 2;
+    const unsigned U = comp ? ((1u << N) - 1) & ~T : T;
+    const float2* lin = inv + (comp ? N + NP : 0);
+    float S = 0.0f, E = 0.0f;
+    auto add = [&](const float2 x) {
+        const float s = S + x.x;
+        const float bb = s - S;
+        const float e = (S - (s - bb)) + (x.x - bb);
+        S = s;
+        E += e + x.y;
+    };
+    for (unsigned a = U; a; a &= a - 1) add(lin[__ffs(a) - 1]);
+    for (unsigned a = U; a; a &= a - 1) {
+        const int i = __ffs(a) - 1;
+        for (unsigned b = a & (a - 1); b; b &= b - 1) add(inv[N + pair_index<N>(i, __ffs(b) - 1)]);
+    }
+    return S + E;
 }
 
 // Record of a point that passed the cuts, from its photon momenta (GeV) and
@@ -675,6 +799,7 @@ __device__ __forceinline__ void pass_to_rec(const MomView& v, double irs, const 
             rec.k[a][m] = rec_value<R>(k);
         }
     if constexpr (N <= 5) fill_denominators<R, N, false>(v, 0.5, 1.0, true, rec);   // n >= 6: denominators_parallel
+    rec.e1 = R(0.5);
     rec.e2 = R(0.5);
     rec.n1 = R(1);
     rec.n2 = R(1);

@@ -2,6 +2,7 @@
 // (compiled and run by tests/test_layout.py; no GPU needed).  Exit status 0
 // when every check holds; each failure prints one line.
 #include <cstdio>
+#include <vector>
 
 #include "heget_kernels.cuh"
 
@@ -115,6 +116,95 @@ static void check_shape(bool even) {
     }
 }
 
+// Met-in-the-middle currents: every buffer holds its sizes' rows; the row an
+// item reads for photon position pos of set S, helicities lambda, is row
+// (S - i, lambda without bit pos) of the size below, helicity-major
+// (lambda' C(n, k-1) + rank(S - i)), inside that level; the contraction's
+// rows for set T and configuration lambda are J(T, pext(lambda, T)) and
+// R(all - T, pext(lambda, all - T)).
+static int host_rank(unsigned S, int n) {
+    int r = 0;
+    for (unsigned u = 0; u < S; ++u)
+        if (popcount(u) == popcount(S) && u < (1u << n)) ++r;
+    return r;
+}
+static int host_pext(int x, unsigned m) {
+    int o = 0, k = 0;
+    for (int b = 0; b < 8; ++b)
+        if ((m >> b) & 1u) o |= ((x >> b) & 1) << k++;
+    return o;
+}
+template <class R, int N, int BLOCK>
+static void check_meet() {
+    using MT = MeetTables<R, N, BLOCK>;
+    auto in_buf = [&](int k, int buf) {
+        CHECK(meet_rows(N, k) <= buf, "n=%d: size-%d currents (%d rows) in a buffer of %d", N, k, meet_rows(N, k), buf);
+    };
+    for (int k = 1; k <= MT::M - 1; ++k) in_buf(k, ((MT::M - k) & 1) ? MT::J1 : MT::J0);
+    for (int k = 1; k <= MT::MK - 1; ++k) in_buf(k, ((MT::MK - 1 - k) & 1) ? MT::K1 : MT::K0);
+    CHECK((MT::CH << MT::M) <= MT::J0 && (MT::CH << MT::MK) <= MT::RR, "n=%d: chunk buffers", N);
+    CHECK(MT::M > 1 || MT::CH == MT::CM, "n=%d: one-photon J read in place needs one chunk", N);
+    CHECK(MT::G * MT::GTH <= BLOCK && MT::PG * MT::CT * MT::GT <= MT::GTH, "n=%d: group shape", N);
+    CHECK(MT::G == 1 || 8 + MT::G <= 16, "n=%d: %d groups exceed the named barriers", N, MT::G);
+    CHECK(!MT::XA_OVER || MT::XAB <= (size_t)(MT::J1 + MT::K0 + MT::K1) * sizeof(Row<R>), "n=%d: overlaid amplitudes", N);
+    for (int k = 2; k <= MT::MK; ++k) {
+        const int B = meet_block(k), LB = meet_lb(k), NB = (1 << k) / B;
+        const int CK1 = set_binom(N, k - 1);
+        for (unsigned S = 0; S < (1u << N); ++S) {
+            if (popcount(S) != k) continue;
+            for (int blk = 0; blk < NB; ++blk) {
+                unsigned s = S;
+                for (int pos = 0; pos < k; ++pos) {
+                    const int i = __builtin_ctz(s);
+                    s &= s - 1;
+                    const int ri = host_rank(S ^ (1u << i), N);
+                    for (int b = 0; b < B; ++b) {
+                        const int lam = blk * B + b;
+                        int got;
+                        if ((1 << pos) < B) {
+                            const int d = meet_drop(b, pos);
+                            CHECK(meet_insert(d, pos, (b >> pos) & 1) == b, "n=%d insert/drop", N);
+                            got = blk * (B / 2) * CK1 + ri + d * CK1;
+                        } else {
+                            got = meet_drop(blk, pos - LB) * B * CK1 + ri + b * CK1;
+                        }
+                        const int want = meet_drop(lam, pos) * CK1 + ri;
+                        CHECK(got == want && got < meet_rows(N, k - 1), "n=%d k=%d S=%u blk=%d pos=%d b=%d: row %d, want %d",
+                              N, k, S, blk, pos, b, got, want);
+                    }
+                }
+            }
+        }
+    }
+    // chunk rows: one row per (place, assignment), inside the buffer
+    for (int LOGK : {MT::M, MT::MK}) {
+        std::vector<int> seen((size_t)MT::CH << LOGK, 0);
+        for (int t = 0; t < MT::CH; ++t)
+            for (int lam = 0; lam < (1 << LOGK); ++lam) {
+                const int rr = LOGK == MT::M ? meet_chunk_row<MT::M>(t, lam, MT::CH) : meet_chunk_row<MT::MK>(t, lam, MT::CH);
+                CHECK(rr >= 0 && rr < (MT::CH << LOGK) && !seen[rr]++, "n=%d chunk row (%d, %d) -> %d", N, t, lam, rr);
+            }
+    }
+    // contraction rows in the chunk buffers, as meet_contract forms them
+    const int M = MT::M, CB = MT::CB, CH = MT::CH;
+    const unsigned FULL = (1u << N) - 1;
+    for (unsigned T = 0; T < (1u << N); ++T) {
+        if (popcount(T) != M) continue;
+        const unsigned V = FULL & ~T;
+        const int r = host_rank(T, N), t = r % CH;
+        const int TL = (int)(T & ((1u << CB) - 1)), VL = ((1 << CB) - 1) & ~TL, a = popcount((unsigned)TL);
+        for (int lam = 0; lam < (1 << N); ++lam) {
+            const int hi = lam >> CB, b = lam & ((1 << CB) - 1);
+            const int lt = (host_pext(hi, T >> CB) << a) | host_pext(b, (unsigned)TL);
+            const int lv = (host_pext(hi, V >> CB) << (CB - a)) | host_pext(b, (unsigned)VL);
+            CHECK(lt == host_pext(lam, T) && lv == host_pext(lam, V), "n=%d T=%u lambda=%d: helicities", N, T, lam);
+            const int jrow = meet_chunk_row<MT::M>(t, lt, CH), rrow = meet_chunk_row<MT::MK>(t, lv, CH);
+            CHECK(jrow >= 0 && jrow < (CH << M) && rrow >= 0 && rrow < (CH << MT::MK), "n=%d T=%u lambda=%d: rows %d %d", N,
+                  T, lam, jrow, rrow);
+        }
+    }
+}
+
 static size_t resident_blocks(size_t smem_per_block) {
     const size_t per_sm = 228 * 1024, reserved = 1024;
     return per_sm / (smem_per_block + reserved);
@@ -162,6 +252,19 @@ int main() {
     CHECK(resident_blocks(t7) >= 2, "tile n=7 tree (224 threads): %zu bytes, fewer than 2 blocks per SM", t7);
     const size_t t8 = xsec_smem_bytes<float, 8, 256, kAlgTree>(8);
     CHECK(resident_blocks(t8) >= 2, "tile n=8 tree: %zu bytes, fewer than 2 blocks per SM", t8);
+    check_meet<float, 2, 256>();
+    check_meet<float, 3, 256>();
+    check_meet<float, 4, 256>();
+    check_meet<float, 5, 256>();
+    check_meet<float, 6, 256>();
+    check_meet<float, 7, 256>();
+    check_meet<float, 8, 256>();
+    check_meet<double, 6, 256>();
+    check_meet<double, 8, 256>();
+    const size_t ws8s = ws_smem_bytes<float, 8, kAlgSubset>() + 2 * ws_stage(8, kAlgSubset) * sizeof(SampleDraw) + 256;
+    CHECK(resident_blocks(ws8s) >= 1, "warp-specialised n=8 subset: %zu bytes", ws8s);
+    const size_t ws6s = ws_smem_bytes<float, 6, kAlgSubset>() + 2 * ws_stage(6, kAlgSubset) * sizeof(SampleDraw) + 256;
+    CHECK(resident_blocks(ws6s) >= 2, "warp-specialised n=6 subset: %zu bytes, fewer than 2 blocks per SM", ws6s);
     CHECK(sizeof(SampleDraw) == 16, "SampleDraw is %zu bytes", sizeof(SampleDraw));
     std::printf("layout checks: %d failures\n", failures);
     return failures ? 1 : 0;
