@@ -81,10 +81,23 @@ def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None):
 
 
 def subset_flops_per_point(n: int) -> int:
-    """FP32 flops of the subset recursion per point: sum_k C(n,k) k 2^k chain
-    steps (acc += r . M, 16 FMA = 32 flops) and n 2^n closure terms (8 FMA)."""
-    steps = sum(math.comb(n, k) * k * (1 << k) for k in range(2, n))
-    return 32 * steps + 16 * n * (1 << n)
+    """FP32 flops of the subset recursion per point, met in the middle at
+    m = n // 2 (an FMA counts 2 flops; a current term r.E or E.c and a Q
+    product are 12 FMA each, a closing J.R product 8): J currents of sizes
+    1..m (sizes >= 2: k terms and the Q product; size 1: the Q product), K
+    currents of sizes 1..n-m-1 (the same), R currents of size n-m (n-m terms,
+    no Q; at n = 2 none), and the contraction over the C(n, m) sets T for all
+    2^n helicity configurations."""
+    m, mk = n // 2, n - n // 2
+    fma = 0
+    for k in range(1, m + 1):
+        fma += math.comb(n, k) * (1 << k) * (12 * k + 12 if k >= 2 else 12)
+    for k in range(1, mk):
+        fma += math.comb(n, k) * (1 << k) * (12 * k + 12 if k >= 2 else 12)
+    if mk >= 2:
+        fma += math.comb(n, mk) * (1 << mk) * 12 * mk
+    fma += math.comb(n, m) * (1 << n) * 8
+    return 2 * fma
 
 
 def helas4_flops_per_point(n: int) -> int:
@@ -299,6 +312,30 @@ def time_xsec(H, ctx, n, N, sampler, precision, steps, stream, seed=SEED, i0=0, 
     if detail:
         return total / steps, kern / steps, sum(r.n_pass for r in rs) / steps
     return total / steps
+
+
+def time_amp2_subset(H, ctx, n, M, sampler, stream, flush, steps=5):
+    """Points/s of heget_amp2 (FP32, the context's algorithm) on M phase-space
+    points of the sampler, device time by CUDA events with L2 flushed between
+    steps; the momenta are generated beforehand, outside the timed region."""
+    import torch
+    mom = torch.empty(M * (n + 2) * 4, dtype=torch.float64, device="cuda")
+    H.heget_phase_space_ex(ctx, SEED + 321, 0, M, n, sampler, momenta=mom, stream=stream)
+    amp = torch.empty(M, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        H.heget_amp2(ctx, n, M, mom, amp, precision=H.HEGET_FP32, stream=stream)
+    stream.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.add_(1)
+        stream.wait_stream(torch.cuda.current_stream())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        H.heget_amp2(ctx, n, M, mom, amp, precision=H.HEGET_FP32, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return M / (sorted(ts)[len(ts) // 2] * 1e-3)
 
 
 HIST_SPECS = [(0, 50, 20.0, 520.0), (1, 50, 20.0, 520.0), (2, 50, -2.5, 2.5), (3, 40, 0.4, 8.4),
@@ -546,8 +583,12 @@ def config_rows(H, ctx, stream, peak32, peak64, flush):
         ms64, k64, ev64 = time_xsec(H, ctx, n, n64, S, H.HEGET_FP64, 2 if n < 8 else 1, stream, flush=flush,
                                     detail=True)
         H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
+        # the subset recursion's launch (warp-specialised or a tile kernel) as the autotuner picks it
+        sub_tile, sub_probe_ms = H.heget_autotune(ctx, n, H.HEGET_FP32, 1, min(N, 1 << 18))
         mss, ks, evs = time_xsec(H, ctx, n, N, S, H.HEGET_FP32, 3, stream, flush=flush, detail=True)
+        H.heget_set_tile(ctx, n, H.HEGET_FP32, 1, 0)
         mss64, ks64, evs64 = time_xsec(H, ctx, n, N, S, H.HEGET_FP64, 2, stream, flush=flush, detail=True)
+        amp_pps = time_amp2_subset(H, ctx, n, min(N, 1 << 18), S, stream, flush)
         H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
         # relative errors of the event weights against the oracle
         if isinstance(err_sample, str):
@@ -576,10 +617,20 @@ def config_rows(H, ctx, stream, peak32, peak64, flush):
             "fp64_plain": {"points_per_s": n64 / (ms64 * 1e-3), "evaluated_per_s": ev64 / (ms64 * 1e-3),
                            "timed_points": n64, "kernel_ms": k64,
                            "frac_of_fp64_peak": tf * ev64 / (k64 * 1e-3) / (FP64_PEAK * 1e12)},
-            "subset_recursion": {"fp32_points_per_s": N / (mss * 1e-3), "fp64_points_per_s": N / (mss64 * 1e-3),
+            "subset_recursion": {"fp32_points_per_s": N / (mss * 1e-3), "fp32_evaluated_per_s": evs / (mss * 1e-3),
+                                 "fp64_points_per_s": N / (mss64 * 1e-3),
                                  "flops_per_evaluated_point": sf,
+                                 "launch": "warp-specialised kernel" if sub_tile == 0 else f"tile kernel, {sub_tile}-point tiles",
+                                 "autotune_probe_ms": sub_probe_ms,
                                  "fp32_frac_of_fp32_peak": sf * evs / (ks * 1e-3) / (FP32_PEAK * 1e12),
-                                 "fp64_frac_of_fp64_peak": sf * evs64 / (ks64 * 1e-3) / (FP64_PEAK * 1e12)},
+                                 "fp32_frac_of_measured_fp32_peak": sf * evs / (ks * 1e-3) / (peak32 * 1e12),
+                                 "fp64_frac_of_fp64_peak": sf * evs64 / (ks64 * 1e-3) / (FP64_PEAK * 1e12),
+                                 "amplitudes_only": {
+                                     "points_per_s": amp_pps,
+                                     "frac_of_fp32_peak": sf * amp_pps / (FP32_PEAK * 1e12),
+                                     "frac_of_measured_fp32_peak": sf * amp_pps / (peak32 * 1e12),
+                                     "path": "heget_amp2 FP32 on this workload's FP64 phase-space points (every "
+                                             "point evaluated; input rows from HBM, FP64 invariants, FP32 recursion)"}},
             "rel_err_vs_oracle": {"fp32_median_max": errs[H.HEGET_FP32][0], "fp64_median_max": errs[H.HEGET_FP64][0],
                                   "points_compared": errs[H.HEGET_FP32][1],
                                   "masks_agree": errs[H.HEGET_FP32][2] and errs[H.HEGET_FP64][2],

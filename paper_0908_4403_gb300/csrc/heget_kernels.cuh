@@ -711,10 +711,11 @@ constexpr int kBarProducers = 6;                              // producers' stag
 __host__ __device__ constexpr int ws_consumers(int n, int alg) { return n == 6 && alg == 0 ? 160 : 256; }
 // Points per stage (= producer threads, a multiple of 32): as many as the
 // shared memory of the ring, the producers' staging and the round tables
-// allows at two (n <= 6) or one (n >= 7) resident blocks per SM; 64 for the
-// tree at n = 6, whose FP64 generation then spans two warps.
+// allows at two resident blocks per SM; 64 at n = 5, 6, whose FP64
+// generation then spans two warps (one warp leaves the FP64 pipe waiting on
+// its own latencies).
 __host__ __device__ constexpr int ws_stage(int n, int alg) {
-    return n <= 4 ? 128 : n == 5 ? 64 : n == 6 && alg == 0 ? 64 : 32;
+    return n <= 4 ? 128 : n <= 6 ? 64 : 32;
 }
 
 __device__ __forceinline__ void named_sync(int id, int count) {

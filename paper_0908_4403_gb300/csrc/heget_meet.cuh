@@ -46,6 +46,8 @@
 // tables built once per call.
 #pragma once
 
+#include <type_traits>
+
 #include "heget_amp.cuh"
 
 namespace heget {
@@ -519,31 +521,40 @@ __device__ __noinline__ void amplitude_rounds_meet(unsigned char* table_smem, Po
                 }
                 if (c0 + CH < CM) meet_sync<BAR, BLOCK, GBAR0, GTH, G>(g);   // before the next chunk's currents
             }
+            // the groups' amplitudes, configuration-major (entry ((u PG + p) 2^CB
+            // + b) CT + hi for lambda = (hi << CB) | b): a warp's lanes store
+            // consecutive words
             if (mine) {
-                R* xa = tb.XA(g) + (((size_t)gt * PG + p) * NS + ((size_t)hi << CB)) * 2;
+                R* xa = tb.XA(g) + (((size_t)gt * PG + p) << CB) * CT * 2 + (size_t)hi * 2;
 #pragma unroll
                 for (int b = 0; b < (1 << CB); ++b) {
-                    xa[2 * b] = are[b];
-                    xa[2 * b + 1] = aim[b];
+                    using V2 = typename std::conditional<sizeof(R) == sizeof(float), float2, double2>::type;
+                    V2 v2;
+                    v2.x = are[b];
+                    v2.y = aim[b];
+                    *reinterpret_cast<V2*>(xa + (size_t)b * CT * 2) = v2;
                 }
             }
             meet_sync<BAR, BLOCK, GBAR0, GTH, G>(g);
-            // one warp per point: groups added in order, w_h |A_h|^2 summed over h
+            // one warp per point: groups added in order, w_h |A_h|^2 summed
+            // over h (lane order: hi fastest, as stored)
             for (int q = lid >> 5; q < rc; q += GTH / 32) {
                 const int lane = lid & 31;
                 const bool valid = rb[q].valid;
                 const int hsel = valid ? rb[q].hsel : -1;
                 R v = R(0);
                 if (valid)
-                    for (int h = lane; h < NS; h += 32) {
+                    for (int x = lane; x < NS; x += 32) {
+                        const int hh = x % CT, b = x / CT;
+                        const unsigned h = ((unsigned)hh << CB) | (unsigned)b;
                         R ar = R(0), ai = R(0);
 #pragma unroll
                         for (int u = 0; u < GT; ++u) {
-                            const R* a = tb.XA(g) + (((size_t)u * PG + q) * NS + h) * 2;
+                            const R* a = tb.XA(g) + ((((size_t)u * PG + q) << CB) + b) * CT * 2 + (size_t)hh * 2;
                             ar += a[0];
                             ai += a[1];
                         }
-                        v += (ar * ar + ai * ai) * R(sel_weight<N>(hsel, (unsigned)h, lane_weight<N>(mask, (unsigned)h)));
+                        v += (ar * ar + ai * ai) * R(sel_weight<N>(hsel, h, lane_weight<N>(mask, h)));
                     }
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
