@@ -59,16 +59,22 @@ FP64_FLOPS_PER_POINT = {4: 714}
 FP64_STEP_TRAFFIC = {4: 154624}
 
 
-def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None):
+def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None, subset=False):
     """Roofline of the fused step's kernel.  At n <= 4 the FP64 pipe binds
     (the phase space is FP64 by design; one SM retires 2 DFMA per clock
     against 128 FFMA), above that the FP32 tree does.  n_eval: points whose
-    amplitudes were evaluated (those that pass the cuts)."""
-    tree = tree_flops_per_point(n) * (N if n_eval is None else n_eval) / kern_s / 1e12
+    amplitudes were evaluated (those that pass the cuts).  subset: the step
+    ran the subset recursion (its own flop count, FP32 pipe)."""
+    fpp = subset_flops_per_point(n) if subset else tree_flops_per_point(n)
+    tree = fpp * (N if n_eval is None else n_eval) / kern_s / 1e12
     fp32 = {"pipe": "fp32 fma", "achieved": tree, "peak": FP32_PEAK, "frac": tree / FP32_PEAK,
-            "flops_per_point": tree_flops_per_point(n), "measured_peak": peak32_meas,
+            "flops_per_point": fpp, "measured_peak": peak32_meas,
             "frac_of_measured": tree / peak32_meas}
-    kern = f"xsec_ws_kernel<float,{n}>" if n <= 5 else f"xsec_kernel<float,{n},256>"
+    if subset:
+        return {"bound": "alu", **fp32, "unit": "TFLOP/s", "traffic": None,
+                "kernel": f"xsec_ws_kernel<float,{n}> (subset recursion)",
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz"}
+    kern = f"xsec_ws_kernel<float,{n}>" if n <= 5 else f"xsec_kernel<float,{n},{ {6: 160, 7: 224}.get(n, 256)}>"
     if n in FP64_FLOPS_PER_POINT:
         a64 = FP64_FLOPS_PER_POINT[n] * N / kern_s / 1e12
         return {"bound": "alu", "pipe": "fp64", "achieved": a64, "peak": FP64_PEAK, "unit": "TFLOP/s",
@@ -656,6 +662,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--n", type=int, default=N_PHOTONS, help="photons (profiling of smaller cases)")
     ap.add_argument("--points", type=int, default=POINTS, help="points per step per GPU")
+    ap.add_argument("--alg", default="tree", choices=["tree", "subset"],
+                    help="ordering-sum algorithm of the timed step (profiling of the subset recursion)")
+    ap.add_argument("--sampler", default="toy", choices=["toy", "uniform"],
+                    help="sqrt(s-hat) sampler of the timed step: toy PDF, or uniform 200 GeV..2 TeV")
     ap.add_argument("--no-configs", action="store_true",
                     help="leave out the per-workload rows (n = 2, 4, 6, 8; profiling runs)")
     ap.add_argument("--matrix", action="store_true", help=argparse.SUPPRESS)   # the rows are in the default line
@@ -680,7 +690,9 @@ def main():
     from paper_0908_4403_gb300 import dist as D
     n, N = args.n, args.points
     i0, _ = D.shard(N * ws, ws, rank)   # weak scaling: N points per rank, contiguous ranges
-    sampler = H.sampler_toy_pdf()
+    sampler = H.sampler_toy_pdf() if args.sampler == "toy" else H.sampler_uniform(200.0, 2000.0)
+    if args.alg == "subset":
+        H.heget_set_algorithm(ctx, H.HEGET_ALG_SUBSET)
     res = torch.zeros(80, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
     flush.random_(0, 255)
@@ -732,6 +744,7 @@ def main():
     if ws > 1:   # the job's cross section of the last step: per-rank sums combined in rank order
         r = D.allreduce_result(r, sampler.kind)
 
+    H.heget_set_algorithm(ctx, H.HEGET_ALG_TREE)
     # the plain FP64 GPU kernel on the same workload (the comparison the
     # workload is quoted with)
     fp64_steps = max(3, min(20, args.steps // 20))
@@ -800,8 +813,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 chain + f64 phase space/accumulation",
             "data": "synthetic (on-device Philox4x32-10 counter RNG from a seed; toy PDF)",
-            "config": {"workload": WORKLOAD if (n, N) == (N_PHOTONS, POINTS) else f"n={n}, {N} points/step, toy PDF",
-                       "n": n, "points_per_step": N * ws, "precision": "fp32", "path": PATH,
+            "config": {"workload": WORKLOAD if (n, N, args.sampler) == (N_PHOTONS, POINTS, "toy")
+                       else f"n={n}, {N} points/step, {args.sampler} sqrt(s-hat)",
+                       "n": n, "points_per_step": N * ws, "precision": "fp32",
+                       "path": PATH if args.alg == "tree" else "subset recursion (HEGET_ALG_SUBSET), FP32",
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "compaction": "value counts the points whose |M|^2 is evaluated: those that pass the "
                                      "cuts (the others have weight 0 and no amplitude); events_per_s counts every "
@@ -809,7 +824,8 @@ def main():
                        "parallelism": f"dp{ws} (point shards)"},
             "events_per_s": total_points / (step_ms * 1e-3),
             "pass_fraction": evaluated / total_points,
-            "roofline": roofline(n, N, kern_s, peak32, peak64, n_eval=evaluated / ws / args.steps),
+            "roofline": roofline(n, N, kern_s, peak32, peak64, n_eval=evaluated / ws / args.steps,
+                                 subset=args.alg == "subset"),
             "gpu_launches": 2 * args.steps,
             "e2e": {"value": e2e_eval / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 80, "events_per_s": N * ws * args.e2e_steps / e2e_s,

@@ -244,8 +244,12 @@ typedef struct {
 
 /* Many cross sections in one fused launch per precision (batching of the
  * serving path; the paper runs one process per kernel call, Sec. 3.1).
- * Every request is cut into the same point tiles heget_xsec uses on the
- * plain (non-warp-specialised) path; the tiles of all requests, whatever
+ * Every request is cut into point tiles: the context's xsec tile if set
+ * (heget_set_tile), else with the tree the tiles heget_xsec uses on the
+ * plain (non-warp-specialised) path, with the subset recursion tiles of 128
+ * points (FP32: 64 at n = 5, 6, 32 at n = 7, 8; FP64: 64 at n = 4, 16 at
+ * n = 5, 8 from n = 6), the largest that let two blocks share an SM.  The
+ * kernel is compiled once per algorithm.  The tiles of all requests, whatever
  * their n and N, form one work list that a single kernel walks, and each
  * request's tile partials are combined in tile order, so a request's result
  * does not depend on what else is in the batch.  reqs: host array of `count`
@@ -453,16 +457,19 @@ void heget_graph_destroy(heget_graph* g);
  * device.  Submitted requests wait in arrival order until fewer than
  * max_inflight are admitted and the device arena (arena_bytes, default
  * min(256 MiB, free HBM x (1 - hbm_reserve_frac))) has room for their tile
- * partials (64 bytes per tile of heget_xsec's tile size, plus the result).
- * Each launch of the mixed-n batch kernel takes tiles round-robin from every
- * admitted request until about max_launch_work FP32-flop
- * equivalents are filled, so requests arriving while others run share the
- * next launch with them; up to two launches are in flight.  A request's
- * result is bitwise the heget_xsec_batch result of the same request, whatever
- * else shared its launches.  Zero fields of cfg (or cfg = NULL) take the
- * defaults: max_inflight 256, max_launch_work 2e11, hbm_reserve_frac 0.1.
- * ctx must outlive the server and must not change its parameters or tiles
- * while requests are in flight. */
+ * partials (64 bytes per tile of heget_xsec_batch's tile size, plus the
+ * result).  Each launch of the mixed-n batch kernel takes tiles round-robin
+ * from every admitted request until about max_launch_work FP32-flop
+ * equivalents are filled (the amplitude flops of the server's algorithm per
+ * point, an FP64 flop counting 16, plus the event generation), so requests
+ * arriving while others run share the next launch with them; up to two
+ * launches are in flight.  A request's result is bitwise the
+ * heget_xsec_batch result of the same request, whatever else shared its
+ * launches.  Zero fields of cfg (or cfg = NULL) take the defaults:
+ * max_inflight 256, max_launch_work 2e11, hbm_reserve_frac 0.1.  The server
+ * keeps the ordering-sum algorithm ctx has at heget_server_start.  ctx must
+ * outlive the server and must not change its parameters or tiles while
+ * requests are in flight. */
 typedef struct heget_server heget_server;
 typedef struct {
     int max_inflight;        /* admitted requests at once (>= 1) */
@@ -544,9 +551,11 @@ int heget_measure_fma_peak(heget_ctx* ctx, int precision, double* tflops);
  * at most 4096 x the default xsec tile (for example 262,144 points at n = 6,
  * 131,072 at n = 7 and 32,768 at n = 8 in FP32, 524,288 at n <= 4 in FP64).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) and keeps it; make that first call before any
- * stream capture.  The address belongs to the device's primary context:
- * after cudaDeviceReset a process must not call this again on that device.
+ * (cudaGetSymbolAddress) and keeps it with the CUDA context current at the
+ * time; make that first call before any stream capture.  A call under
+ * another context of that device (after cudaDeviceReset, or a context made
+ * current through the driver API) looks the address up again, so the same
+ * rule holds for the first call under each new context.
  * Every call shares the one array per device and leaves its contents
  * behind; nothing in it needs clearing, but calls that overlap on the GPU
  * (concurrent streams) race on it and must not be issued.

@@ -390,20 +390,37 @@ namespace {
 // list; 16.7 M points at n = 8, 537 M at n <= 4).
 constexpr long long kMaxBatchTiles = 1ll << 22;
 
-template <class R>
-size_t batch_tile_smem(int n, int tile) {
+template <class R, int ALG>
+size_t batch_tile_smem_t(int n, int tile) {
     switch (n) {
-        case 2: return xsec_smem_bytes<R, 2, kBatchThreads>(tile);
-        case 3: return xsec_smem_bytes<R, 3, kBatchThreads>(tile);
-        case 4: return xsec_smem_bytes<R, 4, kBatchThreads>(tile);
-        case 5: return xsec_smem_bytes<R, 5, kBatchThreads>(tile);
-        case 6: return xsec_smem_bytes<R, 6, kBatchThreads>(tile);
-        case 7: return xsec_smem_bytes<R, 7, kBatchThreads>(tile);
-        default: return xsec_smem_bytes<R, 8, kBatchThreads>(tile);
+        case 2: return xsec_smem_bytes<R, 2, kBatchThreads, ALG>(tile);
+        case 3: return xsec_smem_bytes<R, 3, kBatchThreads, ALG>(tile);
+        case 4: return xsec_smem_bytes<R, 4, kBatchThreads, ALG>(tile);
+        case 5: return xsec_smem_bytes<R, 5, kBatchThreads, ALG>(tile);
+        case 6: return xsec_smem_bytes<R, 6, kBatchThreads, ALG>(tile);
+        case 7: return xsec_smem_bytes<R, 7, kBatchThreads, ALG>(tile);
+        default: return xsec_smem_bytes<R, 8, kBatchThreads, ALG>(tile);
     }
 }
 
 }  // namespace
+
+namespace heget {
+size_t batch_tile_smem(int n, int precision, int alg, int tile) {
+    if (precision == HEGET_FP32)
+        return alg == kAlgSubset ? batch_tile_smem_t<float, kAlgSubset>(n, tile) : batch_tile_smem_t<float, kAlgTree>(n, tile);
+    return alg == kAlgSubset ? batch_tile_smem_t<double, kAlgSubset>(n, tile) : batch_tile_smem_t<double, kAlgTree>(n, tile);
+}
+
+int batch_default_tile(int n, int precision, int alg) {
+    // subset recursion: the largest tile whose block (records, staging and
+    // the recursion's tables) still lets two blocks share an SM, up to 128
+    static const int sub32[9] = {0, 0, 128, 128, 128, 64, 64, 32, 32};
+    static const int sub64[9] = {0, 0, 128, 128, 64, 16, 8, 8, 8};
+    if (alg != kAlgSubset) return default_tile(n, true);
+    return precision == HEGET_FP64 ? sub64[n] : sub32[n];
+}
+}  // namespace heget
 
 namespace heget {
 // Grows a workspace buffer to at least `need` bytes (device or pinned host).
@@ -966,7 +983,7 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
         for (int i = 0; i < count; ++i) {
             const heget_xsec_request& q = reqs[i];
             const int tile_o = ctx->tiles[1][q.precision == HEGET_FP64][q.n];
-            const long long tile = tile_o > 0 ? tile_o : default_tile(q.n, true);
+            const long long tile = tile_o > 0 ? tile_o : batch_default_tile(q.n, q.precision, ctx->alg);
             tiles[q.precision == HEGET_FP64] += (q.N + tile - 1) / tile;
             if (tiles[0] > kMaxBatchTiles || tiles[1] > kMaxBatchTiles)
                 return fail(HEGET_EINVAL, "batch needs more than %lld point tiles per precision: split it",
@@ -989,7 +1006,7 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
             const heget_xsec_request& q = reqs[i];
             if (q.precision != prec) continue;
             const int tile_o = ctx->tiles[1][prec == HEGET_FP64][q.n];
-            const int tile = tile_o > 0 ? tile_o : default_tile(q.n, true);
+            const int tile = tile_o > 0 ? tile_o : batch_default_tile(q.n, prec, ctx->alg);
             BatchReq b{};
             b.seed = q.seed;
             b.i0 = q.i0;
@@ -1005,7 +1022,7 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
                 items.push_back(WorkItem{(int)br.size(), q.n, (int)std::min<long long>(tile, q.N - start), 0, start});
             b.ntiles = (int)items.size() - b.pad;
             br.push_back(b);
-            const size_t sm = prec == HEGET_FP32 ? batch_tile_smem<float>(q.n, tile) : batch_tile_smem<double>(q.n, tile);
+            const size_t sm = batch_tile_smem(q.n, prec, ctx->alg, tile);
             smem = std::max(smem, sm);
         }
         if (br.empty()) continue;
@@ -1045,16 +1062,16 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
         const int grid = std::max(1, std::min(nitems, 8 * ctx->num_sms));
         const int nreq = (int)br.size();
         auto launch = [&](cudaStream_t s2, bool set_attr) {
-            int rr = prec == HEGET_FP32 ? launch_batch_f32(items_d, nitems, reqs_d, smem, grid, s2, set_attr)
-                                        : launch_batch_f64(items_d, nitems, reqs_d, smem, grid, s2, set_attr);
+            int rr = prec == HEGET_FP32 ? launch_batch_f32(items_d, nitems, reqs_d, smem, grid, ctx->alg, s2, set_attr)
+                                        : launch_batch_f64(items_d, nitems, reqs_d, smem, grid, ctx->alg, s2, set_attr);
             if (!rr) rr = launch_batch_finalize(reqs_d, nreq, s2);
             return rr;
         };
         if (ctx->graphs) {
             // the kernel's shared-memory attribute is set outside the capture
-            r = prec == HEGET_FP32 ? prepare_batch_f32(smem) : prepare_batch_f64(smem);
+            r = prec == HEGET_FP32 ? prepare_batch_f32(smem, ctx->alg) : prepare_batch_f64(smem, ctx->alg);
             if (!r)
-                r = ctx->batch_graphs.run(BatchGraphKey{prec, nitems, nreq, grid, smem, items_d, reqs_d, reqs_d}, st,
+                r = ctx->batch_graphs.run(BatchGraphKey{prec, ctx->alg, nitems, nreq, grid, smem, items_d, reqs_d, reqs_d}, st,
                                           [&](cudaStream_t s2) { return launch(s2, false); });
         } else {
             r = launch(st, true);
@@ -1076,10 +1093,12 @@ extern "C" int heget_xsec_batch(heget_ctx* ctx, const heget_xsec_request* reqs, 
 // code cannot hand the array's name to a kernel (in host code it names a
 // host-side stand-in), so the first call on each device looks up the device
 // address with cudaGetSymbolAddress while that device is current and caches
-// it.  The address belongs to the device's primary context: after a
-// cudaDeviceReset the process must not call this again on that device.  Each
-// call's blocks overwrite exactly the entries its own finalize reads, so
-// nothing has to be cleared between calls.
+// it together with the CUDA context that was current then.  The address
+// belongs to that context: a later call under another context of the same
+// device (after cudaDeviceReset, or from a context the caller made current
+// through the driver API) looks it up again instead of reusing a stale
+// address.  Each call's blocks overwrite exactly the entries its own finalize
+// reads, so nothing has to be cleared between calls.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kNoAllocMaxBlocks = 4096;   // 4096 partials x 64 B = 256 KiB per device
@@ -1088,18 +1107,45 @@ constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) Partial g_noalloc_partials[kNoAllocMaxBlocks];
 
 std::mutex g_noalloc_mu;
-Partial* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+struct NoAllocSlot {
+    void* ctx;        // the CUDA context current when ptr was looked up
+    Partial* ptr;
+};
+NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices] = {};
+
+// The calling thread's current CUDA context (cuCtxGetCurrent, reached through
+// the runtime's driver entry points so that the library needs no link to the
+// driver library), or nullptr when there is none or it cannot be queried.
+void* current_context() {
+    using GetCurrent = int (*)(void**);
+    static GetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (GetCurrent) nullptr;
+        }
+        return reinterpret_cast<GetCurrent>(f);
+    }();
+    void* c = nullptr;
+    if (!fn || fn(&c) != 0) return nullptr;
+    return c;
+}
 
 int noalloc_scratch(int device, Partial** out) {
     if (device < 0 || device >= kNoAllocMaxDevices) return fail(HEGET_EINVAL, "device %d out of range", device);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    NoAllocSlot& s = g_noalloc_slot[device];
+    void* ctx = current_context();
+    if (!s.ptr || !ctx || ctx != s.ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);   // caller made `device` current
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
-        g_noalloc_ptr[device] = static_cast<Partial*>(p);
+        s.ptr = static_cast<Partial*>(p);
+        s.ctx = current_context();   // the lookup made the primary context current if none was
     }
-    *out = g_noalloc_ptr[device];
+    *out = s.ptr;
     return HEGET_OK;
 }
 }  // namespace

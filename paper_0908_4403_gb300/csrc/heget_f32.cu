@@ -12,11 +12,11 @@ int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* 
 #undef CALL
 }
 
-int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid, int alg,
                      cudaStream_t st, bool set_attr) {
-    return launch_batch_t<float>(items, nitems, reqs, smem, grid, st, set_attr);
+    return launch_batch_t<float>(items, nitems, reqs, smem, grid, alg, st, set_attr);
 }
 
-int prepare_batch_f32(size_t smem) { return prepare_batch_t<float>(smem); }
+int prepare_batch_f32(size_t smem, int alg) { return prepare_batch_t<float>(smem, alg); }
 
 }  // namespace heget

@@ -12,12 +12,12 @@ int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* 
 #undef CALL
 }
 
-int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid, int alg,
                      cudaStream_t st, bool set_attr) {
-    return launch_batch_t<double>(items, nitems, reqs, smem, grid, st, set_attr);
+    return launch_batch_t<double>(items, nitems, reqs, smem, grid, alg, st, set_attr);
 }
 
-int prepare_batch_f64(size_t smem) { return prepare_batch_t<double>(smem); }
+int prepare_batch_f64(size_t smem, int alg) { return prepare_batch_t<double>(smem, alg); }
 
 int launch_escalate_f64(int n, uint64_t seed, long long i0, const SamplerArgs& S, const Physics& ph, int tile,
                         const EscArgs& esc, Partial* out, double* w_out, int grid, cudaStream_t st) {

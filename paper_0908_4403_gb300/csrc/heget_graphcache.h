@@ -22,14 +22,14 @@
 namespace heget {
 
 struct BatchGraphKey {
-    int prec, nitems, nfin, grid;
+    int prec, alg, nitems, nfin, grid;   // alg: the work-list kernel's ordering-sum algorithm
     size_t smem;
     const void* items;
     const void* reqs;
     const void* fin;
     bool operator==(const BatchGraphKey& o) const {
-        return prec == o.prec && nitems == o.nitems && nfin == o.nfin && grid == o.grid && smem == o.smem &&
-               items == o.items && reqs == o.reqs && fin == o.fin;
+        return prec == o.prec && alg == o.alg && nitems == o.nitems && nfin == o.nfin && grid == o.grid &&
+               smem == o.smem && items == o.items && reqs == o.reqs && fin == o.fin;
     }
 };
 

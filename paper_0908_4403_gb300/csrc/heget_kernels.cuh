@@ -637,7 +637,10 @@ struct WorkItem {
     long long start;  // first point of the tile, relative to the request
 };
 
-template <class R>
+// One instantiation per ordering-sum algorithm (ALG = kAlgTree or kAlgSubset,
+// the context's, uniform over a batch), so that neither algorithm's code
+// shapes the other's registers and instruction footprint.
+template <class R, int ALG>
 __global__ void __launch_bounds__(kBatchThreads)
 xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq* __restrict__ reqs) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -652,8 +655,8 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
         switch (w.n) {
 #define HEGET_BATCH_CASE(NN)                                                                                   \
     case NN:                                                                                                   \
-        xsec_tile<R, NN, kBatchThreads>(smem, rq.tile, rq.seed, first, w.count, rq.S, rq.ph, acc, wo, kNoEsc, \
-                                        esc_n);                                                        \
+        xsec_tile<R, NN, kBatchThreads, false, ALG>(smem, rq.tile, rq.seed, first, w.count, rq.S, rq.ph, acc, wo, \
+                                                     kNoEsc, esc_n);                                           \
         break;
             HEGET_BATCH_CASE(2)
             HEGET_BATCH_CASE(3)
@@ -931,12 +934,19 @@ int launch_ward_f32(int n, const double* mom, long long npts, int ward, double* 
 int launch_ward_f64(int n, const double* mom, long long npts, int ward, double* out, const Physics& ph, int* flag,
                     const AmpLaunch& L, cudaStream_t st);
 // Mixed-n batch launch (one launch per precision); smem sized for the tiles.
-int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+// alg: the ordering-sum algorithm of every item (kAlgTree or kAlgSubset).
+int launch_batch_f32(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid, int alg,
                      cudaStream_t st, bool set_attr = true);
-int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+int launch_batch_f64(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid, int alg,
                      cudaStream_t st, bool set_attr = true);
-int prepare_batch_f32(size_t smem);
-int prepare_batch_f64(size_t smem);
+int prepare_batch_f32(size_t smem, int alg);
+int prepare_batch_f64(size_t smem, int alg);
+// Shared memory of a batch tile of n photons at `precision` with algorithm alg.
+size_t batch_tile_smem(int n, int precision, int alg, int tile);
+// Points per batch tile when the context sets none: the fused tile kernel's
+// default for the tree; for the subset recursion tiles that fill two blocks
+// per SM (its per-point cost is far below the tree's at large n).
+int batch_default_tile(int n, int precision, int alg);
 // One block per request: its tile partials, in order, into its result.
 int launch_batch_finalize(const BatchReq* reqs, int nreqs, cudaStream_t st);
 

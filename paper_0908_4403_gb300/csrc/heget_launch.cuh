@@ -181,18 +181,19 @@ static int launch_ward_n(const double* mom, long long npts, int ward, double* ou
 }
 
 template <class R>
-static int prepare_batch_t(size_t smem) {
-    return (int)cudaFuncSetAttribute(xsec_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static int prepare_batch_t(size_t smem, int alg) {
+    return (int)cudaFuncSetAttribute(alg == kAlgSubset ? xsec_batch_kernel<R, kAlgSubset> : xsec_batch_kernel<R, kAlgTree>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 // set_attr = false: the caller has run prepare_batch_t for this smem (inside
 // a stream capture, where only the launch is recorded).
 template <class R>
-static int launch_batch_t(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid,
+static int launch_batch_t(const WorkItem* items, int nitems, const BatchReq* reqs, size_t smem, int grid, int alg,
                           cudaStream_t st, bool set_attr) {
-    auto k = xsec_batch_kernel<R>;
+    auto k = alg == kAlgSubset ? xsec_batch_kernel<R, kAlgSubset> : xsec_batch_kernel<R, kAlgTree>;
     if (set_attr) {
-        const int e = prepare_batch_t<R>(smem);
+        const int e = prepare_batch_t<R>(smem, alg);
         if (e) return e;
     }
     k<<<grid, kBatchThreads, smem, st>>>(items, nitems, reqs);

@@ -34,18 +34,40 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// FP32-flop equivalents per point: the tree (2^n lanes, 28 flop per step,
-// 16 per closure) plus the phase-space generation (~1e3 FP64 operations at
-// ~1/64 of the FP32 rate).
-double point_cost(int n) {
-    double f = 1;
-    for (int i = 2; i <= n; ++i) f *= i;
-    double steps = 0, term = 1;
-    for (int l = 1; l <= n - 1; ++l) {
-        term *= (n - l + 1);
-        if (l >= 2) steps += term;
+// FP32-flop equivalents per point: the amplitudes of the server's
+// ordering-sum algorithm -- the tree (2^n lanes, 28 flop per step, 16 per
+// closure) or the subset recursion met in the middle (12 multiply-adds per
+// current term and Q product, 8 per contraction term over the sets of n/2
+// photons, for every helicity assignment of each set) -- with an FP64 flop
+// counted as 16 (the measured FP64/FP32 rate ratio of these kernels is 10 to
+// 40), plus the phase-space generation (~1e3 FP64 operations at ~1/64 of
+// the FP32 rate).
+double binom(int n, int k) {
+    double c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+    return c;
+}
+double point_cost(int n, int alg, int precision) {
+    double amp = 0;
+    if (alg == kAlgSubset) {
+        const int m = n / 2, mk = n - m;
+        double fma = 0;
+        for (int k = 1; k <= m; ++k) fma += binom(n, k) * (1 << k) * (k >= 2 ? 12.0 * k + 12.0 : 12.0);
+        for (int k = 1; k < mk; ++k) fma += binom(n, k) * (1 << k) * (k >= 2 ? 12.0 * k + 12.0 : 12.0);
+        if (mk >= 2) fma += binom(n, mk) * (1 << mk) * 12.0 * mk;
+        fma += binom(n, m) * (1 << n) * 8.0;
+        amp = 2.0 * fma;
+    } else {
+        double f = 1;
+        for (int i = 2; i <= n; ++i) f *= i;
+        double steps = 0, term = 1;
+        for (int l = 1; l <= n - 1; ++l) {
+            term *= (n - l + 1);
+            if (l >= 2) steps += term;
+        }
+        amp = (double)(1 << n) * (28.0 * steps + 16.0 * f);
     }
-    return (double)(1 << n) * (28.0 * steps + 16.0 * f) + 6.4e4;
+    return amp * (precision == HEGET_FP64 ? 16.0 : 1.0) + 6.4e4;
 }
 
 struct Req {
@@ -66,19 +88,6 @@ struct Launch {
     bool busy = false;
 };
 
-template <class R>
-size_t xsec_smem_dispatch(int n, int tile) {
-    switch (n) {
-        case 2: return xsec_smem_bytes<R, 2, kBatchThreads>(tile);
-        case 3: return xsec_smem_bytes<R, 3, kBatchThreads>(tile);
-        case 4: return xsec_smem_bytes<R, 4, kBatchThreads>(tile);
-        case 5: return xsec_smem_bytes<R, 5, kBatchThreads>(tile);
-        case 6: return xsec_smem_bytes<R, 6, kBatchThreads>(tile);
-        case 7: return xsec_smem_bytes<R, 7, kBatchThreads>(tile);
-        default: return xsec_smem_bytes<R, 8, kBatchThreads>(tile);
-    }
-}
-
 }  // namespace
 
 struct heget_server {
@@ -92,6 +101,7 @@ struct heget_server {
     Launch launches[2];
     int next_launch = 0;
     bool graphs = false;                         // the context's graph setting when the server started
+    int alg = 0;                                 // the context's ordering-sum algorithm when the server started
     heget::BatchGraphCache graph_cache;          // per-round launches by launch-shape bucket (worker thread)
 
     std::mutex mu;
@@ -174,7 +184,7 @@ int heget_server::build_and_launch(Launch& L) {
             Req* r = take[i];
             if (r->next_tile + ntake[i] >= r->ntiles) continue;
             ++ntake[i];
-            budget -= point_cost(r->q.n) * r->tile;
+            budget -= point_cost(r->q.n, alg, r->q.precision) * r->tile;
             any = true;
         }
     }
@@ -209,8 +219,7 @@ int heget_server::build_and_launch(Launch& L) {
             P.fin.push_back(b);
             finishing.push_back(r);
         }
-        const size_t sm = r->q.precision == HEGET_FP32 ? xsec_smem_dispatch<float>(r->q.n, r->tile)
-                                                       : xsec_smem_dispatch<double>(r->q.n, r->tile);
+        const size_t sm = batch_tile_smem(r->q.n, r->q.precision, alg, r->tile);
         P.smem = std::max(P.smem, sm);
     }
     size_t bytes = 0;
@@ -251,16 +260,16 @@ int heget_server::build_and_launch(Launch& L) {
         const BatchReq* fin_d = reinterpret_cast<const BatchReq*>(L.dev + P.off_fin);
         const int nfin = (int)P.fin.size();
         auto launch = [&](cudaStream_t s2, bool set_attr) {
-            int rr = pi == 0 ? launch_batch_f32(items_d, nitems, br_d, P.smem, grid, s2, set_attr)
-                             : launch_batch_f64(items_d, nitems, br_d, P.smem, grid, s2, set_attr);
+            int rr = pi == 0 ? launch_batch_f32(items_d, nitems, br_d, P.smem, grid, alg, s2, set_attr)
+                             : launch_batch_f64(items_d, nitems, br_d, P.smem, grid, alg, s2, set_attr);
             if (!rr && nfin > 0) rr = launch_batch_finalize(fin_d, nfin, s2);
             return rr;
         };
         int r;
         if (graphs) {
-            r = pi == 0 ? prepare_batch_f32(P.smem) : prepare_batch_f64(P.smem);
+            r = pi == 0 ? prepare_batch_f32(P.smem, alg) : prepare_batch_f64(P.smem, alg);
             if (!r)
-                r = graph_cache.run(BatchGraphKey{pi == 0 ? HEGET_FP32 : HEGET_FP64, nitems, nfin, grid, P.smem,
+                r = graph_cache.run(BatchGraphKey{pi == 0 ? HEGET_FP32 : HEGET_FP64, alg, nitems, nfin, grid, P.smem,
                                                   items_d, br_d, fin_d},
                                     stream, [&](cudaStream_t s2) { return launch(s2, false); });
         } else {
@@ -382,6 +391,7 @@ int heget_server_start(heget_ctx* ctx, const heget_server_cfg* cfg_in, heget_ser
     heget_server* s = new heget_server();
     s->ctx = ctx;
     s->graphs = ctx->graphs != 0;
+    s->alg = ctx->alg;
     s->cfg = cfg;
     e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->arena_dev, arena);
@@ -408,7 +418,7 @@ int heget_submit(heget_server* s, const heget_request* q, uint64_t* ticket) {
     if (r) return r;
     if (q->N < 1) return fail(HEGET_EINVAL, "a request needs N >= 1");
     const int t = s->ctx->tiles[1][q->precision == HEGET_FP64][q->n];
-    const int tile = t > 0 ? t : default_tile(q->n, true);
+    const int tile = t > 0 ? t : batch_default_tile(q->n, q->precision, s->alg);
     const long long ntiles = (q->N + tile - 1) / tile;
     if (ntiles > (long long)(s->arena.size / sizeof(Partial)))
         return fail(HEGET_ENOMEM, "request of %lld tiles cannot fit the arena of %zu bytes", ntiles, s->arena.size);

@@ -150,3 +150,75 @@ def test_algorithm_argument_checks(heget_lib, gpu):
         H.heget_set_algorithm(gpu, 7)
     assert H.heget_get_algorithm(gpu) == H.HEGET_ALG_TREE
     assert H.load().heget_get_algorithm(None) == -1
+
+
+def test_subset_server_equals_batch_and_async(heget_lib, subset):
+    """With the subset recursion the server runs the subset batch kernel with
+    its own tiles: every result is bitwise the batch result of the request
+    alone, and within FP32/FP64 rounding of heget_xsec_async (another launch
+    shape, so another summation order)."""
+    import torch
+    H = heget_lib
+    S = H.sampler_toy_pdf()
+    mix = [(8, 300, 32), (7, 700, 64), (2, 9000, 32), (6, 2500, 64), (5, 4000, 32), (8, 40, 64), (4, 20_000, 32)]
+    srv = H.heget_server_start(subset, max_launch_work=2e9)   # several launches per request
+    try:
+        tickets = [H.heget_submit(srv, n, SEED + 200 + k, N, S, p, i0=5 * k) for k, (n, N, p) in enumerate(mix)]
+        got = [H.heget_wait(srv, t, 120.0) for t in tickets]
+    finally:
+        H.heget_server_stop(srv)
+    for k, ((n, N, p), g) in enumerate(zip(mix, got)):
+        assert g.status == H.HEGET_OK
+        r = torch.zeros(80, dtype=torch.uint8, device="cuda")
+        H.heget_xsec_batch(subset, [dict(n=n, precision=p, seed=SEED + 200 + k, i0=5 * k, N=N, sampler=S,
+                                         result_dev=r)])
+        torch.cuda.synchronize()
+        alone = H.result_from_tensor(r)
+        assert alone.sum_w == g.result.sum_w and alone.sum_w2 == g.result.sum_w2, f"request {k} (n={n})"
+        assert alone.n_pass == g.result.n_pass and alone.n_tries == g.result.n_tries
+        res = torch.zeros(80, dtype=torch.uint8, device="cuda")
+        H.heget_xsec_async(subset, n, SEED + 200 + k, 5 * k, N, S, p, res)
+        torch.cuda.synchronize()
+        ref = H.result_from_tensor(res)
+        assert ref.n_pass == alone.n_pass and ref.n_total == alone.n_total == N
+        rel = 1e-12 if p == 64 else 1e-5
+        assert alone.sum_w == pytest.approx(ref.sum_w, rel=rel, abs=0)
+
+
+def test_batch_graphs_follow_the_algorithm(heget_lib, gpu):
+    """The batch kernel is compiled once per algorithm, and its CUDA graphs
+    are kept per algorithm: with graphs on, alternating the context between
+    the tree and the subset recursion gives each algorithm's direct bits."""
+    import torch
+    H = heget_lib
+    S = H.sampler_toy_pdf()
+    reqs = [(6, 200, 32), (3, 3000, 64), (8, 20, 32)]
+
+    def run():
+        bufs = [torch.zeros(80, dtype=torch.uint8, device="cuda") for _ in reqs]
+        H.heget_xsec_batch(gpu, [dict(n=n, precision=p, seed=SEED + 300 + k, i0=0, N=N, sampler=S, result_dev=b)
+                                 for k, ((n, N, p), b) in enumerate(zip(reqs, bufs))])
+        torch.cuda.synchronize()
+        return [H.result_from_tensor(b) for b in bufs]
+
+    try:
+        tree = run()
+        H.heget_set_algorithm(gpu, H.HEGET_ALG_SUBSET)
+        sub = run()
+        H.heget_set_graphs(gpu, 1)
+        sub_g = run()                        # captures the subset kernel's graphs
+        H.heget_set_algorithm(gpu, H.HEGET_ALG_TREE)
+        tree_g = run()                       # captures the tree's
+        H.heget_set_algorithm(gpu, H.HEGET_ALG_SUBSET)
+        sub_g2 = run()                       # replays the subset kernel's
+        on, captures, replays = H.heget_get_graphs(gpu)
+        assert on == 1 and captures >= 4 and replays >= 2
+    finally:
+        H.heget_set_graphs(gpu, 0)
+        H.heget_set_algorithm(gpu, H.HEGET_ALG_TREE)
+    for a, b in zip(tree, tree_g):
+        assert a.sum_w == b.sum_w and a.n_pass == b.n_pass
+    for a, b, c in zip(sub, sub_g, sub_g2):
+        assert a.sum_w == b.sum_w == c.sum_w and a.n_pass == b.n_pass
+    for a, b in zip(tree, sub):
+        assert a.n_pass == b.n_pass and a.sum_w == pytest.approx(b.sum_w, rel=1e-5)
