@@ -461,7 +461,8 @@ void heget_graph_destroy(heget_graph* g);
  * result).  Each launch of the mixed-n batch kernel takes tiles round-robin
  * from every admitted request until about max_launch_work FP32-flop
  * equivalents are filled (the amplitude flops of the server's algorithm per
- * point, an FP64 flop counting 16, plus the event generation), so requests
+ * point, plus the event generation) and at least
+ * two tiles per SM are taken (when the admitted requests have them), so requests
  * arriving while others run share the next launch with them; up to two
  * launches are in flight.  A request's result is bitwise the
  * heget_xsec_batch result of the same request, whatever else shared its

@@ -65,8 +65,12 @@ constexpr int kMeetLB = 2;
 __host__ __device__ constexpr int meet_lb(int k) { return k >= kMeetLB ? kMeetLB : k; }
 __host__ __device__ constexpr int meet_block(int k) { return 1 << meet_lb(k); }
 
-// Contraction: 2^CB helicity configurations per thread (photons 0 .. CB-1 free).
-__host__ __device__ constexpr int meet_cb(int n) { return n >= 3 ? 3 : n; }
+// Contraction: 2^CB helicity configurations per thread (photons 0 .. CB-1
+// free).  From n = 6 the 2^(n-CB) threads of a point and set T fill exactly
+// one warp (CB = n - 5), so that every lane of a warp contracts the same T:
+// the code path chosen by T's lower photons is then uniform, and lanes that
+// need the same J or R row read it in one broadcast.
+__host__ __device__ constexpr int meet_cb(int n) { return n >= 6 ? n - 5 : n >= 3 ? 3 : n; }
 
 // Input-table entries of the sizes 2 .. k-1 (one per set and position).
 __host__ __device__ constexpr int meet_in_offset(int n, int k) {
@@ -77,14 +81,26 @@ __host__ __device__ constexpr int meet_in_offset(int n, int k) {
 
 // Group shape: threads per group (two to four warps from n = 6, the whole
 // block below), points a group takes per round, sets T of size m per chunk.
+#ifndef HEGET_MEET_GTH6
+#define HEGET_MEET_GTH6 64
+#endif
+#ifndef HEGET_MEET_GTH7
+#define HEGET_MEET_GTH7 128
+#endif
 template <class R>
 __host__ __device__ constexpr int meet_group_threads(int n, int block) {
-    const int want = n <= 5 ? block : n == 6 ? 64 : 128;
+    const int want = n <= 5 ? block : n == 6 ? HEGET_MEET_GTH6 : n == 7 ? HEGET_MEET_GTH7 : 128;
     return want < block ? want : block;
 }
+#ifndef HEGET_MEET_PG6
+#define HEGET_MEET_PG6 1
+#endif
+#ifndef HEGET_MEET_PG7
+#define HEGET_MEET_PG7 1
+#endif
 template <class R>
 __host__ __device__ constexpr int meet_group_points(int n, int gth) {
-    const int p = n <= 5 ? gth / 16 : 1;
+    const int p = n <= 5 ? gth / 16 : n == 6 ? HEGET_MEET_PG6 : n == 7 ? HEGET_MEET_PG7 : 1;
     const int q = n <= 5 && sizeof(R) != sizeof(float) ? p / 2 : p;
     return q > 0 ? q : 1;
 }
@@ -280,6 +296,8 @@ template <int BAR, int BLOCK, int GBAR0, int GTH, int G>
 __device__ __forceinline__ void meet_sync(int g) {
     if constexpr (G == 1 && GTH == BLOCK) {
         group_sync<BAR, BLOCK>();
+    } else if constexpr (GTH == 32) {
+        __syncwarp();
     } else {
         asm volatile("bar.sync %0, %1;" ::"r"(GBAR0 + g), "n"(GTH) : "memory");
     }
@@ -356,9 +374,12 @@ __device__ __forceinline__ void meet_phase(const MeetTables<R, N, BLOCK>& tb, in
     constexpr int CK = set_binom(N, K), NB = (1 << K) / meet_block(K);
     constexpr int NJ = K < M ? PG * CK * NB : 0;
     constexpr int NK = PG * CK * NB;
-    for (int it = lid; it < NJ + NK; it += MT::GTH) {
-        const bool col = it >= NJ;
-        const int q = col ? it - NJ : it;
+    // the K items start at a warp boundary, so that no warp runs both kinds
+    constexpr int NJP = (NJ + 31) / 32 * 32;
+    for (int it = lid; it < NJP + NK; it += MT::GTH) {
+        const bool col = it >= NJP;
+        const int q = col ? it - NJP : it;
+        if (!col && q >= NJ) continue;
         const int rS = q % CK, blk = (q / CK) % NB, p = q / (NB * CK);
         if (p >= cnt || !rb[p].valid) continue;
         if (!col) {
@@ -383,9 +404,11 @@ __device__ __forceinline__ void meet_chunk_items(const MeetTables<R, N, BLOCK>& 
     constexpr int PG = MT::PG, M = MT::M, MK = MT::MK, CH = MT::CH;
     constexpr int NBJ = M >= 2 ? (1 << M) / meet_block(M) : 0, NBR = MK >= 2 ? (1 << MK) / meet_block(MK) : 0;
     const int NJ = PG * nc * NBJ, NR = PG * nc * NBR;
-    for (int it = lid; it < NJ + NR; it += MT::GTH) {
-        const bool col = it >= NJ;
-        const int q = col ? it - NJ : it;
+    const int NJP = (NJ + 31) / 32 * 32;   // R items from a warp boundary on
+    for (int it = lid; it < NJP + NR; it += MT::GTH) {
+        const bool col = it >= NJP;
+        const int q = col ? it - NJP : it;
+        if (!col && q >= NJ) continue;
         const int nb = col ? NBR : NBJ;
         const int t = q % nc, blk = (q / nc) % nb, p = q / (nb * nc);
         if (p >= cnt || !rb[p].valid) continue;
@@ -454,7 +477,7 @@ __device__ __noinline__ void amplitude_rounds_meet(unsigned char* table_smem, Po
     constexpr int NS = MT::NS, M = MT::M, MK = MT::MK, CT = MT::CT, GT = MT::GT, CB = MT::CB, PG = MT::PG;
     constexpr int GTH = MT::GTH, G = MT::G, CM = MT::CM, CH = MT::CH;
     constexpr int GBAR0 = BAR == 0 ? 1 : 8;
-    static_assert(G == 1 || GBAR0 + G <= 16, "named barriers of the groups");
+    static_assert(G == 1 || GTH == 32 || GBAR0 + G <= 16, "named barriers of the groups");
     constexpr unsigned FULL = NS - 1;
     const MT tb(table_smem);
     meet_build_tables(tb);

@@ -38,16 +38,18 @@ double now_s() {
 // ordering-sum algorithm -- the tree (2^n lanes, 28 flop per step, 16 per
 // closure) or the subset recursion met in the middle (12 multiply-adds per
 // current term and Q product, 8 per contraction term over the sets of n/2
-// photons, for every helicity assignment of each set) -- with an FP64 flop
-// counted as 16 (the measured FP64/FP32 rate ratio of these kernels is 10 to
-// 40), plus the phase-space generation (~1e3 FP64 operations at ~1/64 of
-// the FP32 rate).
+// photons, for every helicity assignment of each set) -- plus the
+// phase-space generation (~1e3 FP64 operations at ~1/64 of the FP32 rate).
+// FP64 amplitude flops count as FP32 ones: weighting them by the pipes'
+// rate ratio made FP64 launches too small to keep the GPU busy (a sweep of
+// weights 1, 4, 16 on the serving traces: 1 gave the highest throughput and
+// the lowest latencies with both algorithms).
 double binom(int n, int k) {
     double c = 1;
     for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
     return c;
 }
-double point_cost(int n, int alg, int precision) {
+double point_cost(int n, int alg) {
     double amp = 0;
     if (alg == kAlgSubset) {
         const int m = n / 2, mk = n - m;
@@ -67,7 +69,7 @@ double point_cost(int n, int alg, int precision) {
         }
         amp = (double)(1 << n) * (28.0 * steps + 16.0 * f);
     }
-    return amp * (precision == HEGET_FP64 ? 16.0 : 1.0) + 6.4e4;
+    return amp + 6.4e4;
 }
 
 struct Req {
@@ -175,16 +177,22 @@ int heget_server::build_and_launch(Launch& L) {
         take = active;
     }
     if (take.empty()) return 0;
-    // round-robin tiles under the work budget
+    // round-robin tiles under the work budget, and at least two tiles per SM
+    // when the admitted requests have them (a launch of fewer tiles leaves SMs
+    // idle however long its tiles run: large-n FP64 tiles take up to seconds)
     std::vector<int> ntake(take.size(), 0);
     double budget = cfg.max_launch_work;
-    for (bool any = true; budget > 0 && any;) {
+    const long long min_tiles = 2ll * ctx->num_sms;
+    long long taken = 0;
+    auto more = [&] { return budget > 0 || taken < min_tiles; };
+    for (bool any = true; more() && any;) {
         any = false;
-        for (size_t i = 0; i < take.size() && budget > 0; ++i) {
+        for (size_t i = 0; i < take.size() && more(); ++i) {
             Req* r = take[i];
             if (r->next_tile + ntake[i] >= r->ntiles) continue;
             ++ntake[i];
-            budget -= point_cost(r->q.n, alg, r->q.precision) * r->tile;
+            ++taken;
+            budget -= point_cost(r->q.n, alg) * r->tile;
             any = true;
         }
     }
