@@ -81,26 +81,16 @@ __host__ __device__ constexpr int meet_in_offset(int n, int k) {
 
 // Group shape: threads per group (two to four warps from n = 6, the whole
 // block below), points a group takes per round, sets T of size m per chunk.
-#ifndef HEGET_MEET_GTH6
-#define HEGET_MEET_GTH6 64
-#endif
-#ifndef HEGET_MEET_GTH7
-#define HEGET_MEET_GTH7 128
-#endif
 template <class R>
 __host__ __device__ constexpr int meet_group_threads(int n, int block) {
-    const int want = n <= 5 ? block : n == 6 ? HEGET_MEET_GTH6 : n == 7 ? HEGET_MEET_GTH7 : 128;
+    const int want = n <= 5 ? block : n == 6 ? 64 : 128;
     return want < block ? want : block;
 }
-#ifndef HEGET_MEET_PG6
-#define HEGET_MEET_PG6 1
-#endif
-#ifndef HEGET_MEET_PG7
-#define HEGET_MEET_PG7 1
-#endif
+// (FP64 at n = 6: two points per group, whose longer FP64 phases then
+// share each barrier; in FP32 one point per group is faster.)
 template <class R>
 __host__ __device__ constexpr int meet_group_points(int n, int gth) {
-    const int p = n <= 5 ? gth / 16 : n == 6 ? HEGET_MEET_PG6 : n == 7 ? HEGET_MEET_PG7 : 1;
+    const int p = n <= 5 ? gth / 16 : n == 6 && sizeof(R) != sizeof(float) ? 2 : 1;
     const int q = n <= 5 && sizeof(R) != sizeof(float) ? p / 2 : p;
     return q > 0 ? q : 1;
 }
