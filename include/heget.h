@@ -247,7 +247,7 @@ typedef struct {
  * Every request is cut into point tiles: the context's xsec tile if set
  * (heget_set_tile), else with the tree the tiles heget_xsec uses on the
  * plain (non-warp-specialised) path, with the subset recursion tiles of 128
- * points (FP32: 64 at n = 5, 6, 32 at n = 7, 8; FP64: 64 at n = 4, 16 at
+ * points (FP32: 64 from n = 5; FP64: 64 at n = 4, 16 at
  * n = 5, 8 from n = 6), the largest that let two blocks share an SM.  The
  * kernel is compiled once per algorithm.  The tiles of all requests, whatever
  * their n and N, form one work list that a single kernel walks, and each
@@ -376,7 +376,9 @@ int heget_amp2_escalated(heget_ctx* ctx, void* stream, int64_t* count);
 /* Launch shape (this library's knob; the paper's analogue is the register /
  * block-size scan of Sec. 6.1): points per block tile used by heget_amp2
  * (kind 0) or heget_xsec* (kind 1) for n photons at `precision`.  tile = 0
- * restores the default; otherwise tile must be a positive multiple of
+ * restores the default (for heget_amp2 with the subset recursion, larger
+ * tiles than the tree's: 128 points at n = 4, 5 in FP32, 64 at n = 6, 32 at
+ * n = 7, 8); otherwise tile must be a positive multiple of
  * 256 / 2^n and at most 4096.  A tile whose shared memory exceeds the device
  * limit makes the next launch fail with HEGET_ECUDA. */
 int heget_set_tile(heget_ctx* ctx, int n, int precision, int kind, int tile);

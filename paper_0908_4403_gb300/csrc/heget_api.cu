@@ -234,6 +234,16 @@ int default_tile(int n, bool xsec) {
     return xsec ? xsec_tile[n] : amp2_tile[n];
 }
 
+// heget_amp2 tiles of the subset recursion: larger than the tree's, so that
+// more threads build the tile's records (FP64) at once and the recursion's
+// per-call index tables and barriers are shared by more points (a GB300 sweep:
+// FP32 +30 % at n = 6..8, +69 % at n = 5; FP64 a few per cent).
+int subset_amp2_tile(int n, int precision) {
+    static const int t32[9] = {0, 0, 256, 128, 128, 128, 64, 32, 32};
+    static const int t64[9] = {0, 0, 256, 128, 64, 32, 32, 8, 8};
+    return precision == HEGET_FP64 ? t64[n] : t32[n];
+}
+
 int xsec_shape_count(int n, int precision, int alg) {
     return precision == HEGET_FP32 && alg == kAlgTree && n >= 6 ? 4 : 1;
 }
@@ -264,7 +274,7 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
     L->block = xsec && precision == HEGET_FP32 && alg != kAlgSubset && (n == 6 || n == 7) ? (n == 6 ? 160 : 224)
                                                                                         : kBlockThreads;
     if (L->shape > 0) L->block = tree_tile_shape(n, L->shape).block;
-    L->tile = tile > 0 ? tile : default_tile(n, xsec);
+    L->tile = tile > 0 ? tile : !xsec && alg == kAlgSubset ? subset_amp2_tile(n, precision) : default_tile(n, xsec);
     const bool sub = alg == kAlgSubset;
     const int e = precision == HEGET_FP32
                       ? (sub ? occupancy_alg<float, kAlgSubset>(n, L->tile, &bpsm, &smem)
@@ -415,7 +425,7 @@ size_t batch_tile_smem(int n, int precision, int alg, int tile) {
 int batch_default_tile(int n, int precision, int alg) {
     // subset recursion: the largest tile whose block (records, staging and
     // the recursion's tables) still lets two blocks share an SM, up to 128
-    static const int sub32[9] = {0, 0, 128, 128, 128, 64, 64, 32, 32};
+    static const int sub32[9] = {0, 0, 128, 128, 128, 64, 64, 64, 64};
     static const int sub64[9] = {0, 0, 128, 128, 64, 16, 8, 8, 8};
     if (alg != kAlgSubset) return default_tile(n, true);
     return precision == HEGET_FP64 ? sub64[n] : sub32[n];
@@ -619,7 +629,8 @@ int heget_amp2_escalated(heget_ctx* ctx, void* stream, int64_t* count) {
 int heget_get_tile(const heget_ctx* ctx, int n, int precision, int kind) {
     if (!ctx || n < kMinN || n > kMaxN || (kind != 0 && kind != 1)) return -1;
     const int t = ctx->tiles[kind][precision == HEGET_FP64][n];
-    return t > 0 ? t : default_tile(n, kind == 1);
+    if (t > 0) return t;
+    return kind == 0 && ctx->alg == kAlgSubset ? subset_amp2_tile(n, precision) : default_tile(n, kind == 1);
 }
 
 int heget_set_params(heget_ctx* ctx, const heget_params* p) {
