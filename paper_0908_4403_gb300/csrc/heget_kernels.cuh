@@ -708,17 +708,24 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 constexpr int kBarRounds = 1, kBarFull = 2, kBarEmpty = 4;   // named barrier ids (2,3 / 4,5)
 constexpr int kBarProducers = 6;                              // producers' stage compaction
 
-// Consumer threads: 256, or 160 for the FP32 tree at n = 6 (five pair-unit
+// Consumer threads: 256; 160 for the FP32 tree at n = 6 (five pair-unit
 // slots of two points share out the 15 units evenly, and two blocks of 224
-// threads fit an SM at 144 registers).
-__host__ __device__ constexpr int ws_consumers(int n, int alg) { return n == 6 && alg == 0 ? 160 : 256; }
+// threads fit an SM at 144 registers); 384 for the subset recursion from
+// n = 7 (three groups of four warps, one block per SM).
+__host__ __device__ constexpr int ws_consumers(int n, int alg) {
+    return n == 6 && alg == 0 ? 160 : n >= 7 && alg == 1 ? 384 : 256;
+}
 // Points per stage (= producer threads, a multiple of 32): as many as the
 // shared memory of the ring, the producers' staging and the round tables
 // allows at two resident blocks per SM; 64 at n = 5, 6, whose FP64
 // generation then spans two warps (one warp leaves the FP64 pipe waiting on
-// its own latencies).
+// its own latencies).  The subset recursion from n = 7 takes 96 with its 384
+// consumers at one block per SM: there the FP64 generation of about four
+// events per evaluated point outweighs the recursion, and three producer
+// warps keep three sub-partitions' FP64 units busy (GB300, n = 8: 8.5e7
+// points/s, from 6.2e7 with 32 producers and two blocks per SM).
 __host__ __device__ constexpr int ws_stage(int n, int alg) {
-    return n <= 4 ? 128 : n <= 6 ? 64 : 32;
+    return n <= 4 ? 128 : n <= 6 ? 64 : alg == 1 ? 96 : 32;
 }
 
 __device__ __forceinline__ void named_sync(int id, int count) {

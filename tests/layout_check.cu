@@ -261,8 +261,12 @@ int main() {
     check_meet<float, 8, 256>();
     check_meet<double, 6, 256>();
     check_meet<double, 8, 256>();
+    check_meet<float, 7, ws_consumers(7, kAlgSubset)>();
+    check_meet<float, 8, ws_consumers(8, kAlgSubset)>();
     const size_t ws8s = ws_smem_bytes<float, 8, kAlgSubset>() + 2 * ws_stage(8, kAlgSubset) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws8s) >= 1, "warp-specialised n=8 subset: %zu bytes", ws8s);
+    const size_t ws7s = ws_smem_bytes<float, 7, kAlgSubset>() + 2 * ws_stage(7, kAlgSubset) * sizeof(SampleDraw) + 256;
+    CHECK(resident_blocks(ws7s) >= 1, "warp-specialised n=7 subset: %zu bytes", ws7s);
     const size_t ws6s = ws_smem_bytes<float, 6, kAlgSubset>() + 2 * ws_stage(6, kAlgSubset) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws6s) >= 2, "warp-specialised n=6 subset: %zu bytes, fewer than 2 blocks per SM", ws6s);
     CHECK(sizeof(SampleDraw) == 16, "SampleDraw is %zu bytes", sizeof(SampleDraw));
