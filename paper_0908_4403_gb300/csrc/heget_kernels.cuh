@@ -491,13 +491,10 @@ __device__ __forceinline__ void xsec_tile(unsigned char* smem, int tile, uint64_
 // the FP32 tree from n = 6 as many blocks as 128 registers per thread allow
 // (three 160-thread blocks at n = 6, two blocks of 224 or 256 above); n = 2
 // three blocks (at most 68 KB); elsewhere two blocks (up to 128 registers).
-#ifndef HEGET_TREE_REGS
-#define HEGET_TREE_REGS 128
-#endif
 template <class R, int N, int BLOCK, bool ESC, int ALG>
 __host__ __device__ constexpr int tile_min_blocks() {
     return (sizeof(R) == sizeof(float) && ALG == kAlgTree && !ESC && N >= 6)
-               ? (65536 / (BLOCK * HEGET_TREE_REGS) > 1 ? 65536 / (BLOCK * HEGET_TREE_REGS) : 1)
+               ? (65536 / (BLOCK * 128) > 1 ? 65536 / (BLOCK * 128) : 1)
                : N == 2 ? 3 : 2;
 }
 // Threads of a fused tile kernel's block: for the FP32 tree, as many warps as
