@@ -286,8 +286,6 @@ template <int BAR, int BLOCK, int GBAR0, int GTH, int G>
 __device__ __forceinline__ void meet_sync(int g) {
     if constexpr (G == 1 && GTH == BLOCK) {
         group_sync<BAR, BLOCK>();
-    } else if constexpr (GTH == 32) {
-        __syncwarp();
     } else {
         asm volatile("bar.sync %0, %1;" ::"r"(GBAR0 + g), "n"(GTH) : "memory");
     }
@@ -467,7 +465,7 @@ __device__ __noinline__ void amplitude_rounds_meet(unsigned char* table_smem, Po
     constexpr int NS = MT::NS, M = MT::M, MK = MT::MK, CT = MT::CT, GT = MT::GT, CB = MT::CB, PG = MT::PG;
     constexpr int GTH = MT::GTH, G = MT::G, CM = MT::CM, CH = MT::CH;
     constexpr int GBAR0 = BAR == 0 ? 1 : 8;
-    static_assert(G == 1 || GTH == 32 || GBAR0 + G <= 16, "named barriers of the groups");
+    static_assert(G == 1 || GBAR0 + G <= 16, "named barriers of the groups");
     constexpr unsigned FULL = NS - 1;
     const MT tb(table_smem);
     meet_build_tables(tb);
