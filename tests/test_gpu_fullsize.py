@@ -1,9 +1,11 @@
 """Parity at the benchmark's full sizes, in the launch configuration the
-bench times (the default fused path of heget_xsec_async: the warp-specialised
-kernel at n <= 5, the tile kernel above): per-event weights of sampled
-points (blocks at the start, the middle and the ragged end of the range)
-against the oracle, computed one by one; cut decisions bit for bit; and the
-result's counts and sums against the full weight array."""
+bench times (the default fused path of heget_xsec_async: with the tree the
+warp-specialised kernel at n <= 5 and the tile kernel above, with the subset
+recursion the warp-specialised kernel in FP32 and the tile kernel in FP64):
+per-event weights of sampled points (blocks at the start, the middle and the
+ragged end of the range) against the oracle, computed one by one; cut
+decisions bit for bit; and the result's counts and sums against the full
+weight array, for both ordering-sum algorithms."""
 import math
 
 import numpy as np
@@ -36,9 +38,11 @@ def test_full_size_sampled_parity(oracle, heget_lib, gpu, n, kind, N, B, fp64):
         seed = SEED + n
         starts = [N - B] if n == 8 else [0, N // 2 + 7, N - B]
         ref = {s: oracle.event_weights(n, seed, s, B, so, cut) for s in starts}
-        for prec, tol in ((H.HEGET_FP32, 1e-3), (H.HEGET_FP64, 1e-11)):
+        for alg, prec, tol in ((H.HEGET_ALG_TREE, H.HEGET_FP32, 1e-3), (H.HEGET_ALG_TREE, H.HEGET_FP64, 1e-11),
+                               (H.HEGET_ALG_SUBSET, H.HEGET_FP32, 1e-3), (H.HEGET_ALG_SUBSET, H.HEGET_FP64, 1e-11)):
             if prec == H.HEGET_FP64 and not fp64:
                 continue
+            H.heget_set_algorithm(gpu, alg)
             res = torch.zeros(80, dtype=torch.uint8, device="cuda")
             w = torch.empty(N, dtype=torch.float64, device="cuda")
             H.heget_xsec_async(gpu, n, seed, 0, N, sd, prec, res, w)
@@ -54,4 +58,5 @@ def test_full_size_sampled_parity(oracle, heget_lib, gpu, n, kind, N, B, fp64):
                 if nz.any():
                     assert np.max(np.abs(got[nz] - wo[nz]) / wo[nz]) < tol
     finally:
+        H.heget_set_algorithm(gpu, H.HEGET_ALG_TREE)
         H.heget_set_params(gpu)
