@@ -52,11 +52,14 @@ FP64_PEAK = SMS * 2 * 2 * SM_GHZ / 1e3
 # DADD + DMUL, thread-level predicated-on counts from ncu on 262,144 points
 # of this workload): sqrt(s-hat), RAMBO, cuts, and for the points that pass
 # the cuts the denominators, records, weights and double-double sums.
-FP64_FLOPS_PER_POINT = {4: 714}
+# FP64_INSTR_PER_POINT: the same as instructions (DFMA + DADD + DMUL), each
+# taking one slot of the FP64 pipe, 2 per SM and clock.
+FP64_FLOPS_PER_POINT = {4: 671}
+FP64_INSTR_PER_POINT = {4: 516.4}
 # DRAM bytes per launch of that kernel (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum): its inputs come from the counter-based generator,
 # so this is code, constant tables and block partials, the same at any size.
-FP64_STEP_TRAFFIC = {4: 154624}
+FP64_STEP_TRAFFIC = {4: 152832}
 
 
 def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None, subset=False):
@@ -81,7 +84,9 @@ def roofline(n, N, kern_s, peak32_meas, peak64_meas, n_eval=None, subset=False):
                 "frac": a64 / FP64_PEAK, "traffic": FP64_STEP_TRAFFIC.get(n), "kernel": kern,
                 "flops_per_point": FP64_FLOPS_PER_POINT[n],
                 "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
-                "measured_peak": peak64_meas, "frac_of_measured": a64 / peak64_meas, "fp32_tree": fp32}
+                "measured_peak": peak64_meas, "frac_of_measured": a64 / peak64_meas,
+                "fp64_issue_frac": FP64_INSTR_PER_POINT[n] * N / kern_s / (SMS * 2 * SM_GHZ * 1e9),
+                "fp32_tree": fp32}
     return {"bound": "alu", **fp32, "unit": "TFLOP/s", "traffic": None, "kernel": kern,
             "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz"}
 

@@ -258,7 +258,7 @@ int default_amp_launch(int n, int precision, long long npts, int num_sms, AmpLau
     if (L->ws) {
         // warp-specialised: fixed stage size, one resident wave of blocks that
         // each pipeline many stages
-        L->block = ws_consumers(n, alg) + ws_stage(n, alg);
+        L->block = ws_consumers(n, alg, false) + ws_stage(n, alg);   // (the escalating kernel: more consumers)
         L->tile = ws_stage(n, alg);
         const int e = alg == kAlgSubset ? occupancy_ws_alg<kAlgSubset>(n, &bpsm, &smem)
                                         : occupancy_ws_alg<kAlgTree>(n, &bpsm, &smem);

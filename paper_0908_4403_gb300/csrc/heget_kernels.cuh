@@ -684,7 +684,7 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 // n = 6 still about half of them, and needs many events in flight while the
 // amplitudes run.  Each block therefore splits into roles that run
 // concurrently:
-//   consumers (ws_consumers(n, alg) threads, the first warps): the amplitude
+//   consumers (ws_consumers(n, alg, esc) threads, the first warps): the amplitude
 //               rounds, and the sampler draws of the stage two ahead;
 //   producers (ws_stage(n, alg) threads, the last warps): one event per
 //               thread per stage from its draws: the FP64 rest (sqrt(s-hat),
@@ -708,12 +708,16 @@ xsec_batch_kernel(const WorkItem* __restrict__ items, int nitems, const BatchReq
 constexpr int kBarRounds = 1, kBarFull = 2, kBarEmpty = 4;   // named barrier ids (2,3 / 4,5)
 constexpr int kBarProducers = 6;                              // producers' stage compaction
 
-// Consumer threads: 256; 160 for the FP32 tree at n = 6 (five pair-unit
-// slots of two points share out the 15 units evenly, and two blocks of 224
-// threads fit an SM at 144 registers); 384 for the subset recursion from
-// n = 7 (three groups of four warps, one block per SM).
-__host__ __device__ constexpr int ws_consumers(int n, int alg) {
-    return n == 6 && alg == 0 ? 160 : n >= 7 && alg == 1 ? 384 : 256;
+// Consumer threads: 256; 128 for the tree up to n = 4 without the FP32
+// error bound, whose amplitudes are a small share of the block's work (with
+// 256, the consumer warps took issue slots from the FP64 producers: GB300
+// n = 4, 4.98e8 against 4.77e8 evaluated points/s; 96 or 64 starve the
+// amplitudes, and so does the bound of the escalating kernel, which keeps
+// 256); 160 for the FP32 tree at n = 6 (five pair-unit slots of two points
+// share out the 15 units evenly); 384 for the subset recursion from n = 7
+// (three groups of four warps, one block per SM).
+__host__ __device__ constexpr int ws_consumers(int n, int alg, bool esc) {
+    return n <= 4 && alg == 0 && !esc ? 128 : n == 6 && alg == 0 ? 160 : n >= 7 && alg == 1 ? 384 : 256;
 }
 // Points per stage (= producer threads, a multiple of 32): as many as the
 // shared memory of the ring, the producers' staging and the round tables
@@ -738,9 +742,17 @@ __device__ __forceinline__ void named_arrive(int id, int count) {
 // Shared-memory layout of the warp-specialised kernel of algorithm ALG with
 // table layout TAB: round tables, the double-buffered ring of records, the
 // producers' staging.
+// Threads of a warp-specialised block (one value for the kernel's launch
+// bounds, its barriers and its launch); a table layout with the FP32 error
+// bound marks the escalating kernel.
+__host__ __device__ constexpr bool tab_has_bound(int tab) { return tab == kTabTreeKappa || tab == kTabSubsetKappa; }
+template <int N, int ALG, bool ESC>
+__host__ __device__ constexpr int ws_threads() {
+    return ws_consumers(N, ALG, ESC) + ws_stage(N, ALG);
+}
 template <class R, int N, int ALG, int TAB>
 __host__ __device__ constexpr size_t ws_recs_offset() {
-    return table_bytes<R, N, ws_consumers(N, ALG), TAB>();
+    return table_bytes<R, N, ws_consumers(N, ALG, tab_has_bound(TAB)), TAB>();
 }
 template <class R, int N, int ALG, int TAB>
 __host__ __device__ constexpr size_t ws_stage_offset() {
@@ -756,12 +768,13 @@ __host__ __device__ constexpr int ws_min_blocks() {
 }
 
 template <class R, int N, bool ESC, int ALG>
-__global__ void __launch_bounds__(ws_consumers(N, ALG) + ws_stage(N, ALG), ws_min_blocks<R, N, ALG, table_alg<ALG, ESC>()>())
+__global__ void __launch_bounds__(ws_threads<N, ALG, ESC>(), ws_min_blocks<R, N, ALG, table_alg<ALG, ESC>()>())
 xsec_ws_kernel(uint64_t seed, long long i0, long long npts, SamplerArgs S, Physics ph,
                Partial* __restrict__ partials, double* __restrict__ w_out, EscArgs esc) {
-    constexpr int kWsConsumers = ws_consumers(N, ALG);
+    constexpr int kWsConsumers = ws_consumers(N, ALG, ESC);
     constexpr int kWsStage = ws_stage(N, ALG);
-    constexpr int kWsThreads = kWsConsumers + kWsStage;
+    constexpr int kWsThreads = ws_threads<N, ALG, ESC>();
+    static_assert(kWsThreads == kWsConsumers + kWsStage, "block shape");
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int TAB = table_alg<ALG, ESC>();
     PointRec<R, N>* ring = reinterpret_cast<PointRec<R, N>*>(smem + ws_recs_offset<R, N, ALG, TAB>());

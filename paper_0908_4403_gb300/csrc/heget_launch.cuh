@@ -111,12 +111,14 @@ static int launch_xsec_n(uint64_t seed, long long i0, long long npts, const Samp
                          Partial* partials, double* w_out, const EscArgs& esc, const AmpLaunch& L, cudaStream_t st) {
     if constexpr (has_ws<R, N, ALG>()) {
         if (L.ws) {
+            // the block shape of the instantiation that runs (the escalating
+            // kernel keeps more consumers)
             auto k = esc.idx ? xsec_ws_kernel<R, N, true, ALG> : xsec_ws_kernel<R, N, false, ALG>;
+            const int threads = esc.idx ? ws_threads<N, ALG, true>() : ws_threads<N, ALG, false>();
             const size_t smem = esc.idx ? ws_smem_bytes<R, N, ALG, table_alg<ALG, true>()>() : ws_smem_bytes<R, N, ALG>();
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return (int)e;
-            k<<<L.grid, ws_consumers(N, ALG) + ws_stage(N, ALG), smem, st>>>(seed, i0, npts, S, ph, partials, w_out,
-                                                                             esc);
+            k<<<L.grid, threads, smem, st>>>(seed, i0, npts, S, ph, partials, w_out, esc);
             return (int)cudaGetLastError();
         }
     } else {
@@ -140,8 +142,7 @@ static int occupancy_ws_n(int* blocks_per_sm, size_t* smem_out) {
         auto k = xsec_ws_kernel<float, N, false, ALG>;
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
-        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, ws_consumers(N, ALG) + ws_stage(N, ALG),
-                                                                 smem);
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, ws_threads<N, ALG, false>(), smem);
     } else {
         return (int)cudaErrorInvalidValue;
     }

@@ -239,13 +239,16 @@ int main() {
     CHECK(resident_blocks(ws4) >= 2, "warp-specialised n=4 tree: %zu bytes, fewer than 2 blocks per SM", ws4);
     const size_t ws4s = ws_smem_bytes<float, 4, kAlgSubset>() + draws4;
     CHECK(resident_blocks(ws4s) >= 2, "warp-specialised n=4 subset: %zu bytes, fewer than 2 blocks per SM", ws4s);
+    // the escalating kernel keeps 256 consumers (its FP32 bound runs on them)
+    constexpr int ws4_esc_threads = ws_threads<4, kAlgTree, true>(), ws4_threads = ws_threads<4, kAlgTree, false>();
+    CHECK(ws4_esc_threads == 384 && ws4_threads == 256, "n=4 tree block shapes %d %d", ws4_esc_threads, ws4_threads);
     const size_t ws4e = ws_smem_bytes<float, 4, kAlgTree, table_alg<kAlgTree, true>()>() + draws4;
     CHECK(resident_blocks(ws4e) >= 2, "warp-specialised n=4 tree with escalation: %zu bytes", ws4e);
     const size_t ws5 = ws_smem_bytes<float, 5, kAlgTree>() + 2 * ws_stage(5, kAlgTree) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws5) >= 2, "warp-specialised n=5 tree: %zu bytes", ws5);
     const size_t ws6 = ws_smem_bytes<float, 6, kAlgTree>() + 2 * ws_stage(6, kAlgTree) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws6) >= 2, "warp-specialised n=6 tree: %zu bytes", ws6);
-    check_shape<float, 6, ws_consumers(6, kAlgTree)>(true);
+    check_shape<float, 6, ws_consumers(6, kAlgTree, false)>(true);
     const size_t t6 = xsec_smem_bytes<float, 6, 160, kAlgTree>(64);
     CHECK(resident_blocks(t6) >= 3, "tile n=6 tree (160 threads): %zu bytes, fewer than 3 blocks per SM", t6);
     const size_t t7 = xsec_smem_bytes<float, 7, 224, kAlgTree>(32);
@@ -261,8 +264,8 @@ int main() {
     check_meet<float, 8, 256>();
     check_meet<double, 6, 256>();
     check_meet<double, 8, 256>();
-    check_meet<float, 7, ws_consumers(7, kAlgSubset)>();
-    check_meet<float, 8, ws_consumers(8, kAlgSubset)>();
+    check_meet<float, 7, ws_consumers(7, kAlgSubset, false)>();
+    check_meet<float, 8, ws_consumers(8, kAlgSubset, false)>();
     const size_t ws8s = ws_smem_bytes<float, 8, kAlgSubset>() + 2 * ws_stage(8, kAlgSubset) * sizeof(SampleDraw) + 256;
     CHECK(resident_blocks(ws8s) >= 1, "warp-specialised n=8 subset: %zu bytes", ws8s);
     const size_t ws7s = ws_smem_bytes<float, 7, kAlgSubset>() + 2 * ws_stage(7, kAlgSubset) * sizeof(SampleDraw) + 256;
