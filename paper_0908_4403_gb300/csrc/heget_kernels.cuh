@@ -713,7 +713,8 @@ constexpr int kBarProducers = 6;                              // producers' stag
 // 256, the consumer warps took issue slots from the FP64 producers: GB300
 // n = 4, 4.98e8 against 4.77e8 evaluated points/s; 96 or 64 starve the
 // amplitudes, and so does the bound of the escalating kernel, which keeps
-// 256); 160 for the FP32 tree at n = 6 (five pair-unit slots of two points
+// 256; the subset recursion up to n = 4 and the tree at n = 5 ran 4-16 %
+// slower with 128); 160 for the FP32 tree at n = 6 (five pair-unit slots of two points
 // share out the 15 units evenly); 384 for the subset recursion from n = 7
 // (three groups of four warps, one block per SM).
 __host__ __device__ constexpr int ws_consumers(int n, int alg, bool esc) {
