@@ -594,6 +594,7 @@ __device__ __forceinline__ void generate_from(const PointRng& rng, const SampleD
     rambo<N>(rng, ev.rs, v);
     // the FP32 prefilter keeps 5n floats per photon set live in the producer
     // threads: a gain up to n = 3 (+22 % at n = 2 on GB300), a loss above
+    // (at n = 4 1 % slower even with 124 registers a producer thread)
     if constexpr (N <= 3) ev.mask = ev.ok ? pass_cuts_fast<N>(v, ev.ey, ev.iey, ph) : 0;
     else ev.mask = ev.ok ? pass_cuts<N>(v, ev.ey, ev.iey, ph) : 0;
 }
