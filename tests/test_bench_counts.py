@@ -71,3 +71,24 @@ def test_helas4_flops_by_enumeration(bench, n):
         for l in range(1, n):
             prefixes.add(perm[:l])
     assert bench.helas4_flops_per_point(n) == (1 << (n + 1)) * (128 * len(prefixes) + 88 * math.factorial(n))
+
+
+def test_roofline_fields(bench):
+    """The headline roofline: FP64 flops and FP64 instructions per point (one
+    instruction per issue slot, 2 slots per SM and clock) over the kernel
+    time; the subset recursion's step on the FP32 pipe by its own count."""
+    N, kern_s, n_eval = 1 << 20, 1.2e-3, 600_000
+    r = bench.roofline(4, N, kern_s, 70.0, 1.0, n_eval=n_eval)
+    assert r["pipe"] == "fp64" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(bench.FP64_FLOPS_PER_POINT[4] * N / kern_s / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK)
+    slots = bench.SMS * 2 * bench.SM_GHZ * 1e9
+    assert r["fp64_issue_frac"] == pytest.approx(bench.FP64_INSTR_PER_POINT[4] * N / kern_s / slots)
+    # flops per instruction lie between 1 (DADD, DMUL) and 2 (DFMA)
+    assert bench.FP64_INSTR_PER_POINT[4] <= bench.FP64_FLOPS_PER_POINT[4] <= 2 * bench.FP64_INSTR_PER_POINT[4]
+    assert r["fp32_tree"]["achieved"] == pytest.approx(bench.tree_flops_per_point(4) * n_eval / kern_s / 1e12)
+    s = bench.roofline(8, N, kern_s, 70.0, 1.0, n_eval=n_eval, subset=True)
+    assert s["pipe"] == "fp32 fma" and s["flops_per_point"] == bench.subset_flops_per_point(8)
+    assert s["frac"] == pytest.approx(bench.subset_flops_per_point(8) * n_eval / kern_s / 1e12 / bench.FP32_PEAK)
+    t = bench.roofline(6, N, kern_s, 70.0, 1.0, n_eval=n_eval)
+    assert t["kernel"] == "xsec_kernel<float,6,160>" and t["flops_per_point"] == bench.tree_flops_per_point(6)
